@@ -1,0 +1,166 @@
+"""Seeded synthetic workloads for the Hermitian FEAST hot path.
+
+This module only builds INPUTS (matrices, intervals, subspace sizes and fpm
+overrides); it holds none of the eigensolver's arithmetic.  Both the CUDA
+path's tests/benchmark and the CPU oracle draw their inputs from here.
+
+Randomness is counter-based SplitMix64 (Steele, Lea & Flood 2014):
+value(i) = mix(seed + (i+1) * 0x9E3779B97F4A7C15), so every entry is a pure
+function of (seed, index) and identical on x86 and Arm hosts.  Normals use
+the Box-Muller transform.
+
+Workloads (the guide's example matrices are not available, these synthetic
+problems stand in for them):
+  * ``laplacian``: dense 1-D Laplacian tridiag(-1, 2, -1), B = I; closed-form
+    spectrum 2 - 2 cos(k pi / (n+1)).
+  * ``dense_real_generalized``: A = Q diag(lam) Q^T, Q a product of 8 seeded
+    Householder reflectors, lam ~ U[-1, 1]; B = Q_B diag(mu) Q_B^T with its
+    own reflectors, mu log-uniform in [1, 100]; interval [-delta, delta]
+    holding a fixed count of pencil eigenvalues.
+  * ``dense_complex_hermitian``: A = U diag(lam) U^H, U a product of 8 seeded
+    complex reflectors, lam ~ U[-1, 1], B = I; the spectrum is lam itself.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, idx: np.ndarray) -> np.ndarray:
+    """Counter-based SplitMix64 over an index array (uint64 wrap-around)."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (np.asarray(idx, dtype=np.uint64) + np.uint64(1)) * GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def derive_seed(seed: int, tag: int) -> int:
+    return int(splitmix64(seed, np.array([tag], dtype=np.uint64))[0])
+
+
+def uniform01(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Uniform [0, 1) doubles from the top 53 bits."""
+    idx = np.arange(offset, offset + count, dtype=np.uint64)
+    return (splitmix64(seed, idx) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def uniform(seed: int, count: int, lo: float = -1.0, hi: float = 1.0, offset: int = 0) -> np.ndarray:
+    return lo + (hi - lo) * uniform01(seed, count, offset)
+
+
+def normal(seed: int, count: int) -> np.ndarray:
+    """Box-Muller normals: pairs of uniforms (u1 in (0,1], u2 in [0,1))."""
+    u = uniform01(seed, 2 * count)
+    u1 = 1.0 - u[0::2]
+    u2 = u[1::2]
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def reflector_vectors(seed: int, n: int, count: int = 8, complex_: bool = False) -> list:
+    out = []
+    for r in range(count):
+        s = derive_seed(seed, 1000 + r)
+        v = normal(s, n)
+        if complex_:
+            v = v + 1j * normal(derive_seed(s, 7), n)
+        out.append(v)
+    return out
+
+
+def conjugate_by_reflectors(d: np.ndarray, vs: list) -> np.ndarray:
+    """M = H_1 ... H_k diag(d) H_k ... H_1 with H = I - 2 v v^H / (v^H v).
+
+    Applied as a sequence of two-sided rank-1 updates, innermost reflector
+    first, and symmetrised at the end so M is exactly Hermitian."""
+    cplx = any(np.iscomplexobj(v) for v in vs)
+    M = np.diag(d).astype(np.complex128 if cplx else np.float64)
+    for v in reversed(vs):
+        beta = 2.0 / np.real(np.vdot(v, v))
+        w = v.conj() @ M                      # v^H M
+        M -= beta * np.outer(v, w)            # H M
+        u = M @ v                             # (H M) v
+        M -= beta * np.outer(u, v.conj())     # (H M) H
+    M = 0.5 * (M + M.conj().T)
+    return np.asfortranarray(M)
+
+
+@dataclass
+class Problem:
+    name: str
+    hermitian: bool                 # True: complex Hermitian, False: real symmetric
+    A: np.ndarray
+    B: np.ndarray | None
+    emin: float
+    emax: float
+    m0: int
+    fpm: dict = field(default_factory=dict)   # {fortran index i: value} over feastinit
+    spectrum: np.ndarray | None = None         # exact eigenvalues when known
+    note: str = ""
+
+    @property
+    def n(self) -> int:
+        return self.A.shape[0]
+
+    def apply_fpm(self, fpm):
+        for i, v in self.fpm.items():
+            fpm[i - 1] = v
+        return fpm
+
+
+def laplacian(n: int = 500, emin: float = 0.5, emax: float = 1.0, m0: int = 80) -> Problem:
+    A = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    k = np.arange(1, n + 1)
+    lam = 2.0 - 2.0 * np.cos(k * np.pi / (n + 1))
+    return Problem(f"laplacian-n{n}", False, np.asfortranarray(A), None, emin, emax, m0,
+                   fpm={2: 8, 3: 12, 4: 20, 6: 0}, spectrum=lam,
+                   note="dense 1-D Laplacian, B=I, trace criterion 1e-12, <=20 loops")
+
+
+def dense_complex_hermitian(n: int = 8192, emin: float = 0.0, emax: float = 0.04, m0: int = 240,
+                            ne: int = 16, seed: int = 20260103) -> Problem:
+    lam = uniform(derive_seed(seed, 1), n)
+    A = conjugate_by_reflectors(lam, reflector_vectors(seed, n, 8, complex_=True))
+    return Problem(f"complex-hermitian-n{n}", True, A, None, emin, emax, m0,
+                   fpm={2: ne, 3: 10, 6: 1}, spectrum=np.sort(lam),
+                   note="U diag(lam) U^H, 8 complex reflectors, lam~U[-1,1], B=I")
+
+
+# Half-widths delta of [-delta, delta] holding exactly `count` pencil eigenvalues
+# of dense_real_generalized(n, seed); each value sits halfway between the
+# count-th and (count+1)-th smallest |lambda| of the pencil, from
+# scipy.linalg.eigh(A, B) on the generated matrices (see interval_for_count).
+_DELTA = {
+    (4096, 20260102, 200): 0.0023589538297558448,
+}
+
+
+def dense_real_generalized(n: int = 4096, count: int = 200, m0: int = 300, ne: int = 8,
+                           seed: int = 20260102, delta: float | None = None) -> Problem:
+    lam = uniform(derive_seed(seed, 1), n)
+    mu = 10.0 ** uniform(derive_seed(seed, 2), n, 0.0, 2.0)
+    A = conjugate_by_reflectors(lam, reflector_vectors(seed, n, 8))
+    B = conjugate_by_reflectors(mu, reflector_vectors(derive_seed(seed, 3), n, 8))
+    if delta is None:
+        delta = _DELTA.get((n, seed, count))
+    if delta is None:
+        delta = interval_for_count(A, B, count)
+        _DELTA[(n, seed, count)] = delta
+    return Problem(f"real-generalized-n{n}", False, A, B, -delta, delta, m0,
+                   fpm={2: ne, 3: 10, 6: 1},
+                   note=f"QAQ^T / Q_B M Q_B^T, interval [-d,d] holding {count} eigenvalues")
+
+
+def interval_for_count(A: np.ndarray, B: np.ndarray | None, count: int) -> float:
+    """delta such that [-delta, delta] holds exactly `count` pencil eigenvalues
+    (midpoint of the gap between the count-th and next smallest |lambda|)."""
+    import scipy.linalg as sl
+
+    w = sl.eigh(A, B, eigvals_only=True)
+    a = np.sort(np.abs(w))
+    return float(0.5 * (a[count - 1] + a[count]))
