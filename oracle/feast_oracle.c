@@ -27,6 +27,11 @@
  *     eigenvalue below -1e-8 * max means B is not positive definite (info -3);
  *   - output order: eigenpairs inside [Emin,Emax] ascending, then the others
  *     ascending (the hello-world output lists 1 then 3);
+ *   - spurious Ritz pairs (Table tab_common's remark gives no criterion):
+ *     from loop 1 on, a pair inside the interval whose filter gain
+ *     1/||w_j||_2 on its pre-image in the previous B-orthonormal subspace is
+ *     below f(lambda_j)/4 is spurious; it leaves M, the trace and the
+ *     convergence test and goes to the end of E/X with res = -1;
  *   - info 1 as soon as no Ritz value is inside; info 3 when every one of the
  *     M0 requested Ritz values is inside and M0 < N;
  *   - epsout = 1 at loop 0 (the hello-world output prints 1.0 at loop 0).
@@ -541,9 +546,10 @@ int ora_feast(int kind, int n, const zc *A, int lda, const zc *B, int ldb,
         double *d = (double *)malloc(sizeof(double) * m0), *lam = (double *)malloc(sizeof(double) * m0);
         double *sc = (double *)malloc(sizeof(double) * m0), *rr = (double *)malloc(sizeof(double) * m0);
         int *ord = (int *)malloc(sizeof(int) * m0);
+        int *spur = (int *)malloc(sizeof(int) * m0);
         int *singular = (int *)calloc(ne, sizeof(int));
         if (!Y || !RHS || !Q || !AQ || !BQ || !AX || !BX || !Xn || !Qe || !Aq || !Bq || !V ||
-            !T || !Cm || !U || !Wm || !tmp || !d || !lam || !sc || !rr || !ord || !singular) {
+            !T || !Cm || !U || !Wm || !tmp || !d || !lam || !sc || !rr || !ord || !spur || !singular) {
             info = -1;
             goto cleanup;
         }
@@ -670,12 +676,31 @@ int ora_feast(int kind, int n, const zc *A, int lda, const zc *B, int ldb,
                 }
                 rr[j] = num / den;
             }
-            /* order: inside ascending, then outside ascending (lam ascending) */
+            /* spurious pairs (loops >= 1, Y = previous B-orthonormal Ritz
+             * vectors): x_j = Q w_j is the filter applied to z_j = Y w_j with
+             * ||z_j||_B = ||w_j||_2 and ||x_j||_B = 1, so a_j = 1/||w_j||_2 is
+             * the filter's gain on the pair's pre-image.  A genuine pair has
+             * a_j ~ f(lambda_j) (>= 1/2 inside the interval); a pair inside
+             * whose gain is below f(lambda_j)/4 is spurious. */
+            for (int j = 0; j < mk; ++j) {
+                spur[j] = 0;
+                if (k == 0) continue;
+                if (!(lam[j] >= emin && lam[j] <= emax)) continue;
+                double nw = 0.0;
+                for (int i = 0; i < m; ++i) nw += creal(Wm[IX(i, j, m)] * conj(Wm[IX(i, j, m)]));
+                double fj;
+                ora_rationalx(zne, wne, ne, &lam[j], 1, &fj);
+                if (1.0 / sqrt(nw) < 0.25 * fabs(fj)) spur[j] = 1;
+            }
+            /* order: genuine pairs inside ascending, then outside ascending,
+             * then spurious ones (res = -1), as Table tab_common's remark */
             int nin = 0, pos = 0;
             for (int j = 0; j < mk; ++j)
-                if (lam[j] >= emin && lam[j] <= emax) ord[pos++] = j, ++nin;
+                if (lam[j] >= emin && lam[j] <= emax && !spur[j]) ord[pos++] = j, ++nin;
             for (int j = 0; j < mk; ++j)
                 if (!(lam[j] >= emin && lam[j] <= emax)) ord[pos++] = j;
+            for (int j = 0; j < mk; ++j)
+                if (spur[j]) ord[pos++] = j;
             double trace = 0.0, maxres = 0.0;
             for (int j = 0; j < nin; ++j) {
                 trace += lam[ord[j]];
@@ -690,7 +715,7 @@ int ora_feast(int kind, int n, const zc *A, int lda, const zc *B, int ldb,
             }
             for (int j = 0; j < mk; ++j) {
                 E[j] = lam[ord[j]];
-                res[j] = rr[ord[j]];
+                res[j] = spur[ord[j]] ? -1.0 : rr[ord[j]];
                 memcpy(X + IX(0, j, n), Xn + IX(0, ord[j], n), sizeof(zc) * n);
             }
             *M = nin;
@@ -710,7 +735,7 @@ int ora_feast(int kind, int n, const zc *A, int lda, const zc *B, int ldb,
     cleanup:
         free(zne); free(wne); free(Y); free(RHS); free(Q); free(AQ); free(BQ); free(AX);
         free(BX); free(Xn); free(Qe); free(Aq); free(Bq); free(V); free(T); free(Cm);
-        free(U); free(Wm); free(tmp); free(d); free(lam); free(sc); free(rr); free(ord);
+        free(U); free(Wm); free(tmp); free(d); free(lam); free(sc); free(rr); free(ord); free(spur);
         free(singular);
     }
 done_early:

@@ -187,3 +187,25 @@ def test_fpm14_stops_after_one_contour():
     f[13] = 1
     r = oracle.feast(A, None, 0.5, 3.5, 5, fpm=f)
     assert r["info"] == 4 and r["loop"] == 0
+
+
+@pytest.mark.parametrize("n,count", [(300, 15), (800, 40)])
+def test_spurious_ritz_pairs_leave_the_count(n, count):
+    """Symmetric interval in a dense generalized spectrum: mixtures of outside
+    eigenvectors from both sides produce Ritz values inside with residual ~1.
+    They must not be counted (Table tab_common: spurious pairs go to the end
+    with res = -1); M then equals the Sylvester count and the eigenvalues
+    match a library generalized eigensolver."""
+    p = W.dense_real_generalized(n=n, count=count, m0=int(1.5 * count))
+    r = run(p)
+    assert r["info"] == 0 and r["loop"] <= 5
+    assert r["M"] == count == oracle.eigcount(p.A, p.B, p.emin, p.emax)
+    w = sl.eigh(p.A, p.B, eigvals_only=True)
+    ref = w[(w >= p.emin) & (w <= p.emax)]
+    assert np.max(np.abs(r["E"][:count] - ref)) < 1e-12 * max(abs(p.emin), abs(p.emax))
+    res = r["res"][: r["m0"]]
+    flagged = np.where(res == -1.0)[0]
+    if flagged.size:
+        assert flagged.min() >= r["m0"] - flagged.size      # at the end
+        Ef = r["E"][flagged]
+        assert np.all((Ef >= p.emin) & (Ef <= p.emax))      # only inside pairs are flagged
