@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark: converged eigenpairs/s of FEAST (Hermitian family) on one GB300.
+
+Workload (default): the n=4096 dense real symmetric generalized problem
+A = Q diag(lam) Q^T, B = Q_B diag(mu) Q_B^T (8 seeded Householder reflectors
+each, lam ~ U[-1,1], mu log-uniform [1,100]), interval [-delta, delta]
+holding 200 eigenvalues, M0 = 300, Ne = 8 Gauss-Legendre half-contour
+nodes, residual criterion 1e-10.  Synthetic inputs, seeded.
+
+A step = one complete FEAST solve through the C ABI (gbf_dsygv_dev): shifted
+LU of all nodes, every subspace iteration (solves, quadrature sum,
+Rayleigh-Ritz GEMMs, reduced eigenproblem, residuals) until convergence,
+inputs resident in HBM.  value = eigenpairs with per-pair residual
+||Ax - lBx||/(||A|| ||x||) <= 1e-10, summed over ranks, per second.
+The FP64 path (fpm(42)=0) gives `value`; the mixed path (FP32 factor/solve
+with FP64 correction, fpm(42)=1) is measured the same way under "mixed".
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP64_PEAK_NOMINAL = 1.25e12      # GB300 FP64 (CUDA cores), nominal
+FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.07e9   # 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbf", choices=["gbf", "reference"])
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
+                    help="time one path only (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1].split()[0]))
+                mx.append(float(p[2].split()[0]))
+            except ValueError:
+                continue
+            for k, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(k)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- workload --
+def workload():
+    from paper_1203_4031_gb300 import workloads as W
+
+    return W.dense_real_generalized()
+
+
+def gate_count(A, B, X, E, M, torch):
+    """Pairs (of the first M) with ||Ax - lBx||_2 / (||A||_1 ||x||_2) <= 1e-10."""
+    Xm = X[:, :M]
+    Em = E[:M]
+    R = A @ Xm - (B @ Xm) * Em[None, :]
+    nA = torch.linalg.matrix_norm(A, ord=1)
+    rel = torch.linalg.vector_norm(R, dim=0) / (nA * torch.linalg.vector_norm(Xm, dim=0))
+    return int((rel <= 1e-10).sum().item()), float(rel.max().item()) if M else 0.0
+
+
+def run_gbf(args):
+    import torch
+
+    import paper_1203_4031_gb300 as g
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    g.load()
+    p = workload()
+    n, m0 = p.n, p.m0
+    dev = torch.device("cuda", local)
+    A = g.fortran(torch.from_numpy(np.ascontiguousarray(p.A)).to(dev))
+    B = g.fortran(torch.from_numpy(np.ascontiguousarray(p.B)).to(dev))
+    h = g.Handle()
+    stream = torch.cuda.current_stream(dev)
+
+    def fpm_for(prec):
+        f = p.apply_fpm(g.gbf_init())
+        f[41] = prec
+        return f
+
+    def solve(prec):
+        return g.feast_dev(A, B, p.emin, p.emax, m0, fpm=fpm_for(prec), handle=h, stream=stream)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+
+    def timed(prec, steps, warm, profile=False, clocks=None):
+        for _ in range(warm):
+            r = solve(prec)
+            if r["info"] != 0:
+                raise RuntimeError(f"warm-up solve failed: info {r['info']} ({g.last_error()})")
+        barrier()
+        if clocks:
+            clocks.start()
+        if profile:
+            g.lib().gbf_profile(1)
+        l0 = g.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        rs = [solve(prec) for _ in range(steps)]
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        launches = g.launch_count() - l0
+        cl = clocks.stop() if clocks else None
+        prof = None
+        if profile:
+            import ctypes as C
+
+            L = g.lib()
+            L.gbf_profile_name.restype = C.c_char_p
+            prof = {}
+            for c in range(L.gbf_profile_categories()):
+                nl, t, fl = C.c_longlong(), C.c_double(), C.c_double()
+                L.gbf_profile_read(c, C.byref(nl), C.byref(t), C.byref(fl))
+                prof[L.gbf_profile_name(c).decode()] = (nl.value, t.value, fl.value)
+            L.gbf_profile(0)
+        r = rs[-1]
+        if any(x["info"] != 0 for x in rs):
+            raise RuntimeError(f"timed solve failed: {[x['info'] for x in rs]}")
+        ok, worst = gate_count(A, B, r["X"], r["E"], r["M"], torch)
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        tot = torch.tensor([ok * steps], dtype=torch.float64, device=dev)
+        if dist:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        return dict(ms=t.item(), pairs=tot.item(), M=r["M"], ok=ok, worst=worst, loop=r["loop"],
+                    launches=launches, prof=prof, clocks=cl)
+
+    if args.only == "mixed":
+        mx = timed(1, args.steps, args.warmup, profile=True)
+        if rank == 0:
+            print(json.dumps({"path": "mixed", "ms_per_step": mx["ms"] / args.steps, "M": mx["M"],
+                              "kernels_ms": {k: v[1] / args.steps for k, v in mx["prof"].items()}}), flush=True)
+        return
+    clocks = ClockSampler(local)
+    fp = timed(0, args.steps, args.warmup, profile=True, clocks=clocks)
+    value = fp["pairs"] / (fp["ms"] / 1e3)
+    mixed = None
+    if not args.no_mixed and args.only is None:
+        mx = timed(1, args.steps, args.warmup, profile=True)
+        mixed = {"value": mx["pairs"] / (mx["ms"] / 1e3), "ms_per_step": mx["ms"] / args.steps,
+                 "M": mx["M"], "loops": mx["loop"], "max_rel_residual": mx["worst"],
+                 "gpu_launches": mx["launches"], "dtype": "c32 factor/solve + f64 correction",
+                 "kernels_ms": {k: round(v[1] / args.steps, 3) for k, v in mx["prof"].items()},
+                 "roofline": roofline(mx["prof"], "mixed")}
+
+    # end to end through the host-pointer C entry (pinned host buffers)
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.from_numpy(np.asfortranarray(p.A).ravel(order="F")).pin_memory()
+        Bh = torch.from_numpy(np.asfortranarray(p.B).ravel(order="F")).pin_memory()
+        a_np = Ah.numpy().reshape((n, n), order="F")
+        b_np = Bh.numpy().reshape((n, n), order="F")
+        ks = max(1, min(args.steps, 3))
+        g.feast_host(a_np, b_np, p.emin, p.emax, m0, fpm=fpm_for(0))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ks):
+            rh = g.feast_host(a_np, b_np, p.emin, p.emax, m0, fpm=fpm_for(0))
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        tt = torch.tensor([dt], dtype=torch.float64, device=dev)
+        if dist:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": (rh["M"] * ks * world) / tt.item(), "unit": "eigenpairs/s",
+               "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": (n * m0 + 2 * m0) * 8,
+               "steps": ks, "api": "gbf_dsygv (host pointers, pinned)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(p, fp["M"])
+
+    if rank == 0:
+        line = {
+            "metric": "converged eigenpairs/s at residual<=1e-10 (FP64 FEAST; mixed under 'mixed')",
+            "value": value, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": fp["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{p.name}: dense real symmetric generalized, n={n}, M0={m0}, Ne=8, "
+                                   f"[-{p.emax:.6g},{p.emax:.6g}] holding 200, res<1e-10",
+                       "M": fp["M"], "loops": fp["loop"], "parallelism": f"replicas x{world}",
+                       "l2": "inputs A,B (2 x 134 MB) exceed L2 (129 MB)"},
+            "max_rel_residual": fp["worst"], "gpu_launches": fp["launches"],
+            "kernels_ms": {k: round(v[1] / args.steps, 3) for k, v in fp["prof"].items()},
+            "roofline": roofline(fp["prof"], "fp64"),
+            "clocks": fp["clocks"], "e2e": e2e, "mixed": mixed, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def roofline(prof, path):
+    """Dominant category by device time; achieved = its algorithmic flops per
+    second over its launches.  FP64 kernels are bound by the FP64 ALU rate,
+    the FP32 factor/solve GEMMs by the FP32 ALU rate."""
+    name, (nl, ms, fl) = max(prof.items(), key=lambda kv: kv[1][1])
+    if ms <= 0:
+        return None
+    fp64_cats = {"project_gemm_fp64", "reduced_eig"}
+    peak = FP64_PEAK_NOMINAL if (path == "fp64" or name in fp64_cats) else FP32_PEAK_NOMINAL
+    achieved = fl / (ms / 1e3)
+    return {"kernel": name, "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "launches": nl,
+            "avg_launch_ms": ms / max(nl, 1),
+            "peak_source": "nominal (FP64 1.25 TFLOP/s from the GB300 table)" if peak == FP64_PEAK_NOMINAL
+            else "152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz"}
+
+
+# ------------------------------------------------------------- CPU oracle --
+SAMPLE_K = 2048
+
+
+def oracle_sample(p):
+    """One bounded sample of the oracle's dominant work on this workload:
+    LU (oracle zgetrf, one thread) of the leading SAMPLE_K x SAMPLE_K block
+    of the first node's shifted system z_1 B - A."""
+    import oracle
+
+    z, _ = oracle.contour(p.emin, p.emax, 8)
+    k = SAMPLE_K
+    S = np.asfortranarray(z[0] * p.B[:k, :k] - p.A[:k, :k])
+    t0 = time.perf_counter()
+    oracle.zgetrf(S)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(p, M):
+    dt = oracle_sample(p)
+    t_node = dt * (p.n / SAMPLE_K) ** 3
+    return {"value": M / (8 * t_node), "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle zgetrf of the leading {SAMPLE_K}^2 block of one shifted system "
+                      f"({dt:.2f} s), scaled by (n/{SAMPLE_K})^3 to one n={p.n} factorisation; value = "
+                      f"M / (Ne x t_factor): an upper bound of the single-thread oracle (its solves, "
+                      f"Rayleigh-Ritz and loops not counted)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = workload()
+    M = 200
+    for _ in range(args.warmup):
+        oracle_sample(p)
+    ts = [oracle_sample(p) for _ in range(args.steps)]
+    t = float(np.sum(ts))
+    t_node = (t / args.steps) * (p.n / SAMPLE_K) ** 3
+    value = M / (8 * t_node)
+    line = {
+        "impl": "reference", "metric": "converged eigenpairs/s at residual<=1e-10 (FP64 FEAST)",
+        "value": value, "unit": "eigenpairs/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{p.name}: dense real symmetric generalized, n={p.n}, M0={p.m0}, Ne=8"},
+        "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: oracle zgetrf of the leading {SAMPLE_K}^2 block of one shifted "
+                                   f"system; value = M / (Ne x t scaled by (n/{SAMPLE_K})^3)"},
+        "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gbf(a)

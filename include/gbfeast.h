@@ -1,0 +1,177 @@
+/*
+ * gbfeast -- FEAST's spectral projection + Rayleigh-Ritz subspace iteration
+ * (Hermitian family, dense storage) on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Problem (FEAST v3.0 user guide, arXiv:1203.4031, "The FEAST Algorithm"):
+ * find all eigenpairs of A x = lambda B x (A Hermitian / real symmetric, B
+ * Hermitian positive definite, or B = I) with lambda in [Emin, Emax], using
+ * a search subspace of size M0 and Ne = fpm(2) quadrature nodes on the upper
+ * half of a contour through Emin and Emax.
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are column-major (the guide's dense format, "Matrix storage");
+ *    lda >= n.  uplo: 'F' full, 'L' lower, 'U' upper triangle referenced.
+ *  - Complex arrays are interleaved (re, im) doubles: C99 double _Complex,
+ *    numpy complex128.  Pointers named d* are DEVICE pointers (cudaMalloc'ed
+ *    or torch CUDA tensors); all others are host pointers.
+ *  - fpm is the 64-entry parameter array of Table "tab_fpm"; C index i-1
+ *    holds fpm(i).  gbf_init writes the defaults.  Extensions in the unused
+ *    range fpm(40..63):
+ *        fpm(42) arithmetic of the factorisation and solves:
+ *                0 = complex FP64 (default),
+ *                1 = complex FP32 with FP64 correction: every FEAST iteration
+ *                    after the first solves only for the FP64 eigen-residual
+ *                    R = A X - B X Lambda (see gbf_dsygv), so the subspace
+ *                    reaches FP64 accuracy.
+ *        fpm(43) LU panel width / diagonal block size (0 = default 32).
+ *  - Outputs follow Table "tab_common": E[M0] eigenvalues (first M inside the
+ *    interval, ascending, then the remaining Ritz values ascending), X (N x
+ *    M0, ld N) B-orthonormal Ritz vectors in the same order, res[M0] relative
+ *    residuals ||A x_i - lambda_i B x_i||_1 / ||alpha B x_i||_1 with alpha =
+ *    max(|Emin|, |Emax|), M the count inside, loop the number of refinement
+ *    loops, epsout = |trace_k - trace_{k-1}| / alpha (1 at loop 0).  On exit
+ *    M0 holds the subspace size kept after B-orthonormalisation (the "new
+ *    suitable M0"); entries past it are zero.
+ *  - Return value == *info, codes of Table "tab_info": 202 bad N, 201 bad M0,
+ *    200 Emin >= Emax, 100+i bad fpm(i), 4 subspace returned (fpm(14)=1),
+ *    3 M0 too small (every Ritz value inside and M0 < N), 2 no convergence
+ *    within fpm(4) loops, 1 no eigenvalue in the interval, 0 success,
+ *    -1 allocation failure, -2 inner solver failure (zero pivot or
+ *    non-finite values), -3 reduced eigensolver failure (B not positive
+ *    definite on the subspace), -(100+i) bad argument i.  Extension: -4 CUDA
+ *    error; text through gbf_last_error().
+ *  - Initial subspace when fpm(5)=0: entries uniform in [-1, 1) from the
+ *    counter-based SplitMix64 generator (Steele, Lea & Flood 2014) with seed
+ *    0x3C6EF372FE94F82B, value i (column-major linear index; complex: real
+ *    part 2i, imaginary part 2i+1).
+ *  - Memory: the library owns its workspace (stored factorisations for all
+ *    nodes, as fpm(10)=1 in the guide, subspace blocks, reduced matrices);
+ *    it lives in the handle and is reused across calls.  Inputs are read
+ *    only; nothing the caller owns is overwritten except the outputs.
+ *  - Threading: one call at a time per handle.
+ */
+#ifndef GBFEAST_H
+#define GBFEAST_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbf_context *gbf_handle;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int gbf_version(void);
+
+/* Text of the last error (CUDA failure or argument problem); never NULL. */
+const char *gbf_last_error(void);
+
+/* Kernels launched by this library since load (monotone counter). */
+long long gbf_launch_count(void);
+
+/* Launch profiling.  gbf_profile(1) clears the records and starts timing
+ * instrumented launches with CUDA events on their own stream (GEMMs, LU
+ * panels, Jacobi sweeps), bucketed by category; gbf_profile(0) stops.
+ * gbf_profile_read waits for the recorded events and returns, for category
+ * cat (0 <= cat < gbf_profile_categories()), the number of timed launches,
+ * their summed device time in ms and their algorithmic flops (complex
+ * multiply-add = 8 flops, real = 2).  Names: gbf_profile_name(cat). */
+int gbf_profile(int enable);
+int gbf_profile_categories(void);
+const char *gbf_profile_name(int cat);
+int gbf_profile_read(int cat, long long *launches, double *ms, double *flops);
+
+/* Handle for the current CUDA device.  Returns 0, or -1 (allocation) / -4. */
+int gbf_create(gbf_handle *h);
+/* Releases the handle's device workspace. */
+int gbf_destroy(gbf_handle h);
+
+/* feastinit (Table tab_fpm defaults): fpm(2)=8, fpm(3)=12, fpm(4)=20,
+ * fpm(6)=1, fpm(7)=5, fpm(8)=16, fpm(17)=1, fpm(18)=100, rest 0. */
+void gbf_init(int *fpm);
+
+/* Quadrature nodes and weights of the half contour (tool zfeast_contour,
+ * "Defining a search contour").  Contour z(t) = r0 + R cos t + i rho R sin t,
+ * t in (0, pi), r0 = (Emin+Emax)/2, R = (Emax-Emin)/2, rho = fpm18/100;
+ * t_e = (pi/2)(1 - x_e) for Gauss-Legendre x_e, omega_e on [-1,1]
+ * (fpm16 = 0) or the midpoint rule (fpm16 = 1, x_e equispaced, omega_e =
+ * 2/ne); w_e = omega_e R (rho cos t_e + i sin t_e) / 2, so the projector is
+ * (1/2) sum_e [w_e (z_e B - A)^{-1} + conj(w_e) (conj(z_e) B - A)^{-1}] B.
+ * Nodes are ordered from the Emin side.  Zne, Wne: host, 2*ne doubles each.
+ * Returns 0, 200 (Emin >= Emax), 102 (ne < 1), 116 (fpm16), 118 (fpm18). */
+int gbf_contour(double emin, double emax, int ne, int fpm16, int fpm18, double *Zne, double *Wne);
+
+/* Rational filter f(l) = sum_e Re[w_e / (z_e - l)] of that contour at the
+ * m real points eig (tool dfeast_rational); f = 1 at the centre of a circle
+ * and 1/2 at its ends.  Host arrays.  Returns as gbf_contour. */
+int gbf_rational(double emin, double emax, int ne, int fpm16, int fpm18, const double *eig, int m, double *f);
+/* Same with user nodes/weights (dfeast_rationalx). */
+int gbf_rationalx(const double *Zne, const double *Wne, int ne, const double *eig, int m, double *f);
+
+/* ---------------------------------------------------------------------
+ * Dense drivers, HOST pointers (Tfeast_YFgv / Tfeast_YFev of the guide,
+ * "FEAST predefined interfaces").  The library copies A (and B) to the
+ * device, runs the device driver below and copies E, X, res back.
+ *   d: real symmetric A, B (double); z: complex Hermitian (interleaved).
+ *   *ev: standard problem (B = I).  X (N x M0) is read when fpm(5)=1.
+ * ------------------------------------------------------------------- */
+int gbf_dsyev(char uplo, int n, const double *A, int lda, int *fpm, double *epsout, int *loop, double emin,
+              double emax, int *M0, double *E, double *X, int *M, double *res, int *info);
+int gbf_dsygv(char uplo, int n, const double *A, int lda, const double *B, int ldb, int *fpm, double *epsout,
+              int *loop, double emin, double emax, int *M0, double *E, double *X, int *M, double *res,
+              int *info);
+int gbf_zheev(char uplo, int n, const double *A, int lda, int *fpm, double *epsout, int *loop, double emin,
+              double emax, int *M0, double *E, double *X, int *M, double *res, int *info);
+int gbf_zhegv(char uplo, int n, const double *A, int lda, const double *B, int ldb, int *fpm, double *epsout,
+              int *loop, double emin, double emax, int *M0, double *E, double *X, int *M, double *res,
+              int *info);
+/* Expert variants ("...x"): user quadrature Zne, Wne (host, 2*fpm(2)
+ * doubles each) replace the contour of fpm(2)/fpm(16)/fpm(18). */
+int gbf_dsygvx(char uplo, int n, const double *A, int lda, const double *B, int ldb, int *fpm, double *epsout,
+               int *loop, double emin, double emax, int *M0, double *E, double *X, int *M, double *res,
+               int *info, const double *Zne, const double *Wne);
+int gbf_zhegvx(char uplo, int n, const double *A, int lda, const double *B, int ldb, int *fpm, double *epsout,
+               int *loop, double emin, double emax, int *M0, double *E, double *X, int *M, double *res,
+               int *info, const double *Zne, const double *Wne);
+
+/* ---------------------------------------------------------------------
+ * Dense drivers, DEVICE pointers, on the caller's stream (cudaStream_t
+ * passed as void*, NULL = legacy default stream).  dA, dB (NULL: B = I)
+ * stay device-resident; dE[M0], dX (N x M0, ld N), dres[M0] are device
+ * outputs; dX is read first when fpm(5)=1.  Scalars (epsout, loop, M0, M,
+ * info) are host pointers.  The call returns after the stream has
+ * finished the solve (the host reads a few scalars per iteration to steer
+ * the loop).  Zne/Wne: host, NULL for the contour from fpm.
+ * ------------------------------------------------------------------- */
+int gbf_dsygv_dev(gbf_handle h, void *stream, char uplo, int n, const double *dA, int lda, const double *dB,
+                  int ldb, int *fpm, double *epsout, int *loop, double emin, double emax, int *M0, double *dE,
+                  double *dX, int *M, double *dres, int *info, const double *Zne, const double *Wne);
+int gbf_zhegv_dev(gbf_handle h, void *stream, char uplo, int n, const double *dA, int lda, const double *dB,
+                  int ldb, int *fpm, double *epsout, int *loop, double emin, double emax, int *M0, double *dE,
+                  double *dX, int *M, double *dres, int *info, const double *Zne, const double *Wne);
+
+/* ---------------------------------------------------------------------
+ * Step-level entry points (device pointers) exposing single rows of the
+ * hot path for verification and for callers that drive the iteration
+ * themselves (the RCI pattern of Fig. "fig_rci").
+ * ------------------------------------------------------------------- */
+/* RCI case 10 for every node: form S_e = z_e B - A (dB NULL: B = I) and
+ * factor P_e S_e = L_e U_e with partial pivoting (|re|+|im| pivot), kept in
+ * the handle.  kind 0: dA/dB real double; 1: complex interleaved.  prec:
+ * 0 complex FP64, 1 complex FP32.  Zne: host, 2*ne doubles.  Returns 0,
+ * -2 when some S_e has a zero pivot, or an error code. */
+int gbf_factor_dev(gbf_handle h, void *stream, int kind, int prec, char uplo, int n, const double *dA, int lda,
+                   const double *dB, int ldb, int ne, const double *Zne);
+/* RCI case 11 (trans 0) / case 21 (trans 1) with the stored factors:
+ * dY_e = S_e^{-1} dRHS or S_e^{-H} dRHS for every node e.  dRHS: complex
+ * n x nrhs (ld n); dY: complex ne x n x nrhs (node-major, ld n), FP64
+ * interleaved whatever prec the factors were made in. */
+int gbf_solve_dev(gbf_handle h, void *stream, int trans, int nrhs, const double *dRHS, double *dY);
+/* Reduced dense eigensolver of the Rayleigh-Ritz step (cyclic Jacobi):
+ * dA (m x m, ld m; real if kind 0, complex interleaved if kind 1) is
+ * overwritten; dW[m] ascending eigenvalues; dV (m x m) eigenvectors. */
+int gbf_heev_dev(gbf_handle h, void *stream, int kind, int m, double *dA, double *dW, double *dV);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

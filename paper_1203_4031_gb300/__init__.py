@@ -1,0 +1,287 @@
+"""Python binding of libgbfeast (include/gbfeast.h): argument marshalling only.
+
+Every function forwards to the C ABI of the same name; all arithmetic runs in
+the CUDA library.  Host-pointer drivers take numpy arrays; ``*_dev`` entry
+points take CUDA tensors (torch) in column-major layout (stride (1, ld)).
+There is no fallback: if the library cannot be built or loaded, ``load()``
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def load(build: bool = True):
+    """Load (building first if needed) libgbfeast.so; raises on failure."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgbfeast.so not found at {path}")
+    L = C.CDLL(path)
+    vp, ip, dp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)
+    L.gbf_version.restype = C.c_int
+    L.gbf_last_error.restype = C.c_char_p
+    L.gbf_launch_count.restype = C.c_longlong
+    L.gbf_create.argtypes = [C.POINTER(vp)]
+    L.gbf_destroy.argtypes = [vp]
+    L.gbf_init.argtypes = [ip]
+    L.gbf_contour.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, dp, dp]
+    L.gbf_rational.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, dp, C.c_int, dp]
+    L.gbf_rationalx.argtypes = [dp, dp, C.c_int, dp, C.c_int, dp]
+    host_ev = [C.c_char, C.c_int, vp, C.c_int, ip, dp, ip, C.c_double, C.c_double, ip, vp, vp, ip, vp, ip]
+    host_gv = [C.c_char, C.c_int, vp, C.c_int, vp, C.c_int, ip, dp, ip, C.c_double, C.c_double, ip, vp, vp,
+               ip, vp, ip]
+    for name in ("gbf_dsyev", "gbf_zheev"):
+        getattr(L, name).argtypes = host_ev
+    for name in ("gbf_dsygv", "gbf_zhegv"):
+        getattr(L, name).argtypes = host_gv
+    for name in ("gbf_dsygvx", "gbf_zhegvx"):
+        getattr(L, name).argtypes = host_gv + [vp, vp]
+    dev = [vp, vp, C.c_char, C.c_int, vp, C.c_int, vp, C.c_int, ip, dp, ip, C.c_double, C.c_double, ip, vp, vp,
+           ip, vp, ip, vp, vp]
+    L.gbf_dsygv_dev.argtypes = dev
+    L.gbf_zhegv_dev.argtypes = dev
+    L.gbf_factor_dev.argtypes = [vp, vp, C.c_int, C.c_int, C.c_char, C.c_int, vp, C.c_int, vp, C.c_int, C.c_int, vp]
+    L.gbf_solve_dev.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp]
+    L.gbf_heev_dev.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp, vp]
+    _lib = L
+    return L
+
+
+def lib():
+    return load()
+
+
+# ------------------------------------------------------------------ helpers --
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _fortran(a, dtype):
+    return np.asfortranarray(np.asarray(a, dtype=dtype))
+
+
+def fortran(t):
+    """Column-major view-copy of a 2-D torch tensor (stride (1, rows))."""
+    return t.t().contiguous().t()
+
+
+def _check_colmajor(t, rows):
+    if t.dim() != 2 or t.stride(0) != 1 or t.stride(1) < rows:
+        raise ValueError("expected a column-major CUDA tensor (use paper_1203_4031_gb300.fortran)")
+    return t.stride(1)
+
+
+def version():
+    return lib().gbf_version()
+
+
+def last_error():
+    return lib().gbf_last_error().decode()
+
+
+def launch_count():
+    return lib().gbf_launch_count()
+
+
+def gbf_init():
+    fpm = np.zeros(64, dtype=np.int32)
+    lib().gbf_init(_ip(fpm))
+    return fpm
+
+
+def gbf_contour(emin, emax, ne, fpm16=0, fpm18=100):
+    z = np.zeros(ne, dtype=np.complex128)
+    w = np.zeros(ne, dtype=np.complex128)
+    rc = lib().gbf_contour(float(emin), float(emax), int(ne), int(fpm16), int(fpm18),
+                           z.ctypes.data_as(C.POINTER(C.c_double)), w.ctypes.data_as(C.POINTER(C.c_double)))
+    if rc:
+        raise ValueError(f"gbf_contour: info {rc}")
+    return z, w
+
+
+def gbf_rational(emin, emax, ne, eig, fpm16=0, fpm18=100):
+    eig = np.ascontiguousarray(eig, dtype=np.float64)
+    f = np.zeros(eig.shape[0])
+    rc = lib().gbf_rational(float(emin), float(emax), int(ne), int(fpm16), int(fpm18), _dp(eig), eig.shape[0],
+                            _dp(f))
+    if rc:
+        raise ValueError(f"gbf_rational: info {rc}")
+    return f
+
+
+def gbf_rationalx(zne, wne, eig):
+    zne = np.ascontiguousarray(zne, dtype=np.complex128)
+    wne = np.ascontiguousarray(wne, dtype=np.complex128)
+    eig = np.ascontiguousarray(eig, dtype=np.float64)
+    f = np.zeros(eig.shape[0])
+    lib().gbf_rationalx(zne.ctypes.data_as(C.POINTER(C.c_double)), wne.ctypes.data_as(C.POINTER(C.c_double)),
+                        len(zne), _dp(eig), eig.shape[0], _dp(f))
+    return f
+
+
+class Handle:
+    """Owner of a gbf_handle (device workspace cache)."""
+
+    def __init__(self):
+        h = C.c_void_p()
+        rc = lib().gbf_create(C.byref(h))
+        if rc:
+            raise RuntimeError(f"gbf_create failed ({rc}): {last_error()}")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().gbf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _scalars():
+    return (C.c_double(0.0), C.c_int(0), C.c_int(0), C.c_int(0))
+
+
+def feast_host(A, B, emin, emax, m0, fpm=None, X0=None, uplo="F", hermitian=None, Zne=None, Wne=None):
+    """Host-pointer drivers gbf_{dsyev,dsygv,zheev,zhegv}[x]; returns a dict
+    with E, X, res, M, loop, epsout, m0 (kept subspace) and info."""
+    if fpm is None:
+        fpm = gbf_init()
+    fpm = np.ascontiguousarray(fpm, dtype=np.int32).copy()
+    if hermitian is None:
+        hermitian = np.iscomplexobj(A) or (B is not None and np.iscomplexobj(B))
+    dt = np.complex128 if hermitian else np.float64
+    A = _fortran(A, dt)
+    n = A.shape[0]
+    Bf = None if B is None else _fortran(B, dt)
+    X = np.zeros((n, m0), dtype=dt, order="F")
+    if X0 is not None:
+        X[:, :] = X0
+    E = np.zeros(m0)
+    res = np.zeros(m0)
+    eps, loop, M, info = _scalars()
+    M0 = C.c_int(int(m0))
+    u = C.c_char(uplo.encode())
+    L = lib()
+    args_tail = (_ip(fpm), C.byref(eps), C.byref(loop), float(emin), float(emax), C.byref(M0), _ptr(E), _ptr(X),
+                 C.byref(M), _ptr(res), C.byref(info))
+    if Zne is not None:
+        zne = np.ascontiguousarray(Zne, dtype=np.complex128)
+        wne = np.ascontiguousarray(Wne, dtype=np.complex128)
+        Bp = Bf if Bf is not None else None
+        fn = L.gbf_zhegvx if hermitian else L.gbf_dsygvx
+        fn(u, n, _ptr(A), n, _ptr(Bp), n, *args_tail, _ptr(zne), _ptr(wne))
+    elif Bf is None:
+        (L.gbf_zheev if hermitian else L.gbf_dsyev)(u, n, _ptr(A), n, *args_tail)
+    else:
+        (L.gbf_zhegv if hermitian else L.gbf_dsygv)(u, n, _ptr(A), n, _ptr(Bf), n, *args_tail)
+    return dict(E=E, X=X, res=res, M=M.value, loop=loop.value, epsout=eps.value, m0=M0.value, info=info.value)
+
+
+def feast_dev(A, B, emin, emax, m0, fpm=None, E=None, X=None, res=None, uplo="F", handle=None, stream=None,
+              Zne=None, Wne=None):
+    """Device-pointer drivers gbf_dsygv_dev / gbf_zhegv_dev on torch CUDA
+    tensors (A, B column-major; B None for the standard problem).  E, X, res
+    are allocated if not given (X is read when fpm(5)=1)."""
+    import torch
+
+    if fpm is None:
+        fpm = gbf_init()
+    fpm = np.ascontiguousarray(fpm, dtype=np.int32).copy()
+    herm = A.is_complex()
+    n = A.shape[0]
+    lda = _check_colmajor(A, n)
+    ldb = _check_colmajor(B, n) if B is not None else n
+    dev = A.device
+    if E is None:
+        E = torch.zeros(m0, dtype=torch.float64, device=dev)
+    if res is None:
+        res = torch.zeros(m0, dtype=torch.float64, device=dev)
+    if X is None:
+        X = torch.zeros((m0, n), dtype=A.dtype, device=dev).t()
+    eps, loop, M, info = _scalars()
+    M0 = C.c_int(int(m0))
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    sp = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    zp = wp = None
+    if Zne is not None:
+        zne = np.ascontiguousarray(Zne, dtype=np.complex128)
+        wne = np.ascontiguousarray(Wne, dtype=np.complex128)
+        zp, wp = _ptr(zne), _ptr(wne)
+    fn = lib().gbf_zhegv_dev if herm else lib().gbf_dsygv_dev
+    fn(handle.h if handle is not None else None, sp, C.c_char(uplo.encode()), n, _ptr(A), lda, _ptr(B), ldb,
+       _ip(fpm), C.byref(eps), C.byref(loop), float(emin), float(emax), C.byref(M0), _ptr(E), _ptr(X),
+       C.byref(M), _ptr(res), C.byref(info), zp, wp)
+    return dict(E=E, X=X, res=res, M=M.value, loop=loop.value, epsout=eps.value, m0=M0.value, info=info.value)
+
+
+def gbf_factor_dev(handle, A, B, zne, prec=0, uplo="F", stream=None):
+    import torch
+
+    n = A.shape[0]
+    lda = _check_colmajor(A, n)
+    ldb = _check_colmajor(B, n) if B is not None else n
+    zne = np.ascontiguousarray(zne, dtype=np.complex128)
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device)
+    return lib().gbf_factor_dev(handle.h if handle else None, C.c_void_p(stream.cuda_stream),
+                                1 if A.is_complex() else 0, int(prec), C.c_char(uplo.encode()), n, _ptr(A), lda,
+                                _ptr(B), ldb, len(zne), _ptr(zne))
+
+
+def gbf_solve_dev(handle, rhs, ne, trans=0, stream=None):
+    """rhs: complex128 CUDA tensor n x nrhs (column-major); returns the
+    ne x n x nrhs node solutions as a (ne, nrhs, n) tensor (so [e].t() is
+    the n x nrhs block) and the return code."""
+    import torch
+
+    n, nrhs = rhs.shape
+    _check_colmajor(rhs, n)
+    Y = torch.zeros((ne, nrhs, n), dtype=torch.complex128, device=rhs.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(rhs.device)
+    rc = lib().gbf_solve_dev(handle.h if handle else None, C.c_void_p(stream.cuda_stream), int(trans), nrhs,
+                             _ptr(rhs), _ptr(Y))
+    return Y, rc
+
+
+def gbf_heev_dev(handle, A, stream=None):
+    """A: m x m CUDA tensor (float64 or complex128, column-major), overwritten.
+    Returns (w, V, rc)."""
+    import torch
+
+    m = A.shape[0]
+    _check_colmajor(A, m)
+    w = torch.zeros(m, dtype=torch.float64, device=A.device)
+    V = torch.zeros((m, m), dtype=A.dtype, device=A.device).t()
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device)
+    rc = lib().gbf_heev_dev(handle.h if handle else None, C.c_void_p(stream.cuda_stream),
+                            1 if A.is_complex() else 0, m, _ptr(A), _ptr(w), _ptr(V))
+    return w, V, rc

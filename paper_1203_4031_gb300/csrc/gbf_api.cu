@@ -1,0 +1,945 @@
+// Host driver and C ABI of the FEAST hot path (see include/gbfeast.h).
+//
+// One call runs, on the caller's stream (FEAST v3.0 guide: "The FEAST
+// Algorithm" summary, RCI loop of Fig. "fig_rci", outputs of Table
+// "tab_common", info codes of Table "tab_info"):
+//   nodes/weights (host) -> S_e = z_e B - A and LU for all nodes (kept) ->
+//   loop k: RHS = B Y -> Y_e = S_e^{-1} RHS (+ adjoint solves for complex
+//   Hermitian) -> Q = sum_e w_e Y_e (fused quadrature sum) -> AQ, BQ,
+//   Aq = Q^H A Q, Bq = Q^H B Q -> B-orthonormalise + reduced eigenproblem ->
+//   X = Q W, AX, BX -> residuals, ordering, trace -> convergence.
+// Every n-sized step runs in this library's kernels; the host reads back a
+// few scalars per iteration (Jacobi sweep flags, the M0 eigenvalues of the
+// scaled Q^H B Q, and M / trace / max residual) to steer the loop.
+//
+// Mixed precision (fpm(42)=1): factors and solves in complex FP32.  The first
+// contour solves S_e Y_e = B Y in FP32.  Later contours use the identity
+//   S_e^{-1} B X = X (z_e - Lambda)^{-1} + S_e^{-1} R (z_e - Lambda)^{-1},
+//   R = A X - B X Lambda  (FP64, from the previous Rayleigh-Ritz step),
+// so Q = X f(Lambda) + sum_e Re[w_e S_e^{-1} R D_e] (Hermitian: the adjoint
+// pair), and the FP32 solve error is proportional to ||R||, which the
+// subspace iteration drives to FP64 rounding level.
+#include <math.h>
+#include <stdarg.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "gbf_common.cuh"
+#include "gbfeast.h"
+
+namespace gbf {
+std::atomic<long long> g_launches{0};
+static std::mutex g_err_mu;
+static char g_err[1024] = "";
+void set_error(const char *fmt, ...) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+}  // namespace gbf
+
+using namespace gbf;
+
+static const uint64_t SUBSPACE_SEED = 0x3C6EF372FE94F82BULL;
+static const double PI_ = 3.14159265358979323846264338327950288;
+
+struct gbf_context {
+  int device = 0;
+  char *arena = nullptr;
+  size_t cap = 0;
+  int *hflag = nullptr;       // pinned
+  double *hbuf = nullptr;     // pinned scratch
+  size_t hbuf_cap = 0;
+  cudaStream_t own = nullptr;  // stream of the host-pointer entries
+  // factors kept by gbf_factor_dev
+  int f_n = 0, f_ne = 0, f_prec = -1, f_bs = 32;
+  size_t f_bytes = 0;
+};
+
+// ------------------------------------------------------------ quadrature --
+// Legendre roots by Newton iteration from cos(pi (i + 3/4) / (ne + 1/2)),
+// with P_ne from the three-term recurrence and P'_ne from
+// (x^2 - 1) P'_n = n (x P_n - P_{n-1}); weights 2 / ((1 - x^2) P'_n^2).
+static void gl_nodes(int ne, double *x, double *om) {
+  for (int i = 0; i < ne; ++i) {
+    double t = cos(PI_ * (i + 0.75) / (ne + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = t;
+      for (int k = 2; k <= ne; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (ne == 1) p0 = 1.0;
+      dp = ne * (t * p1 - p0) / (t * t - 1.0);
+      const double dt = p1 / dp;
+      t -= dt;
+      if (fabs(dt) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = t;
+    for (int k = 2; k <= ne; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = ne * (t * p1 - p0) / (t * t - 1.0);
+    x[ne - 1 - i] = t;
+    om[ne - 1 - i] = 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+static int make_contour(double emin, double emax, int ne, int qtype, int ratio, zd *z, zd *w) {
+  if (!(emin < emax)) return 200;
+  if (ne < 1) return 102;
+  if (qtype != 0 && qtype != 1) return 116;
+  if (ratio <= 0) return 118;
+  std::vector<double> x(ne), om(ne);
+  if (qtype == 0) {
+    gl_nodes(ne, x.data(), om.data());
+  } else {
+    for (int e = 0; e < ne; ++e) {
+      x[e] = 1.0 - 2.0 * (ne - e - 0.5) / ne;
+      om[e] = 2.0 / ne;
+    }
+  }
+  const double r0 = 0.5 * (emin + emax), R = 0.5 * (emax - emin), rho = ratio / 100.0;
+  for (int e = 0; e < ne; ++e) {
+    const double t = 0.5 * PI_ * (1.0 - x[e]);
+    z[e] = zd{r0 + R * cos(t), rho * R * sin(t)};
+    w[e] = zd{0.5 * om[e] * R * rho * cos(t), 0.5 * om[e] * R * sin(t)};
+  }
+  return 0;
+}
+
+static int check_fpm(const int *fpm) {
+  const int ne = fpm[1], qtype = fpm[15];
+  if (qtype != 0 && qtype != 1) return 116;
+  if (qtype == 0) {
+    const bool ok = (ne >= 1 && ne <= 20) || ne == 24 || ne == 32 || ne == 40 || ne == 48 || ne == 56;
+    if (!ok) return 102;
+  } else if (ne < 1) {
+    return 102;
+  }
+  if (fpm[2] < 0 || fpm[2] > 16) return 103;
+  if (fpm[3] < 0) return 104;
+  if (fpm[4] != 0 && fpm[4] != 1) return 105;
+  if (fpm[5] != 0 && fpm[5] != 1) return 106;
+  if (fpm[13] != 0 && fpm[13] != 1 && fpm[13] != 2) return 114;
+  if (fpm[17] <= 0) return 118;
+  if (fpm[41] != 0 && fpm[41] != 1) return 142;
+  if (fpm[42] != 0 && (fpm[42] < 8 || fpm[42] > 64 || fpm[42] % 8)) return 143;
+  return 0;
+}
+
+// ----------------------------------------------------------------- arena --
+struct Bump {
+  char *base;
+  size_t off = 0;
+  explicit Bump(char *b) : base(b) {}
+  template <class T> T *take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T *p = reinterpret_cast<T *>(base + off);
+    off += count * sizeof(T) + 16;
+    return p;
+  }
+};
+
+static int ensure_arena(gbf_context *h, size_t need) {
+  if (h->cap >= need) return 0;
+  if (h->arena) {
+    cudaDeviceSynchronize();
+    cudaFree(h->arena);
+    h->arena = nullptr;
+    h->cap = 0;
+  }
+  cudaError_t e = cudaMalloc((void **)&h->arena, need);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of %zu bytes failed: %s", need, cudaGetErrorString(e));
+    h->arena = nullptr;
+    return -1;
+  }
+  h->cap = need;
+  h->f_prec = -1;  // any stored factors are gone
+  return 0;
+}
+
+static int ensure_hbuf(gbf_context *h, size_t count) {
+  if (h->hbuf_cap >= count) return 0;
+  if (h->hbuf) cudaFreeHost(h->hbuf);
+  h->hbuf = nullptr;
+  if (cudaMallocHost((void **)&h->hbuf, count * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMallocHost failed");
+    h->hbuf_cap = 0;
+    return -1;
+  }
+  h->hbuf_cap = count;
+  return 0;
+}
+
+// --------------------------------------------------------- small kernels --
+template <class TQ>
+__global__ void expand_uplo_kernel(int n, char uplo, const TQ *A, long lda, TQ *F) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= n) return;
+  const bool mirror = (uplo == 'L' && i < j) || (uplo == 'U' && i > j);
+  TQ v = mirror ? tr<TQ>::conj(A[j + (long)i * lda]) : A[i + (long)j * lda];
+  if (i == j) v = cvt<TQ, double>(tr<TQ>::re(v));
+  F[i + (long)j * n] = v;
+}
+
+template <class TQ>
+__global__ void copy_cols_kernel(int n, int m, const TQ *src, long lds, TQ *dst, long ldd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i < n && j < m) dst[i + (long)j * ldd] = src[i + (long)j * lds];
+}
+
+template <class TL>
+__global__ void widen_kernel(long count, const TL *src, zd *dst) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t < count) dst[t] = cvt<zd, TL>(src[t]);
+}
+
+// ---------------------------------------------------------------- driver --
+template <class TQ> struct kind_of;
+template <> struct kind_of<double> { static constexpr int v = 0; };
+template <> struct kind_of<zd> { static constexpr int v = 1; };
+
+struct Req {
+  char uplo;
+  int n;
+  const void *A;
+  long lda;
+  const void *B;
+  long ldb;
+  const int *fpm;
+  double emin, emax;
+  int m0;
+  const double *Zne, *Wne;
+  double *E;
+  void *X;
+  double *res;
+};
+struct Res {
+  double epsout = 1.0;
+  int loop = 0, M = 0, m0 = 0, info = 0;
+};
+
+template <class TQ, class TL> struct WS {
+  TL *S, *Linv, *Uinv, *Ysol, *Yadj, *Ytmp;
+  int *ipiv, *perm, *sing, *pos, *nin, *iwork, *flag, *spur;
+  TQ *Af, *Bf, *Q, *AQ, *BQ, *Xc, *AXc, *BXc, *Xu, *AXu, *BXu, *R, *RHS;
+  TQ *Aq, *Bq, *As, *Bs, *V, *Tm, *Ctmp, *Cm, *Cs, *U, *W, *jwork, *kwork;
+  double *d, *lam, *s, *resu, *Es, *Rs, *f, *dwork, *stats;
+  zd *z, *w, *D, *Dc;
+
+  void layout(Bump &b, int n, int m0, int ne, int bs, bool herm, bool hasB, bool needAf, bool needBf,
+              int ksplit) {
+    const size_t nn = (size_t)n * n, nm = (size_t)n * m0, mm = (size_t)m0 * m0;
+    const int nblk = ceil_div(n, bs);
+    S = b.take<TL>((size_t)ne * nn);
+    Linv = b.take<TL>((size_t)ne * nblk * bs * bs);
+    Uinv = b.take<TL>((size_t)ne * nblk * bs * bs);
+    Ysol = b.take<TL>((size_t)ne * nm);
+    Yadj = herm ? b.take<TL>((size_t)ne * nm) : nullptr;
+    Ytmp = herm ? b.take<TL>((size_t)ne * nm) : nullptr;
+    ipiv = b.take<int>((size_t)ne * n);
+    perm = b.take<int>((size_t)ne * n);
+    sing = b.take<int>(ne);
+    pos = b.take<int>(m0);
+    spur = b.take<int>(m0);
+    nin = b.take<int>(4);
+    iwork = b.take<int>(m0 + 8);
+    flag = b.take<int>(4);
+    Af = needAf ? b.take<TQ>(nn) : nullptr;
+    Bf = needBf ? b.take<TQ>(nn) : nullptr;
+    Q = b.take<TQ>(nm);
+    AQ = b.take<TQ>(nm);
+    BQ = hasB ? b.take<TQ>(nm) : nullptr;
+    Xc = b.take<TQ>(nm);
+    AXc = b.take<TQ>(nm);
+    BXc = hasB ? b.take<TQ>(nm) : nullptr;
+    Xu = b.take<TQ>(nm);
+    AXu = b.take<TQ>(nm);
+    BXu = hasB ? b.take<TQ>(nm) : nullptr;
+    R = b.take<TQ>(nm);
+    RHS = hasB ? b.take<TQ>(nm) : nullptr;
+    Aq = b.take<TQ>(mm);
+    Bq = b.take<TQ>(mm);
+    As = b.take<TQ>(mm);
+    Bs = b.take<TQ>(mm);
+    V = b.take<TQ>(mm);
+    Tm = b.take<TQ>(mm);
+    Ctmp = b.take<TQ>(mm);
+    Cm = b.take<TQ>(mm);
+    Cs = b.take<TQ>(mm);
+    U = b.take<TQ>(mm);
+    W = b.take<TQ>(mm);
+    jwork = b.take<TQ>(2 * mm);
+    kwork = b.take<TQ>((size_t)std::max(ksplit, 1) * mm);
+    d = b.take<double>(m0);
+    lam = b.take<double>(m0);
+    s = b.take<double>(m0);
+    resu = b.take<double>(m0);
+    Es = b.take<double>(m0);
+    Rs = b.take<double>(m0);
+    f = b.take<double>(m0);
+    dwork = b.take<double>(8);
+    stats = b.take<double>(8);
+    z = b.take<zd>(ne);
+    w = b.take<zd>(ne);
+    D = b.take<zd>((size_t)ne * m0);
+    Dc = b.take<zd>((size_t)ne * m0);
+  }
+};
+
+static int pick_ksplit(int m, int k) {
+  const int tiles = ceil_div(m, 64) * ceil_div(m, 64);
+  int ks = ceil_div(4 * 152, tiles);
+  ks = std::min(ks, std::max(1, k / 128));
+  return std::max(ks, 1);
+}
+
+#define CK(...)                            \
+  do {                                     \
+    int rc_ = (__VA_ARGS__);               \
+    if (rc_) {                             \
+      out.info = rc_ == -1 ? -1 : -4;      \
+      return out.info;                     \
+    }                                      \
+  } while (0)
+
+template <class TQ, class TL>
+static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
+  using XQ = tr<TQ>;
+  const int n = q.n, m0 = q.m0;
+  const int *fpm = q.fpm;
+  const bool herm = kind_of<TQ>::v == 1;
+  const bool hasB = q.B != nullptr;
+  const bool mixed = fpm[41] == 1;
+  const int ne = fpm[1];
+  const int bs = fpm[42] ? fpm[42] : 32;
+  const double eps = pow(10.0, -fpm[2]);
+  const double alpha = std::max(fabs(q.emin), fabs(q.emax));
+  out = Res{};
+  out.m0 = m0;
+
+  // contour
+  std::vector<zd> zh(ne), wh(ne);
+  if (q.Zne && q.Wne) {
+    for (int e = 0; e < ne; ++e) {
+      zh[e] = zd{q.Zne[2 * e], q.Zne[2 * e + 1]};
+      wh[e] = zd{q.Wne[2 * e], q.Wne[2 * e + 1]};
+    }
+  } else {
+    const int rc = make_contour(q.emin, q.emax, ne, fpm[15], fpm[17], zh.data(), wh.data());
+    if (rc) return out.info = rc;
+  }
+
+  // workspace
+  const bool needAf = q.uplo != 'F';
+  const bool needBf = hasB && q.uplo != 'F';
+  const int ksplit = pick_ksplit(m0, n);
+  WS<TQ, TL> ws;
+  {
+    Bump sizing(nullptr);
+    ws.layout(sizing, n, m0, ne, bs, herm, hasB, needAf, needBf, ksplit);
+    if (ensure_arena(h, sizing.off + 4096)) return out.info = -1;
+    Bump real(h->arena);
+    ws.layout(real, n, m0, ne, bs, herm, hasB, needAf, needBf, ksplit);
+  }
+  if (ensure_hbuf(h, (size_t)std::max(m0, ne) + 64)) return out.info = -1;
+  h->f_prec = -1;
+
+  GBF_CUDA(cudaMemcpyAsync(ws.z, zh.data(), sizeof(zd) * ne, cudaMemcpyHostToDevice, st));
+  GBF_CUDA(cudaMemcpyAsync(ws.w, wh.data(), sizeof(zd) * ne, cudaMemcpyHostToDevice, st));
+  GBF_CUDA(cudaMemsetAsync(ws.sing, 0, sizeof(int) * ne, st));
+  GBF_CUDA(cudaMemsetAsync(ws.flag, 0, sizeof(int) * 4, st));
+
+  const TQ *Af = (const TQ *)q.A;
+  long lda = q.lda;
+  const TQ *Bf = (const TQ *)q.B;
+  long ldb = q.ldb;
+  if (needAf) {
+    expand_uplo_kernel<TQ><<<dim3(ceil_div(n, 256), n), 256, 0, st>>>(n, q.uplo, (const TQ *)q.A, q.lda, ws.Af);
+    GBF_LAUNCHED();
+    Af = ws.Af;
+    lda = n;
+  }
+  if (needBf) {
+    expand_uplo_kernel<TQ><<<dim3(ceil_div(n, 256), n), 256, 0, st>>>(n, q.uplo, (const TQ *)q.B, q.ldb, ws.Bf);
+    GBF_LAUNCHED();
+    Bf = ws.Bf;
+    ldb = n;
+  }
+
+  // factor all nodes (kept for the whole iteration)
+  CatScope cat_other(CAT_OTHER);
+  CK(form_shift<TL>(st, n, ne, ws.z, kind_of<TQ>::v, 'F', Af, lda, hasB ? (const void *)Bf : nullptr, ldb, ws.S));
+  CK(getrf_batched<TL>(st, n, ne, ws.S, ws.ipiv, ws.perm, ws.Linv, ws.Uinv, bs, ws.sing, nullptr));
+  {
+    int *hs = (int *)h->hbuf;
+    GBF_CUDA(cudaMemcpyAsync(hs, ws.sing, sizeof(int) * ne, cudaMemcpyDeviceToHost, st));
+    GBF_CUDA(cudaStreamSynchronize(st));
+    for (int e = 0; e < ne; ++e)
+      if (hs[e]) {
+        set_error("zero pivot in column %d of the shifted system of node %d", hs[e], e);
+        return out.info = -2;
+      }
+  }
+
+  // initial subspace into Xc
+  if (fpm[4] == 1) {
+    copy_cols_kernel<TQ><<<dim3(ceil_div(n, 256), m0), 256, 0, st>>>(n, m0, (const TQ *)q.X, n, ws.Xc, n);
+    GBF_LAUNCHED();
+  } else {
+    CK(random_subspace<TQ>(st, (long)n * m0, SUBSPACE_SEED, ws.Xc));
+  }
+
+  const TQ one = XQ::one(), zero = XQ::zero();
+  const int kindR = kind_of<TQ>::v;
+  int m = m0;
+  double trace_prev = 0.0;
+  for (int k = 0;; ++k) {
+    // ---- spectral projection: Q = sum_e w_e S_e^{-1} B Y (Y = Xc) ----
+    const bool rc_form = mixed && k > 0;
+    const TQ *rhs;
+    const zd *scale = nullptr, *scalec = nullptr;
+    if (rc_form) {
+      const TQ *BXp = hasB ? ws.BXc : ws.Xc;
+      CK(eig_residual<TQ>(st, n, m, ws.AXc, BXp, ws.Es, ws.R));
+      CK(filter_values(st, m, ne, ws.z, ws.w, ws.Es, ws.f, ws.D, ws.Dc));
+      rhs = ws.R;
+      scale = ws.D;
+      scalec = ws.Dc;
+    } else if (hasB) {
+      if (k == 0)
+        CK(gemm<TQ>(st, 'N', 'N', n, m, n, one, Bf, ldb, 0, ws.Xc, n, 0, zero, ws.RHS, n, 0, 1));
+      rhs = (k == 0) ? ws.RHS : ws.BXc;
+    } else {
+      rhs = ws.Xc;
+    }
+    CK(gather_rhs<TL>(st, n, ne, m, ws.perm, kindR, rhs, n, scale, ws.Ysol));
+    CK(getrs_inplace<TL>(st, 0, n, ne, m, ws.S, ws.Linv, ws.Uinv, bs, ws.Ysol, nullptr));
+    if (herm) {
+      CK(gather_rhs<TL>(st, n, ne, m, nullptr, kindR, rhs, n, scalec, ws.Ytmp));
+      CK(getrs_inplace<TL>(st, 1, n, ne, m, ws.S, ws.Linv, ws.Uinv, bs, ws.Ytmp, nullptr));
+      CK(scatter_perm<TL>(st, n, ne, m, ws.perm, ws.Ytmp, ws.Yadj));
+    }
+    CK(accumulate<TL, TQ>(st, n, m, ne, ws.w, ws.Ysol, herm ? ws.Yadj : nullptr, rc_form ? ws.Xc : nullptr,
+                          rc_form ? ws.f : nullptr, ws.Q));
+
+    if (fpm[13] == 1) {  // return the subspace after one contour
+      GBF_CUDA(cudaMemsetAsync(q.X, 0, sizeof(TQ) * (size_t)n * m0, st));
+      copy_cols_kernel<TQ><<<dim3(ceil_div(n, 256), m), 256, 0, st>>>(n, m, ws.Q, n, (TQ *)q.X, n);
+      GBF_LAUNCHED();
+      GBF_CUDA(cudaMemsetAsync(q.E, 0, sizeof(double) * m0, st));
+      GBF_CUDA(cudaMemsetAsync(q.res, 0, sizeof(double) * m0, st));
+      GBF_CUDA(cudaStreamSynchronize(st));
+      out.loop = k;
+      out.m0 = m;
+      return out.info = 4;
+    }
+
+    // ---- Rayleigh-Ritz ----
+    CatScope cat_proj(CAT_PROJECT);
+    CK(gemm<TQ>(st, 'N', 'N', n, m, n, one, Af, lda, 0, ws.Q, n, 0, zero, ws.AQ, n, 0, 1));
+    const TQ *BQ = ws.Q;
+    if (hasB) {
+      CK(gemm<TQ>(st, 'N', 'N', n, m, n, one, Bf, ldb, 0, ws.Q, n, 0, zero, ws.BQ, n, 0, 1));
+      BQ = ws.BQ;
+    }
+    // split-K chunks, capped by the workspace sized for (ksplit, m0)
+    const int ks = std::max(1, std::min(pick_ksplit(m, n), (int)(((size_t)ksplit * m0 * m0) / ((size_t)m * m))));
+    CK(gemm<TQ>(st, 'C', 'N', m, m, n, one, ws.Q, n, 0, ws.AQ, n, 0, zero, ws.Aq, m, 0, 1, ks, ws.kwork));
+    CK(gemm<TQ>(st, 'C', 'N', m, m, n, one, ws.Q, n, 0, BQ, n, 0, zero, ws.Bq, m, 0, 1, ks, ws.kwork));
+    CK(rr_prepare<TQ>(st, m, ws.Aq, ws.Bq, ws.s, ws.flag, ws.As, ws.Bs));
+    CK(heev_jacobi<TQ>(st, m, ws.Bs, ws.d, ws.V, ws.jwork, ws.dwork, ws.iwork, h->hflag, nullptr));
+    double *hd = h->hbuf;
+    GBF_CUDA(cudaMemcpyAsync(hd, ws.d, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    GBF_CUDA(cudaMemcpyAsync(h->hflag, ws.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GBF_CUDA(cudaStreamSynchronize(st));
+    const double dmax = hd[m - 1];
+    if (*h->hflag || !(dmax > 0.0) || !(hd[0] >= -1e-8 * dmax)) {
+      set_error("Q^H B Q is not positive definite (B not HPD on the subspace)");
+      return out.info = -3;
+    }
+    int first = 0;
+    while (first < m && !(hd[first] > 1e-12 * dmax)) ++first;
+    const int mk = m - first;
+    {
+    CatScope cat_red(CAT_REDUCED);
+    CK(make_t<TQ>(st, m, mk, first, ws.V, ws.d, ws.Tm));
+    CK(gemm<TQ>(st, 'N', 'N', m, mk, m, one, ws.As, m, 0, ws.Tm, m, 0, zero, ws.Ctmp, m, 0, 1));
+    CK(gemm<TQ>(st, 'C', 'N', mk, mk, m, one, ws.Tm, m, 0, ws.Ctmp, m, 0, zero, ws.Cm, mk, 0, 1));
+    CK(hermitize<TQ>(st, mk, ws.Cm, ws.Cs));
+    CK(heev_jacobi<TQ>(st, mk, ws.Cs, ws.lam, ws.U, ws.jwork, ws.dwork, ws.iwork, h->hflag, nullptr));
+    CK(gemm<TQ>(st, 'N', 'N', m, mk, mk, one, ws.Tm, m, 0, ws.U, mk, 0, zero, ws.W, m, 0, 1));
+    CK(scale_rows<TQ>(st, m, mk, ws.s, ws.W));
+    }
+    CK(gemm<TQ>(st, 'N', 'N', n, mk, m, one, ws.Q, n, 0, ws.W, m, 0, zero, ws.Xu, n, 0, 1));
+    CK(gemm<TQ>(st, 'N', 'N', n, mk, m, one, ws.AQ, n, 0, ws.W, m, 0, zero, ws.AXu, n, 0, 1));
+    const TQ *BXu = ws.Xu;
+    if (hasB) {
+      CK(gemm<TQ>(st, 'N', 'N', n, mk, m, one, ws.BQ, n, 0, ws.W, m, 0, zero, ws.BXu, n, 0, 1));
+      BXu = ws.BXu;
+    }
+    CK(ritz_residual<TQ>(st, n, mk, ws.AXu, BXu, ws.lam, alpha, ws.resu));
+    // spurious pairs: from loop 1 on, Y = Xc holds the previous B-orthonormal Ritz vectors
+    CK(filter_values(st, mk, ne, ws.z, ws.w, ws.lam, ws.f, ws.D, ws.Dc));
+    CK(spurious_flags<TQ>(st, m, mk, ws.W, ws.lam, q.emin, q.emax, ws.f, k >= 1 ? 1 : 0, ws.spur));
+    CK(order_and_stats(st, mk, ws.lam, ws.resu, ws.spur, q.emin, q.emax, ws.pos, ws.nin, ws.Es, ws.Rs,
+                       ws.stats));
+    CK(permute_cols<TQ>(st, n, mk, ws.pos, ws.Xu, ws.Xc));
+    CK(permute_cols<TQ>(st, n, mk, ws.pos, ws.AXu, ws.AXc));
+    if (hasB) CK(permute_cols<TQ>(st, n, mk, ws.pos, ws.BXu, ws.BXc));
+    double *hs = h->hbuf;
+    GBF_CUDA(cudaMemcpyAsync(hs, ws.stats, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+    GBF_CUDA(cudaStreamSynchronize(st));
+    const int nin = (int)hs[0];
+    const double trace = hs[1], maxres = hs[2];
+    const bool finite = hs[3] != 0.0;
+    const double eout = (k == 0) ? 1.0 : fabs(trace - trace_prev) / alpha;
+    out.M = nin;
+    out.loop = k;
+    out.epsout = eout;
+    out.m0 = mk;
+    if (fpm[0] == 1)  // runtime comments (fpm(1)): one line per loop, as the guide's output
+      fprintf(stderr, "%d\t%d\t%.15e\t%.15e\t%.15e\t(M0 %d)\n", k, nin, trace, eout, maxres, mk);
+    int info = -99;
+    if (!finite) {
+      set_error("non-finite Ritz values or residuals");
+      info = -2;
+    } else if (nin == 0) {
+      info = 1;
+    } else if (nin >= m0 && m0 < n) {
+      info = 3;
+    } else if ((fpm[5] == 0) ? (eout < eps) : (maxres < eps)) {
+      info = 0;
+    } else if (k >= fpm[3]) {
+      info = 2;
+    }
+    if (info != -99) {
+      // outputs: E, res (first mk), X (n x mk), zero past mk
+      GBF_CUDA(cudaMemsetAsync(q.E, 0, sizeof(double) * m0, st));
+      GBF_CUDA(cudaMemsetAsync(q.res, 0, sizeof(double) * m0, st));
+      GBF_CUDA(cudaMemsetAsync(q.X, 0, sizeof(TQ) * (size_t)n * m0, st));
+      GBF_CUDA(cudaMemcpyAsync(q.E, ws.Es, sizeof(double) * mk, cudaMemcpyDeviceToDevice, st));
+      GBF_CUDA(cudaMemcpyAsync(q.res, ws.Rs, sizeof(double) * mk, cudaMemcpyDeviceToDevice, st));
+      GBF_CUDA(cudaMemcpyAsync(q.X, ws.Xc, sizeof(TQ) * (size_t)n * mk, cudaMemcpyDeviceToDevice, st));
+      GBF_CUDA(cudaStreamSynchronize(st));
+      return out.info = info;
+    }
+    m = mk;
+    trace_prev = trace;
+  }
+}
+
+// ----------------------------------------------------------- validation --
+static int validate(char uplo, int n, long lda, bool hasB, long ldb, const int *fpm, double emin, double emax,
+                    int m0) {
+  if (uplo != 'F' && uplo != 'L' && uplo != 'U') return -101;
+  if (n < 1) return 202;
+  if (lda < n) return -104;
+  if (hasB && ldb < n) return -106;
+  if (!fpm) return -107;
+  if (m0 < 1 || m0 > n) return 201;
+  if (!(emin < emax)) return 200;
+  return check_fpm(fpm);
+}
+
+static gbf_context *default_ctx() {
+  static std::mutex mu;
+  static gbf_context *ctx[64] = {nullptr};
+  std::lock_guard<std::mutex> lk(mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!ctx[dev]) {
+    gbf_handle h = nullptr;
+    if (gbf_create(&h) != 0) return nullptr;
+    ctx[dev] = h;
+  }
+  return ctx[dev];
+}
+
+template <class TQ>
+static int run_dev(gbf_handle h, void *stream, char uplo, int n, const double *dA, int lda, const double *dB,
+                   int ldb, int *fpm, double *epsout, int *loop, double emin, double emax, int *M0, double *dE,
+                   double *dX, int *M, double *dres, int *info, const double *Zne, const double *Wne) {
+  int code = validate(uplo, n, lda, dB != nullptr, ldb, fpm, emin, emax, M0 ? *M0 : 0);
+  Res out;
+  if (code == 0 && (!dA || !dE || !dX || !dres)) code = -103;
+  if (code == 0) {
+    Req q{uplo, n, dA, lda, dB, ldb, fpm, emin, emax, *M0, Zne, Wne, dE, dX, dres};
+    cudaStream_t st = (cudaStream_t)stream;
+    if (fpm[41] == 1)
+      code = feast_run<TQ, cf>(h, st, q, out);
+    else
+      code = feast_run<TQ, zd>(h, st, q, out);
+    if (epsout) *epsout = out.epsout;
+    if (loop) *loop = out.loop;
+    if (M) *M = out.M;
+    if (M0 && code >= 0) *M0 = out.m0;
+  }
+  if (info) *info = code;
+  return code;
+}
+
+template <class TQ>
+static int run_host(char uplo, int n, const double *A, int lda, const double *B, int ldb, int *fpm,
+                    double *epsout, int *loop, double emin, double emax, int *M0, double *E, double *X, int *M,
+                    double *res, int *info, const double *Zne, const double *Wne) {
+  int code = validate(uplo, n, lda, B != nullptr, ldb, fpm, emin, emax, M0 ? *M0 : 0);
+  if (code != 0 || !A || !E || !X || !res) {
+    if (code == 0) code = -103;
+    if (info) *info = code;
+    return code;
+  }
+  gbf_context *h = default_ctx();
+  if (!h) {
+    if (info) *info = -4;
+    return -4;
+  }
+  const int m0 = *M0;
+  const size_t szq = sizeof(TQ);
+  const size_t bytes_a = szq * (size_t)lda * n, bytes_b = B ? szq * (size_t)ldb * n : 0;
+  const size_t bytes_x = szq * (size_t)n * m0, bytes_e = sizeof(double) * m0;
+  char *buf = nullptr;
+  const size_t total = bytes_a + bytes_b + bytes_x + 2 * bytes_e + 4 * 256;
+  if (cudaMalloc((void **)&buf, total) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of %zu bytes failed", total);
+    if (info) *info = -1;
+    return -1;
+  }
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  double *dA = (double *)buf;
+  double *dB = B ? (double *)(buf + al(bytes_a)) : nullptr;
+  double *dX = (double *)(buf + al(bytes_a) + al(bytes_b));
+  double *dE = (double *)((char *)dX + al(bytes_x));
+  double *dR = (double *)((char *)dE + al(bytes_e));
+  cudaStream_t st = h->own;
+  int rc = 0;
+  if (cudaMemcpyAsync(dA, A, bytes_a, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      (B && cudaMemcpyAsync(dB, B, bytes_b, cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+      (fpm[4] == 1 && cudaMemcpyAsync(dX, X, bytes_x, cudaMemcpyHostToDevice, st) != cudaSuccess))
+    rc = -4;
+  if (rc == 0)
+    rc = run_dev<TQ>(h, st, uplo, n, dA, lda, dB, ldb, fpm, epsout, loop, emin, emax, M0, dE, dX, M, dR, info, Zne,
+                     Wne);
+  if (rc >= 0 && rc != 200 && rc != 201 && rc != 202 && !(rc > 100 && rc < 200)) {
+    if (cudaMemcpyAsync(E, dE, bytes_e, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(res, dR, bytes_e, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(X, dX, bytes_x, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = -4;
+  }
+  if (rc == -4) set_error("CUDA error in host-pointer driver: %s", cudaGetErrorString(cudaGetLastError()));
+  cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (info) *info = rc;
+  return rc;
+}
+
+// ================================================================== C ABI ==
+extern "C" {
+
+int gbf_version(void) { return 100; }
+
+const char *gbf_last_error(void) { return g_err; }
+
+long long gbf_launch_count(void) { return g_launches.load(); }
+
+int gbf_create(gbf_handle *hp) {
+  if (!hp) return -101;
+  gbf_context *h = new (std::nothrow) gbf_context();
+  if (!h) return -1;
+  GBF_CUDA(cudaGetDevice(&h->device));
+  GBF_CUDA(cudaMallocHost((void **)&h->hflag, sizeof(int) * 4));
+  GBF_CUDA(cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking));
+  *hp = h;
+  return 0;
+}
+
+int gbf_destroy(gbf_handle h) {
+  if (!h) return 0;
+  cudaDeviceSynchronize();
+  if (h->arena) cudaFree(h->arena);
+  if (h->hflag) cudaFreeHost(h->hflag);
+  if (h->hbuf) cudaFreeHost(h->hbuf);
+  if (h->own) cudaStreamDestroy(h->own);
+  delete h;
+  return 0;
+}
+
+void gbf_init(int *fpm) {
+  if (!fpm) return;
+  for (int i = 0; i < 64; ++i) fpm[i] = 0;
+  fpm[1] = 8;
+  fpm[2] = 12;
+  fpm[3] = 20;
+  fpm[5] = 1;
+  fpm[6] = 5;
+  fpm[7] = 16;
+  fpm[16] = 1;
+  fpm[17] = 100;
+}
+
+int gbf_contour(double emin, double emax, int ne, int fpm16, int fpm18, double *Zne, double *Wne) {
+  if (ne < 1) return 102;
+  std::vector<zd> z(ne), w(ne);
+  const int rc = make_contour(emin, emax, ne, fpm16, fpm18, z.data(), w.data());
+  if (rc) return rc;
+  for (int e = 0; e < ne; ++e) {
+    Zne[2 * e] = z[e].x;
+    Zne[2 * e + 1] = z[e].y;
+    Wne[2 * e] = w[e].x;
+    Wne[2 * e + 1] = w[e].y;
+  }
+  return 0;
+}
+
+int gbf_rationalx(const double *Zne, const double *Wne, int ne, const double *eig, int m, double *f) {
+  if (ne < 1) return 102;
+  for (int i = 0; i < m; ++i) {
+    double s = 0.0;
+    for (int e = 0; e < ne; ++e) {
+      const zd q = zdiv(zd{Wne[2 * e], Wne[2 * e + 1]}, zd{Zne[2 * e] - eig[i], Zne[2 * e + 1]});
+      s += q.x;
+    }
+    f[i] = s;
+  }
+  return 0;
+}
+
+int gbf_rational(double emin, double emax, int ne, int fpm16, int fpm18, const double *eig, int m, double *f) {
+  if (ne < 1) return 102;
+  std::vector<double> z(2 * ne), w(2 * ne);
+  const int rc = gbf_contour(emin, emax, ne, fpm16, fpm18, z.data(), w.data());
+  if (rc) return rc;
+  return gbf_rationalx(z.data(), w.data(), ne, eig, m, f);
+}
+
+int gbf_dsyev(char uplo, int n, const double *A, int lda, int *fpm, double *epsout, int *loop, double emin,
+              double emax, int *M0, double *E, double *X, int *M, double *res, int *info) {
+  return run_host<double>(uplo, n, A, lda, nullptr, n, fpm, epsout, loop, emin, emax, M0, E, X, M, res, info,
+                          nullptr, nullptr);
+}
+int gbf_dsygv(char uplo, int n, const double *A, int lda, const double *B, int ldb, int *fpm, double *epsout,
+              int *loop, double emin, double emax, int *M0, double *E, double *X, int *M, double *res, int *info) {
+  return run_host<double>(uplo, n, A, lda, B, ldb, fpm, epsout, loop, emin, emax, M0, E, X, M, res, info, nullptr,
+                          nullptr);
+}
+int gbf_zheev(char uplo, int n, const double *A, int lda, int *fpm, double *epsout, int *loop, double emin,
+              double emax, int *M0, double *E, double *X, int *M, double *res, int *info) {
+  return run_host<zd>(uplo, n, A, lda, nullptr, n, fpm, epsout, loop, emin, emax, M0, E, X, M, res, info, nullptr,
+                      nullptr);
+}
+int gbf_zhegv(char uplo, int n, const double *A, int lda, const double *B, int ldb, int *fpm, double *epsout,
+              int *loop, double emin, double emax, int *M0, double *E, double *X, int *M, double *res, int *info) {
+  return run_host<zd>(uplo, n, A, lda, B, ldb, fpm, epsout, loop, emin, emax, M0, E, X, M, res, info, nullptr,
+                      nullptr);
+}
+int gbf_dsygvx(char uplo, int n, const double *A, int lda, const double *B, int ldb, int *fpm, double *epsout,
+               int *loop, double emin, double emax, int *M0, double *E, double *X, int *M, double *res, int *info,
+               const double *Zne, const double *Wne) {
+  return run_host<double>(uplo, n, A, lda, B, ldb, fpm, epsout, loop, emin, emax, M0, E, X, M, res, info, Zne,
+                          Wne);
+}
+int gbf_zhegvx(char uplo, int n, const double *A, int lda, const double *B, int ldb, int *fpm, double *epsout,
+               int *loop, double emin, double emax, int *M0, double *E, double *X, int *M, double *res, int *info,
+               const double *Zne, const double *Wne) {
+  return run_host<zd>(uplo, n, A, lda, B, ldb, fpm, epsout, loop, emin, emax, M0, E, X, M, res, info, Zne, Wne);
+}
+
+int gbf_dsygv_dev(gbf_handle h, void *stream, char uplo, int n, const double *dA, int lda, const double *dB,
+                  int ldb, int *fpm, double *epsout, int *loop, double emin, double emax, int *M0, double *dE,
+                  double *dX, int *M, double *dres, int *info, const double *Zne, const double *Wne) {
+  if (!h) h = default_ctx();
+  if (!h) return -4;
+  return run_dev<double>(h, stream, uplo, n, dA, lda, dB, ldb, fpm, epsout, loop, emin, emax, M0, dE, dX, M, dres,
+                         info, Zne, Wne);
+}
+int gbf_zhegv_dev(gbf_handle h, void *stream, char uplo, int n, const double *dA, int lda, const double *dB,
+                  int ldb, int *fpm, double *epsout, int *loop, double emin, double emax, int *M0, double *dE,
+                  double *dX, int *M, double *dres, int *info, const double *Zne, const double *Wne) {
+  if (!h) h = default_ctx();
+  if (!h) return -4;
+  return run_dev<zd>(h, stream, uplo, n, dA, lda, dB, ldb, fpm, epsout, loop, emin, emax, M0, dE, dX, M, dres,
+                     info, Zne, Wne);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------- step entries --
+template <class TL>
+static int factor_impl(gbf_handle h, cudaStream_t st, int kind, char uplo, int n, const double *dA, int lda,
+                       const double *dB, int ldb, int ne, const double *Zne) {
+  const int bs = 32;
+  const size_t nn = (size_t)n * n;
+  const int nblk = ceil_div(n, bs);
+  Bump sz(nullptr);
+  sz.take<TL>(ne * nn);
+  sz.take<TL>((size_t)ne * nblk * bs * bs);
+  sz.take<TL>((size_t)ne * nblk * bs * bs);
+  sz.take<int>((size_t)ne * n);
+  sz.take<int>((size_t)ne * n);
+  sz.take<int>(ne);
+  sz.take<zd>(ne);
+  if (ensure_arena(h, sz.off + 4096)) return -1;
+  if (ensure_hbuf(h, (size_t)ne + 8)) return -1;
+  Bump b(h->arena);
+  TL *S = b.take<TL>(ne * nn);
+  TL *Li = b.take<TL>((size_t)ne * nblk * bs * bs);
+  TL *Ui = b.take<TL>((size_t)ne * nblk * bs * bs);
+  int *ipiv = b.take<int>((size_t)ne * n);
+  int *perm = b.take<int>((size_t)ne * n);
+  int *sing = b.take<int>(ne);
+  zd *z = b.take<zd>(ne);
+  std::vector<zd> zh(ne);
+  for (int e = 0; e < ne; ++e) zh[e] = zd{Zne[2 * e], Zne[2 * e + 1]};
+  GBF_CUDA(cudaMemcpyAsync(z, zh.data(), sizeof(zd) * ne, cudaMemcpyHostToDevice, st));
+  GBF_CUDA(cudaMemsetAsync(sing, 0, sizeof(int) * ne, st));
+  int rc = form_shift<TL>(st, n, ne, z, kind, uplo, dA, lda, dB, ldb, S);
+  if (!rc) rc = getrf_batched<TL>(st, n, ne, S, ipiv, perm, Li, Ui, bs, sing, nullptr);
+  if (rc) return rc;
+  int *hs = (int *)h->hbuf;
+  GBF_CUDA(cudaMemcpyAsync(hs, sing, sizeof(int) * ne, cudaMemcpyDeviceToHost, st));
+  GBF_CUDA(cudaStreamSynchronize(st));
+  h->f_n = n;
+  h->f_ne = ne;
+  h->f_bs = bs;
+  h->f_bytes = b.off;
+  for (int e = 0; e < ne; ++e)
+    if (hs[e]) {
+      h->f_prec = -1;
+      set_error("zero pivot in node %d", e);
+      return -2;
+    }
+  return 0;
+}
+
+template <class TL>
+static int solve_impl(gbf_handle h, cudaStream_t st, int trans, int nrhs, const double *dRHS, double *dY) {
+  const int n = h->f_n, ne = h->f_ne, bs = h->f_bs;
+  const size_t nn = (size_t)n * n;
+  const int nblk = ceil_div(n, bs);
+  const size_t ny = (size_t)ne * n * nrhs;
+  Bump b(h->arena);
+  TL *S = b.take<TL>(ne * nn);
+  TL *Li = b.take<TL>((size_t)ne * nblk * bs * bs);
+  TL *Ui = b.take<TL>((size_t)ne * nblk * bs * bs);
+  b.take<int>((size_t)ne * n);
+  int *perm = b.take<int>((size_t)ne * n);
+  b.take<int>(ne);
+  b.take<zd>(ne);
+  const size_t base = b.off;
+  TL *Y = b.take<TL>(ny);
+  TL *Y2 = b.take<TL>(ny);
+  if (b.off + 4096 > h->cap) {
+    // grow while keeping the factors
+    char *na = nullptr;
+    const size_t need = b.off + 4096;
+    if (cudaMalloc((void **)&na, need) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    GBF_CUDA(cudaMemcpyAsync(na, h->arena, base, cudaMemcpyDeviceToDevice, st));
+    GBF_CUDA(cudaStreamSynchronize(st));
+    cudaFree(h->arena);
+    h->arena = na;
+    h->cap = need;
+    return solve_impl<TL>(h, st, trans, nrhs, dRHS, dY);
+  }
+  int rc;
+  if (!trans) {
+    rc = gather_rhs<TL>(st, n, ne, nrhs, perm, 1, dRHS, n, nullptr, Y);
+    if (!rc) rc = getrs_inplace<TL>(st, 0, n, ne, nrhs, S, Li, Ui, bs, Y, nullptr);
+  } else {
+    rc = gather_rhs<TL>(st, n, ne, nrhs, nullptr, 1, dRHS, n, nullptr, Y2);
+    if (!rc) rc = getrs_inplace<TL>(st, 1, n, ne, nrhs, S, Li, Ui, bs, Y2, nullptr);
+    if (!rc) rc = scatter_perm<TL>(st, n, ne, nrhs, perm, Y2, Y);
+  }
+  if (rc) return rc;
+  widen_kernel<TL><<<ceil_div((long)ny, 256), 256, 0, st>>>((long)ny, Y, (zd *)dY);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaStreamSynchronize(st));
+  return 0;
+}
+
+extern "C" int gbf_factor_dev(gbf_handle h, void *stream, int kind, int prec, char uplo, int n, const double *dA, int lda,
+                   const double *dB, int ldb, int ne, const double *Zne) {
+  if (!h) h = default_ctx();
+  if (!h) return -4;
+  if (kind != 0 && kind != 1) return -103;
+  if (prec != 0 && prec != 1) return -104;
+  if (uplo != 'F' && uplo != 'L' && uplo != 'U') return -105;
+  if (n < 1) return 202;
+  if (lda < n) return -108;
+  if (dB && ldb < n) return -110;
+  if (ne < 1) return -111;
+  if (!dA || !Zne) return -107;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int rc = prec ? factor_impl<cf>(h, st, kind, uplo, n, dA, lda, dB, ldb, ne, Zne)
+                      : factor_impl<zd>(h, st, kind, uplo, n, dA, lda, dB, ldb, ne, Zne);
+  if (rc == 0) h->f_prec = prec;
+  return rc;
+}
+
+extern "C" int gbf_solve_dev(gbf_handle h, void *stream, int trans, int nrhs, const double *dRHS, double *dY) {
+  if (!h) h = default_ctx();
+  if (!h) return -4;
+  if (h->f_prec < 0) {
+    set_error("gbf_solve_dev: no stored factorisation (call gbf_factor_dev first)");
+    return -2;
+  }
+  if (trans != 0 && trans != 1) return -103;
+  if (nrhs < 1) return -104;
+  if (!dRHS || !dY) return -105;
+  cudaStream_t st = (cudaStream_t)stream;
+  return h->f_prec ? solve_impl<cf>(h, st, trans, nrhs, dRHS, dY) : solve_impl<zd>(h, st, trans, nrhs, dRHS, dY);
+}
+
+template <class T>
+static int heev_impl(gbf_handle h, cudaStream_t st, int m, T *A, double *w, T *V) {
+  Bump sz(nullptr);
+  sz.take<T>(2 * (size_t)m * m);
+  sz.take<double>(8);
+  sz.take<int>(m + 8);
+  if (ensure_arena(h, sz.off + 4096)) return -1;
+  h->f_prec = -1;
+  Bump b(h->arena);
+  T *work = b.take<T>(2 * (size_t)m * m);
+  double *dwork = b.take<double>(8);
+  int *iwork = b.take<int>(m + 8);
+  int sweeps = 0;
+  const int rc = heev_jacobi<T>(st, m, A, w, V, work, dwork, iwork, h->hflag, &sweeps);
+  if (rc) return rc;
+  GBF_CUDA(cudaStreamSynchronize(st));
+  if (sweeps < 0) {
+    set_error("Jacobi did not converge in 80 sweeps");
+    return -3;
+  }
+  return 0;
+}
+
+extern "C" int gbf_heev_dev(gbf_handle h, void *stream, int kind, int m, double *dA, double *dW, double *dV) {
+  if (!h) h = default_ctx();
+  if (!h) return -4;
+  if (kind != 0 && kind != 1) return -103;
+  if (m < 1) return -104;
+  if (!dA || !dW || !dV) return -105;
+  cudaStream_t st = (cudaStream_t)stream;
+  return kind ? heev_impl<zd>(h, st, m, (zd *)dA, dW, (zd *)dV) : heev_impl<double>(h, st, m, dA, dW, dV);
+}
+
+

@@ -1,0 +1,227 @@
+// Shared device/host helpers of the CUDA path (complex types, launch
+// bookkeeping, kernel entry points used across translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <atomic>
+
+namespace gbf {
+
+// ---------------------------------------------------------------- complex --
+struct __align__(16) zd {
+  double x, y;
+};
+struct __align__(8) cf {
+  float x, y;
+};
+
+__host__ __device__ inline zd mkz(double a, double b) { return zd{a, b}; }
+__host__ __device__ inline cf mkc(float a, float b) { return cf{a, b}; }
+
+// Scalar traits: real double, complex double (zd), complex float (cf).
+template <class T> struct tr;
+template <> struct tr<double> {
+  using R = double;
+  static constexpr bool cplx = false;
+  __host__ __device__ static double zero() { return 0.0; }
+  __host__ __device__ static double one() { return 1.0; }
+  __host__ __device__ static double conj(double a) { return a; }
+  __host__ __device__ static double mul(double a, double b) { return a * b; }
+  __host__ __device__ static double fma(double a, double b, double c) { return ::fma(a, b, c); }
+  __host__ __device__ static double add(double a, double b) { return a + b; }
+  __host__ __device__ static double sub(double a, double b) { return a - b; }
+  __host__ __device__ static double re(double a) { return a; }
+  __host__ __device__ static double abs1(double a) { return fabs(a); }
+  __host__ __device__ static double neg(double a) { return -a; }
+};
+template <> struct tr<zd> {
+  using R = double;
+  static constexpr bool cplx = true;
+  __host__ __device__ static zd zero() { return zd{0.0, 0.0}; }
+  __host__ __device__ static zd one() { return zd{1.0, 0.0}; }
+  __host__ __device__ static zd conj(zd a) { return zd{a.x, -a.y}; }
+  __host__ __device__ static zd mul(zd a, zd b) { return zd{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+  // a*b + c
+  __host__ __device__ static zd fma(zd a, zd b, zd c) {
+    c.x = ::fma(a.x, b.x, c.x);
+    c.x = ::fma(-a.y, b.y, c.x);
+    c.y = ::fma(a.x, b.y, c.y);
+    c.y = ::fma(a.y, b.x, c.y);
+    return c;
+  }
+  __host__ __device__ static zd add(zd a, zd b) { return zd{a.x + b.x, a.y + b.y}; }
+  __host__ __device__ static zd sub(zd a, zd b) { return zd{a.x - b.x, a.y - b.y}; }
+  __host__ __device__ static double re(zd a) { return a.x; }
+  __host__ __device__ static double abs1(zd a) { return fabs(a.x) + fabs(a.y); }
+  __host__ __device__ static zd neg(zd a) { return zd{-a.x, -a.y}; }
+};
+template <> struct tr<cf> {
+  using R = float;
+  static constexpr bool cplx = true;
+  __host__ __device__ static cf zero() { return cf{0.f, 0.f}; }
+  __host__ __device__ static cf one() { return cf{1.f, 0.f}; }
+  __host__ __device__ static cf conj(cf a) { return cf{a.x, -a.y}; }
+  __host__ __device__ static cf mul(cf a, cf b) { return cf{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+  __host__ __device__ static cf fma(cf a, cf b, cf c) {
+    c.x = fmaf(a.x, b.x, c.x);
+    c.x = fmaf(-a.y, b.y, c.x);
+    c.y = fmaf(a.x, b.y, c.y);
+    c.y = fmaf(a.y, b.x, c.y);
+    return c;
+  }
+  __host__ __device__ static cf add(cf a, cf b) { return cf{a.x + b.x, a.y + b.y}; }
+  __host__ __device__ static cf sub(cf a, cf b) { return cf{a.x - b.x, a.y - b.y}; }
+  __host__ __device__ static float re(cf a) { return a.x; }
+  __host__ __device__ static float abs1(cf a) { return fabsf(a.x) + fabsf(a.y); }
+  __host__ __device__ static cf neg(cf a) { return cf{-a.x, -a.y}; }
+};
+
+// Complex double arithmetic used by host and device helpers.
+__host__ __device__ inline zd zmul(zd a, zd b) { return tr<zd>::mul(a, b); }
+__host__ __device__ inline zd zdiv(zd a, zd b) {
+  // Smith's algorithm (scaled division)
+  if (fabs(b.x) >= fabs(b.y)) {
+    double r = b.y / b.x, d = b.x + b.y * r;
+    return zd{(a.x + a.y * r) / d, (a.y - a.x * r) / d};
+  } else {
+    double r = b.x / b.y, d = b.x * r + b.y;
+    return zd{(a.x * r + a.y) / d, (a.y * r - a.x) / d};
+  }
+}
+__host__ __device__ inline double zabs(zd a) { return hypot(a.x, a.y); }
+
+// Conversions between the arithmetic types.
+template <class D, class S> __host__ __device__ inline D cvt(S s);
+template <> __host__ __device__ inline zd cvt<zd, zd>(zd s) { return s; }
+template <> __host__ __device__ inline cf cvt<cf, zd>(zd s) { return cf{(float)s.x, (float)s.y}; }
+template <> __host__ __device__ inline zd cvt<zd, cf>(cf s) { return zd{(double)s.x, (double)s.y}; }
+template <> __host__ __device__ inline cf cvt<cf, cf>(cf s) { return s; }
+template <> __host__ __device__ inline zd cvt<zd, double>(double s) { return zd{s, 0.0}; }
+template <> __host__ __device__ inline cf cvt<cf, double>(double s) { return cf{(float)s, 0.f}; }
+template <> __host__ __device__ inline double cvt<double, double>(double s) { return s; }
+
+// ------------------------------------------------------------ bookkeeping --
+// Number of kernels launched through this library (all launches go through
+// the GBF_LAUNCHED macro after a <<<>>> launch).
+extern std::atomic<long long> g_launches;
+#define GBF_LAUNCHED() (::gbf::g_launches.fetch_add(1, std::memory_order_relaxed))
+
+// Last error text for gbf_last_error(); set by the host driver.
+void set_error(const char *fmt, ...);
+
+#define GBF_CUDA(call)                                                               \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      ::gbf::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      return -4;                                                                     \
+    }                                                                                \
+  } while (0)
+
+inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+// -------------------------------------------------------------- profiling --
+// Optional per-category timing of launches (gbf_profile): a CUDA event pair
+// on the launching stream around each instrumented launch, with the
+// algorithmic flop count of that launch; summed by gbf_profile_read.
+enum Cat {
+  CAT_LU_UPDATE = 0,  // trailing update GEMM of the blocked LU
+  CAT_LU_PANEL,       // panel factorisation + row swaps / U12 solve
+  CAT_SOLVE,          // GEMM steps of the triangular solves
+  CAT_PROJECT,        // n-sized FP64 GEMMs of the Rayleigh-Ritz step
+  CAT_REDUCED,        // M0-sized GEMMs + Jacobi rounds
+  CAT_OTHER,          // everything else (shift, gather, accumulate, ...)
+  CAT_COUNT
+};
+extern thread_local int g_cat;
+struct CatScope {
+  int prev;
+  explicit CatScope(int c) : prev(g_cat) { g_cat = c; }
+  ~CatScope() { g_cat = prev; }
+};
+bool prof_on();
+int prof_begin(cudaStream_t st);                      // slot or -1
+void prof_end(cudaStream_t st, int slot, double flops);
+
+// ------------------------------------------------------------------ GEMM --
+// C = alpha * op(A) * op(B) + beta * C, column-major, strided batches.
+// op: 'N' (as stored), 'T' (transpose), 'C' (conjugate transpose).
+// A is m x k after op, B is k x n after op.  When ksplit > 1 the k range is
+// split into ksplit chunks whose partial products go to `work` (ksplit *
+// batch * m * n elements) and are summed in chunk order by a second kernel.
+template <class T>
+int gemm(cudaStream_t st, char opa, char opb, int m, int n, int k, T alpha, const T *A, long lda,
+         long sa, const T *B, long ldb, long sb, T beta, T *C, long ldc, long sc, int batch,
+         int ksplit = 1, T *work = nullptr);
+
+// ------------------------------------------------------ LU / solve (lu.cu) --
+// Form S_e = z_e B - A for all nodes (B == nullptr: B = I) in type T.
+// kindA: 0 real input (double), 1 complex input (zd). uplo: 'F','L','U'.
+template <class T>
+int form_shift(cudaStream_t st, int n, int ne, const zd *z, int kindA, char uplo, const void *A,
+               long lda, const void *B, long ldb, T *S);
+
+// Blocked right-looking LU with partial pivoting of ne matrices (stride n*n,
+// ld n).  ipiv 0-based absolute rows (ne x n).  perm receives the final row
+// permutation (P b)[i] = b[perm[i]].  Linv/Uinv receive inverted diagonal
+// blocks (bs x bs each, n/bs rounded up per node).  sing: per-node first
+// zero pivot (0 = none).
+template <class T>
+int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T *Linv, T *Uinv,
+                  int bs, int *sing, T *gemm_work);
+
+// Solve S_e Y_e = P-gathered RHS for all nodes (trans 0) or S_e^H Y_e = RHS
+// (trans 1).  Y: ne x (n x nrhs), ld n.  The RHS gather is done by the caller
+// (gather kernels below); this applies the triangular solves in place.
+template <class T>
+int getrs_inplace(cudaStream_t st, int trans, int n, int ne, int nrhs, const T *S, const T *Linv,
+                  const T *Uinv, int bs, T *Y, T *tmp);
+
+// Y_e[i, j] = RHS[perm_e[i], j] * scale_e[j]  (scale may be null => 1).
+// RHS kind: 0 real double, 1 complex double.  Output type T.
+template <class T>
+int gather_rhs(cudaStream_t st, int n, int ne, int nrhs, const int *perm, int kindR, const void *RHS,
+               long ldr, const zd *scale, T *Y);
+
+// Inverse permutation for adjoint solves: out[perm_e[i], j] = Y_e[i, j] (in place via tmp).
+template <class T>
+int scatter_perm(cudaStream_t st, int n, int ne, int nrhs, const int *perm, const T *Yin, T *Yout);
+
+// ------------------------------------------------------------ eig (eig.cu) --
+// Hermitian (T = zd) or real symmetric (T = double) Jacobi eigensolver of an
+// m x m matrix A (ld m, overwritten); w ascending (device), V eigenvectors.
+// work: 2 m^2 T; dwork: >= 1 double; iwork: >= m + 1 ints (device);
+// hflag: pinned host int used to read the per-sweep convergence flag.
+template <class T>
+int heev_jacobi(cudaStream_t st, int m, T *A, double *w, T *V, T *work, double *dwork, int *iwork, int *hflag,
+                int *sweeps_out);
+
+// Rayleigh-Ritz glue (eig.cu).
+template <class T>
+int rr_prepare(cudaStream_t st, int m, const T *Aq, const T *Bq, double *s, int *flag, T *As, T *Bs);
+template <class T>
+int make_t(cudaStream_t st, int m, int mk, int first, const T *V, const double *d, T *Tm);
+template <class T> int hermitize(cudaStream_t st, int m, const T *Cin, T *Cout);
+template <class T> int scale_rows(cudaStream_t st, int m, int mk, const double *s, T *W);
+template <class T>
+int ritz_residual(cudaStream_t st, int n, int mk, const T *AX, const T *BX, const double *lam, double alpha,
+                  double *res);
+int order_and_stats(cudaStream_t st, int mk, const double *lam, const double *res, const int *spur, double emin,
+                    double emax, int *pos, int *nin, double *E, double *R, double *stats);
+template <class T>
+int spurious_flags(cudaStream_t st, int m, int mk, const T *W, const double *lam, double emin, double emax,
+                   const double *f, int check, int *spur);
+template <class T> int permute_cols(cudaStream_t st, int n, int m, const int *pos, const T *in, T *out);
+int filter_values(cudaStream_t st, int mk, int ne, const zd *z, const zd *w, const double *lam, double *f, zd *D,
+                  zd *Dc);
+template <class T>
+int eig_residual(cudaStream_t st, int n, int mk, const T *AX, const T *BX, const double *lam, T *R);
+template <class TY, class TQ>
+int accumulate(cudaStream_t st, int n, int m, int ne, const zd *w, const TY *Y, const TY *Yadj, const TQ *X0,
+               const double *f, TQ *Q);
+template <class TQ> int random_subspace(cudaStream_t st, long count, uint64_t seed, TQ *Y);
+
+}  // namespace gbf

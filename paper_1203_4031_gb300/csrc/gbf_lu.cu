@@ -1,0 +1,439 @@
+// Shifted-system factorisation and multi-RHS solves for all contour nodes
+// (the dense driver's inner solver: RCI cases 10, 11 and 21 of the FEAST
+// v3.0 guide, Fig. "fig_rci").
+//
+//   form_shift     S_e = z_e B - A for every node in one pass over A and B
+//   getrf_batched  blocked right-looking LU with partial pivoting, all nodes
+//                  in each launch (node = grid dimension):
+//                    panel  : one CTA per node, warp-shuffle argmax pivot
+//                             search, row swap, scale, rank-1 updates
+//                    laswp+trsm : swaps outside the panel, U12 = L11^{-1} A12
+//                    update : A22 -= L21 U12 (batched GEMM)
+//                  then the row permutation and inverted bs x bs diagonal
+//                  blocks of L and U (reused by every solve of every FEAST
+//                  iteration, since the factors are kept: fpm(10)=1 style).
+//   getrs_inplace  blocked triangular solves in which every step is a GEMM:
+//                  Y_b <- inv(T_bb) Y_b, then the trailing update.  trans=1
+//                  gives S^H Y = R from the same factors (case 21).
+#include <algorithm>
+
+#include "gbf_common.cuh"
+
+namespace gbf {
+
+template <class T> __device__ inline T cinv(T a);
+template <> __device__ inline zd cinv<zd>(zd a) { return zdiv(zd{1.0, 0.0}, a); }
+template <> __device__ inline cf cinv<cf>(cf a) {
+  zd r = zdiv(zd{1.0, 0.0}, zd{(double)a.x, (double)a.y});
+  return cf{(float)r.x, (float)r.y};
+}
+
+// ------------------------------------------------------------ form_shift --
+template <class T>
+__global__ void form_shift_kernel(int n, int ne, const zd *__restrict__ z, int kindA, char uplo,
+                                  const void *__restrict__ Av, long lda, const void *__restrict__ Bv,
+                                  long ldb, T *__restrict__ S) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= n) return;
+  // element (i, j) of the full Hermitian matrix from the referenced triangle
+  const bool mirror = (uplo == 'L' && i < j) || (uplo == 'U' && i > j);
+  const long src = mirror ? (j + (long)i * lda) : (i + (long)j * lda);
+  const long srcb = mirror ? (j + (long)i * ldb) : (i + (long)j * ldb);
+  zd a, b;
+  if (kindA == 0) {
+    a = zd{((const double *)Av)[src], 0.0};
+    b = Bv ? zd{((const double *)Bv)[srcb], 0.0} : zd{i == j ? 1.0 : 0.0, 0.0};
+  } else {
+    a = ((const zd *)Av)[src];
+    b = Bv ? ((const zd *)Bv)[srcb] : zd{i == j ? 1.0 : 0.0, 0.0};
+    if (mirror) {
+      a.y = -a.y;
+      b.y = -b.y;
+    }
+    if (i == j) {
+      a.y = 0.0;
+      b.y = 0.0;
+    }
+  }
+  const long nn = (long)n * n;
+  const long off = i + (long)j * n;
+  for (int e = 0; e < ne; ++e) {
+    const zd ze = z[e];
+    zd s = zd{ze.x * b.x - ze.y * b.y - a.x, ze.x * b.y + ze.y * b.x - a.y};
+    S[e * nn + off] = cvt<T, zd>(s);
+  }
+}
+
+template <class T>
+int form_shift(cudaStream_t st, int n, int ne, const zd *z, int kindA, char uplo, const void *A, long lda,
+               const void *B, long ldb, T *S) {
+  dim3 grid(ceil_div(n, 256), n);
+  form_shift_kernel<T><<<grid, 256, 0, st>>>(n, ne, z, kindA, uplo, A, lda, B, ldb, S);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+
+// ---------------------------------------------------------------- panel --
+// One CTA per node factors columns [k, k+w) of rows [k, n).
+constexpr int PANEL_THREADS = 512;
+constexpr int MAX_NB = 64;
+
+template <class T>
+__global__ void __launch_bounds__(PANEL_THREADS)
+    lu_panel_kernel(int n, int k, int w, T *S, int *ipiv, int *sing) {
+  using X = tr<T>;
+  using R = typename X::R;
+  const int e = blockIdx.x;
+  const long nn = (long)n * n;
+  T *a = S + e * nn;
+  int *piv = ipiv + (long)e * n;
+  __shared__ R sval[32];
+  __shared__ int sidx[32];
+  __shared__ T urow[MAX_NB];
+  __shared__ int s_p, s_ok;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = blockDim.x >> 5;
+
+  for (int j = 0; j < w; ++j) {
+    const int c = k + j;
+    const T *col = a + (long)c * n;
+    R best = (R)-1;
+    int bidx = n;
+    for (int r = c + tid; r < n; r += blockDim.x) {
+      const R v = X::abs1(col[r]);
+      if (v > best) {
+        best = v;
+        bidx = r;
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const R ov = __shfl_down_sync(0xffffffffu, best, off);
+      const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
+      if (ov > best || (ov == best && oi < bidx)) {
+        best = ov;
+        bidx = oi;
+      }
+    }
+    if (lane == 0) {
+      sval[warp] = best;
+      sidx[warp] = bidx;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < nwarps ? sval[lane] : (R)-1;
+      bidx = lane < nwarps ? sidx[lane] : n;
+      for (int off = 16; off > 0; off >>= 1) {
+        const R ov = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
+        if (ov > best || (ov == best && oi < bidx)) {
+          best = ov;
+          bidx = oi;
+        }
+      }
+      if (lane == 0) {
+        const int ok = (best > (R)0) && (bidx < n);
+        s_ok = ok;
+        s_p = ok ? bidx : c;
+        piv[c] = ok ? bidx : c;
+        if (!ok && sing[e] == 0) sing[e] = c + 1;
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (!s_ok) continue;  // zero column: nothing to eliminate (reported via sing)
+    if (p != c)
+      for (int jj = tid; jj < w; jj += blockDim.x) {
+        T *cj = a + (long)(k + jj) * n;
+        const T t = cj[c];
+        cj[c] = cj[p];
+        cj[p] = t;
+      }
+    __syncthreads();
+    for (int jj = tid; jj < w; jj += blockDim.x) urow[jj] = a[c + (long)(k + jj) * n];
+    __syncthreads();
+    const T inv = cinv<T>(urow[j]);
+    T *colc = a + (long)c * n;
+    for (int r = c + 1 + tid; r < n; r += blockDim.x) {
+      const T l = X::mul(colc[r], inv);
+      colc[r] = l;
+      for (int jj = j + 1; jj < w; ++jj) {
+        T *cj = a + (long)(k + jj) * n;
+        const T u = urow[jj];
+        cj[r] = X::fma(l, X::neg(u), cj[r]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------- laswp + trsm --
+// Columns outside the panel: apply the panel's row swaps; columns right of
+// the panel additionally get U12 = L11^{-1} A12 (unit lower forward solve).
+constexpr int SWAP_COLS = 64;
+
+template <class T>
+__global__ void __launch_bounds__(SWAP_COLS)
+    laswp_trsm_kernel(int n, int k, int w, T *S, const int *ipiv) {
+  using X = tr<T>;
+  const int e = blockIdx.y;
+  const long nn = (long)n * n;
+  T *a = S + e * nn;
+  const int *piv = ipiv + (long)e * n + k;
+  // dynamic shared memory: L11 (w x w, ld w) then the w pivots
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *L = reinterpret_cast<T *>(smem_raw);
+  int *sp = reinterpret_cast<int *>(L + w * w);
+  for (int t = threadIdx.x; t < w; t += blockDim.x) sp[t] = piv[t];
+  for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+    const int ii = t % w, jj = t / w;
+    L[ii + jj * w] = a[(k + ii) + (long)(k + jj) * n];
+  }
+  __syncthreads();
+  const int idx = blockIdx.x * SWAP_COLS + threadIdx.x;
+  if (idx >= n - w) return;
+  const int col = idx < k ? idx : idx + w;
+  T *cj = a + (long)col * n;
+  for (int jj = 0; jj < w; ++jj) {
+    const int p = sp[jj];
+    if (p != k + jj) {
+      const T t = cj[k + jj];
+      cj[k + jj] = cj[p];
+      cj[p] = t;
+    }
+  }
+  if (col < k + w) return;
+  T x[MAX_NB];
+  for (int jj = 0; jj < w; ++jj) x[jj] = cj[k + jj];
+  for (int jj = 0; jj < w; ++jj) {
+    const T xj = x[jj];
+    for (int ii = jj + 1; ii < w; ++ii) x[ii] = X::fma(L[ii + jj * w], X::neg(xj), x[ii]);
+  }
+  for (int jj = 0; jj < w; ++jj) cj[k + jj] = x[jj];
+}
+
+// -------------------------------------------------------- permutation --
+__global__ void perm_from_ipiv_kernel(int n, const int *ipiv, int *perm) {
+  const int e = blockIdx.x;
+  const int *pv = ipiv + (long)e * n;
+  int *pe = perm + (long)e * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) pe[i] = i;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 0; i < n; ++i) {
+      const int p = pv[i];
+      if (p != i) {
+        const int t = pe[i];
+        pe[i] = pe[p];
+        pe[p] = t;
+      }
+    }
+}
+
+// ----------------------------------------- inverted diagonal blocks --
+// Block b of node e: Linv = inverse of the unit lower triangle, Uinv of the
+// upper triangle, both bs x bs (identity-padded past n).  Thread j forms
+// column j by substitution against e_j.
+template <class T>
+__global__ void tri_inverse_kernel(int n, int bs, int nblk, const T *S, T *Linv, T *Uinv) {
+  using X = tr<T>;
+  const int b = blockIdx.x, e = blockIdx.y;
+  const int r0 = b * bs;
+  const int bsz = min(bs, n - r0);
+  const long nn = (long)n * n;
+  const T *a = S + e * nn + r0 + (long)r0 * n;  // top-left of the diagonal block
+  T *li = Linv + ((long)e * nblk + b) * bs * bs;
+  T *ui = Uinv + ((long)e * nblk + b) * bs * bs;
+  const int j = threadIdx.x;
+  if (j >= bs) return;
+  T x[MAX_NB];
+  // L: unit lower, forward substitution
+  for (int i = 0; i < bs; ++i) x[i] = (i == j) ? X::one() : X::zero();
+  if (j < bsz)
+    for (int i = j + 1; i < bsz; ++i) {
+      T s = x[i];
+      for (int l = j; l < i; ++l) s = X::fma(a[i + (long)l * n], X::neg(x[l]), s);
+      x[i] = s;
+    }
+  for (int i = 0; i < bs; ++i) li[i + (long)j * bs] = x[i];
+  // U: upper, backward substitution
+  for (int i = 0; i < bs; ++i) x[i] = (i == j) ? X::one() : X::zero();
+  if (j < bsz)
+    for (int i = j; i >= 0; --i) {
+      T s = x[i];
+      for (int l = i + 1; l <= j; ++l) s = X::fma(a[i + (long)l * n], X::neg(x[l]), s);
+      x[i] = X::mul(s, cinv<T>(a[i + (long)i * n]));
+    }
+  for (int i = 0; i < bs; ++i) ui[i + (long)j * bs] = x[i];
+}
+
+template <class T>
+int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T *Linv, T *Uinv, int bs,
+                  int *sing, T *) {
+  using X = tr<T>;
+  const int nb = std::min(bs, MAX_NB);
+  const long nn = (long)n * n;
+  for (int k = 0; k < n; k += nb) {
+    const int w = std::min(nb, n - k);
+    CatScope cat_panel(CAT_LU_PANEL);
+    const int slot = prof_begin(st);
+    lu_panel_kernel<T><<<ne, PANEL_THREADS, 0, st>>>(n, k, w, S, ipiv, sing);
+    GBF_LAUNCHED();
+    if (n - w > 0) {
+      dim3 g(ceil_div(n - w, SWAP_COLS), ne);
+      const size_t sm = (size_t)w * w * sizeof(T) + (size_t)w * sizeof(int);
+      static bool attr_set = false;
+      if (!attr_set) {
+        GBF_CUDA(cudaFuncSetAttribute(laswp_trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(MAX_NB * MAX_NB * sizeof(T) + MAX_NB * sizeof(int))));
+        attr_set = true;
+      }
+      laswp_trsm_kernel<T><<<g, SWAP_COLS, sm, st>>>(n, k, w, S, ipiv);
+      GBF_LAUNCHED();
+    }
+    prof_end(st, slot, 0.0);
+    const int rest = n - k - w;
+    if (rest > 0) {
+      CatScope cat_update(CAT_LU_UPDATE);
+      T m1 = X::zero();
+      m1 = X::sub(m1, X::one());
+      int rc = gemm<T>(st, 'N', 'N', rest, rest, w, m1, S + (k + w) + (long)k * n, n, nn,
+                       S + k + (long)(k + w) * n, n, nn, X::one(), S + (k + w) + (long)(k + w) * n, n, nn,
+                       ne);
+      if (rc) return rc;
+    }
+  }
+  perm_from_ipiv_kernel<<<ne, 256, 0, st>>>(n, ipiv, perm);
+  GBF_LAUNCHED();
+  const int nblk = ceil_div(n, bs);
+  dim3 g(nblk, ne);
+  tri_inverse_kernel<T><<<g, bs, 0, st>>>(n, bs, nblk, S, Linv, Uinv);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+
+// ---------------------------------------------------------------- solves --
+template <class T>
+int getrs_inplace(cudaStream_t st, int trans, int n, int ne, int nrhs, const T *S, const T *Linv,
+                  const T *Uinv, int bs, T *Y, T *) {
+  using X = tr<T>;
+  CatScope cat_solve(CAT_SOLVE);
+  const long nn = (long)n * n, ny = (long)n * nrhs;
+  const int nblk = ceil_div(n, bs);
+  const long sblk = (long)nblk * bs * bs;
+  const T one = X::one();
+  const T m1 = X::sub(X::zero(), X::one());
+  const T zero = X::zero();
+  int rc;
+  auto blk = [&](int b) { return std::min(bs, n - b * bs); };
+  if (!trans) {
+    // L (unit lower): Y_b <- Linv_b Y_b ; Y_below -= L_{below,b} Y_b
+    for (int b = 0; b < nblk; ++b) {
+      const int r0 = b * bs, bsz = blk(b);
+      if ((rc = gemm<T>(st, 'N', 'N', bsz, nrhs, bsz, one, Linv + (long)b * bs * bs, bs, sblk, Y + r0, n, ny,
+                        zero, Y + r0, n, ny, ne)))
+        return rc;
+      const int below = n - r0 - bsz;
+      if (below > 0 &&
+          (rc = gemm<T>(st, 'N', 'N', below, nrhs, bsz, m1, S + (r0 + bsz) + (long)r0 * n, n, nn, Y + r0, n, ny,
+                        one, Y + r0 + bsz, n, ny, ne)))
+        return rc;
+    }
+    // U (upper): backward
+    for (int b = nblk - 1; b >= 0; --b) {
+      const int r0 = b * bs, bsz = blk(b);
+      if ((rc = gemm<T>(st, 'N', 'N', bsz, nrhs, bsz, one, Uinv + (long)b * bs * bs, bs, sblk, Y + r0, n, ny,
+                        zero, Y + r0, n, ny, ne)))
+        return rc;
+      if (r0 > 0 && (rc = gemm<T>(st, 'N', 'N', r0, nrhs, bsz, m1, S + (long)r0 * n, n, nn, Y + r0, n, ny, one,
+                                  Y, n, ny, ne)))
+        return rc;
+    }
+  } else {
+    // U^H (lower): forward
+    for (int b = 0; b < nblk; ++b) {
+      const int r0 = b * bs, bsz = blk(b);
+      if ((rc = gemm<T>(st, 'C', 'N', bsz, nrhs, bsz, one, Uinv + (long)b * bs * bs, bs, sblk, Y + r0, n, ny,
+                        zero, Y + r0, n, ny, ne)))
+        return rc;
+      const int below = n - r0 - bsz;
+      if (below > 0 &&
+          (rc = gemm<T>(st, 'C', 'N', below, nrhs, bsz, m1, S + r0 + (long)(r0 + bsz) * n, n, nn, Y + r0, n, ny,
+                        one, Y + r0 + bsz, n, ny, ne)))
+        return rc;
+    }
+    // L^H (unit upper): backward
+    for (int b = nblk - 1; b >= 0; --b) {
+      const int r0 = b * bs, bsz = blk(b);
+      if ((rc = gemm<T>(st, 'C', 'N', bsz, nrhs, bsz, one, Linv + (long)b * bs * bs, bs, sblk, Y + r0, n, ny,
+                        zero, Y + r0, n, ny, ne)))
+        return rc;
+      if (r0 > 0 && (rc = gemm<T>(st, 'C', 'N', r0, nrhs, bsz, m1, S + r0, n, nn, Y + r0, n, ny, one, Y, n, ny,
+                                  ne)))
+        return rc;
+    }
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------- gather/scatter --
+template <class T>
+__global__ void gather_rhs_kernel(int n, int nrhs, const int *__restrict__ perm, int kindR, const void *RHS,
+                                  long ldr, const zd *__restrict__ scale, T *__restrict__ Y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, e = blockIdx.z;
+  if (i >= n) return;
+  const int src = perm ? perm[(long)e * n + i] : i;
+  zd v;
+  if (kindR == 0)
+    v = zd{((const double *)RHS)[src + (long)j * ldr], 0.0};
+  else
+    v = ((const zd *)RHS)[src + (long)j * ldr];
+  if (scale) v = zmul(v, scale[(long)e * nrhs + j]);
+  Y[(long)e * n * nrhs + i + (long)j * n] = cvt<T, zd>(v);
+}
+
+template <class T>
+int gather_rhs(cudaStream_t st, int n, int ne, int nrhs, const int *perm, int kindR, const void *RHS, long ldr,
+               const zd *scale, T *Y) {
+  dim3 g(ceil_div(n, 256), nrhs, ne);
+  gather_rhs_kernel<T><<<g, 256, 0, st>>>(n, nrhs, perm, kindR, RHS, ldr, scale, Y);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+
+template <class T>
+__global__ void scatter_perm_kernel(int n, int nrhs, const int *__restrict__ perm, const T *__restrict__ Yin,
+                                    T *__restrict__ Yout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, e = blockIdx.z;
+  if (i >= n) return;
+  const long base = (long)e * n * nrhs + (long)j * n;
+  Yout[base + perm[(long)e * n + i]] = Yin[base + i];
+}
+
+template <class T>
+int scatter_perm(cudaStream_t st, int n, int ne, int nrhs, const int *perm, const T *Yin, T *Yout) {
+  dim3 g(ceil_div(n, 256), nrhs, ne);
+  scatter_perm_kernel<T><<<g, 256, 0, st>>>(n, nrhs, perm, Yin, Yout);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+
+#define GBF_INST(T)                                                                                        \
+  template int form_shift<T>(cudaStream_t, int, int, const zd *, int, char, const void *, long, const void *, \
+                             long, T *);                                                                   \
+  template int getrf_batched<T>(cudaStream_t, int, int, T *, int *, int *, T *, T *, int, int *, T *);       \
+  template int getrs_inplace<T>(cudaStream_t, int, int, int, int, const T *, const T *, const T *, int, T *,  \
+                                T *);                                                                      \
+  template int gather_rhs<T>(cudaStream_t, int, int, int, const int *, int, const void *, long, const zd *,  \
+                             T *);                                                                         \
+  template int scatter_perm<T>(cudaStream_t, int, int, int, const int *, const T *, T *);
+GBF_INST(zd)
+GBF_INST(cf)
+
+}  // namespace gbf

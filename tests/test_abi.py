@@ -1,0 +1,96 @@
+"""C-ABI boundary checks that need no GPU: the library builds, loads and
+exports every symbol include/gbfeast.h declares; host-only entry points
+(feastinit defaults, contour, rational filter, argument validation) match
+the oracle and the guide's tables."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1203_4031_gb300 as g
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "gbfeast.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(gbf_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = g.load()
+    names = declared_symbols()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_version_and_error_text():
+    assert g.version() >= 100
+    assert isinstance(g.last_error(), str)
+
+
+def test_feastinit_defaults_table():
+    """Table tab_fpm defaults (fpm[i-1] = fpm(i))."""
+    fpm = g.gbf_init()
+    expect = {2: 8, 3: 12, 4: 20, 6: 1, 7: 5, 8: 16, 17: 1, 18: 100}
+    for i in range(1, 65):
+        assert fpm[i - 1] == expect.get(i, 0), i
+    assert np.array_equal(fpm, oracle.feastinit())
+
+
+@pytest.mark.parametrize("ne", [1, 2, 8, 16, 20, 56])
+@pytest.mark.parametrize("qtype,ratio", [(0, 100), (1, 100), (0, 50), (1, 200)])
+def test_contour_matches_oracle(ne, qtype, ratio):
+    for emin, emax in [(-5.0, 5.0), (0.5, 1.0), (-0.0023589538297558448, 0.0023589538297558448)]:
+        z, w = g.gbf_contour(emin, emax, ne, qtype, ratio)
+        zo, wo = oracle.contour(emin, emax, ne, qtype, ratio)
+        scale = emax - emin
+        assert np.max(np.abs(z - zo)) <= 4e-16 * scale * 4 + 1e-300
+        assert np.max(np.abs(w - wo)) <= 4e-16 * scale * 4 + 1e-300
+
+
+@pytest.mark.parametrize("ne", [8, 16])
+def test_rational_matches_oracle_and_invariants(ne):
+    x = np.linspace(-2.0, 3.0, 101)
+    f = g.gbf_rational(-0.5, 1.5, ne, x)
+    fo = oracle.rational(-0.5, 1.5, ne, x)
+    assert np.max(np.abs(f - fo)) < 1e-14
+    fc = g.gbf_rational(-0.5, 1.5, ne, np.array([0.5, -0.5, 1.5]))
+    assert abs(fc[0] - 1) < 1e-14 and abs(fc[1] - 0.5) < 1e-13 and abs(fc[2] - 0.5) < 1e-13
+    z, w = g.gbf_contour(-0.5, 1.5, ne)
+    assert np.max(np.abs(g.gbf_rationalx(z, w, x) - f)) == 0.0
+
+
+def test_contour_info_codes():
+    L = g.load()
+    z = np.zeros(16)
+    w = np.zeros(16)
+    dp = C.POINTER(C.c_double)
+    zp, wp = z.ctypes.data_as(dp), w.ctypes.data_as(dp)
+    assert L.gbf_contour(1.0, 1.0, 8, 0, 100, zp, wp) == 200
+    assert L.gbf_contour(0.0, 1.0, 0, 0, 100, zp, wp) == 102
+    assert L.gbf_contour(0.0, 1.0, 8, 2, 100, zp, wp) == 116
+    assert L.gbf_contour(0.0, 1.0, 8, 0, 0, zp, wp) == 118
+
+
+def test_driver_argument_validation_without_gpu():
+    """Codes of Table tab_info that are decided before any device work."""
+    A = np.diag(np.arange(1.0, 11.0))
+    r = g.feast_host(A[:0, :0].reshape(0, 0), None, 0, 1, 1)
+    assert r["info"] == 202
+    assert g.feast_host(A, None, 0.0, 5.0, 0)["info"] == 201
+    assert g.feast_host(A, None, 0.0, 5.0, 11)["info"] == 201
+    assert g.feast_host(A, None, 5.0, 5.0, 4)["info"] == 200
+    assert g.feast_host(A, None, 0.0, 5.0, 4, uplo="X")["info"] == -101
+    base = g.gbf_init()
+    for idx, bad, code in [(1, 21, 102), (1, 0, 102), (2, -1, 103), (3, -1, 104), (4, 2, 105),
+                           (5, 3, 106), (13, 3, 114), (15, 2, 116), (17, 0, 118), (41, 2, 142),
+                           (42, 5, 143)]:
+        f = base.copy()
+        f[idx] = bad
+        assert g.feast_host(A, None, 0.5, 3.5, 5, fpm=f)["info"] == code, (idx, bad)
