@@ -202,6 +202,14 @@ __global__ void copy_cols_kernel(int n, int m, const TQ *src, long lds, TQ *dst,
   if (i < n && j < m) dst[i + (long)j * ldd] = src[i + (long)j * lds];
 }
 
+// out = in^H (m x m)
+template <class TQ>
+__global__ void copy_t_kernel(int m, const TQ *in, TQ *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i < m) out[i + (long)j * m] = tr<TQ>::conj(in[j + (long)i * m]);
+}
+
 template <class TL>
 __global__ void widen_kernel(long count, const TL *src, zd *dst) {
   const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -257,7 +265,7 @@ template <class TQ, class TL> struct WS {
     pos = b.take<int>(m0);
     spur = b.take<int>(m0);
     nin = b.take<int>(4);
-    iwork = b.take<int>(m0 + 8);
+    iwork = b.take<int>(3 * m0 + 96);
     flag = b.take<int>(4);
     Af = needAf ? b.take<TQ>(nn) : nullptr;
     Bf = needBf ? b.take<TQ>(nn) : nullptr;
@@ -283,7 +291,7 @@ template <class TQ, class TL> struct WS {
     Cs = b.take<TQ>(mm);
     U = b.take<TQ>(mm);
     W = b.take<TQ>(mm);
-    jwork = b.take<TQ>(2 * mm);
+    jwork = b.take<TQ>(2 * mm + 2 * m0);
     kwork = b.take<TQ>((size_t)std::max(ksplit, 1) * mm);
     d = b.take<double>(m0);
     lam = b.take<double>(m0);
@@ -292,7 +300,7 @@ template <class TQ, class TL> struct WS {
     Es = b.take<double>(m0);
     Rs = b.take<double>(m0);
     f = b.take<double>(m0);
-    dwork = b.take<double>(8);
+    dwork = b.take<double>(8 + 4 * m0);
     stats = b.take<double>(8);
     z = b.take<zd>(ne);
     w = b.take<zd>(ne);
@@ -462,26 +470,73 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
     CK(gemm<TQ>(st, 'C', 'N', m, m, n, one, ws.Q, n, 0, ws.AQ, n, 0, zero, ws.Aq, m, 0, 1, ks, ws.kwork));
     CK(gemm<TQ>(st, 'C', 'N', m, m, n, one, ws.Q, n, 0, BQ, n, 0, zero, ws.Bq, m, 0, 1, ks, ws.kwork));
     CK(rr_prepare<TQ>(st, m, ws.Aq, ws.Bq, ws.s, ws.flag, ws.As, ws.Bs));
-    CK(heev_jacobi<TQ>(st, m, ws.Bs, ws.d, ws.V, ws.jwork, ws.dwork, ws.iwork, h->hflag, nullptr));
+    // B-orthonormal basis T of span(Q) (scaled): CholeskyQR passes on the
+    // scaled Q^H B Q (T <- T L^{-H}, G <- T^H Bs T, until ||G - I||_F is at
+    // rounding level, at most 3 passes); when a pivot is not positive or
+    // the passes stall, the rank-revealing Jacobi route with truncation.
+    int mk = m, first = 0;
+    bool ns_done = false;  // "orthonormal basis found without Jacobi"
+    int sw_b = -2, sw_c = -2, ns_it = 0;
     double *hd = h->hbuf;
-    GBF_CUDA(cudaMemcpyAsync(hd, ws.d, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
-    GBF_CUDA(cudaMemcpyAsync(h->hflag, ws.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-    GBF_CUDA(cudaStreamSynchronize(st));
-    const double dmax = hd[m - 1];
-    if (*h->hflag || !(dmax > 0.0) || !(hd[0] >= -1e-8 * dmax)) {
-      set_error("Q^H B Q is not positive definite (B not HPD on the subspace)");
-      return out.info = -3;
+    {
+      CatScope cat_red(CAT_REDUCED);
+      TQ *G = ws.Ctmp, *Gw = ws.Cm, *L = ws.U, *Li = ws.V, *Tn = ws.W;
+      GBF_CUDA(cudaMemcpyAsync(G, ws.Bs, sizeof(TQ) * (size_t)m * m, cudaMemcpyDeviceToDevice, st));
+      for (int pass = 0; pass < 3; ++pass) {
+        ns_it = pass + 1;
+        GBF_CUDA(cudaMemcpyAsync(Gw, G, sizeof(TQ) * (size_t)m * m, cudaMemcpyDeviceToDevice, st));
+        GBF_CUDA(cudaMemsetAsync(ws.flag + 1, 0, sizeof(int), st));
+        CK(chol_lower<TQ>(st, m, Gw, L, ws.flag + 1));
+        CK(trinv_lower<TQ>(st, m, L, Li));
+        if (pass == 0) {
+          // T = L^{-H}
+          copy_t_kernel<TQ><<<dim3(ceil_div(m, 256), m), 256, 0, st>>>(m, Li, ws.Tm);
+          GBF_LAUNCHED();
+        } else {
+          CK(gemm<TQ>(st, 'N', 'C', m, m, m, one, ws.Tm, m, 0, Li, m, 0, zero, Tn, m, 0, 1));
+          GBF_CUDA(cudaMemcpyAsync(ws.Tm, Tn, sizeof(TQ) * (size_t)m * m, cudaMemcpyDeviceToDevice, st));
+        }
+        // G = T^H Bs T
+        CK(gemm<TQ>(st, 'N', 'N', m, m, m, one, ws.Bs, m, 0, ws.Tm, m, 0, zero, Tn, m, 0, 1));
+        CK(gemm<TQ>(st, 'C', 'N', m, m, m, one, ws.Tm, m, 0, Tn, m, 0, zero, G, m, 0, 1));
+        CK(ns_prep<TQ>(st, m, G, (TQ *)nullptr, ws.dwork + 4));
+        GBF_CUDA(cudaMemcpyAsync(hd, ws.dwork + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+        GBF_CUDA(cudaMemcpyAsync(h->hflag, ws.flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+        GBF_CUDA(cudaStreamSynchronize(st));
+        if (h->hflag[0]) {
+          set_error("Q^H B Q has a non-positive diagonal (B not HPD on the subspace)");
+          return out.info = -3;
+        }
+        if (h->hflag[1] || !(hd[0] == hd[0])) break;  // not positive definite: Jacobi route
+        // at rounding level (or, after the last pass, at the rounding floor
+        // u*kappa of a full-rank basis with kappa below ~1e10, where the
+        // truncation route would keep every direction as well)
+        if (hd[0] < 1e-13 * m || (pass == 2 && hd[0] < 1e-5)) {
+          ns_done = true;
+          break;
+        }
+      }
     }
-    int first = 0;
-    while (first < m && !(hd[first] > 1e-12 * dmax)) ++first;
-    const int mk = m - first;
+    if (!ns_done) {
+      CK(heev_jacobi<TQ>(st, m, ws.Bs, ws.d, ws.V, ws.jwork, ws.dwork, ws.iwork, h->hflag, &sw_b));
+      GBF_CUDA(cudaMemcpyAsync(hd, ws.d, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+      GBF_CUDA(cudaMemcpyAsync(h->hflag, ws.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+      GBF_CUDA(cudaStreamSynchronize(st));
+      const double dmax = hd[m - 1];
+      if (*h->hflag || !(dmax > 0.0) || !(hd[0] >= -1e-8 * dmax)) {
+        set_error("Q^H B Q is not positive definite (B not HPD on the subspace)");
+        return out.info = -3;
+      }
+      while (first < m && !(hd[first] > 1e-12 * dmax)) ++first;
+      mk = m - first;
+    }
     {
     CatScope cat_red(CAT_REDUCED);
-    CK(make_t<TQ>(st, m, mk, first, ws.V, ws.d, ws.Tm));
+    if (!ns_done) CK(make_t<TQ>(st, m, mk, first, ws.V, ws.d, ws.Tm));
     CK(gemm<TQ>(st, 'N', 'N', m, mk, m, one, ws.As, m, 0, ws.Tm, m, 0, zero, ws.Ctmp, m, 0, 1));
     CK(gemm<TQ>(st, 'C', 'N', mk, mk, m, one, ws.Tm, m, 0, ws.Ctmp, m, 0, zero, ws.Cm, mk, 0, 1));
     CK(hermitize<TQ>(st, mk, ws.Cm, ws.Cs));
-    CK(heev_jacobi<TQ>(st, mk, ws.Cs, ws.lam, ws.U, ws.jwork, ws.dwork, ws.iwork, h->hflag, nullptr));
+    CK(heev_jacobi<TQ>(st, mk, ws.Cs, ws.lam, ws.U, ws.jwork, ws.dwork, ws.iwork, h->hflag, &sw_c));
     CK(gemm<TQ>(st, 'N', 'N', m, mk, mk, one, ws.Tm, m, 0, ws.U, mk, 0, zero, ws.W, m, 0, 1));
     CK(scale_rows<TQ>(st, m, mk, ws.s, ws.W));
     }
@@ -513,7 +568,9 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
     out.epsout = eout;
     out.m0 = mk;
     if (fpm[0] == 1)  // runtime comments (fpm(1)): one line per loop, as the guide's output
-      fprintf(stderr, "%d\t%d\t%.15e\t%.15e\t%.15e\t(M0 %d)\n", k, nin, trace, eout, maxres, mk);
+      fprintf(stderr, "%d\t%d\t%.15e\t%.15e\t%.15e\t(M0 %d; B-orth: %s %d; reduced sweeps %d)\n", k, nin,
+              trace, eout, maxres, mk, ns_done ? "CholeskyQR passes" : "Jacobi sweeps",
+              ns_done ? ns_it : sw_b + 1, sw_c + 1);
     int info = -99;
     if (!finite) {
       set_error("non-finite Ritz values or residuals");
@@ -912,15 +969,15 @@ extern "C" int gbf_solve_dev(gbf_handle h, void *stream, int trans, int nrhs, co
 template <class T>
 static int heev_impl(gbf_handle h, cudaStream_t st, int m, T *A, double *w, T *V) {
   Bump sz(nullptr);
-  sz.take<T>(2 * (size_t)m * m);
-  sz.take<double>(8);
-  sz.take<int>(m + 8);
+  sz.take<T>(2 * (size_t)m * m + 2 * m);
+  sz.take<double>(8 + 4 * m);
+  sz.take<int>(3 * m + 96);
   if (ensure_arena(h, sz.off + 4096)) return -1;
   h->f_prec = -1;
   Bump b(h->arena);
-  T *work = b.take<T>(2 * (size_t)m * m);
-  double *dwork = b.take<double>(8);
-  int *iwork = b.take<int>(m + 8);
+  T *work = b.take<T>(2 * (size_t)m * m + 2 * m);
+  double *dwork = b.take<double>(8 + 4 * m);
+  int *iwork = b.take<int>(3 * m + 96);
   int sweeps = 0;
   const int rc = heev_jacobi<T>(st, m, A, w, V, work, dwork, iwork, h->hflag, &sweeps);
   if (rc) return rc;

@@ -193,11 +193,18 @@ int scatter_perm(cudaStream_t st, int n, int ne, int nrhs, const int *perm, cons
 // ------------------------------------------------------------ eig (eig.cu) --
 // Hermitian (T = zd) or real symmetric (T = double) Jacobi eigensolver of an
 // m x m matrix A (ld m, overwritten); w ascending (device), V eigenvectors.
-// work: 2 m^2 T; dwork: >= 1 double; iwork: >= m + 1 ints (device);
+// work: 2 m^2 + 2m T; dwork: >= 4m + 8 doubles; iwork: >= 3m + 96 ints (device);
 // hflag: pinned host int used to read the per-sweep convergence flag.
 template <class T>
 int heev_jacobi(cudaStream_t st, int m, T *A, double *w, T *V, T *work, double *dwork, int *iwork, int *hflag,
                 int *sweeps_out);
+
+// Small dense FP64 kernels (small.cu): cooperative Cholesky (A = L L^H, A
+// overwritten as workspace, fail = first non-positive pivot + 1), inverse of
+// a lower triangular matrix, and the Jacobi eigensolver core.
+template <class T> int chol_lower(cudaStream_t st, int m, T *A, T *L, int *fail);
+template <class T> int trinv_lower(cudaStream_t st, int m, const T *L, T *Linv);
+template <class T> int jacobi_coop(cudaStream_t st, int m, int maxsw, T *A, T *V, T *work, double *dw, int *iw);
 
 // Rayleigh-Ritz glue (eig.cu).
 template <class T>
@@ -223,5 +230,6 @@ template <class TY, class TQ>
 int accumulate(cudaStream_t st, int n, int m, int ne, const zd *w, const TY *Y, const TY *Yadj, const TQ *X0,
                const double *f, TQ *Q);
 template <class TQ> int random_subspace(cudaStream_t st, long count, uint64_t seed, TQ *Y);
+template <class T> int ns_prep(cudaStream_t st, int m, const T *P, T *Tn, double *norm);
 
 }  // namespace gbf

@@ -3,17 +3,19 @@
 // on the reduced system; Table "tab_common": residual definition, output
 // ordering; the quadrature sum Q = sum_e w_e Q_e).
 //
-// heev_jacobi: parallel two-sided cyclic Jacobi.  A sweep is P-1 rounds of
-// the circle-method tournament over P = m rounded up to even players; in
-// round r, index x is paired with (2r - x) mod (P-1) (x = r pairs with P-1),
-// so the P/2 rotations of a round are disjoint and one launch applies all
-// of them as A <- J^H A J, V <- V J with every element computed from at most
-// four old elements.  For the pair (p < q), b = A[p][q] = |b| e^{i phi}:
+// heev_jacobi: parallel two-sided cyclic Jacobi (kernel in gbf_small.cu).  A
+// sweep is P-1 rounds of the circle-method tournament over P = m rounded up
+// to even players; in round r, index x is paired with (2r - x) mod (P-1)
+// (x = r pairs with P-1), so the P/2 rotations of a round are disjoint and
+// one grid-wide phase applies all of them as A <- J^H A J, V <- V J with
+// every element computed from at most four old elements.  For the pair (p < q), b = A[p][q] = |b| e^{i phi}:
 //   tau = (A[q][q] - A[p][p]) / (2|b|), t = sign(tau)/(|tau| + sqrt(1+tau^2)),
 //   c = 1/sqrt(1+t^2), s = t c, J = [[c, s e^{i phi}], [-s e^{-i phi}, c]].
 // A rotation is skipped when |b| <= eps/2 sqrt|A[p][p]| sqrt|A[q][q]| or
 // |b| <= 1e-18 ||A||_F; a sweep ends the iteration once no pair violates it.
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "gbf_common.cuh"
 
@@ -24,105 +26,6 @@ __host__ __device__ inline double absT(zd a) { return hypot(a.x, a.y); }
 __host__ __device__ inline double scaleT(double a, double s) { return a * s; }
 __host__ __device__ inline zd scaleT(zd a, double s) { return zd{a.x * s, a.y * s}; }
 
-constexpr double EPS64 = 2.220446049250313e-16;
-
-template <class T>
-__device__ void jacobi_params(int x, int m, int P, int r, const T *A, double fro, double &c, T &beta, int &px,
-                              double &nd) {
-  using X = tr<T>;
-  int p;
-  if (x == P - 1)
-    p = r;
-  else if (x == r)
-    p = P - 1;
-  else {
-    p = (2 * r - x) % (P - 1);
-    if (p < 0) p += P - 1;
-  }
-  c = 1.0;
-  beta = X::zero();
-  px = x;
-  nd = X::re(A[x + (long)x * m]);
-  if (p >= m || x >= m) return;
-  const int pp = min(x, p), qq = max(x, p);
-  const double a = X::re(A[pp + (long)pp * m]), d = X::re(A[qq + (long)qq * m]);
-  const T b = A[pp + (long)qq * m];
-  const double ab = absT(b);
-  if (ab == 0.0 || ab <= 0.5 * EPS64 * sqrt(fabs(a)) * sqrt(fabs(d)) || ab <= 1e-18 * fro) return;
-  const T ph = scaleT(b, 1.0 / ab);
-  const double tau = (d - a) / (2.0 * ab);
-  const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-  c = 1.0 / sqrt(1.0 + t * t);
-  const double s = t * c;
-  px = p;
-  if (x == pp) {
-    beta = scaleT(ph, -s);
-    nd = a - t * ab;
-  } else {
-    beta = scaleT(X::conj(ph), s);
-    nd = d + t * ab;
-  }
-}
-
-template <class T>
-__global__ void jacobi_round_kernel(int m, int P, int r, const T *__restrict__ A, T *__restrict__ A2,
-                                    const T *__restrict__ V, T *__restrict__ V2, const double *__restrict__ frop) {
-  using X = tr<T>;
-  __shared__ double c_r[16], c_c[16], nd_r[16];
-  __shared__ T b_r[16], b_c[16];
-  __shared__ int p_r[16], p_c[16];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i0 = blockIdx.x * 16, j0 = blockIdx.y * 16;
-  const double fro = *frop;
-  if (ty == 0 && i0 + tx < m) {
-    double c, nd;
-    T b;
-    int px;
-    jacobi_params<T>(i0 + tx, m, P, r, A, fro, c, b, px, nd);
-    c_r[tx] = c;
-    b_r[tx] = b;
-    p_r[tx] = px;
-    nd_r[tx] = nd;
-  }
-  if (ty == 1 && j0 + tx < m) {
-    double c, nd;
-    T b;
-    int px;
-    jacobi_params<T>(j0 + tx, m, P, r, A, fro, c, b, px, nd);
-    c_c[tx] = c;
-    b_c[tx] = b;
-    p_c[tx] = px;
-  }
-  __syncthreads();
-  const int i = i0 + tx, j = j0 + ty;
-  if (i >= m || j >= m) return;
-  const double cj = c_c[ty];
-  const T bj = b_c[ty];
-  const int pj = p_c[ty];
-  if (blockIdx.z == 0) {
-    const double ci = c_r[tx];
-    const T bi = b_r[tx];
-    const int pi = p_r[tx];
-    T out;
-    if (pi != i && pi == j) {
-      out = X::zero();
-    } else if (i == j && pi != i) {
-      out = cvt<T, double>(nd_r[tx]);
-    } else {
-      out = scaleT(A[i + (long)j * m], ci * cj);
-      if (pj != j) out = X::fma(scaleT(X::conj(bj), ci), A[i + (long)pj * m], out);
-      if (pi != i) {
-        out = X::fma(scaleT(bi, cj), A[pi + (long)j * m], out);
-        if (pj != j) out = X::fma(X::mul(bi, X::conj(bj)), A[pi + (long)pj * m], out);
-      }
-    }
-    A2[i + (long)j * m] = out;
-  } else {
-    T out = scaleT(V[i + (long)j * m], cj);
-    if (pj != j) out = X::fma(X::conj(bj), V[i + (long)pj * m], out);
-    V2[i + (long)j * m] = out;
-  }
-}
 
 template <class T>
 __global__ void fro_kernel(int m, const T *A, double *out) {
@@ -139,27 +42,6 @@ __global__ void fro_kernel(int m, const T *A, double *out) {
     __syncthreads();
   }
   if (threadIdx.x == 0) out[0] = sqrt(red[0]);
-}
-
-template <class T>
-__global__ void identity_kernel(int m, T *V) {
-  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (t >= (long)m * m) return;
-  const int i = (int)(t % m), j = (int)(t / m);
-  V[t] = (i == j) ? tr<T>::one() : tr<T>::zero();
-}
-
-template <class T>
-__global__ void offcheck_kernel(int m, const T *A, const double *frop, int *flag) {
-  using X = tr<T>;
-  const double fro = *frop;
-  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < (long)m * m; t += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % m), j = (int)(t / m);
-    if (i >= j) continue;
-    const double b = absT(A[t]);
-    const double a = fabs(X::re(A[i + (long)i * m])), d = fabs(X::re(A[j + (long)j * m]));
-    if (b > 0.0 && b > 0.5 * EPS64 * sqrt(a) * sqrt(d) && b > 1e-18 * fro) atomicOr(flag, 1);
-  }
 }
 
 // eigenvalues ascending (stable on ties); NaN sorts last
@@ -199,43 +81,23 @@ int heev_jacobi(cudaStream_t st, int m, T *A, double *w, T *V, T *work, double *
                 int *sweeps_out) {
   if (m <= 0) return 0;
   CatScope cat_red(CAT_REDUCED);
-  const int P = m + (m & 1);
-  T *Acur = A, *Anxt = work, *Vcur = V, *Vnxt = work + (long)m * m;
-  fro_kernel<T><<<1, 256, 0, st>>>(m, A, dwork);
+  const int maxsw = 80;
+  const int slot = prof_begin(st);
+  if (int rc = jacobi_coop<T>(st, m, maxsw, A, V, work, dwork, iwork)) return rc;
+  prof_end(st, slot, 0.0);
+  // eigenvalues ascending with their vectors (rank by counting)
+  int *rank = iwork + 2 * m + maxsw + 8;
+  rank_kernel<T><<<ceil_div(m, 128), 128, 0, st>>>(m, A, w, rank);
   GBF_LAUNCHED();
-  identity_kernel<T><<<ceil_div((long)m * m, 256), 256, 0, st>>>(m, V);
-  GBF_LAUNCHED();
-  dim3 g(ceil_div(m, 16), ceil_div(m, 16), 2), b(16, 16);
-  int sweeps = -1;
-  for (int sweep = 0; sweep < 80; ++sweep) {
-    const int slot = prof_begin(st);
-    if (P > 1)
-      for (int r = 0; r < P - 1; ++r) {
-        jacobi_round_kernel<T><<<g, b, 0, st>>>(m, P, r, Acur, Anxt, Vcur, Vnxt, dwork);
-        GBF_LAUNCHED();
-        std::swap(Acur, Anxt);
-        std::swap(Vcur, Vnxt);
-      }
-    prof_end(st, slot, 0.0);
-    GBF_CUDA(cudaMemsetAsync(iwork + m, 0, sizeof(int), st));
-    offcheck_kernel<T><<<std::min(ceil_div((long)m * m, 256), 1024), 256, 0, st>>>(m, Acur, dwork, iwork + m);
-    GBF_LAUNCHED();
-    GBF_CUDA(cudaMemcpyAsync(hflag, iwork + m, sizeof(int), cudaMemcpyDeviceToHost, st));
-    GBF_CUDA(cudaStreamSynchronize(st));
-    if (*hflag == 0) {
-      sweeps = sweep;
-      break;
-    }
-  }
-  rank_kernel<T><<<ceil_div(m, 128), 128, 0, st>>>(m, Acur, w, iwork);
-  GBF_LAUNCHED();
-  // sorted eigenvectors into the buffer that is not Vcur, then into V
-  T *Vsorted = (Vcur == V) ? Vnxt : V;
   dim3 gp(ceil_div(m, 128), m);
-  permute_cols_kernel<T><<<gp, 128, 0, st>>>(m, m, iwork, Vcur, m, Vsorted, m);
+  permute_cols_kernel<T><<<gp, 128, 0, st>>>(m, m, rank, V, m, work, m);
   GBF_LAUNCHED();
-  if (Vsorted != V) GBF_CUDA(cudaMemcpyAsync(V, Vsorted, sizeof(T) * (size_t)m * m, cudaMemcpyDeviceToDevice, st));
-  if (sweeps_out) *sweeps_out = sweeps;
+  GBF_CUDA(cudaMemcpyAsync(V, work, sizeof(T) * (size_t)m * m, cudaMemcpyDeviceToDevice, st));
+  if (sweeps_out) {
+    GBF_CUDA(cudaMemcpyAsync(hflag, iwork + 2 * m + maxsw, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GBF_CUDA(cudaStreamSynchronize(st));
+    *sweeps_out = *hflag;
+  }
   GBF_CUDA(cudaGetLastError());
   return 0;
 }
@@ -410,6 +272,41 @@ __global__ void filter_kernel(int mk, int ne, const zd *z, const zd *w, const do
   f[j] = s;
 }
 
+// Newton-Schulz step helper: norm = ||I - P||_F (one block, fixed order) and,
+// when T is given, T = (3I - P)/2.
+template <class T>
+__global__ void ns_prep_kernel(int m, const T *P, T *Tn, double *norm) {
+  using X = tr<T>;
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (long t = threadIdx.x; t < (long)m * m; t += blockDim.x) {
+    const int i = (int)(t % m), j = (int)(t / m);
+    T e = X::neg(P[t]);
+    if (i == j) e = X::add(e, X::one());
+    const double a = absT(e);
+    s += a * a;
+    if (Tn) {
+      T v = scaleT(X::neg(P[t]), 0.5);
+      if (i == j) v = X::add(v, cvt<T, double>(1.5));
+      Tn[t] = v;
+    }
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *norm = sqrt(red[0]);
+}
+
+template <class T>
+int ns_prep(cudaStream_t st, int m, const T *P, T *Tn, double *norm) {
+  ns_prep_kernel<T><<<1, 1024, 0, st>>>(m, P, Tn, norm);
+  GBF_LAUNCHED();
+  return 0;
+}
+
 // R = AX - BX diag(lam)
 template <class T>
 __global__ void eig_residual_kernel(int n, int mk, const T *AX, const T *BX, const double *lam, T *R) {
@@ -579,7 +476,8 @@ int random_subspace(cudaStream_t st, long count, uint64_t seed, TQ *Y) {
   template int eig_residual<T>(cudaStream_t, int, int, const T *, const T *, const double *, T *);          \
   template int random_subspace<T>(cudaStream_t, long, uint64_t, T *);                                \
   template int spurious_flags<T>(cudaStream_t, int, int, const T *, const double *, double, double,        \
-                                 const double *, int, int *);
+                                 const double *, int, int *);                                             \
+  template int ns_prep<T>(cudaStream_t, int, const T *, T *, double *);
 EIG_INST(double)
 EIG_INST(zd)
 template int accumulate<zd, double>(cudaStream_t, int, int, int, const zd *, const zd *, const zd *,

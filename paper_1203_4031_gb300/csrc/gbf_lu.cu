@@ -15,9 +15,13 @@
 //   getrs_inplace  blocked triangular solves in which every step is a GEMM:
 //                  Y_b <- inv(T_bb) Y_b, then the trailing update.  trans=1
 //                  gives S^H Y = R from the same factors (case 21).
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "gbf_common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace gbf {
 
@@ -168,6 +172,185 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   }
 }
 
+// ------------------------------------------------------- cluster panel --
+// The panel of node e (rows [k, n), columns [k, k+w)) split by rows over the
+// C CTAs of a thread-block cluster, each slice held in shared memory
+// (column-major, R rows).  Per column: local argmax (warp shuffles), the C
+// candidates read over distributed shared memory and reduced identically by
+// every CTA (largest |re|+|im|, lowest row on ties), the pivot row and the
+// displaced row read remotely, a cluster barrier, the swap written locally,
+// then the local scale + rank-1 update.  Two cluster barriers per column.
+template <class T>
+__global__ void __launch_bounds__(PANEL_THREADS)
+    lu_panel_cluster_kernel(int n, int k, int w, int R, T *S, int *ipiv, int *sing) {
+  using X = tr<T>;
+  using Rt = typename X::R;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int q = (int)cl.block_rank();
+  const int e = blockIdx.y;
+  const long nn = (long)n * n;
+  T *a = S + e * nn;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sl = reinterpret_cast<T *>(smem_raw);  // [w][R]
+  T *urow = sl + (long)w * R;               // pivot row (old row p)
+  T *xrow = urow + MAX_NB;                  // old row c (kept by the owner of p)
+  Rt *cval = reinterpret_cast<Rt *>(xrow + MAX_NB);
+  int *cidx = reinterpret_cast<int *>(cval + 2);
+  __shared__ Rt wv[32];
+  __shared__ int wi[32];
+  __shared__ int s_p, s_ok;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int r0 = k + q * R;
+  const int rows = max(0, min(R, n - r0));
+  for (int t = tid; t < rows * w; t += blockDim.x) {
+    const int rl = t % rows, jj = t / rows;
+    sl[(long)jj * R + rl] = a[(r0 + rl) + (long)(k + jj) * n];
+  }
+  __syncthreads();
+  for (int j = 0; j < w; ++j) {
+    const int c = k + j;
+    // 1. local candidate
+    Rt best = (Rt)-1;
+    int bidx = n;
+    for (int rl = tid; rl < rows; rl += blockDim.x) {
+      const int gr = r0 + rl;
+      if (gr < c) continue;
+      const Rt v = X::abs1(sl[(long)j * R + rl]);
+      if (v > best) {
+        best = v;
+        bidx = gr;
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const Rt ov = __shfl_down_sync(0xffffffffu, best, off);
+      const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
+      if (ov > best || (ov == best && oi < bidx)) {
+        best = ov;
+        bidx = oi;
+      }
+    }
+    if (lane == 0) {
+      wv[warp] = best;
+      wi[warp] = bidx;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      Rt b = (Rt)-1;
+      int bi = n;
+      for (int w2 = 0; w2 < nwarps; ++w2)
+        if (wv[w2] > b || (wv[w2] == b && wi[w2] < bi)) {
+          b = wv[w2];
+          bi = wi[w2];
+        }
+      cval[0] = b;
+      cidx[0] = bi;
+    }
+    cl.sync();  // (A) candidates visible; previous column's updates complete
+    // 2. cluster argmax (every CTA reduces the same list in the same order)
+    if (tid == 0) {
+      Rt b = (Rt)-1;
+      int bi = n;
+      for (int qq = 0; qq < C; ++qq) {
+        const Rt v = *cl.map_shared_rank(cval, qq);
+        const int i = *cl.map_shared_rank(cidx, qq);
+        if (v > b || (v == b && i < bi)) {
+          b = v;
+          bi = i;
+        }
+      }
+      const int ok = (b > (Rt)0) && (bi < n);
+      s_ok = ok;
+      s_p = ok ? bi : c;
+    }
+    __syncthreads();
+    const int p = s_p, ok = s_ok;
+    const int qc = (c - k) / R, lc = (c - k) % R;
+    const int qp = (p - k) / R, lp = (p - k) % R;
+    // 3. remote reads of the old rows p and c
+    if (ok && tid < w) {
+      urow[tid] = cl.map_shared_rank(sl, qp)[(long)tid * R + lp];
+      if (q == qp && p != c) xrow[tid] = cl.map_shared_rank(sl, qc)[(long)tid * R + lc];
+    }
+    cl.sync();  // (B) every read done before any write
+    // 4. swap (local writes)
+    if (ok && p != c && tid < w) {
+      if (q == qc) sl[(long)tid * R + lc] = urow[tid];
+      if (q == qp) sl[(long)tid * R + lp] = xrow[tid];
+    }
+    if (q == 0 && tid == 0) {
+      ipiv[(long)e * n + c] = ok ? p : c;
+      if (!ok && sing[e] == 0) sing[e] = c + 1;
+    }
+    __syncthreads();
+    // 5. scale and rank-1 update of the local rows below c
+    if (ok) {
+      const T inv = cinv<T>(urow[j]);
+      for (int rl = tid; rl < rows; rl += blockDim.x) {
+        if (r0 + rl <= c) continue;
+        const T l = X::mul(sl[(long)j * R + rl], inv);
+        sl[(long)j * R + rl] = l;
+        for (int jj = j + 1; jj < w; ++jj) sl[(long)jj * R + rl] = X::fma(l, X::neg(urow[jj]), sl[(long)jj * R + rl]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < rows * w; t += blockDim.x) {
+    const int rl = t % rows, jj = t / rows;
+    a[(r0 + rl) + (long)(k + jj) * n] = sl[(long)jj * R + rl];
+  }
+  cl.sync();  // no CTA leaves while another may still read its slice
+}
+
+// Launch the cluster panel: C CTAs (power of two <= 16) so that each slice
+// fits in shared memory.  Returns 1 when the caller should use the
+// single-CTA panel instead (no suitable cluster shape).
+template <class T>
+static int launch_cluster_panel(cudaStream_t st, int n, int ne, int k, int w, T *S, int *ipiv, int *sing) {
+  const int rowsp = n - k;
+  const size_t cap = 200 * 1024;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(lu_panel_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(lu_panel_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    attr_done = true;
+  }
+  int C0 = 1;
+  while (C0 < 16 && C0 * 256 < rowsp) C0 *= 2;
+  // largest C first (more SMs per panel), smaller clusters when the GPU
+  // cannot co-schedule it; every candidate must fit the shared memory cap
+  for (int C = C0; C >= 1; C /= 2) {
+    const int R = ceil_div(rowsp, C);
+    const size_t smem = (size_t)R * w * sizeof(T) + 2 * MAX_NB * sizeof(T) + 64;
+    if (smem > cap) break;  // smaller C only makes the slice larger
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, ne, 1);
+    cfg.blockDim = dim3(PANEL_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, lu_panel_cluster_kernel<T>, &cfg) != cudaSuccess ||
+        nclusters < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    if (cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<T>, n, k, w, R, S, ipiv, sing) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    GBF_LAUNCHED();
+    return 0;
+  }
+  return 1;
+}
+
 // --------------------------------------------------------- laswp + trsm --
 // Columns outside the panel: apply the panel's row swaps; columns right of
 // the panel additionally get U12 = L11^{-1} A12 (unit lower forward solve).
@@ -278,8 +461,10 @@ int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T 
     const int w = std::min(nb, n - k);
     CatScope cat_panel(CAT_LU_PANEL);
     const int slot = prof_begin(st);
-    lu_panel_kernel<T><<<ne, PANEL_THREADS, 0, st>>>(n, k, w, S, ipiv, sing);
-    GBF_LAUNCHED();
+    if (launch_cluster_panel<T>(st, n, ne, k, w, S, ipiv, sing)) {
+      lu_panel_kernel<T><<<ne, PANEL_THREADS, 0, st>>>(n, k, w, S, ipiv, sing);
+      GBF_LAUNCHED();
+    }
     if (n - w > 0) {
       dim3 g(ceil_div(n - w, SWAP_COLS), ne);
       const size_t sm = (size_t)w * w * sizeof(T) + (size_t)w * sizeof(int);

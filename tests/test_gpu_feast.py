@@ -59,11 +59,16 @@ def test_laplacian_n500(gbf, prec):
     assert b_orth_error(None, X) < 1e-12
     fo = p.apply_fpm(oracle.feastinit())
     o = oracle.feast(p.A, None, p.emin, p.emax, p.m0, fpm=fo)
-    assert o["M"] == M
-    assert compare_eigs(r["E"][:M], o["E"][:M], p.emin, p.emax) < TOL_E
+    # lambda_167 = 1 + 2e-16 lies on Emax: it may be counted on either side
+    Mc = min(M, o["M"])
+    assert abs(M - o["M"]) <= 1
+    if M != o["M"]:
+        extra = (r["E"][Mc] if M > Mc else o["E"][Mc])
+        assert abs(extra - p.emax) < 1e-12 * p.emax
+    assert compare_eigs(r["E"][:Mc], o["E"][:Mc], p.emin, p.emax) < TOL_E
     if prec == 0:
         assert r["loop"] == o["loop"]
-    assert vector_alignment(None, X, o["X"][:, :M], o["E"][:M]) > 1 - 1e-9
+    assert vector_alignment(None, X[:, :Mc], o["X"][:, :Mc], o["E"][:Mc]) > 1 - 1e-9
 
 
 def small_problem(herm, gen, n, count, seed):
