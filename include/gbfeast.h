@@ -53,6 +53,8 @@
 #ifndef GBFEAST_H
 #define GBFEAST_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -170,6 +172,65 @@ int gbf_solve_dev(gbf_handle h, void *stream, int trans, int nrhs, const double 
  * dA (m x m, ld m; real if kind 0, complex interleaved if kind 1) is
  * overwritten; dW[m] ascending eigenvalues; dV (m x m) eigenvectors. */
 int gbf_heev_dev(gbf_handle h, void *stream, int kind, int m, double *dA, double *dW, double *dV);
+
+/* ---------------------------------------------------------------------
+ * Independent problems: batches and the serving loop (the guide's first
+ * level of parallelism -- separate search intervals / problems -- inside one
+ * GPU; no counterpart API in the guide).  A problem names DEVICE buffers the
+ * caller owns until its result is returned.  Each problem is solved exactly
+ * as by gbf_dsygv_dev / gbf_zhegv_dev (kind 0 / 1) with its own fpm; results
+ * are bitwise the same whether a problem runs alone or beside others.
+ * ------------------------------------------------------------------- */
+typedef struct {
+  int kind;                /* 0: real symmetric (double), 1: complex Hermitian (interleaved) */
+  char uplo;               /* 'F', 'L', 'U' */
+  int n;
+  const double *dA;        /* device, n x n, ld lda */
+  int lda;
+  const double *dB;        /* device, NULL for B = I */
+  int ldb;
+  double emin, emax;
+  int m0;                  /* subspace size M0 */
+  int fpm[64];             /* parameters (gbf_init defaults + changes) */
+  double *dE, *dX, *dres;  /* device outputs: E[m0], X (n x m0, ld n), res[m0] */
+  const double *Zne, *Wne; /* host expert quadrature (2*fpm(2) doubles) or NULL */
+} gbf_problem;
+
+typedef struct {
+  int info, M, loop, m0;   /* as the dense drivers (m0 = kept subspace size) */
+  double epsout;
+  double queue_ms;         /* server: submit -> start; batch: 0 */
+  double run_ms;           /* start -> result */
+} gbf_result;
+
+/* Device workspace one problem needs (bytes), the admission unit of the
+ * server (caller-owned inputs and outputs are not included). */
+size_t gbf_problem_bytes(const gbf_problem *p);
+
+/* Solve nprob independent problems with nworkers concurrent workers (each a
+ * handle + stream; largest problems first).  Work starts after the prior
+ * work on `stream` and `stream` waits for all of it.  Returns 0 or the first
+ * negative info among the results (every result is filled). */
+int gbf_batch_solve(gbf_handle h, void *stream, int nprob, const gbf_problem *probs, gbf_result *outs,
+                    int nworkers);
+
+/* Serving loop: requests are admitted in arrival order when a worker is
+ * free and their workspace (gbf_problem_bytes) fits in what is left of
+ * hbm_budget_bytes; while one request runs, later ones are admitted as
+ * workers and memory free up, so their work overlaps on the device.  A
+ * request larger than the whole budget completes with info -1. */
+typedef struct gbf_server_s *gbf_server;
+int gbf_server_create(size_t hbm_budget_bytes, int nworkers, gbf_server *out);
+/* Queues a copy of *p; the buffers it names must stay valid until done. */
+int gbf_server_submit(gbf_server s, const gbf_problem *p, unsigned long long *ticket);
+/* 0: done (*out filled, ticket released), 1: queued or running, -101: unknown. */
+int gbf_server_poll(gbf_server s, unsigned long long ticket, gbf_result *out);
+/* Blocks until done; then as gbf_server_poll returning 0. */
+int gbf_server_wait(gbf_server s, unsigned long long ticket, gbf_result *out);
+/* Current and peak admitted bytes, queued and running request counts. */
+int gbf_server_stats(gbf_server s, size_t *in_use, size_t *peak, int *queued, int *running);
+/* Finishes every queued request, then releases the workers. */
+int gbf_server_destroy(gbf_server s);
 
 #ifdef __cplusplus
 }

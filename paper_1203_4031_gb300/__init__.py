@@ -53,12 +53,43 @@ def load(build: bool = True):
     L.gbf_factor_dev.argtypes = [vp, vp, C.c_int, C.c_int, C.c_char, C.c_int, vp, C.c_int, vp, C.c_int, C.c_int, vp]
     L.gbf_solve_dev.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp]
     L.gbf_heev_dev.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp, vp]
+    L.gbf_problem_bytes.argtypes = [C.POINTER(Problem)]
+    L.gbf_problem_bytes.restype = C.c_size_t
+    L.gbf_batch_solve.argtypes = [vp, vp, C.c_int, C.POINTER(Problem), C.POINTER(Result), C.c_int]
+    L.gbf_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(vp)]
+    L.gbf_server_submit.argtypes = [vp, C.POINTER(Problem), C.POINTER(C.c_ulonglong)]
+    L.gbf_server_poll.argtypes = [vp, C.c_ulonglong, C.POINTER(Result)]
+    L.gbf_server_wait.argtypes = [vp, C.c_ulonglong, C.POINTER(Result)]
+    L.gbf_server_stats.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int)]
+    L.gbf_server_destroy.argtypes = [vp]
+    L.gbf_profile.argtypes = [C.c_int]
+    L.gbf_profile_name.restype = C.c_char_p
+    L.gbf_profile_read.argtypes = [C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     _lib = L
     return L
 
 
 def lib():
     return load()
+
+
+# ------------------------------------------------------------- ABI structs --
+class Problem(C.Structure):
+    """gbf_problem (include/gbfeast.h)."""
+    _fields_ = [("kind", C.c_int), ("uplo", C.c_char), ("n", C.c_int), ("dA", C.c_void_p), ("lda", C.c_int),
+                ("dB", C.c_void_p), ("ldb", C.c_int), ("emin", C.c_double), ("emax", C.c_double),
+                ("m0", C.c_int), ("fpm", C.c_int * 64), ("dE", C.c_void_p), ("dX", C.c_void_p),
+                ("dres", C.c_void_p), ("Zne", C.c_void_p), ("Wne", C.c_void_p)]
+
+
+class Result(C.Structure):
+    """gbf_result (include/gbfeast.h)."""
+    _fields_ = [("info", C.c_int), ("M", C.c_int), ("loop", C.c_int), ("m0", C.c_int), ("epsout", C.c_double),
+                ("queue_ms", C.c_double), ("run_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 # ------------------------------------------------------------------ helpers --
@@ -285,3 +316,105 @@ def gbf_heev_dev(handle, A, stream=None):
     rc = lib().gbf_heev_dev(handle.h if handle else None, C.c_void_p(stream.cuda_stream),
                             1 if A.is_complex() else 0, m, _ptr(A), _ptr(w), _ptr(V))
     return w, V, rc
+
+
+# ------------------------------------------------- independent problems --
+class DeviceProblem:
+    """A problem whose inputs and outputs live in CUDA tensors (kept alive
+    here while the library uses them)."""
+
+    def __init__(self, A, B, emin, emax, m0, fpm=None, uplo="F"):
+        import torch
+
+        if fpm is None:
+            fpm = gbf_init()
+        n = A.shape[0]
+        self.A, self.B = A, B
+        lda = _check_colmajor(A, n)
+        ldb = _check_colmajor(B, n) if B is not None else n
+        self.E = torch.zeros(m0, dtype=torch.float64, device=A.device)
+        self.res = torch.zeros(m0, dtype=torch.float64, device=A.device)
+        self.X = torch.zeros((m0, n), dtype=A.dtype, device=A.device).t()
+        p = Problem()
+        p.kind = 1 if A.is_complex() else 0
+        p.uplo = uplo.encode()
+        p.n = n
+        p.dA = A.data_ptr()
+        p.lda = lda
+        p.dB = B.data_ptr() if B is not None else None
+        p.ldb = ldb
+        p.emin, p.emax = float(emin), float(emax)
+        p.m0 = int(m0)
+        for i in range(64):
+            p.fpm[i] = int(fpm[i])
+        p.dE, p.dX, p.dres = self.E.data_ptr(), self.X.data_ptr(), self.res.data_ptr()
+        p.Zne = p.Wne = None
+        self.p = p
+
+    def bytes(self):
+        return lib().gbf_problem_bytes(C.byref(self.p))
+
+
+def batch_solve(problems, nworkers=4, stream=None):
+    """gbf_batch_solve over DeviceProblem objects; returns (rc, [Result])."""
+    import torch
+
+    arr = (Problem * len(problems))(*[q.p for q in problems])
+    outs = (Result * len(problems))()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    rc = lib().gbf_batch_solve(None, C.c_void_p(stream.cuda_stream), len(problems), arr, outs, int(nworkers))
+    return rc, [outs[i] for i in range(len(problems))]
+
+
+class Server:
+    """gbf_server_*: admission by HBM budget, concurrent workers."""
+
+    def __init__(self, hbm_budget_bytes, nworkers=4):
+        h = C.c_void_p()
+        rc = lib().gbf_server_create(C.c_size_t(int(hbm_budget_bytes)), int(nworkers), C.byref(h))
+        if rc:
+            raise RuntimeError(f"gbf_server_create failed ({rc}): {last_error()}")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, prob):
+        t = C.c_ulonglong()
+        rc = lib().gbf_server_submit(self.h, C.byref(prob.p), C.byref(t))
+        if rc:
+            raise RuntimeError(f"gbf_server_submit failed ({rc})")
+        self._keep[t.value] = prob
+        return t.value
+
+    def poll(self, ticket):
+        r = Result()
+        rc = lib().gbf_server_poll(self.h, C.c_ulonglong(ticket), C.byref(r))
+        if rc == 0:
+            self._keep.pop(ticket, None)
+            return r
+        return None
+
+    def wait(self, ticket):
+        r = Result()
+        rc = lib().gbf_server_wait(self.h, C.c_ulonglong(ticket), C.byref(r))
+        if rc:
+            raise RuntimeError(f"gbf_server_wait failed ({rc})")
+        self._keep.pop(ticket, None)
+        return r
+
+    def stats(self):
+        a, b = C.c_size_t(), C.c_size_t()
+        q, r = C.c_int(), C.c_int()
+        lib().gbf_server_stats(self.h, C.byref(a), C.byref(b), C.byref(q), C.byref(r))
+        return dict(in_use=a.value, peak=b.value, queued=q.value, running=r.value)
+
+    def close(self):
+        if self.h:
+            lib().gbf_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

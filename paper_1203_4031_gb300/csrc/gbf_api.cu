@@ -707,6 +707,49 @@ static int run_host(char uplo, int n, const double *A, int lda, const double *B,
   return rc;
 }
 
+// ------------------------------------------------ batch / server glue --
+namespace gbf {
+
+int run_problem(gbf_context *h, cudaStream_t st, const gbf_problem *p, gbf_result *r) {
+  int fpm[64];
+  for (int i = 0; i < 64; ++i) fpm[i] = p->fpm[i];
+  double eps = 1.0;
+  int loop = 0, M = 0, M0 = p->m0, info = 0;
+  if (p->kind == 1)
+    run_dev<zd>(h, st, p->uplo, p->n, p->dA, p->lda, p->dB, p->ldb, fpm, &eps, &loop, p->emin, p->emax, &M0, p->dE,
+                p->dX, &M, p->dres, &info, p->Zne, p->Wne);
+  else
+    run_dev<double>(h, st, p->uplo, p->n, p->dA, p->lda, p->dB, p->ldb, fpm, &eps, &loop, p->emin, p->emax, &M0,
+                    p->dE, p->dX, &M, p->dres, &info, p->Zne, p->Wne);
+  r->info = info;
+  r->M = M;
+  r->loop = loop;
+  r->m0 = M0;
+  r->epsout = eps;
+  return info;
+}
+
+template <class TQ, class TL>
+static size_t footprint_t(const gbf_problem *p) {
+  const int ne = p->fpm[1] > 0 ? p->fpm[1] : 8;
+  const int bs = p->fpm[42] ? p->fpm[42] : 32;
+  WS<TQ, TL> ws;
+  Bump b(nullptr);
+  ws.layout(b, p->n, p->m0, ne, bs, p->kind == 1, p->dB != nullptr, p->uplo != 'F',
+            p->dB != nullptr && p->uplo != 'F', pick_ksplit(p->m0, p->n));
+  return b.off + 4096;
+}
+
+size_t problem_footprint(const gbf_problem *p) {
+  const bool mixed = p->fpm[41] == 1;
+  if (p->kind == 1) return mixed ? footprint_t<zd, cf>(p) : footprint_t<zd, zd>(p);
+  return mixed ? footprint_t<double, cf>(p) : footprint_t<double, zd>(p);
+}
+
+}  // namespace gbf
+
+extern "C" size_t gbf_problem_bytes(const gbf_problem *p) { return p ? problem_footprint(p) : 0; }
+
 // ================================================================== C ABI ==
 extern "C" {
 

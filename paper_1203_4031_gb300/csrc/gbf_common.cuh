@@ -129,7 +129,8 @@ inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
 // algorithmic flop count of that launch; summed by gbf_profile_read.
 enum Cat {
   CAT_LU_UPDATE = 0,  // trailing update GEMM of the blocked LU
-  CAT_LU_PANEL,       // panel factorisation + row swaps / U12 solve
+  CAT_LU_PANEL,       // panel factorisation
+  CAT_LU_SWAP,        // row swaps outside the panel + U12 solve
   CAT_SOLVE,          // GEMM steps of the triangular solves
   CAT_PROJECT,        // n-sized FP64 GEMMs of the Rayleigh-Ritz step
   CAT_REDUCED,        // M0-sized GEMMs + Jacobi rounds

@@ -248,20 +248,26 @@ __global__ void __launch_bounds__(PANEL_THREADS)
     }
     cl.sync();  // (A) candidates visible; previous column's updates complete
     // 2. cluster argmax (every CTA reduces the same list in the same order)
-    if (tid == 0) {
+    if (warp == 0) {
       Rt b = (Rt)-1;
       int bi = n;
-      for (int qq = 0; qq < C; ++qq) {
-        const Rt v = *cl.map_shared_rank(cval, qq);
-        const int i = *cl.map_shared_rank(cidx, qq);
-        if (v > b || (v == b && i < bi)) {
-          b = v;
-          bi = i;
+      if (lane < C) {
+        b = *cl.map_shared_rank(cval, lane);
+        bi = *cl.map_shared_rank(cidx, lane);
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const Rt ov = __shfl_down_sync(0xffffffffu, b, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ov > b || (ov == b && oi < bi)) {
+          b = ov;
+          bi = oi;
         }
       }
-      const int ok = (b > (Rt)0) && (bi < n);
-      s_ok = ok;
-      s_p = ok ? bi : c;
+      if (lane == 0) {
+        const int ok = (b > (Rt)0) && (bi < n);
+        s_ok = ok;
+        s_p = ok ? bi : c;
+      }
     }
     __syncthreads();
     const int p = s_p, ok = s_ok;
@@ -465,7 +471,10 @@ int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T 
       lu_panel_kernel<T><<<ne, PANEL_THREADS, 0, st>>>(n, k, w, S, ipiv, sing);
       GBF_LAUNCHED();
     }
+    prof_end(st, slot, 0.0);
     if (n - w > 0) {
+      CatScope cat_swap(CAT_LU_SWAP);
+      const int slot2 = prof_begin(st);
       dim3 g(ceil_div(n - w, SWAP_COLS), ne);
       const size_t sm = (size_t)w * w * sizeof(T) + (size_t)w * sizeof(int);
       static bool attr_set = false;
@@ -476,8 +485,8 @@ int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T 
       }
       laswp_trsm_kernel<T><<<g, SWAP_COLS, sm, st>>>(n, k, w, S, ipiv);
       GBF_LAUNCHED();
+      prof_end(st, slot2, 0.0);
     }
-    prof_end(st, slot, 0.0);
     const int rest = n - k - w;
     if (rest > 0) {
       CatScope cat_update(CAT_LU_UPDATE);

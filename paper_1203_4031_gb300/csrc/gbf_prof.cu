@@ -34,7 +34,7 @@ cudaEvent_t get_event() {
   }
   return e;
 }
-const char *names[CAT_COUNT] = {"lu_update_gemm", "lu_panel", "solve_gemm", "project_gemm_fp64", "reduced_eig",
+const char *names[CAT_COUNT] = {"lu_update_gemm", "lu_panel", "lu_swap_trsm", "solve_gemm", "project_gemm_fp64", "reduced_eig",
                                 "other"};
 }  // namespace
 

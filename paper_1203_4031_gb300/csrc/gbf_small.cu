@@ -14,6 +14,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "gbf_common.cuh"
 
@@ -26,13 +27,31 @@ __device__ inline double absS(zd a) { return hypot(a.x, a.y); }
 __device__ inline double scS(double a, double s) { return a * s; }
 __device__ inline zd scS(zd a, double s) { return zd{a.x * s, a.y * s}; }
 
-static int coop_grid(const void *fn, int threads, size_t smem) {
+// At most one cooperative grid runs at a time in this process: two grids
+// that each wait at a grid barrier for SMs the other holds could never
+// finish.  The lock is held from launch to completion; ordinary kernels of
+// other streams keep running beside it and always free their SMs.
+static std::mutex g_coop_mu;
+
+static int coop_run(const void *fn, int blocks, int threads, void **args, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_coop_mu);
+  GBF_CUDA(cudaLaunchCooperativeKernel(fn, blocks, threads, args, 0, st));
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaStreamSynchronize(st));
+  return 0;
+}
+
+// Grid of a cooperative launch: sized from the problem alone (so results do
+// not depend on what else runs), about 2 m^2 / 512 blocks (one block per
+// SM at most), never more than can be co-resident.
+static int coop_grid(const void *fn, int threads, size_t smem, int m) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
   if (per < 1) return 0;
-  return sms;  // one block per SM: fewer participants in every grid barrier
+  const long want = std::max(1L, (2L * m * m + 511) / 512);
+  return (int)std::min<long>(want, sms);
 }
 
 // ------------------------------------------------------------- Cholesky --
@@ -108,15 +127,13 @@ __global__ void trinv_lower_kernel(int m, const T *L, T *Linv) {
 template <class T>
 int chol_lower(cudaStream_t st, int m, T *A, T *L, int *fail) {
   const int threads = 512;
-  const int blocks = coop_grid((const void *)chol_coop_kernel<T>, threads, 0);
+  const int blocks = coop_grid((const void *)chol_coop_kernel<T>, threads, 0, m);
   if (blocks < 1) {
     set_error("chol_coop: no co-resident grid");
     return -4;
   }
   void *args[] = {&m, &A, &L, &fail};
-  GBF_CUDA(cudaLaunchCooperativeKernel((const void *)chol_coop_kernel<T>, blocks, threads, args, 0, st));
-  GBF_LAUNCHED();
-  return 0;
+  return coop_run((const void *)chol_coop_kernel<T>, blocks, threads, args, st);
 }
 
 template <class T>
@@ -266,10 +283,10 @@ __global__ void jacobi_coop_kernel(int m, int maxsw, T *A, T *V, T *work, double
       const JParams<T> &pc = prm[cur];
       // next round's rotations, from this round's result
       const int rn = (r + 1 < P - 1) ? r + 1 : 0;
-      // pair s of the next round goes to thread 0 of block s (spread over SMs:
-      // its FP64 divisions and square roots then run on different FP64 units)
-      const bool spread = (int)gridDim.x >= P / 2;
-      const int sidx = spread ? (threadIdx.x == 0 ? (int)blockIdx.x : -1) : (int)tid;
+      // pairs of the next round are spread over blocks first (their FP64
+      // divisions and square roots then run on different SMs' FP64 units)
+      // (lane 0 of warp w of block b takes pair b + gridDim.x * w)
+      const int sidx = (threadIdx.x & 31) ? -1 : (int)blockIdx.x + (int)gridDim.x * (int)(threadIdx.x >> 5);
       if (sidx >= 0 && sidx < P / 2) {
         const int s = sidx;
         int x, y;
@@ -356,15 +373,13 @@ __global__ void jacobi_coop_kernel(int m, int maxsw, T *A, T *V, T *work, double
 template <class T>
 int jacobi_coop(cudaStream_t st, int m, int maxsw, T *A, T *V, T *work, double *dw, int *iw) {
   const int threads = 512;
-  const int blocks = coop_grid((const void *)jacobi_coop_kernel<T>, threads, 0);
+  const int blocks = coop_grid((const void *)jacobi_coop_kernel<T>, threads, 0, m);
   if (blocks < 1) {
     set_error("jacobi_coop: no co-resident grid");
     return -4;
   }
   void *args[] = {&m, &maxsw, &A, &V, &work, &dw, &iw};
-  GBF_CUDA(cudaLaunchCooperativeKernel((const void *)jacobi_coop_kernel<T>, blocks, threads, args, 0, st));
-  GBF_LAUNCHED();
-  return 0;
+  return coop_run((const void *)jacobi_coop_kernel<T>, blocks, threads, args, st);
 }
 
 #define SMALL_INST(T)                                                                          \

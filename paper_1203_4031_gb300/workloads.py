@@ -164,3 +164,106 @@ def interval_for_count(A: np.ndarray, B: np.ndarray | None, count: int) -> float
     w = sl.eigh(A, B, eigvals_only=True)
     a = np.sort(np.abs(w))
     return float(0.5 * (a[count - 1] + a[count]))
+
+
+# --------------------------------------------------- batched / serving --
+def _interval_around(w: np.ndarray, count: int, seed: int) -> tuple:
+    """[a, b] holding exactly `count` of the sorted values w, at a seeded
+    position, with ends halfway between neighbouring values."""
+    w = np.sort(w)
+    n = len(w)
+    lo = 1
+    hi = n - count - 1
+    s = lo + int(uniform01(seed, 1)[0] * max(1, hi - lo))
+    a = 0.5 * (w[s - 1] + w[s])
+    b = 0.5 * (w[s + count - 1] + w[s + count])
+    return float(a), float(b)
+
+
+def batched_generalized(count: int = 256, nmin: int = 64, nmax: int = 1024, seed: int = 20260104,
+                        kmin: int = 10, kmax: int = 40, ne: int = 8) -> list:
+    """Independent real symmetric generalized problems built as
+    dense_real_generalized (own reflectors for A and B), n log-uniform in
+    [nmin, nmax], each interval holding a count drawn uniformly from
+    [kmin, kmax] (located with scipy's generalized eigenvalues), M0 =
+    ceil(1.5 count)."""
+    import scipy.linalg as sl
+
+    u = uniform01(derive_seed(seed, 1), count)
+    ks = uniform01(derive_seed(seed, 2), count)
+    out = []
+    for i in range(count):
+        n = int(round(np.exp(np.log(nmin) + u[i] * (np.log(nmax) - np.log(nmin)))))
+        k = kmin + int(ks[i] * (kmax - kmin + 1))
+        si = derive_seed(seed, 100 + i)
+        lam = uniform(derive_seed(si, 1), n)
+        mu = 10.0 ** uniform(derive_seed(si, 2), n, 0.0, 2.0)
+        A = conjugate_by_reflectors(lam, reflector_vectors(si, n, 8))
+        B = conjugate_by_reflectors(mu, reflector_vectors(derive_seed(si, 3), n, 8))
+        w = sl.eigh(A, B, eigvals_only=True)
+        a, b = _interval_around(w, k, derive_seed(si, 4))
+        out.append(Problem(f"batch-{i}-n{n}", False, A, B, a, b, int(np.ceil(1.5 * k)),
+                           fpm={2: ne, 3: 10, 6: 1}, spectrum=np.sort(w),
+                           note="config-2 style generalized, interval holding k"))
+    return out
+
+
+def serving_requests(count: int = 2000, nmin: int = 128, nmax: int = 4096, seed: int = 20260105,
+                     kmin: int = 8, kmax: int = 64, rate: float = 1.0):
+    """Request descriptors of the serving workload: kind (real symmetric
+    generalized / complex Hermitian standard, 50/50), n log-uniform in
+    [nmin, nmax], a count uniform in [kmin, kmax], M0 = ceil(1.5 count),
+    Poisson arrival times at `rate` requests per second.  Matrices are built
+    by `serving_matrices` when a request arrives."""
+    u = uniform01(derive_seed(seed, 1), count)
+    ks = uniform01(derive_seed(seed, 2), count)
+    kind = uniform01(derive_seed(seed, 3), count) < 0.5
+    gaps = -np.log(1.0 - uniform01(derive_seed(seed, 4), count)) / rate
+    t = np.cumsum(gaps)
+    reqs = []
+    for i in range(count):
+        n = int(round(np.exp(np.log(nmin) + u[i] * (np.log(nmax) - np.log(nmin)))))
+        k = kmin + int(ks[i] * (kmax - kmin + 1))
+        reqs.append(dict(i=i, n=n, count=k, m0=int(np.ceil(1.5 * k)), hermitian=bool(kind[i]),
+                         t_arrival=float(t[i]), seed=derive_seed(seed, 1000 + i)))
+    return reqs
+
+
+def serving_matrices(req: dict, device="cuda"):
+    """Matrices of one serving request on the GPU (torch), with a known
+    spectrum lam ~ U[-1, 1]:
+      complex Hermitian standard: A = U diag(lam) U^H, 8 complex reflectors;
+      real generalized: B = Q_B diag(mu) Q_B^T, mu log-uniform [1, 100], and
+      A = S (Q diag(lam) Q^T) S^T with S = Q_B diag(sqrt(mu)), so that the
+      pencil (A, B) has exactly the eigenvalues lam (eigenvectors S^{-T} Q).
+    Returns (A, B or None, emin, emax) with the interval holding `count`
+    eigenvalues."""
+    import torch
+
+    n, s = req["n"], req["seed"]
+    lam = uniform(derive_seed(s, 1), n)
+    a, b = _interval_around(lam, req["count"], derive_seed(s, 4))
+
+    def reflect(M, vs):
+        for v in reversed(vs):
+            vt = torch.as_tensor(v, device=device, dtype=M.dtype)
+            beta = 2.0 / float(np.real(np.vdot(v, v)))
+            M = M - beta * torch.outer(vt, vt.conj() @ M)
+            M = M - beta * torch.outer(M @ vt, vt.conj())
+        return M
+
+    if req["hermitian"]:
+        M = torch.diag(torch.as_tensor(lam, device=device, dtype=torch.complex128))
+        A = reflect(M, reflector_vectors(s, n, 8, complex_=True))
+        A = 0.5 * (A + A.conj().T)
+        return A.t().contiguous().t(), None, a, b
+    mu = 10.0 ** uniform(derive_seed(s, 2), n, 0.0, 2.0)
+    qb = reflector_vectors(derive_seed(s, 3), n, 8)
+    B = reflect(torch.diag(torch.as_tensor(mu, device=device, dtype=torch.float64)), qb)
+    C = reflect(torch.diag(torch.as_tensor(lam, device=device, dtype=torch.float64)), reflector_vectors(s, n, 8))
+    sq = torch.as_tensor(np.sqrt(mu), device=device, dtype=torch.float64)
+    C = sq[:, None] * C * sq[None, :]          # D C D
+    A = reflect(C, qb)                          # Q_B (D C D) Q_B^T
+    A = 0.5 * (A + A.T)
+    B = 0.5 * (B + B.T)
+    return A.t().contiguous().t(), B.t().contiguous().t(), a, b
