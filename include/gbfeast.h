@@ -173,6 +173,16 @@ int gbf_solve_dev(gbf_handle h, void *stream, int trans, int nrhs, const double 
  * overwritten; dW[m] ascending eigenvalues; dV (m x m) eigenvectors. */
 int gbf_heev_dev(gbf_handle h, void *stream, int kind, int m, double *dA, double *dW, double *dV);
 
+/* Tensor-core building block (tcgen05 + TMA + TMEM, sm_103a): dC (FP32,
+ * column-major, ld ldc, batch stride sc) = dA dB^T per batch, dA
+ * [batch][M][K] and dB [batch][N][K] bf16 row-major (K contiguous, K a
+ * multiple of 8, 16-byte aligned bases).  dErr: one device int (scratch).
+ * Returns 0, -4 (CUDA error), -5 (an in-kernel bounded wait timed out).
+ * The guide has no counterpart: this is the contraction engine the sliced
+ * FP64 and split-FP32 products are built on. */
+int gbf_tc_gemm_bf16(void *stream, int M, int N, int K, int batch, const void *dA, const void *dB, float *dC,
+                     long ldc, long sc, int *dErr);
+
 /* ---------------------------------------------------------------------
  * Independent problems: batches and the serving loop (the guide's first
  * level of parallelism -- separate search intervals / problems -- inside one

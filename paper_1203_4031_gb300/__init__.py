@@ -63,6 +63,7 @@ def load(build: bool = True):
     L.gbf_server_stats.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.POINTER(C.c_int),
                                    C.POINTER(C.c_int)]
     L.gbf_server_destroy.argtypes = [vp]
+    L.gbf_tc_gemm_bf16.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_long, C.c_long, vp]
     L.gbf_profile.argtypes = [C.c_int]
     L.gbf_profile_name.restype = C.c_char_p
     L.gbf_profile_read.argtypes = [C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -418,3 +419,23 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def tc_gemm_bf16(A, B, stream=None):
+    """gbf_tc_gemm_bf16: A (batch, M, K), B (batch, N, K) bf16 CUDA tensors
+    (contiguous) -> C (batch, N, M) float32, i.e. C[b].t() = A[b] @ B[b]^T."""
+    import torch
+
+    bt, M, K = A.shape
+    N = B.shape[1]
+    C = torch.empty((bt, N, M), dtype=torch.float32, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device)
+    rc = lib().gbf_tc_gemm_bf16(_stream_ptr(stream), M, N, K, bt,
+                                _ptr(A), _ptr(B), _ptr(C), M, M * N, _ptr(err))
+    return C, rc
+
+
+def _stream_ptr(stream):
+    return C.c_void_p(stream.cuda_stream)
