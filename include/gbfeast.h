@@ -183,6 +183,22 @@ int gbf_heev_dev(gbf_handle h, void *stream, int kind, int m, double *dA, double
 int gbf_tc_gemm_bf16(void *stream, int M, int N, int K, int batch, const void *dA, const void *dB, float *dC,
                      long ldc, long sc, int *dErr);
 
+/* Sliced complex GEMM on the tensor cores (verification entry of the
+ * engine behind the FP64 factorisation and solves): dC = alpha op(dA)
+ * op(dB) + beta dC for interleaved complex data (prec 0: FP64, 1: FP32),
+ * op in 'N','T','C', op(A) m x k, op(B) k x n with k <= 32, alpha = +1 or
+ * -1, beta 0 or 1, S = 7 (FP64-class) or 3 (FP32-class) digits, batches
+ * strided by sa, sb, sc elements.  Every operand row of op(A) / column of
+ * op(B) is scaled by a power of two and split into S base-2^7 integer
+ * digits held exactly in bf16; digit products are summed exactly in FP32
+ * tensor memory and recombined in FP64.  dWork: gbf_zgemm_sliced_work
+ * bytes; dErr: one device int.  Returns 0, -4 (CUDA error / bad shape),
+ * -5 (an in-kernel bounded wait timed out).  No counterpart in the guide. */
+size_t gbf_zgemm_sliced_work(int m, int n, int batch, int S);
+int gbf_zgemm_sliced(void *stream, int prec, int S, char opa, char opb, int m, int n, int k, double alpha,
+                     const void *dA, long lda, long sa, const void *dB, long ldb, long sb, int beta, void *dC,
+                     long ldc, long sc, int batch, void *dWork, size_t work_bytes, int *dErr);
+
 /* ---------------------------------------------------------------------
  * Independent problems: batches and the serving loop (the guide's first
  * level of parallelism -- separate search intervals / problems -- inside one

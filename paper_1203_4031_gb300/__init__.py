@@ -64,6 +64,11 @@ def load(build: bool = True):
                                    C.POINTER(C.c_int)]
     L.gbf_server_destroy.argtypes = [vp]
     L.gbf_tc_gemm_bf16.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_long, C.c_long, vp]
+    L.gbf_zgemm_sliced_work.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
+    L.gbf_zgemm_sliced_work.restype = C.c_size_t
+    L.gbf_zgemm_sliced.argtypes = [vp, C.c_int, C.c_int, C.c_char, C.c_char, C.c_int, C.c_int, C.c_int, C.c_double,
+                                   vp, C.c_long, C.c_long, vp, C.c_long, C.c_long, C.c_int, vp, C.c_long, C.c_long,
+                                   C.c_int, vp, C.c_size_t, vp]
     L.gbf_profile.argtypes = [C.c_int]
     L.gbf_profile_name.restype = C.c_char_p
     L.gbf_profile_read.argtypes = [C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -439,3 +444,26 @@ def tc_gemm_bf16(A, B, stream=None):
 
 def _stream_ptr(stream):
     return C.c_void_p(stream.cuda_stream)
+
+
+def zgemm_sliced(opa, opb, A, B, C_, alpha=1.0, beta=0, S=7, stream=None):
+    """gbf_zgemm_sliced on column-major complex CUDA tensors of shape
+    (batch, rows, cols) stored as (batch, cols, rows) contiguous: A, B, C_ are
+    lists of per-batch column-major 2-D tensors packed in 3-D tensors whose
+    [b].t() is the matrix.  C_ is updated in place; returns the code."""
+    import torch
+
+    bt = A.shape[0]
+    am, ak = A.shape[2], A.shape[1]       # stored matrix (rows, cols) = (shape[2], shape[1])
+    bk, bn = B.shape[2], B.shape[1]
+    m = am if opa == "N" else ak
+    k = ak if opa == "N" else am
+    n = bn if opb == "N" else bk
+    prec = 0 if A.dtype == torch.complex128 else 1
+    work = torch.empty(lib().gbf_zgemm_sliced_work(m, n, bt, S), dtype=torch.uint8, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device)
+    return lib().gbf_zgemm_sliced(_stream_ptr(stream), prec, S, opa.encode(), opb.encode(), m, n, k, float(alpha),
+                                  _ptr(A), am, am * ak, _ptr(B), bk, bk * bn, int(beta), _ptr(C_), C_.shape[2],
+                                  C_.shape[1] * C_.shape[2], bt, _ptr(work), work.numel(), _ptr(err))

@@ -21,3 +21,41 @@ def test_tc_gemm_bf16(gbf, M, N, K, batch):
     err = (C.double() - ref).abs().max().item()
     scale = torch.einsum("bmk,bnk->bnm", A.double().abs(), B.double().abs()).max().item()
     assert err <= 2 * K * 6e-8 * scale, (err, scale)
+
+
+def colmajor_batch(torch, mats):
+    """(batch, cols, rows) contiguous storage of column-major matrices."""
+    return torch.stack([x.t().contiguous() for x in mats])
+
+
+@pytest.mark.parametrize("S,prec", [(7, 0), (3, 1), (3, 0)])
+@pytest.mark.parametrize("m,n,k,batch", [(1, 1, 1, 1), (37, 33, 7, 2), (200, 100, 32, 1), (1000, 300, 32, 3),
+                                         (65, 129, 17, 2)])
+@pytest.mark.parametrize("opa,opb", [("N", "N"), ("C", "N"), ("T", "C")])
+@pytest.mark.parametrize("alpha,beta", [(-1.0, 1), (1.0, 0)])
+def test_zgemm_sliced(gbf, S, prec, m, n, k, batch, opa, opb, alpha, beta):
+    import torch
+
+    dt = torch.complex128 if prec == 0 else torch.complex64
+    g = torch.Generator(device="cuda").manual_seed(m + 3 * n + 7 * k)
+    def rnd(r, c):
+        return torch.complex(torch.randn((r, c), device="cuda", dtype=torch.float64, generator=g),
+                             torch.randn((r, c), device="cuda", dtype=torch.float64, generator=g))
+    As = [rnd(m, k) if opa == "N" else rnd(k, m) for _ in range(batch)]
+    Bs = [rnd(k, n) if opb == "N" else rnd(n, k) for _ in range(batch)]
+    Cs = [rnd(m, n) for _ in range(batch)]
+    A = colmajor_batch(torch, As).to(dt)
+    B = colmajor_batch(torch, Bs).to(dt)
+    Cd = colmajor_batch(torch, Cs).to(dt)
+    op = {"N": lambda x: x, "T": lambda x: x.t(), "C": lambda x: x.conj().t()}
+    ref = [alpha * (op[opa](a.to(dt).to(torch.complex128)) @ op[opb](b.to(dt).to(torch.complex128)))
+           + (beta * c.to(dt).to(torch.complex128)) for a, b, c in zip(As, Bs, Cs)]
+    rc = gbf.zgemm_sliced(opa, opb, A, B, Cd, alpha=alpha, beta=beta, S=S)
+    torch.cuda.synchronize()
+    assert rc == 0, gbf.last_error()
+    got = [Cd[i].t().to(torch.complex128) for i in range(batch)]
+    tol = (4e-14 if S == 7 else 2e-6) * k
+    if prec == 1:
+        tol = max(tol, 1e-6 * k)   # FP32 output rounding
+    for gt, rf in zip(got, ref):
+        assert (gt - rf).abs().max().item() <= tol * (1 + rf.abs().max().item()), (gt - rf).abs().max().item()
