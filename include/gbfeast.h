@@ -24,6 +24,10 @@
  *                    R = A X - B X Lambda (see gbf_dsygv), so the subspace
  *                    reaches FP64 accuracy.
  *        fpm(43) LU panel width / diagonal block size (0 = default 32).
+ *        fpm(44) engine of the complex FP64 GEMMs of the factorisation
+ *                and the solves: 0 = tensor cores (default; exact bf16
+ *                digit products, 7 digits, see gbf_zgemm_sliced), 1 =
+ *                CUDA-core FMA.  FP32 factors (fpm(42)=1) use CUDA cores.
  *  - Outputs follow Table "tab_common": E[M0] eigenvalues (first M inside the
  *    interval, ascending, then the remaining Ritz values ascending), X (N x
  *    M0, ld N) B-orthonormal Ritz vectors in the same order, res[M0] relative

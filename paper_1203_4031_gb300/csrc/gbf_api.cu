@@ -133,6 +133,7 @@ static int check_fpm(const int *fpm) {
   if (fpm[17] <= 0) return 118;
   if (fpm[41] != 0 && fpm[41] != 1) return 142;
   if (fpm[42] != 0 && (fpm[42] < 8 || fpm[42] > 64 || fpm[42] % 8)) return 143;
+  if (fpm[43] != 0 && fpm[43] != 1) return 144;
   return 0;
 }
 
@@ -248,9 +249,12 @@ template <class TQ, class TL> struct WS {
   TQ *Aq, *Bq, *As, *Bs, *V, *Tm, *Ctmp, *Cm, *Cs, *U, *W, *jwork, *kwork;
   double *d, *lam, *s, *resu, *Es, *Rs, *f, *dwork, *stats;
   zd *z, *w, *D, *Dc;
+  void *tcw;
+  size_t tcw_bytes;
+  int *tc_err;
 
   void layout(Bump &b, int n, int m0, int ne, int bs, bool herm, bool hasB, bool needAf, bool needBf,
-              int ksplit) {
+              int ksplit, int tcS) {
     const size_t nn = (size_t)n * n, nm = (size_t)n * m0, mm = (size_t)m0 * m0;
     const int nblk = ceil_div(n, bs);
     S = b.take<TL>((size_t)ne * nn);
@@ -306,6 +310,9 @@ template <class TQ, class TL> struct WS {
     w = b.take<zd>(ne);
     D = b.take<zd>((size_t)ne * m0);
     Dc = b.take<zd>((size_t)ne * m0);
+    tcw_bytes = tcS ? std::max(zgemm_sliced_work(n, n, ne, tcS), zgemm_sliced_work(n, m0, ne, tcS)) : 0;
+    tcw = tcS ? (void *)b.take<char>(tcw_bytes) : nullptr;
+    tc_err = b.take<int>(4);
   }
 };
 
@@ -356,20 +363,30 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
   const bool needAf = q.uplo != 'F';
   const bool needBf = hasB && q.uplo != 'F';
   const int ksplit = pick_ksplit(m0, n);
+  // complex GEMMs of the FP64 factorisation and solves: tensor cores
+  // (sliced, 7 digits) unless fpm(44) = 1; FP32 factors use CUDA cores
+  const int tcS = (fpm[43] == 0 && bs <= 32 && sizeof(TL) == sizeof(zd)) ? 7 : 0;
   WS<TQ, TL> ws;
   {
     Bump sizing(nullptr);
-    ws.layout(sizing, n, m0, ne, bs, herm, hasB, needAf, needBf, ksplit);
+    ws.layout(sizing, n, m0, ne, bs, herm, hasB, needAf, needBf, ksplit, tcS);
     if (ensure_arena(h, sizing.off + 4096)) return out.info = -1;
     Bump real(h->arena);
-    ws.layout(real, n, m0, ne, bs, herm, hasB, needAf, needBf, ksplit);
+    ws.layout(real, n, m0, ne, bs, herm, hasB, needAf, needBf, ksplit, tcS);
   }
+  TcCtx tcx;
+  tcx.work = ws.tcw;
+  tcx.bytes = ws.tcw_bytes;
+  tcx.gerr = ws.tc_err;
+  tcx.S = tcS;
+  TcScope tc_scope(tcS ? &tcx : nullptr);
   if (ensure_hbuf(h, (size_t)std::max(m0, ne) + 64)) return out.info = -1;
   h->f_prec = -1;
 
   GBF_CUDA(cudaMemcpyAsync(ws.z, zh.data(), sizeof(zd) * ne, cudaMemcpyHostToDevice, st));
   GBF_CUDA(cudaMemcpyAsync(ws.w, wh.data(), sizeof(zd) * ne, cudaMemcpyHostToDevice, st));
   GBF_CUDA(cudaMemsetAsync(ws.sing, 0, sizeof(int) * ne, st));
+  GBF_CUDA(cudaMemsetAsync(ws.tc_err, 0, sizeof(int) * 4, st));
   GBF_CUDA(cudaMemsetAsync(ws.flag, 0, sizeof(int) * 4, st));
 
   const TQ *Af = (const TQ *)q.A;
@@ -396,7 +413,12 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
   {
     int *hs = (int *)h->hbuf;
     GBF_CUDA(cudaMemcpyAsync(hs, ws.sing, sizeof(int) * ne, cudaMemcpyDeviceToHost, st));
+    GBF_CUDA(cudaMemcpyAsync(hs + ne, ws.tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     GBF_CUDA(cudaStreamSynchronize(st));
+    if (hs[ne]) {
+      set_error("tensor-core GEMM: bounded wait timed out (code %d)", hs[ne]);
+      return out.info = -4;
+    }
     for (int e = 0; e < ne; ++e)
       if (hs[e]) {
         set_error("zero pivot in column %d of the shifted system of node %d", hs[e], e);
@@ -558,7 +580,12 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
     if (hasB) CK(permute_cols<TQ>(st, n, mk, ws.pos, ws.BXu, ws.BXc));
     double *hs = h->hbuf;
     GBF_CUDA(cudaMemcpyAsync(hs, ws.stats, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+    GBF_CUDA(cudaMemcpyAsync(h->hflag + 2, ws.tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     GBF_CUDA(cudaStreamSynchronize(st));
+    if (h->hflag[2]) {
+      set_error("tensor-core GEMM: bounded wait timed out (code %d)", h->hflag[2]);
+      return out.info = -4;
+    }
     const int nin = (int)hs[0];
     const double trace = hs[1], maxres = hs[2];
     const bool finite = hs[3] != 0.0;
@@ -735,8 +762,9 @@ static size_t footprint_t(const gbf_problem *p) {
   const int bs = p->fpm[42] ? p->fpm[42] : 32;
   WS<TQ, TL> ws;
   Bump b(nullptr);
+  const int tcS = (p->fpm[43] == 0 && bs <= 32 && sizeof(TL) == sizeof(zd)) ? 7 : 0;
   ws.layout(b, p->n, p->m0, ne, bs, p->kind == 1, p->dB != nullptr, p->uplo != 'F',
-            p->dB != nullptr && p->uplo != 'F', pick_ksplit(p->m0, p->n));
+            p->dB != nullptr && p->uplo != 'F', pick_ksplit(p->m0, p->n), tcS);
   return b.off + 4096;
 }
 
@@ -895,6 +923,10 @@ static int factor_impl(gbf_handle h, cudaStream_t st, int kind, char uplo, int n
   sz.take<int>((size_t)ne * n);
   sz.take<int>(ne);
   sz.take<zd>(ne);
+  const int tcS = sizeof(TL) == sizeof(zd) ? 7 : 0;
+  const size_t tcb = tcS ? zgemm_sliced_work(n, n, ne, tcS) : 0;
+  sz.take<char>(tcb);
+  sz.take<int>(4);
   if (ensure_arena(h, sz.off + 4096)) return -1;
   if (ensure_hbuf(h, (size_t)ne + 8)) return -1;
   Bump b(h->arena);
@@ -905,6 +937,13 @@ static int factor_impl(gbf_handle h, cudaStream_t st, int kind, char uplo, int n
   int *perm = b.take<int>((size_t)ne * n);
   int *sing = b.take<int>(ne);
   zd *z = b.take<zd>(ne);
+  TcCtx tcx;
+  tcx.work = b.take<char>(tcb);
+  tcx.bytes = tcb;
+  tcx.gerr = b.take<int>(4);
+  tcx.S = tcS;
+  TcScope tc_scope(&tcx);
+  GBF_CUDA(cudaMemsetAsync(tcx.gerr, 0, sizeof(int), st));
   std::vector<zd> zh(ne);
   for (int e = 0; e < ne; ++e) zh[e] = zd{Zne[2 * e], Zne[2 * e + 1]};
   GBF_CUDA(cudaMemcpyAsync(z, zh.data(), sizeof(zd) * ne, cudaMemcpyHostToDevice, st));
@@ -914,7 +953,13 @@ static int factor_impl(gbf_handle h, cudaStream_t st, int kind, char uplo, int n
   if (rc) return rc;
   int *hs = (int *)h->hbuf;
   GBF_CUDA(cudaMemcpyAsync(hs, sing, sizeof(int) * ne, cudaMemcpyDeviceToHost, st));
+  GBF_CUDA(cudaMemcpyAsync(hs + ne, tcx.gerr, sizeof(int), cudaMemcpyDeviceToHost, st));
   GBF_CUDA(cudaStreamSynchronize(st));
+  if (hs[ne]) {
+    h->f_prec = -1;
+    set_error("tensor-core GEMM: bounded wait timed out (code %d)", hs[ne]);
+    return -4;
+  }
   h->f_n = n;
   h->f_ne = ne;
   h->f_bs = bs;
@@ -942,9 +987,14 @@ static int solve_impl(gbf_handle h, cudaStream_t st, int trans, int nrhs, const 
   int *perm = b.take<int>((size_t)ne * n);
   b.take<int>(ne);
   b.take<zd>(ne);
+  const int tcS = sizeof(TL) == sizeof(zd) ? 7 : 0;
+  b.take<char>(tcS ? zgemm_sliced_work(n, n, ne, tcS) : 0);
+  int *tc_err = b.take<int>(4);
   const size_t base = b.off;
   TL *Y = b.take<TL>(ny);
   TL *Y2 = b.take<TL>(ny);
+  const size_t tcb = tcS ? zgemm_sliced_work(n, nrhs, ne, tcS) : 0;
+  void *tcw = b.take<char>(tcb);
   if (b.off + 4096 > h->cap) {
     // grow while keeping the factors
     char *na = nullptr;
@@ -960,6 +1010,12 @@ static int solve_impl(gbf_handle h, cudaStream_t st, int trans, int nrhs, const 
     h->cap = need;
     return solve_impl<TL>(h, st, trans, nrhs, dRHS, dY);
   }
+  TcCtx tcx;
+  tcx.work = tcw;
+  tcx.bytes = tcb;
+  tcx.gerr = tc_err;
+  tcx.S = tcS;
+  TcScope tc_scope(&tcx);
   int rc;
   if (!trans) {
     rc = gather_rhs<TL>(st, n, ne, nrhs, perm, 1, dRHS, n, nullptr, Y);
@@ -972,7 +1028,12 @@ static int solve_impl(gbf_handle h, cudaStream_t st, int trans, int nrhs, const 
   if (rc) return rc;
   widen_kernel<TL><<<ceil_div((long)ny, 256), 256, 0, st>>>((long)ny, Y, (zd *)dY);
   GBF_LAUNCHED();
+  GBF_CUDA(cudaMemcpyAsync(h->hflag + 2, tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   GBF_CUDA(cudaStreamSynchronize(st));
+  if (h->hflag[2]) {
+    set_error("tensor-core GEMM: bounded wait timed out (code %d)", h->hflag[2]);
+    return -4;
+  }
   return 0;
 }
 

@@ -148,6 +148,29 @@ int prof_begin(cudaStream_t st);                      // slot or -1
 void prof_end(cudaStream_t st, int slot, double flops);
 
 // ------------------------------------------------------------------ GEMM --
+// Tensor-core engine for complex GEMMs with k <= 32 (LU trailing updates and
+// solve steps): while a TcScope is active on this thread, gemm<zd> / gemm<cf>
+// calls that fit (k <= 32, alpha = +-1, beta in {0, 1}, m and n large
+// enough) run as sliced tcgen05 GEMMs with S digits (7: FP64-class for zd,
+// 3: FP32-class for cf) using the scope's workspace and error word.
+struct TcCtx {
+  void *work = nullptr;
+  size_t bytes = 0;
+  int *gerr = nullptr;
+  int S = 0;
+};
+extern thread_local TcCtx *g_tc;
+struct TcScope {
+  TcCtx *prev;
+  explicit TcScope(TcCtx *c) : prev(g_tc) { g_tc = c; }
+  ~TcScope() { g_tc = prev; }
+};
+size_t zgemm_sliced_work(int m, int n, int batch, int S);
+template <class T>
+int zgemm_sliced(cudaStream_t st, int S, char opa, char opb, int m, int n, int k, double alpha, const T *A, long lda,
+                 long sa, const T *B, long ldb, long sb, int beta_one, T *C, long ldc, long sc, int batch, void *work,
+                 size_t work_bytes, int *gerr);
+
 // C = alpha * op(A) * op(B) + beta * C, column-major, strided batches.
 // op: 'N' (as stored), 'T' (transpose), 'C' (conjugate transpose).
 // A is m x k after op, B is k x n after op.  When ksplit > 1 the k range is

@@ -11,6 +11,8 @@
 
 namespace gbf {
 
+thread_local TcCtx *g_tc = nullptr;
+
 template <class T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     gemm_kernel(int m, int n, int k, T alpha, const T *__restrict__ A, long lda, long sa,
@@ -143,10 +145,41 @@ template <> bool is_zero<double>(double v) { return v == 0.0; }
 template <> bool is_zero<zd>(zd v) { return v.x == 0.0 && v.y == 0.0; }
 template <> bool is_zero<cf>(cf v) { return v.x == 0.f && v.y == 0.f; }
 
+// real scalar +-1 / 0-1 tests for the sliced tensor-core path
+template <class T> static bool sliced_ok(T alpha, T beta, double &a, int &b);
+template <> bool sliced_ok<double>(double, double, double &, int &) { return false; }
+template <> bool sliced_ok<zd>(zd alpha, zd beta, double &a, int &b) {
+  if (alpha.y != 0.0 || (alpha.x != 1.0 && alpha.x != -1.0) || beta.y != 0.0 || (beta.x != 0.0 && beta.x != 1.0))
+    return false;
+  a = alpha.x;
+  b = beta.x != 0.0;
+  return true;
+}
+template <> bool sliced_ok<cf>(cf alpha, cf beta, double &a, int &b) {
+  if (alpha.y != 0.f || (alpha.x != 1.f && alpha.x != -1.f) || beta.y != 0.f || (beta.x != 0.f && beta.x != 1.f))
+    return false;
+  a = alpha.x;
+  b = beta.x != 0.f;
+  return true;
+}
+
 template <class T>
 int gemm(cudaStream_t st, char opa, char opb, int m, int n, int k, T alpha, const T *A, long lda, long sa,
          const T *B, long ldb, long sb, T beta, T *C, long ldc, long sc, int batch, int ksplit, T *work) {
   if (m <= 0 || n <= 0 || batch <= 0) return 0;
+  if constexpr (tr<T>::cplx) {
+    double a = 0.0;
+    int b1 = 0;
+    TcCtx *tcx = g_tc;
+    if (tcx && tcx->S > 0 && k >= 1 && k <= 32 && m >= 64 && n >= 32 && sliced_ok<T>(alpha, beta, a, b1) &&
+        zgemm_sliced_work(m, n, batch, tcx->S) <= tcx->bytes) {
+      const int slot = prof_begin(st);
+      const int rc = zgemm_sliced<T>(st, tcx->S, opa, opb, m, n, k, a, A, lda, sa, B, ldb, sb, b1, C, ldc, sc, batch,
+                                     tcx->work, tcx->bytes, tcx->gerr);
+      prof_end(st, slot, 8.0 * m * (double)n * k * batch);
+      return rc;
+    }
+  }
   using G = gemm_cfg<T>;
   if (ksplit < 1 || !work) ksplit = 1;
   int kchunk = k;

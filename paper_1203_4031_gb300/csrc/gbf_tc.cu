@@ -547,10 +547,17 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (ok) {
       const int rr = r0 + q * 32 + lane;  // real row
       const double sg = (rr < rows) ? sigma[(long)b * rows + rr] : 0.0;
+      // The weight sums S_a (exact integers below 2^24, weight 2^{-7(a+2)})
+      // are recombined in 64-bit integers (Horner in base 2^7, two words so
+      // nothing overflows), leaving a handful of FP64 operations per entry:
+      //   x = hi 2^{7(S-H)} + lo,  value = sigma tau 2^{-7(S+1)} x.
+      constexpr int H = (S + 1) / 2 < 3 ? (S + 1) / 2 : 3;
+      const double base_scale = alpha * sg * ldexp(1.0, -7 * (S + 1));
+      const double hi_w = ldexp(1.0, 7 * (S - H));
       for (int c0 = 0; c0 < ZBN; c0 += 16) {
-        double v[16];
+        long long hi[16], lo[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = 0.0;
+        for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
 #pragma unroll
         for (int a = 0; a < S; ++a) {
           uint32_t r[16];
@@ -563,9 +570,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                 "=r"(r[15])
               : "r"(taddr));
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          const double wgt = ldexp(1.0, -7 * (a + 2));
 #pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] += wgt * (double)__uint_as_float(r[j]);
+          for (int j = 0; j < 16; ++j) {
+            const long long v = (long long)__float2int_rn(__uint_as_float(r[j]));
+            if (a < H)
+              hi[j] = hi[j] * 128 + v;
+            else
+              lo[j] = lo[j] * 128 + v;
+          }
         }
         if (rr < rows) {
           const int i = rr >> 1, part = rr & 1;
@@ -573,7 +585,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int j = 0; j < 16; ++j) {
             const int col = n0 + c0 + j;
             if (col < n) {
-              const double val = alpha * sg * tau[(long)b * n + col] * v[j];
+              const double x = fma((double)hi[j], hi_w, (double)lo[j]);
+              const double val = base_scale * tau[(long)b * n + col] * x;
               R *cp = reinterpret_cast<R *>(C + (long)b * sc + i + (long)col * ldc) + part;
               *cp = (R)(beta_one ? (double)*cp + val : val);
             }

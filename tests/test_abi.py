@@ -90,7 +90,7 @@ def test_driver_argument_validation_without_gpu():
     base = g.gbf_init()
     for idx, bad, code in [(1, 21, 102), (1, 0, 102), (2, -1, 103), (3, -1, 104), (4, 2, 105),
                            (5, 3, 106), (13, 3, 114), (15, 2, 116), (17, 0, 118), (41, 2, 142),
-                           (42, 5, 143)]:
+                           (42, 5, 143), (43, 2, 144)]:
         f = base.copy()
         f[idx] = bad
         assert g.feast_host(A, None, 0.5, 3.5, 5, fpm=f)["info"] == code, (idx, bad)

@@ -36,13 +36,14 @@ def cfg2(gbf):
     return p, A, B
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_real_generalized_4096(gbf, cfg2, prec):
+@pytest.mark.parametrize("prec,engine", [(0, 0), (1, 0), (0, 1)])
+def test_real_generalized_4096(gbf, cfg2, prec, engine):
     import torch
 
     p, A, B = cfg2
     fpm = p.apply_fpm(gbf.gbf_init())
     fpm[41] = prec
+    fpm[43] = engine
     h = gbf.Handle()
     r = gbf.feast_dev(A, B, p.emin, p.emax, p.m0, fpm=fpm, handle=h)
     torch.cuda.synchronize()
