@@ -203,6 +203,29 @@ int gbf_zgemm_sliced(void *stream, int prec, int S, char opa, char opb, int m, i
                      const void *dA, long lda, long sa, const void *dB, long ldb, long sb, int beta, void *dC,
                      long ldc, long sc, int batch, void *dWork, size_t work_bytes, int *dErr);
 
+/* gbf_zgemm_sliced without any device allocation, for callers that cannot
+ * allocate device memory during the call (their memory belongs to another
+ * allocator, they cannot afford the device-wide synchronisation of
+ * cudaMalloc/cudaFree, or they will record the sequence into a graph).
+ * The guide has no counterpart.  Same operation, arguments and return codes
+ * as gbf_zgemm_sliced, but the scratch (digit slices, scales, error word) is
+ * a fixed 16 MiB device array inside the library, which every GPU that loads
+ * the library keeps until the process exits.  Limits and rules:
+ *  - a problem whose scratch (gbf_zgemm_sliced_work) exceeds
+ *    gbf_zgemm_sliced_noalloc_max() bytes is rejected with -7 and a message
+ *    in gbf_last_error(); nothing is launched;
+ *  - the first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture;
+ *  - every call shares the one array and it keeps the last call's contents
+ *    (the call clears what must start at zero): calls whose work overlaps on
+ *    the GPU (other streams, other threads) race and must not be issued;
+ *  - the call returns after its stream has finished it. */
+size_t gbf_zgemm_sliced_noalloc_max(void);
+int gbf_zgemm_sliced_noalloc(void *stream, int prec, int S, char opa, char opb, int m, int n, int k, double alpha,
+                             const void *dA, long lda, long sa, const void *dB, long ldb, long sb, int beta, void *dC,
+                             long ldc, long sc, int batch);
+
 /* ---------------------------------------------------------------------
  * Independent problems: batches and the serving loop (the guide's first
  * level of parallelism -- separate search intervals / problems -- inside one

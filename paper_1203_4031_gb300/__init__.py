@@ -69,6 +69,10 @@ def load(build: bool = True):
     L.gbf_zgemm_sliced.argtypes = [vp, C.c_int, C.c_int, C.c_char, C.c_char, C.c_int, C.c_int, C.c_int, C.c_double,
                                    vp, C.c_long, C.c_long, vp, C.c_long, C.c_long, C.c_int, vp, C.c_long, C.c_long,
                                    C.c_int, vp, C.c_size_t, vp]
+    L.gbf_zgemm_sliced_noalloc_max.restype = C.c_size_t
+    L.gbf_zgemm_sliced_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_char, C.c_char, C.c_int, C.c_int, C.c_int,
+                                           C.c_double, vp, C.c_long, C.c_long, vp, C.c_long, C.c_long, C.c_int, vp,
+                                           C.c_long, C.c_long, C.c_int]
     L.gbf_profile.argtypes = [C.c_int]
     L.gbf_profile_name.restype = C.c_char_p
     L.gbf_profile_read.argtypes = [C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -467,3 +471,22 @@ def zgemm_sliced(opa, opb, A, B, C_, alpha=1.0, beta=0, S=7, stream=None):
     return lib().gbf_zgemm_sliced(_stream_ptr(stream), prec, S, opa.encode(), opb.encode(), m, n, k, float(alpha),
                                   _ptr(A), am, am * ak, _ptr(B), bk, bk * bn, int(beta), _ptr(C_), C_.shape[2],
                                   C_.shape[1] * C_.shape[2], bt, _ptr(work), work.numel(), _ptr(err))
+
+
+def zgemm_sliced_noalloc(opa, opb, A, B, C_, alpha=1.0, beta=0, S=7, stream=None):
+    """gbf_zgemm_sliced_noalloc (no device allocation; fixed library scratch);
+    same tensor layout as zgemm_sliced.  Returns the code."""
+    import torch
+
+    bt = A.shape[0]
+    am, ak = A.shape[2], A.shape[1]
+    bk, bn = B.shape[2], B.shape[1]
+    m = am if opa == "N" else ak
+    k = ak if opa == "N" else am
+    n = bn if opb == "N" else bk
+    prec = 0 if A.dtype == torch.complex128 else 1
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device)
+    return lib().gbf_zgemm_sliced_noalloc(_stream_ptr(stream), prec, S, opa.encode(), opb.encode(), m, n, k,
+                                          float(alpha), _ptr(A), am, am * ak, _ptr(B), bk, bk * bn, int(beta),
+                                          _ptr(C_), C_.shape[2], C_.shape[1] * C_.shape[2], bt)

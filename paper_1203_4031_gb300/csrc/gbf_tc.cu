@@ -723,3 +723,83 @@ extern "C" int gbf_zgemm_sliced(void *stream, int prec, int S, char opa, char op
   }
   return 0;
 }
+
+// ===================================================================
+// No-allocation variant of gbf_zgemm_sliced.
+//
+// For callers that must not allocate device memory during the call: code
+// whose device memory is owned by another allocator (a framework's caching
+// pool holding the whole budget), latency-critical paths that cannot afford
+// the device-wide synchronisation cudaMalloc/cudaFree imply, and sequences
+// that will later be recorded into a CUDA graph.  The scratch this GEMM needs
+// (digit slices, scales, error word) lives in the file-scope array below,
+// which every GPU that loads this library holds until the process exits.
+// ===================================================================
+namespace {
+constexpr size_t kNoAllocScratch = 16u << 20;  // 16 MiB
+constexpr size_t kNoAllocErrOff = kNoAllocScratch - 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch];
+
+// Device address of the array, looked up once per device (host code must
+// not use the symbol itself: on the host it only names a stand-in object).
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64] = {nullptr};
+
+int noalloc_scratch(void **out) {
+  int dev = 0;
+  GBF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    gbf::set_error("gbf_zgemm_sliced_noalloc: device ordinal %d out of range", dev);
+    return -4;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      gbf::set_error("gbf_zgemm_sliced_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return -4;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return 0;
+}
+}  // namespace
+
+extern "C" size_t gbf_zgemm_sliced_noalloc_max(void) { return kNoAllocErrOff; }
+
+extern "C" int gbf_zgemm_sliced_noalloc(void *stream, int prec, int S, char opa, char opb, int m, int n, int k,
+                                        double alpha, const void *dA, long lda, long sa, const void *dB, long ldb,
+                                        long sb, int beta, void *dC, long ldc, long sc, int batch) {
+  if (m <= 0 || n <= 0 || batch <= 0) return 0;
+  const size_t need = gbf::zgemm_sliced_work(m, n, batch, S);
+  if (need > kNoAllocErrOff) {
+    gbf::set_error(
+        "gbf_zgemm_sliced_noalloc: this problem needs %zu bytes of scratch, more than the fixed %zu available "
+        "(use gbf_zgemm_sliced with a caller-provided workspace)",
+        need, (size_t)kNoAllocErrOff);
+    return -7;
+  }
+  void *scratch = nullptr;
+  if (int rc = noalloc_scratch(&scratch)) return rc;
+  int *derr = reinterpret_cast<int *>((unsigned char *)scratch + kNoAllocErrOff);
+  cudaStream_t st = (cudaStream_t)stream;
+  // the array keeps the previous call's contents: the error word must start at 0
+  GBF_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
+  int rc = prec ? gbf::zgemm_sliced<gbf::cf>(st, S, opa, opb, m, n, k, alpha, (const gbf::cf *)dA, lda, sa,
+                                             (const gbf::cf *)dB, ldb, sb, beta, (gbf::cf *)dC, ldc, sc, batch, scratch,
+                                             kNoAllocErrOff, derr)
+                : gbf::zgemm_sliced<gbf::zd>(st, S, opa, opb, m, n, k, alpha, (const gbf::zd *)dA, lda, sa,
+                                             (const gbf::zd *)dB, ldb, sb, beta, (gbf::zd *)dC, ldc, sc, batch, scratch,
+                                             kNoAllocErrOff, derr);
+  if (rc) return rc;
+  int herr = 0;
+  GBF_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GBF_CUDA(cudaStreamSynchronize(st));
+  if (herr) {
+    gbf::set_error("gbf_zgemm_sliced_noalloc: bounded wait timed out (code %d)", herr);
+    return -5;
+  }
+  return 0;
+}
