@@ -21,6 +21,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "gbf_common.cuh"
@@ -334,15 +335,15 @@ extern "C" int gbf_tc_gemm_bf16(void *stream, int M, int N, int K, int batch, co
 // Real embedding: complex row i of op(A) -> real rows 2i = [Re | -Im] and
 // 2i+1 = [Im | Re] (length 2k); column c of op(B) -> [Re ; Im].  Then
 // real row 2i (2i+1) times column c is Re (Im) of the complex product.
-// Slicing (exact error-free split): each real row r is scaled by a power of
-// two sigma_r >= its largest magnitude, each column c by tau_c; x/sigma in
-// [-1, 1] is written as sum_{t=1..S} d_t 2^{-7t} with integer digits d_t
-// (|d_1| <= 128, |d_t| <= 64 after), each exact in bf16.  For digit pairs
-// (t, u) with t + u <= S + 1, the products D_t E_u^T are integers below
-// 2^24 in magnitude even summed over all pairs of one weight (64 terms of
-// at most 2^14, at most S pairs), so one FP32 TMEM accumulator per weight
-// w = t + u holds them exactly; the epilogue forms
-//   sigma_r tau_c sum_w 2^{-7w} S_w  in FP64.
+// Slicing: each real row r is scaled by a power of two sigma_r above its
+// largest magnitude, each column c by tau_c; x/sigma (|x/sigma| < 1) is
+// rounded once to 7S fractional bits and written as sum_{t=1..S} d_t 2^{-7t}
+// with integer digits d_t (|d_1| <= 128, |d_t| <= 64 after), each exact in
+// bf16.  For digit pairs (t, u) with t + u <= S + 1, the products
+// D_t E_u^T are integers below 2^22 in magnitude even summed over all pairs
+// of one weight (64 terms, at most S pairs), so one FP32 TMEM accumulator
+// per weight w = t + u holds them exactly; the epilogue combines the S_w
+// exactly in int64 and rounds sigma_r tau_c sum_w 2^{-7w} S_w once.
 // S = 7 keeps 49 bits per operand relative to its row/column maximum
 // (FP64-class products); S = 3 keeps 21 bits (FP32-class).
 // ===================================================================
@@ -362,32 +363,76 @@ template <> struct cplx_io<cf> {
   using R = float;
 };
 
-__device__ __forceinline__ double pow2_ceil(double mx) {
-  if (!(mx > 0.0)) return 1.0;
-  int e;
-  const double f = frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
-  (void)f;
-  return ldexp(1.0, e);            // 2^e >= mx
-}
+// Slicing.  A row (or column) of op(A) (op(B)) is scaled by a power of two
+// 2^e above its largest real or imaginary part, so every scaled part v has
+// |v| < 1; v is rounded once to X = rint(v 2^{7S}) (an integer, |X| <= 2^{7S})
+// and X is split into S balanced base-2^7 digits, least significant first:
+// d = ((X + 64) mod 128) - 64, X <- (X - d) / 128; the leading digit takes
+// what remains (|d_0| <= 128, the others <= 64), so v = sum_t d_t 2^{-7(t+1)}
+// up to 2^{-7S-1}.  All of it is integer work on the FP64 bit patterns.
 
-// digits of v in [-1, 1]: v = sum_t d_t 2^{-7t} + rest (exact recursion)
-template <int S>
-__device__ __forceinline__ void digits(double v, float *d) {
+// Largest |re|, |im| bit pattern (ordered like the magnitudes) over the warp.
+__device__ __forceinline__ unsigned long long warp_absmax_bits(double re, double im) {
+  const unsigned long long a = (unsigned long long)__double_as_longlong(re) & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long c = (unsigned long long)__double_as_longlong(im) & 0x7FFFFFFFFFFFFFFFull;
+  unsigned long long m = a > c ? a : c;
 #pragma unroll
-  for (int t = 0; t < S; ++t) {
-    v *= 128.0;
-    const double r = rint(v);
-    d[t] = (float)r;
-    v -= r;
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
+    m = o > m ? o : m;
   }
+  return m;
 }
 
-// A side: one block per complex row i of op(A) (m x k), thread p < k.
-// Out: slices [S][batch][2m][ZK] bf16, sigma [batch][2m].
+// e with 2^e > the magnitude whose bit pattern is mb (the frexp exponent);
+// 0 for a zero row.
+__device__ __forceinline__ int scale_exp(unsigned long long mb) {
+  if (mb == 0) return 0;
+  const int f = (int)(mb >> 52);
+  if (f == 0) return ilogb(__longlong_as_double((long long)mb)) + 1;
+  return f - 1022;
+}
+
+// rint(v 2^{7S - e}) for a finite v with |v| < 2^e, ties to even.
+template <int S>
+__device__ __forceinline__ long long fixed_point(double v, int e) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int f = (int)((bits >> 52) & 0x7FF);
+  const unsigned long long mant = (bits & 0x000FFFFFFFFFFFFFull) | (f ? 0x0010000000000000ull : 0ull);
+  // v = mant 2^{ev - 52}; v 2^{7S - e} = mant 2^{-r}, r >= 1 because |v| < 2^e
+  const int ev = (f ? f : 1) - 1023;
+  const int r = 52 - ev - 7 * S + e;
+  long long X;
+  if (mant == 0 || r > 54) {
+    X = 0;
+  } else if (r <= 0) {  // not reached for |v| < 2^e; kept total
+    X = (long long)(mant << (-r));
+  } else {
+    X = (long long)((mant + ((1ull << (r - 1)) - 1ull) + ((mant >> r) & 1ull)) >> r);
+  }
+  return (bits >> 63) ? -X : X;
+}
+
+template <int S>
+__device__ __forceinline__ void int_digits(long long X, float *d) {
+#pragma unroll
+  for (int t = S - 1; t > 0; --t) {
+    const long long dt = ((X + 64) & 127) - 64;
+    d[t] = (float)(int)dt;
+    X = (X - dt) >> 7;
+  }
+  d[0] = (float)(int)X;
+}
+
+// A side: one warp per complex row i of op(A) (m x k), lane p < k holds
+// element (i, p).  Out: slices [S][batch][2m][ZK] bf16 holding rows
+// 2i = [Re | -Im] and 2i+1 = [Im | Re] of the scaled row, zero-padded to ZK;
+// sexp [batch][2m] = e, the row's scale 2^e.
 template <class T, int S>
 __global__ void slice_a_kernel(char opa, int m, int k, const T *A, long lda, long sa, int batch,
-                               __nv_bfloat16 *out, double *sigma) {
-  const int i = blockIdx.x, b = blockIdx.y, p = threadIdx.x;
+                               __nv_bfloat16 *out, int *sexp) {
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), b = blockIdx.y, p = threadIdx.x & 31;
+  if (i >= m) return;  // warp-uniform
   const T *Ab = A + (long)b * sa;
   double re = 0.0, im = 0.0;
   if (p < k) {
@@ -395,16 +440,10 @@ __global__ void slice_a_kernel(char opa, int m, int k, const T *A, long lda, lon
     re = (double)a.x;
     im = (opa == 'C') ? -(double)a.y : (double)a.y;
   }
-  double mx = fmax(fabs(re), fabs(im));
-  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  __shared__ double wm[2];
-  if ((p & 31) == 0) wm[p >> 5] = mx;
-  __syncthreads();
-  mx = (blockDim.x > 32) ? fmax(wm[0], wm[1]) : wm[0];
-  const double sg = pow2_ceil(mx);
+  const int e = scale_exp(warp_absmax_bits(re, im));
   float dr[S], di[S];
-  digits<S>(re / sg, dr);
-  digits<S>(im / sg, di);
+  int_digits<S>(fixed_point<S>(re, e), dr);
+  int_digits<S>(fixed_point<S>(im, e), di);
   const long rows = 2L * m;
   for (int t = 0; t < S; ++t) {
     __nv_bfloat16 *o = out + (((long)t * batch + b) * rows) * ZK;
@@ -415,23 +454,25 @@ __global__ void slice_a_kernel(char opa, int m, int k, const T *A, long lda, lon
       r1[p] = __float2bfloat16_rn(di[t]);
       r1[k + p] = __float2bfloat16_rn(dr[t]);
     }
-    for (int q = 2 * k + p; q < ZK; q += blockDim.x) {
+    for (int q = 2 * k + p; q < ZK; q += 32) {
       r0[q] = __float2bfloat16_rn(0.f);
       r1[q] = __float2bfloat16_rn(0.f);
     }
   }
   if (p == 0) {
-    sigma[(long)b * rows + 2 * i] = sg;
-    sigma[(long)b * rows + 2 * i + 1] = sg;
+    sexp[(long)b * rows + 2 * i] = e;
+    sexp[(long)b * rows + 2 * i + 1] = e;
   }
 }
 
-// B side: one block per column c of op(B) (k x n), thread p < k.
-// Out: slices [S][batch][n][ZK] bf16, tau [batch][n].
+// B side: one warp per column c of op(B) (k x n), lane p < k holds element
+// (p, c).  Out: slices [S][batch][n][ZK] bf16 holding [Re ; Im] of the scaled
+// column, zero-padded; texp [batch][n] = e, the column's scale 2^e.
 template <class T, int S>
 __global__ void slice_b_kernel(char opb, int k, int n, const T *B, long ldb, long sb, int batch,
-                               __nv_bfloat16 *out, double *tau) {
-  const int c = blockIdx.x, b = blockIdx.y, p = threadIdx.x;
+                               __nv_bfloat16 *out, int *texp) {
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), b = blockIdx.y, p = threadIdx.x & 31;
+  if (c >= n) return;  // warp-uniform
   const T *Bb = B + (long)b * sb;
   double re = 0.0, im = 0.0;
   if (p < k) {
@@ -439,25 +480,19 @@ __global__ void slice_b_kernel(char opb, int k, int n, const T *B, long ldb, lon
     re = (double)v.x;
     im = (opb == 'C') ? -(double)v.y : (double)v.y;
   }
-  double mx = fmax(fabs(re), fabs(im));
-  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  __shared__ double wm[2];
-  if ((p & 31) == 0) wm[p >> 5] = mx;
-  __syncthreads();
-  mx = (blockDim.x > 32) ? fmax(wm[0], wm[1]) : wm[0];
-  const double tg = pow2_ceil(mx);
+  const int e = scale_exp(warp_absmax_bits(re, im));
   float dr[S], di[S];
-  digits<S>(re / tg, dr);
-  digits<S>(im / tg, di);
+  int_digits<S>(fixed_point<S>(re, e), dr);
+  int_digits<S>(fixed_point<S>(im, e), di);
   for (int t = 0; t < S; ++t) {
     __nv_bfloat16 *o = out + (((long)t * batch + b) * n + c) * ZK;
     if (p < k) {
       o[p] = __float2bfloat16_rn(dr[t]);
       o[k + p] = __float2bfloat16_rn(di[t]);
     }
-    for (int q = 2 * k + p; q < ZK; q += blockDim.x) o[q] = __float2bfloat16_rn(0.f);
+    for (int q = 2 * k + p; q < ZK; q += 32) o[q] = __float2bfloat16_rn(0.f);
   }
-  if (p == 0) tau[(long)b * n + c] = tg;
+  if (p == 0) texp[(long)b * n + c] = e;
 }
 
 // Instruction descriptor for N = ZBN.
@@ -466,33 +501,139 @@ __host__ __device__ constexpr uint32_t idesc_bf16_n(int n) {
 }
 
 template <int S> struct zlay {
-  static constexpr int SMEM = S * (ZA_TILE + ZB_TILE) + 1024 + 256;
-  static constexpr int ACC = S;  // weights 2 .. S+1
-  static constexpr int COLS = (S * ZBN <= 32) ? 32 : (S * ZBN <= 64) ? 64 : (S * ZBN <= 128) ? 128 : 256;
+  // A slices of one 128-row block (resident per work item) + a ring of NB
+  // stages of the B slices of one 32-column tile, as deep as fits in 227 KB
+  static constexpr int FIXED = S * ZA_TILE + 1024 + 256;
+  static constexpr int NB = (FIXED + 4 * S * ZB_TILE <= 232448) ? 4 : (FIXED + 3 * S * ZB_TILE <= 232448) ? 3 : 2;
+  static constexpr int SMEM = FIXED + NB * S * ZB_TILE;
+  static constexpr int ACC_COLS = S * ZBN;  // one accumulator buffer (S weights x ZBN)
+  static constexpr int COLS = (2 * ACC_COLS <= 64) ? 64 : (2 * ACC_COLS <= 128) ? 128 : (2 * ACC_COLS <= 256) ? 256 : 512;
 };
 
-template <class T, int S>
-__global__ void __launch_bounds__(THREADS, 1)
+// Sum over the weights of (float bits of s_a + 1.5 2^23) 2^{7(S-1-a)} taken
+// mod 2^64 equals x + KS with the constant below, so x comes out of S
+// multiply-adds and one subtraction (wrap-around is harmless: |x| < 2^63).
+template <int S> __host__ __device__ constexpr unsigned long long acc_bias() {
+  unsigned long long k = 0;
+  for (int a = 0; a < S; ++a) k += 0x4B400000ull << (7 * (S - 1 - a));
+  return k;
+}
+
+// x + a 2^w for w < 32 (one wide multiply-add) and for 32 <= w < 64 (a
+// multiply-add on the high word).
+template <int W>
+__device__ __forceinline__ unsigned long long add_shifted(unsigned long long x, uint32_t a) {
+  unsigned long long r;
+  if (W < 32) {
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(a), "r"(1u << (W & 31)), "l"(x));
+  } else {
+    asm("{\n\t.reg .u32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\tmad.lo.u32 hi, %2, %3, hi;\n\tmov.b64 %0, {lo, hi};\n\t}"
+        : "=l"(r)
+        : "l"(x), "r"(a), "r"(1u << (W & 31)));
+  }
+  return r;
+}
+
+// x 2^E for an exact int64 x, rounded to nearest (ties to even) once, from
+// integer operations alone (leading-zero count, shift, round, exponent
+// field); the caller guarantees -1022 <= E <= 960, so every nonzero result
+// is a normal number.  `sgn` (0 or the sign bit) flips the sign.
+__device__ __forceinline__ double i64_scaled(long long x, int E, unsigned long long sgn) {
+  const unsigned long long sx = (unsigned long long)(x >> 63);              // 0 or all ones
+  unsigned long long u = ((unsigned long long)x ^ sx) - sx;                  // |x|
+  const int lz = __clzll((long long)u);
+  u <<= lz;                                                                  // leading one at bit 63
+  unsigned long long mant = u >> 11;                                         // 53 bits
+  const unsigned long long half = (u >> 10) & 1ull, sticky = (u & 0x3FFull) | (mant & 1ull);
+  mant += half & (sticky != 0 ? 1ull : 0ull);
+  // (biased exponent - 1) 2^52 + mant: the leading one completes the
+  // exponent, and a mantissa rounded up to 2^53 carries into it
+  const unsigned long long bits = ((unsigned long long)(1085 - lz + E) << 52) + mant;
+  return x == 0 ? 0.0 : __longlong_as_double((long long)((bits) ^ (sgn ^ (sx << 63))));
+}
+
+// Reads the weight sums a = A, A+1 of 16 columns from TMEM (this warp's 32
+// lanes; column of weight a at taddr + a ZBN) and adds them into x.
+template <int S, int A>
+__device__ __forceinline__ void combine_weights(unsigned long long *x, uint32_t taddr) {
+  if constexpr (A < S) {
+    constexpr bool two = A + 1 < S;
+    uint32_t r0[16], r1[16];
+    const uint32_t t0 = taddr + (uint32_t)(A * ZBN);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+        "[%16];"
+        : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3]), "=r"(r0[4]), "=r"(r0[5]), "=r"(r0[6]), "=r"(r0[7]),
+          "=r"(r0[8]), "=r"(r0[9]), "=r"(r0[10]), "=r"(r0[11]), "=r"(r0[12]), "=r"(r0[13]), "=r"(r0[14]),
+          "=r"(r0[15])
+        : "r"(t0));
+    if constexpr (two)
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+          "[%16];"
+          : "=r"(r1[0]), "=r"(r1[1]), "=r"(r1[2]), "=r"(r1[3]), "=r"(r1[4]), "=r"(r1[5]), "=r"(r1[6]),
+            "=r"(r1[7]), "=r"(r1[8]), "=r"(r1[9]), "=r"(r1[10]), "=r"(r1[11]), "=r"(r1[12]), "=r"(r1[13]),
+            "=r"(r1[14]), "=r"(r1[15])
+          : "r"(t0 + (uint32_t)ZBN));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    constexpr int w0 = 7 * (S - 1 - A);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      x[j] = add_shifted<w0>(x[j], __float_as_uint(__uint_as_float(r0[j]) + 12582912.0f));
+      if constexpr (two) x[j] = add_shifted<w0 - 7>(x[j], __float_as_uint(__uint_as_float(r1[j]) + 12582912.0f));
+    }
+    combine_weights<S, A + 2>(x, taddr);
+  }
+}
+
+// Persistent sliced GEMM.  Work item = (column chunk, 128-row block of the
+// real embedding, batch); a CTA takes items blockIdx.x, +gridDim.x, ...  Per
+// item the A slices are loaded once, then the chunk's 32-column tiles flow
+// through:
+//   warp 0 (one thread): TMA of A slices (barrier a_full, freed by a_empty)
+//                        and of each tile's B slices (b_full[2] / b_empty[2]);
+//   warp 1 (one thread): S(S+1)/2 digit-pair MMAs per tile into accumulator
+//                        buffer g % 2 (acc_full[2] / acc_empty[2]);
+//   warps 2-5:           epilogue of tile g while tile g+1 is loaded and
+//                        multiplied.
+// g counts the tiles this CTA has processed; buffer = g % 2, use = g / 2.
+constexpr int ZTHREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+
+template <class T, int S, bool BETA>
+__global__ void __launch_bounds__(ZTHREADS, 1)
     zgemm_sliced_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int m,
-                        int n, int batch, const double *sigma, const double *tau, double alpha, int beta_one,
+                        int n, int batch, int nch, int tpc, const int *__restrict__ sexp, const int *__restrict__ texp, double alpha,
                         T *C, long ldc, long sc, int *gerr) {
   using R = typename cplx_io<T>::R;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char *sA = base;                        // S x [128][64] bf16
-  unsigned char *sB = base + S * ZA_TILE;          // S x [ZBN][64] bf16
-  uint64_t *full = reinterpret_cast<uint64_t *>(base + S * (ZA_TILE + ZB_TILE));
-  uint64_t *accb = full + 1;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accb + 1);
+  constexpr int NB = zlay<S>::NB;
+  unsigned char *sA = base;                 // S x [128][64]
+  unsigned char *sB = base + S * ZA_TILE;   // NB x S x [32][64]
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + S * ZA_TILE + NB * S * ZB_TILE);
+  uint64_t *a_full = bars, *a_empty = bars + S;           // a_full[t]: slice t landed
+  uint64_t *b_full = bars + S + 1, *b_empty = b_full + NB;
+  uint64_t *acc_full = b_empty + NB, *acc_empty = acc_full + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rows = 2 * m;
-  const int r0 = blockIdx.x * BM, n0 = blockIdx.y * ZBN, b = blockIdx.z;
+  const int nrb = (rows + BM - 1) / BM, nct = (n + ZBN - 1) / ZBN;
+  const int items = nch * nrb * batch;
   constexpr uint32_t NCOLS = zlay<S>::COLS;
+  constexpr int ACC = zlay<S>::ACC_COLS;
 
   if (threadIdx.x == 0) {
-    mbar_init(full, 1);
-    mbar_init(accb, 1);
+    for (int t = 0; t < S; ++t) mbar_init(&a_full[t], 1);
+    mbar_init(a_empty, 1);
+    for (int j = 0; j < NB; ++j) {
+      mbar_init(&b_full[j], 1);
+      mbar_init(&b_empty[j], 1);
+    }
+    for (int j = 0; j < 2; ++j) {
+      mbar_init(&acc_full[j], 1);
+      mbar_init(&acc_empty[j], 8);  // one arrival per epilogue warp
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -508,90 +649,221 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    mbar_expect_tx(full, S * (ZA_TILE + ZB_TILE));
-    for (int t = 0; t < S; ++t) {
-      tma_load_3d(sA + t * ZA_TILE, &ta, full, 0, r0, t * batch + b);
-      tma_load_3d(sB + t * ZB_TILE, &tb, full, 0, n0, t * batch + b);
+    // ------------------------------------------------------------ TMA --
+    // B tile g goes to ring stage g % NB once the MMAs of tile g - NB are done
+    int g = 0, it_local = 0, last_b = -1;
+    bool ok = true;
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it_local) {
+      const int cc = item % nch, rb = (item / nch) % nrb, b = item / (nch * nrb);
+      const int ct1 = min(nct, (cc + 1) * tpc);
+      if (it_local > 0 && !mbar_wait(a_empty, (it_local - 1) & 1, abort_flag, gerr, 21)) {
+        ok = false;
+        break;
+      }
+      for (int t = 0; t < S; ++t) {
+        mbar_expect_tx(&a_full[t], ZA_TILE);
+        tma_load_3d(sA + t * ZA_TILE, &ta, &a_full[t], 0, rb * BM, t * batch + b);
+      }
+      for (int ct = cc * tpc; ct < ct1; ++ct, ++g) {
+        const int st = g % NB, use = g / NB;
+        if (use > 0 && !mbar_wait(&b_empty[st], (use - 1) & 1, abort_flag, gerr, 22)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&b_full[st], S * ZB_TILE);
+        for (int u = 0; u < S; ++u)
+          tma_load_3d(sB + (st * S + u) * ZB_TILE, &tb, &b_full[st], 0, ct * ZBN, u * batch + b);
+        last_b = g;
+      }
     }
-    mbar_drain(full, 0, gerr, 12);
+    // drain the copies this thread issued
+    if (it_local > 0)
+      for (int t = 0; t < S; ++t) mbar_drain(&a_full[t], (it_local - 1) & 1, gerr, 23);
+    for (int gg = (last_b - NB + 1 > 0 ? last_b - NB + 1 : 0); gg <= last_b; ++gg)
+      mbar_drain(&b_full[gg % NB], (gg / NB) & 1, gerr, 24);
   } else if (warp == 1 && lane == 0) {
-    constexpr uint32_t idesc = idesc_bf16_n(ZBN);
-    if (mbar_wait(full, 0, abort_flag, gerr, 13)) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      uint32_t used = 0;  // accumulator a (weight a + 2) already written
-#pragma unroll
-      for (int t = 0; t < S; ++t)
-#pragma unroll
-        for (int u = 0; u < S; ++u) {
-          if (t + u > S - 1) continue;  // digits 1-based: (t+1)+(u+1) <= S+1
-          const int a = t + u;
-          const uint64_t ad = sdesc_sw128(sm_u32(sA + t * ZA_TILE));
-          const uint64_t bd = sdesc_sw128(sm_u32(sB + u * ZB_TILE));
-#pragma unroll
-          for (int kk = 0; kk < ZK / 16; ++kk) {
-            const uint32_t acc = ((used >> a) & 1u) || kk > 0 ? 1u : 0u;
-            mma_bf16(tmem + (uint32_t)(a * ZBN), ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, acc);
-          }
-          used |= 1u << a;
+    // ------------------------------------------------------------ MMA --
+    int g = 0, it_local = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it_local) {
+      const int cc = item % nch;
+      const int ct0 = cc * tpc, ct1 = min(nct, ct0 + tpc);
+      for (int ct = ct0; ct < ct1; ++ct, ++g) {
+        const int st = g % NB, buf = g & 1;
+        if (!mbar_wait(&b_full[st], (g / NB) & 1, abort_flag, gerr, 26) ||
+            (g >= 2 && !mbar_wait(&acc_empty[buf], ((g >> 1) - 1) & 1, abort_flag, gerr, 27))) {
+          ok = false;
+          break;
         }
-    }
-    mma_commit(accb);
-    mbar_drain(accb, 0, gerr, 14);
-  } else if (warp >= 2) {
-    const int q = warp & 3;
-    int okw = 0;
-    if (lane == 0) okw = mbar_wait(accb, 0, abort_flag, gerr, 15) ? 1 : 0;
-    const bool ok = __shfl_sync(0xffffffffu, okw, 0) != 0;
-    __syncwarp();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-      const int rr = r0 + q * 32 + lane;  // real row
-      const double sg = (rr < rows) ? sigma[(long)b * rows + rr] : 0.0;
-      // The weight sums S_a (exact integers below 2^24, weight 2^{-7(a+2)})
-      // are recombined in 64-bit integers (Horner in base 2^7, two words so
-      // nothing overflows), leaving a handful of FP64 operations per entry:
-      //   x = hi 2^{7(S-H)} + lo,  value = sigma tau 2^{-7(S+1)} x.
-      constexpr int H = (S + 1) / 2 < 3 ? (S + 1) / 2 : 3;
-      const double base_scale = alpha * sg * ldexp(1.0, -7 * (S + 1));
-      const double hi_w = ldexp(1.0, 7 * (S - H));
-      for (int c0 = 0; c0 < ZBN; c0 += 16) {
-        long long hi[16], lo[16];
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // A slice t times the stacked B slices u = 0 .. S-1-t (contiguous
+        // 32-row tiles in shared memory, one operand of N = (S-t) 32 rows)
+        // lands in accumulators t+u = t .. S-1, which are contiguous TMEM
+        // columns: one MMA per (t, k-step).  t = 0 covers every weight, so
+        // its first k-step initialises the buffer.  On an item's first tile
+        // each A slice is waited for just before its MMAs.
+        const uint32_t dbase = tmem + (uint32_t)(buf * ACC);
+        const uint64_t bd = sdesc_sw128(sm_u32(sB + st * S * ZB_TILE));
+        bool issued = false;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
-#pragma unroll
-        for (int a = 0; a < S; ++a) {
-          uint32_t r[16];
-          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * ZBN + c0);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-              "[%16];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                "=r"(r[15])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const long long v = (long long)__float2int_rn(__uint_as_float(r[j]));
-            if (a < H)
-              hi[j] = hi[j] * 128 + v;
-            else
-              lo[j] = lo[j] * 128 + v;
-          }
-        }
-        if (rr < rows) {
-          const int i = rr >> 1, part = rr & 1;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int col = n0 + c0 + j;
-            if (col < n) {
-              const double x = fma((double)hi[j], hi_w, (double)lo[j]);
-              const double val = base_scale * tau[(long)b * n + col] * x;
-              R *cp = reinterpret_cast<R *>(C + (long)b * sc + i + (long)col * ldc) + part;
-              *cp = (R)(beta_one ? (double)*cp + val : val);
+        for (int t = 0; t < S; ++t) {
+          if (ct == ct0) {
+            if (!mbar_wait(&a_full[t], it_local & 1, abort_flag, gerr, 25)) {
+              ok = false;
+              break;
             }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          }
+          const uint32_t idesc = idesc_bf16_n((S - t) * ZBN);
+          const uint64_t ad = sdesc_sw128(sm_u32(sA + t * ZA_TILE));
+#pragma unroll
+          for (int kk = 0; kk < ZK / 16; ++kk)
+            mma_bf16(dbase + (uint32_t)(t * ZBN), ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                     (t > 0 || kk > 0) ? 1u : 0u);
+          issued = true;
+        }
+        if (!ok) {
+          if (issued) {  // track the MMAs already issued for the drain below
+            mma_commit(&acc_full[buf]);
+            ++g;
+          }
+          break;
+        }
+        mma_commit(&b_empty[st]);
+        mma_commit(&acc_full[buf]);
+      }
+      if (ok) mma_commit(a_empty);  // A slices free once this item's MMAs complete
+    }
+    // every MMA issued has completed before TMEM is freed
+    if (g > 0) mbar_drain(&acc_full[(g - 1) & 1], ((g - 1) >> 1) & 1, gerr, 28);
+  } else if (warp >= 2) {
+    // ------------------------------------------------------- epilogue --
+    // Warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of the tile) and
+    // columns half*16 .. +15 of each tile, half = (w - 2) / 4.  Per tile it
+    // waits for the accumulators, copies its S x 16 sums out of TMEM, frees
+    // the buffer for the MMA of tile g + 2, issues the loads of C for its
+    // next tile, and then combines and stores this tile.
+    // Weight sums s_a (a = 0..S-1, weight 2^{-7(a+2)}) are combined exactly as
+    // x = sum_a s_a 2^{7(S-1-a)} in 64-bit integers (|x| < 2^63: |s_0| <= 2^20
+    // and |s_a| < 2^22); the entry is alpha sigma_i tau_j 2^{-7(S+1)} x.
+    const int q = warp & 3, c0 = ((warp - 2) >> 2) * 16;
+    const bool neg = alpha < 0.0;
+    R cnext[16];
+    int tnext = 0;   // lane j < 16: exponent of column col0 + j, for shuffles
+    int esnext = 0;  // exponent of this lane's row
+    // first column of (item, ct) handled by this thread's warp, its row, batch
+    auto tile_of = [&](int item, int ct, int &rr, int &b, int &col0) {
+      const int rb = (item / nch) % nrb;
+      b = item / (nch * nrb);
+      rr = rb * BM + q * 32 + lane;
+      col0 = ct * ZBN + c0;
+    };
+    auto load_c = [&](int item, int ct) {
+      int rr, b, col0;
+      tile_of(item, ct, rr, b, col0);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) cnext[j] = (R)0;
+      tnext = (col0 + (lane & 15) < n) ? __ldg(texp + (long)b * n + col0 + (lane & 15)) : 0;
+      esnext = (rr < rows) ? __ldg(sexp + (long)b * rows + rr) : 0;
+      if (BETA && rr < rows) {
+        const R *crow = reinterpret_cast<const R *>(C + (long)b * sc + (rr >> 1)) + (rr & 1);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (col0 + j < n) cnext[j] = crow[2L * (col0 + j) * ldc];
+      }
+    };
+    int item = blockIdx.x, ct = 0, ct1 = 0;
+    if (item < items) {
+      ct = (item % nch) * tpc;
+      ct1 = min(nct, ct + tpc);
+      load_c(item, ct);
+    }
+    for (int g = 0; item < items; ++g) {
+      const int buf = g & 1, use = g >> 1;
+      int okw = 0;
+      if (lane == 0) okw = mbar_wait(&acc_full[buf], use & 1, abort_flag, gerr, 29) ? 1 : 0;
+      if (__shfl_sync(0xffffffffu, okw, 0) == 0) break;
+      __syncwarp();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      unsigned long long x[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) x[j] = 0ull - acc_bias<S>();
+      combine_weights<S, 0>(x, tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * ACC + c0));
+      // accumulator buffer free for the MMA of tile g + 2
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(&acc_empty[buf])) : "memory");
+      // this tile's C entries and scales (loaded during the previous tile),
+      // then the loads for the next tile of this CTA, which overlap the work
+      // below
+      R cur[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) cur[j] = cnext[j];
+      const int tcur = tnext, escur = esnext;
+      int nitem = item, nct0 = ct + 1;
+      if (nct0 >= ct1) {
+        nitem = item + gridDim.x;
+        if (nitem < items) {
+          nct0 = (nitem % nch) * tpc;
+        }
+      }
+      if (nitem < items) load_c(nitem, nct0);
+      int rr, b, col0;
+      tile_of(item, ct, rr, b, col0);
+      const bool rv = rr < rows;
+      // entry = +-2^{es+et} x (row scale es, column scale et); the warp checks
+      // once per tile that every exponent stays in the integer path's range
+      const int es = rv ? escur - 7 * (S + 1) : 0;
+      const bool fast = __reduce_min_sync(0xffffffffu, es) + __reduce_min_sync(0xffffffffu, tcur) >= -1022 &&
+                        __reduce_max_sync(0xffffffffu, es) + __reduce_max_sync(0xffffffffu, tcur) <= 960;
+      R *crow = reinterpret_cast<R *>(C + (long)b * sc + (rr >> 1)) + (rr & 1);
+      const unsigned long long sgn = neg ? 0x8000000000000000ull : 0ull;
+      int et[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) et[j] = __shfl_sync(0xffffffffu, tcur, j);
+      // the product entry is rounded once to FP64 (exactly scaled), then added
+      // to C with one more rounding
+      if (fast && __all_sync(0xffffffffu, rv) && col0 + 15 < n) {
+        // whole 32 x 16 block in range: straight-line code, so the 16
+        // independent conversions interleave
+        double v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = i64_scaled((long long)x[j], es + et[j], sgn);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          if constexpr (BETA)
+            crow[2L * (col0 + j) * ldc] = (R)((double)cur[j] + v[j]);
+          else
+            crow[2L * (col0 + j) * ldc] = (R)v[j];
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = col0 + j;
+          if (rv && col < n) {
+            double v;
+            if (fast) {
+              v = i64_scaled((long long)x[j], es + et[j], sgn);
+            } else {
+              v = ldexp(__ll2double_rn((long long)x[j]), es + et[j]);
+              if (neg) v = -v;
+            }
+            if constexpr (BETA)
+              crow[2L * col * ldc] = (R)((double)cur[j] + v);
+            else
+              crow[2L * col * ldc] = (R)v;
           }
         }
+      }
+      if (nitem != item) {
+        item = nitem;
+        if (item < items) {
+          ct = nct0;
+          ct1 = min(nct, ct + tpc);
+        }
+      } else {
+        ct = nct0;
       }
     }
   }
@@ -631,6 +903,10 @@ static int zgemm_sliced_run(cudaStream_t st, char opa, char opb, int m, int n, i
     set_error("sliced GEMM: k must be in [1, 32]");
     return -4;
   }
+  if (alpha != 1.0 && alpha != -1.0) {
+    set_error("sliced GEMM: alpha must be +1 or -1");
+    return -4;
+  }
   const long rows = 2L * m;
   const size_t a_bytes = (size_t)S * batch * rows * ZK * 2, b_bytes = (size_t)S * batch * n * ZK * 2;
   const size_t s_bytes = (size_t)batch * rows * 8, t_bytes = (size_t)batch * n * 8;
@@ -642,23 +918,38 @@ static int zgemm_sliced_run(cudaStream_t st, char opa, char opb, int m, int n, i
   char *w = (char *)work;
   __nv_bfloat16 *As = (__nv_bfloat16 *)w;
   __nv_bfloat16 *Bs = (__nv_bfloat16 *)(w + al(a_bytes));
-  double *sg = (double *)(w + al(a_bytes) + al(b_bytes));
-  double *tg = (double *)(w + al(a_bytes) + al(b_bytes) + al(s_bytes));
-  slice_a_kernel<T, S><<<dim3(m, batch), 64, 0, st>>>(opa, m, k, A, lda, sa, batch, As, sg);
-  slice_b_kernel<T, S><<<dim3(n, batch), 64, 0, st>>>(opb, k, n, B, ldb, sb, batch, Bs, tg);
+  int *sg = (int *)(w + al(a_bytes) + al(b_bytes));
+  int *tg = (int *)(w + al(a_bytes) + al(b_bytes) + al(s_bytes));
+  slice_a_kernel<T, S><<<dim3(ceil_div(m, 8), batch), 256, 0, st>>>(opa, m, k, A, lda, sa, batch, As, sg);
+  slice_b_kernel<T, S><<<dim3(ceil_div(n, 8), batch), 256, 0, st>>>(opb, k, n, B, ldb, sb, batch, Bs, tg);
   g_launches.fetch_add(2, std::memory_order_relaxed);
   CUtensorMap ta, tb;
   if (int rc = make_map_rows(&ta, As, rows, S * batch, BM)) return rc;
   if (int rc = make_map_rows(&tb, Bs, n, S * batch, ZBN)) return rc;
   static bool attr = false;
   if (!attr) {
-    GBF_CUDA(cudaFuncSetAttribute(zgemm_sliced_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GBF_CUDA(cudaFuncSetAttribute(zgemm_sliced_kernel<T, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  zlay<S>::SMEM));
+    GBF_CUDA(cudaFuncSetAttribute(zgemm_sliced_kernel<T, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   zlay<S>::SMEM));
     attr = true;
   }
-  dim3 grid(ceil_div(rows, BM), ceil_div(n, ZBN), batch);
-  zgemm_sliced_kernel<T, S><<<grid, THREADS, zlay<S>::SMEM, st>>>(ta, tb, m, n, batch, sg, tg, alpha, beta_one, C,
-                                                                   ldc, sc, gerr);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // split the columns into chunks until there are about four work items
+  // per SM (the A slices are reloaded once per chunk)
+  const int base_items = (int)ceil_div(rows, (long)BM) * batch, nct = ceil_div(n, ZBN);
+  const int want = std::max(1, std::min(nct, ceil_div(4 * sms, base_items)));
+  const int tpc = ceil_div(nct, want), nch = ceil_div(nct, tpc);  // no chunk is empty
+  const int items = base_items * nch;
+  dim3 grid(std::min(items, sms));
+  if (beta_one)
+    zgemm_sliced_kernel<T, S, true><<<grid, ZTHREADS, zlay<S>::SMEM, st>>>(ta, tb, m, n, batch, nch, tpc, sg, tg,
+                                                                            alpha, C, ldc, sc, gerr);
+  else
+    zgemm_sliced_kernel<T, S, false><<<grid, ZTHREADS, zlay<S>::SMEM, st>>>(ta, tb, m, n, batch, nch, tpc, sg, tg,
+                                                                             alpha, C, ldc, sc, gerr);
   GBF_LAUNCHED();
   GBF_CUDA(cudaGetLastError());
   return 0;
