@@ -187,6 +187,23 @@ int gbf_heev_dev(gbf_handle h, void *stream, int kind, int m, double *dA, double
 int gbf_tc_gemm_bf16(void *stream, int M, int N, int K, int batch, const void *dA, const void *dB, float *dC,
                      long ldc, long sc, int *dErr);
 
+/* Sliced GEMM for any k on the tensor cores (verification entry of the
+ * engine behind the Rayleigh-Ritz projections A Q and B Q of the FP64
+ * path): dC = alpha op(dA) op(dB) + beta dC on FP64 data, real (cplx 0) or
+ * interleaved complex (cplx 1), op in 'N','T','C', op(A) m x k, op(B) k x n,
+ * k >= 1, alpha = +1 or -1, beta 0 or 1, batches strided by sa, sb, sc
+ * elements.  Each row of op(A) and column of op(B) is scaled by a power of
+ * two and split into 8 base-2^7 digits (56 bits) held exactly in bf16; the
+ * digit products of each 64-wide K chunk are summed exactly in FP32 tensor
+ * memory and accumulated exactly in 64-bit integers across chunks; the FP64
+ * entry is formed once.  dWork: gbf_gemm_sliced_work bytes; dErr: one
+ * device int.  Returns 0, -4 (CUDA error / bad argument), -5 (an in-kernel
+ * bounded wait timed out).  No counterpart in the guide. */
+size_t gbf_gemm_sliced_work(int cplx, int m, int n, int k, int batch);
+int gbf_gemm_sliced(void *stream, int cplx, char opa, char opb, int m, int n, int k, double alpha, const void *dA,
+                    long lda, long sa, const void *dB, long ldb, long sb, int beta, void *dC, long ldc, long sc,
+                    int batch, void *dWork, size_t work_bytes, int *dErr);
+
 /* Sliced complex GEMM on the tensor cores (verification entry of the
  * engine behind the FP64 factorisation and solves): dC = alpha op(dA)
  * op(dB) + beta dC for interleaved complex data (prec 0: FP64, 1: FP32),

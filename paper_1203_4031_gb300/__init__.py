@@ -69,6 +69,11 @@ def load(build: bool = True):
     L.gbf_zgemm_sliced.argtypes = [vp, C.c_int, C.c_int, C.c_char, C.c_char, C.c_int, C.c_int, C.c_int, C.c_double,
                                    vp, C.c_long, C.c_long, vp, C.c_long, C.c_long, C.c_int, vp, C.c_long, C.c_long,
                                    C.c_int, vp, C.c_size_t, vp]
+    L.gbf_gemm_sliced_work.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
+    L.gbf_gemm_sliced_work.restype = C.c_size_t
+    L.gbf_gemm_sliced.argtypes = [vp, C.c_int, C.c_char, C.c_char, C.c_int, C.c_int, C.c_int, C.c_double, vp,
+                                  C.c_long, C.c_long, vp, C.c_long, C.c_long, C.c_int, vp, C.c_long, C.c_long,
+                                  C.c_int, vp, C.c_size_t, vp]
     L.gbf_zgemm_sliced_noalloc_max.restype = C.c_size_t
     L.gbf_zgemm_sliced_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_char, C.c_char, C.c_int, C.c_int, C.c_int,
                                            C.c_double, vp, C.c_long, C.c_long, vp, C.c_long, C.c_long, C.c_int, vp,
@@ -471,6 +476,28 @@ def zgemm_sliced(opa, opb, A, B, C_, alpha=1.0, beta=0, S=7, stream=None):
     return lib().gbf_zgemm_sliced(_stream_ptr(stream), prec, S, opa.encode(), opb.encode(), m, n, k, float(alpha),
                                   _ptr(A), am, am * ak, _ptr(B), bk, bk * bn, int(beta), _ptr(C_), C_.shape[2],
                                   C_.shape[1] * C_.shape[2], bt, _ptr(work), work.numel(), _ptr(err))
+
+
+def gemm_sliced(opa, opb, A, B, C_, alpha=1.0, beta=0, stream=None):
+    """gbf_gemm_sliced (any k, FP64 real or complex) on column-major CUDA
+    tensors packed as for zgemm_sliced: (batch, cols, rows) contiguous, whose
+    [b].t() is the matrix.  C_ is updated in place; returns the code."""
+    import torch
+
+    bt = A.shape[0]
+    am, ak = A.shape[2], A.shape[1]
+    bk, bn = B.shape[2], B.shape[1]
+    m = am if opa == "N" else ak
+    k = ak if opa == "N" else am
+    n = bn if opb == "N" else bk
+    cplx = 1 if A.dtype == torch.complex128 else 0
+    work = torch.empty(lib().gbf_gemm_sliced_work(cplx, m, n, k, bt), dtype=torch.uint8, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device)
+    return lib().gbf_gemm_sliced(_stream_ptr(stream), cplx, opa.encode(), opb.encode(), m, n, k, float(alpha),
+                                 _ptr(A), am, am * ak, _ptr(B), bk, bk * bn, int(beta), _ptr(C_), C_.shape[2],
+                                 C_.shape[1] * C_.shape[2], bt, _ptr(work), work.numel(), _ptr(err))
 
 
 def zgemm_sliced_noalloc(opa, opb, A, B, C_, alpha=1.0, beta=0, S=7, stream=None):

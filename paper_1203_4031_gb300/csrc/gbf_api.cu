@@ -252,9 +252,10 @@ template <class TQ, class TL> struct WS {
   void *tcw;
   size_t tcw_bytes;
   int *tc_err;
+  void *pja, *pjb, *pjq;  // sliced operands of the projections: A, B (rows), Q / Y (columns)
 
   void layout(Bump &b, int n, int m0, int ne, int bs, bool herm, bool hasB, bool needAf, bool needBf,
-              int ksplit, int tcS) {
+              int ksplit, int tcS, bool proj) {
     const size_t nn = (size_t)n * n, nm = (size_t)n * m0, mm = (size_t)m0 * m0;
     const int nblk = ceil_div(n, bs);
     S = b.take<TL>((size_t)ne * nn);
@@ -313,6 +314,14 @@ template <class TQ, class TL> struct WS {
     tcw_bytes = tcS ? std::max(zgemm_sliced_work(n, n, ne, tcS), zgemm_sliced_work(n, m0, ne, tcS)) : 0;
     tcw = tcS ? (void *)b.take<char>(tcw_bytes) : nullptr;
     tc_err = b.take<int>(4);
+    pja = pjb = pjq = nullptr;
+    if (proj) {
+      const bool cx = sizeof(TQ) == sizeof(zd);
+      const long Kp = sliced_kp(n, cx), R = cx ? 2L * n : n;
+      pja = b.take<char>(sliced_op_bytes(R, Kp, 1));
+      pjb = hasB ? (void *)b.take<char>(sliced_op_bytes(R, Kp, 1)) : nullptr;
+      pjq = b.take<char>(sliced_op_bytes(m0, Kp, 1));
+    }
   }
 };
 
@@ -366,13 +375,16 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
   // complex GEMMs of the FP64 factorisation and solves: tensor cores
   // (sliced, 7 digits) unless fpm(44) = 1; FP32 factors use CUDA cores
   const int tcS = (fpm[43] == 0 && bs <= 32 && sizeof(TL) == sizeof(zd)) ? 7 : 0;
+  // the n x n products of the projections (A Q, B Q, B Y): sliced tensor-core
+  // GEMMs with A and B sliced once per call, unless fpm(44) = 1
+  const bool proj = fpm[43] == 0;
   WS<TQ, TL> ws;
   {
     Bump sizing(nullptr);
-    ws.layout(sizing, n, m0, ne, bs, herm, hasB, needAf, needBf, ksplit, tcS);
+    ws.layout(sizing, n, m0, ne, bs, herm, hasB, needAf, needBf, ksplit, tcS, proj);
     if (ensure_arena(h, sizing.off + 4096)) return out.info = -1;
     Bump real(h->arena);
-    ws.layout(real, n, m0, ne, bs, herm, hasB, needAf, needBf, ksplit, tcS);
+    ws.layout(real, n, m0, ne, bs, herm, hasB, needAf, needBf, ksplit, tcS, proj);
   }
   TcCtx tcx;
   tcx.work = ws.tcw;
@@ -426,6 +438,21 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
       }
   }
 
+  // rows of A and B (A^T = A, A^H = A: contiguous columns) sliced once
+  SlicedOp opA{}, opB{};
+  const char opS = herm ? 'C' : 'T';
+  if (proj) {
+    CatScope cat_pj(CAT_PROJECT);
+    CK(slice_rows<TQ>(st, opS, n, n, Af, lda, 0, 1, ws.pja, &opA));
+    if (hasB) CK(slice_rows<TQ>(st, opS, n, n, Bf, ldb, 0, 1, ws.pjb, &opB));
+  }
+  // Y -> op Y for a sliced operand (columns of Y, n x mm)
+  auto sliced_product = [&](const SlicedOp &opM, const TQ *Y, int mm, TQ *out_) -> int {
+    SlicedOp opY;
+    if (int rc = slice_cols<TQ>(st, 'N', n, mm, Y, n, 0, 1, ws.pjq, &opY)) return rc;
+    return gemm_sliced_ops<TQ>(st, opM, opY, 1, 1.0, 0, out_, n, 0, ws.tc_err);
+  };
+
   // initial subspace into Xc
   if (fpm[4] == 1) {
     copy_cols_kernel<TQ><<<dim3(ceil_div(n, 256), m0), 256, 0, st>>>(n, m0, (const TQ *)q.X, n, ws.Xc, n);
@@ -451,8 +478,12 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
       scale = ws.D;
       scalec = ws.Dc;
     } else if (hasB) {
-      if (k == 0)
-        CK(gemm<TQ>(st, 'N', 'N', n, m, n, one, Bf, ldb, 0, ws.Xc, n, 0, zero, ws.RHS, n, 0, 1));
+      if (k == 0) {
+        if (proj)
+          CK(sliced_product(opB, ws.Xc, m, ws.RHS));
+        else
+          CK(gemm<TQ>(st, 'N', 'N', n, m, n, one, Bf, ldb, 0, ws.Xc, n, 0, zero, ws.RHS, n, 0, 1));
+      }
       rhs = (k == 0) ? ws.RHS : ws.BXc;
     } else {
       rhs = ws.Xc;
@@ -481,11 +512,21 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
 
     // ---- Rayleigh-Ritz ----
     CatScope cat_proj(CAT_PROJECT);
-    CK(gemm<TQ>(st, 'N', 'N', n, m, n, one, Af, lda, 0, ws.Q, n, 0, zero, ws.AQ, n, 0, 1));
     const TQ *BQ = ws.Q;
-    if (hasB) {
-      CK(gemm<TQ>(st, 'N', 'N', n, m, n, one, Bf, ldb, 0, ws.Q, n, 0, zero, ws.BQ, n, 0, 1));
-      BQ = ws.BQ;
+    if (proj) {
+      SlicedOp opQ;
+      CK(slice_cols<TQ>(st, 'N', n, m, ws.Q, n, 0, 1, ws.pjq, &opQ));
+      CK(gemm_sliced_ops<TQ>(st, opA, opQ, 1, 1.0, 0, ws.AQ, n, 0, ws.tc_err));
+      if (hasB) {
+        CK(gemm_sliced_ops<TQ>(st, opB, opQ, 1, 1.0, 0, ws.BQ, n, 0, ws.tc_err));
+        BQ = ws.BQ;
+      }
+    } else {
+      CK(gemm<TQ>(st, 'N', 'N', n, m, n, one, Af, lda, 0, ws.Q, n, 0, zero, ws.AQ, n, 0, 1));
+      if (hasB) {
+        CK(gemm<TQ>(st, 'N', 'N', n, m, n, one, Bf, ldb, 0, ws.Q, n, 0, zero, ws.BQ, n, 0, 1));
+        BQ = ws.BQ;
+      }
     }
     // split-K chunks, capped by the workspace sized for (ksplit, m0)
     const int ks = std::max(1, std::min(pick_ksplit(m, n), (int)(((size_t)ksplit * m0 * m0) / ((size_t)m * m))));
@@ -764,7 +805,7 @@ static size_t footprint_t(const gbf_problem *p) {
   Bump b(nullptr);
   const int tcS = (p->fpm[43] == 0 && bs <= 32 && sizeof(TL) == sizeof(zd)) ? 7 : 0;
   ws.layout(b, p->n, p->m0, ne, bs, p->kind == 1, p->dB != nullptr, p->uplo != 'F',
-            p->dB != nullptr && p->uplo != 'F', pick_ksplit(p->m0, p->n), tcS);
+            p->dB != nullptr && p->uplo != 'F', pick_ksplit(p->m0, p->n), tcS, p->fpm[43] == 0);
   return b.off + 4096;
 }
 

@@ -165,6 +165,30 @@ struct TcScope {
   explicit TcScope(TcCtx *c) : prev(g_tc) { g_tc = c; }
   ~TcScope() { g_tc = prev; }
 };
+// Operand sliced for the any-k sliced GEMM: digit planes (bf16) of the rows
+// of op(A) (or columns of op(B)), per-row exponents, rows, padded K.
+struct SlicedOp {
+  const void *slices;
+  const int *exps;
+  long rows;
+  long Kp;
+};
+long sliced_kp(int k, bool cplx);
+size_t sliced_op_bytes(long rows, long Kp, int batch);
+template <class T>
+int slice_rows(cudaStream_t st, char op, int m, int k, const T *A, long lda, long sa, int batch, void *buf,
+               SlicedOp *out);
+template <class T>
+int slice_cols(cudaStream_t st, char op, int k, int n, const T *B, long ldb, long sb, int batch, void *buf,
+               SlicedOp *out);
+template <class T>
+int gemm_sliced_ops(cudaStream_t st, const SlicedOp &a, const SlicedOp &b, int batch, double alpha, int beta_one,
+                    T *C, long ldc, long sc, int *gerr);
+size_t gemm_sliced_k_work(bool cplx, int m, int n, int k, int batch);
+template <class T>
+int gemm_sliced_k(cudaStream_t st, char opa, char opb, int m, int n, int k, double alpha, const T *A, long lda,
+                  long sa, const T *B, long ldb, long sb, int beta_one, T *C, long ldc, long sc, int batch, void *work,
+                  size_t work_bytes, int *gerr);
 size_t zgemm_sliced_work(int m, int n, int batch, int S);
 template <class T>
 int zgemm_sliced(cudaStream_t st, int S, char opa, char opb, int m, int n, int k, double alpha, const T *A, long lda,

@@ -955,6 +955,589 @@ static int zgemm_sliced_run(cudaStream_t st, char opa, char opb, int m, int n, i
   return 0;
 }
 
+// ===================================================================
+// Sliced GEMM for any k (real or complex FP64 operands):
+//   C = alpha op(A) op(B) + beta C,  alpha in {+1, -1}, beta in {0, 1}.
+// Operands are sliced once into SK = 8 base-2^7 digits (56 bits relative to
+// the row / column maximum) laid out K-major in chunks of KC = 64 real
+// positions; a complex operand is embedded as real rows 2i = (Re, -Im),
+// 2i+1 = (Im, Re) against columns (Re, Im), interleaved per complex index p
+// (positions 2p, 2p+1), so any chunk holds whole complex terms.  The kernel
+// streams A and B chunks through TMA rings; per chunk the digit products of
+// each weight are summed exactly in an FP32 TMEM accumulator (64 terms of at
+// most 2^14 in magnitude per pair, at most 8 pairs: below 2^22), the
+// epilogue adds the chunk's sums into two 64-bit integers per entry (weights
+// 0-3 and 4-7), and after the last chunk forms the FP64 entry.
+// ===================================================================
+constexpr int SK = 8;                       // digits per operand
+constexpr int KC = 64;                      // real K positions per chunk
+constexpr int KBN = 32;                     // columns per tile
+constexpr int KA_STAGE = BM * KC * 2;       // one A slice of one chunk (16 KB)
+constexpr int KB_STAGE = SK * KBN * KC * 2; // all B slices of one chunk (32 KB)
+constexpr int KNA = 6, KNB = 3;             // ring depths
+constexpr int K_SMEM = KNA * KA_STAGE + KNB * KB_STAGE + 1024 + 512;
+constexpr int K_ACC = SK * KBN;             // TMEM columns of one accumulator buffer
+constexpr int KTHREADS = 320;               // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+
+template <class T> struct is_cplx { static constexpr bool v = false; };
+template <> struct is_cplx<zd> { static constexpr bool v = true; };
+
+// Element (i, p) of op(X) for a column-major X.
+template <class T>
+__device__ __forceinline__ void op_elem(char op, const T *X, long ldx, int i, int p, double &re, double &im) {
+  if constexpr (is_cplx<T>::v) {
+    const T v = (op == 'N') ? X[i + (long)p * ldx] : X[p + (long)i * ldx];
+    re = v.x;
+    im = (op == 'C') ? -v.y : v.y;
+  } else {
+    re = (op == 'N') ? X[i + (long)p * ldx] : X[p + (long)i * ldx];
+    im = 0.0;
+  }
+}
+
+// Digits d_0..d_{S-1} of rint(v 2^{7S - e}) (balanced, least significant
+// first; the leading digit takes what remains).
+template <int S>
+__device__ __forceinline__ void digits_of(double v, int e, float *d) {
+  int_digits<S>(fixed_point<S>(v, e), d);
+}
+
+// Rows of op(A) (m x k) -> slices [SK][batch][R][Kp] bf16 with R = m (real) or
+// 2m (complex embedding) and scale exponents [batch][R].  One warp per row of
+// op(A); lanes stride over p.
+template <class T>
+__global__ void slice_rows_kernel(char op, int m, int k, const T *A, long lda, long sa, int batch, int Kp,
+                                  __nv_bfloat16 *out, int *exps) {
+  constexpr bool CX = is_cplx<T>::v;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), b = blockIdx.y, lane = threadIdx.x & 31;
+  if (i >= m) return;  // warp-uniform
+  const T *Ab = A + (long)b * sa;
+  unsigned long long mb = 0;
+  for (int p = lane; p < k; p += 32) {
+    double re, im;
+    op_elem<T>(op, Ab, lda, i, p, re, im);
+    const unsigned long long a = (unsigned long long)__double_as_longlong(re) & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned long long c = (unsigned long long)__double_as_longlong(im) & 0x7FFFFFFFFFFFFFFFull;
+    mb = a > mb ? a : mb;
+    mb = c > mb ? c : mb;
+  }
+  const int e = scale_exp(warp_absmax_bits(__longlong_as_double((long long)mb), 0.0));
+  const long R = CX ? 2L * m : m;
+  const long plane = R * Kp;
+  for (int p = lane; p < k; p += 32) {
+    double re, im;
+    op_elem<T>(op, Ab, lda, i, p, re, im);
+    float dr[SK], di[SK];
+    digits_of<SK>(re, e, dr);
+    if constexpr (CX) {
+      digits_of<SK>(im, e, di);
+      for (int t = 0; t < SK; ++t) {
+        __nv_bfloat16 *o = out + ((long)t * batch + b) * plane + (2L * i) * Kp + 2 * p;
+        *reinterpret_cast<__nv_bfloat162 *>(o) = __floats2bfloat162_rn(dr[t], -di[t]);
+        *reinterpret_cast<__nv_bfloat162 *>(o + Kp) = __floats2bfloat162_rn(di[t], dr[t]);
+      }
+    } else {
+      for (int t = 0; t < SK; ++t) out[((long)t * batch + b) * plane + (long)i * Kp + p] = __float2bfloat16_rn(dr[t]);
+    }
+  }
+  const int kr = CX ? 2 * k : k;  // zero padding of positions kr .. Kp-1
+  for (int q = kr + lane; q < Kp; q += 32)
+    for (int t = 0; t < SK; ++t) {
+      __nv_bfloat16 *o = out + ((long)t * batch + b) * plane + (CX ? 2L * i : (long)i) * Kp + q;
+      *o = __float2bfloat16_rn(0.f);
+      if (CX) o[Kp] = __float2bfloat16_rn(0.f);
+    }
+  if (lane == 0) {
+    if (CX) {
+      exps[(long)b * R + 2 * i] = e;
+      exps[(long)b * R + 2 * i + 1] = e;
+    } else {
+      exps[(long)b * R + i] = e;
+    }
+  }
+}
+
+// Columns of op(B) (k x n) -> slices [SK][batch][n][Kp] bf16 (complex:
+// positions 2p, 2p+1 = Re, Im) and exponents [batch][n].  One warp per column.
+template <class T>
+__global__ void slice_cols_kernel(char op, int k, int n, const T *B, long ldb, long sb, int batch, int Kp,
+                                  __nv_bfloat16 *out, int *exps) {
+  constexpr bool CX = is_cplx<T>::v;
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), b = blockIdx.y, lane = threadIdx.x & 31;
+  if (c >= n) return;  // warp-uniform
+  const T *Bb = B + (long)b * sb;
+  // element (p, c) of op(B): N reads B[p + c ldb], T and C read B[c + p ldb]
+  auto elem = [&](int p, double &re, double &im) {
+    if constexpr (CX) {
+      const T v = (op == 'N') ? Bb[p + (long)c * ldb] : Bb[c + (long)p * ldb];
+      re = v.x;
+      im = (op == 'C') ? -v.y : v.y;
+    } else {
+      re = (op == 'N') ? Bb[p + (long)c * ldb] : Bb[c + (long)p * ldb];
+      im = 0.0;
+    }
+  };
+  unsigned long long mb = 0;
+  for (int p = lane; p < k; p += 32) {
+    double re, im;
+    elem(p, re, im);
+    const unsigned long long a = (unsigned long long)__double_as_longlong(re) & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned long long d = (unsigned long long)__double_as_longlong(im) & 0x7FFFFFFFFFFFFFFFull;
+    mb = a > mb ? a : mb;
+    mb = d > mb ? d : mb;
+  }
+  const int e = scale_exp(warp_absmax_bits(__longlong_as_double((long long)mb), 0.0));
+  const long plane = (long)n * Kp;
+  for (int p = lane; p < k; p += 32) {
+    double re, im;
+    elem(p, re, im);
+    float dr[SK], di[SK];
+    digits_of<SK>(re, e, dr);
+    if constexpr (CX) {
+      digits_of<SK>(im, e, di);
+      for (int t = 0; t < SK; ++t)
+        *reinterpret_cast<__nv_bfloat162 *>(out + ((long)t * batch + b) * plane + (long)c * Kp + 2 * p) =
+            __floats2bfloat162_rn(dr[t], di[t]);
+    } else {
+      for (int t = 0; t < SK; ++t) out[((long)t * batch + b) * plane + (long)c * Kp + p] = __float2bfloat16_rn(dr[t]);
+    }
+  }
+  const int kr = CX ? 2 * k : k;
+  for (int q = kr + lane; q < Kp; q += 32)
+    for (int t = 0; t < SK; ++t) out[((long)t * batch + b) * plane + (long)c * Kp + q] = __float2bfloat16_rn(0.f);
+  if (lane == 0) exps[(long)b * n + c] = e;
+}
+
+// Bias of the sums of (float bits of s_a + 1.5 2^23) 2^{7(3-a)} over four
+// weights, taken mod 2^64 (the same for weights 0-3 and 4-7).
+__host__ __device__ constexpr unsigned long long quad_bias() {
+  unsigned long long k = 0;
+  for (int a = 0; a < 4; ++a) k += 0x4B400000ull << (7 * (3 - a));
+  return k;
+}
+
+// Adds the 8 weight sums of 16 columns (this warp's 32 lanes) of one chunk:
+// weights 0-3 into hi, 4-7 into lo, each as sum_a bits_a 2^{7(3-(a mod 4))}.
+template <int A>
+__device__ __forceinline__ void add_chunk(unsigned long long *hi, unsigned long long *lo, uint32_t taddr) {
+  if constexpr (A < SK) {
+    uint32_t r0[16], r1[16];
+    const uint32_t t0 = taddr + (uint32_t)(A * KBN);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+        "[%16];"
+        : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3]), "=r"(r0[4]), "=r"(r0[5]), "=r"(r0[6]), "=r"(r0[7]),
+          "=r"(r0[8]), "=r"(r0[9]), "=r"(r0[10]), "=r"(r0[11]), "=r"(r0[12]), "=r"(r0[13]), "=r"(r0[14]),
+          "=r"(r0[15])
+        : "r"(t0));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+        "[%16];"
+        : "=r"(r1[0]), "=r"(r1[1]), "=r"(r1[2]), "=r"(r1[3]), "=r"(r1[4]), "=r"(r1[5]), "=r"(r1[6]), "=r"(r1[7]),
+          "=r"(r1[8]), "=r"(r1[9]), "=r"(r1[10]), "=r"(r1[11]), "=r"(r1[12]), "=r"(r1[13]), "=r"(r1[14]),
+          "=r"(r1[15])
+        : "r"(t0 + (uint32_t)KBN));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    constexpr int w0 = 7 * (3 - (A & 3)), w1 = w0 - 7;
+    unsigned long long *dst = (A < 4) ? hi : lo;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      dst[j] = add_shifted<w0>(dst[j], __float_as_uint(__uint_as_float(r0[j]) + 12582912.0f));
+      dst[j] = add_shifted<w1>(dst[j], __float_as_uint(__uint_as_float(r1[j]) + 12582912.0f));
+    }
+    add_chunk<A + 2>(hi, lo, taddr);
+  }
+}
+
+// Work item = (column chunk, 128-row block, batch); each tile (row block x
+// 32 columns) runs over all nkc K chunks.  Counters per CTA: h = chunks
+// processed (B ring stage h % KNB, accumulator buffer h % 2), h*SK + t =
+// A slices processed (A ring stage (h*SK+t) % KNA).
+template <class T, bool BETA>
+__global__ void __launch_bounds__(KTHREADS, 1)
+    gemm_sliced_k_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int R,
+                         int n, int batch, int nkc, int nch, int tpc, const int *__restrict__ sexp,
+                         const int *__restrict__ texp, double alpha, T *C, long ldc, long sc, int *gerr) {
+  constexpr bool CX = is_cplx<T>::v;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char *sA = base;                        // KNA x [128][64]
+  unsigned char *sB = base + KNA * KA_STAGE;       // KNB x SK x [32][64]
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + KNA * KA_STAGE + KNB * KB_STAGE);
+  uint64_t *a_full = bars, *a_empty = bars + KNA;
+  uint64_t *b_full = bars + 2 * KNA, *b_empty = b_full + KNB;
+  uint64_t *acc_full = b_empty + KNB, *acc_empty = acc_full + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nrb = (R + BM - 1) / BM, nct = (n + KBN - 1) / KBN;
+  const int items = nch * nrb * batch;
+  constexpr uint32_t NCOLS = 2 * K_ACC;  // 512
+
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < KNA; ++j) {
+      mbar_init(&a_full[j], 1);
+      mbar_init(&a_empty[j], 1);
+    }
+    for (int j = 0; j < KNB; ++j) {
+      mbar_init(&b_full[j], 1);
+      mbar_init(&b_empty[j], 1);
+    }
+    for (int j = 0; j < 2; ++j) {
+      mbar_init(&acc_full[j], 1);
+      mbar_init(&acc_empty[j], 8);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_u32(tmem_slot)),
+                 "r"(NCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ TMA --
+    long h = 0;
+    long last_a = -1, last_b = -1;
+    bool ok = true;
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      const int cc = item % nch, rb = (item / nch) % nrb, b = item / (nch * nrb);
+      const int ct1 = min(nct, (cc + 1) * tpc);
+      for (int ct = cc * tpc; ct < ct1 && ok; ++ct)
+        for (int c = 0; c < nkc && ok; ++c, ++h) {
+          const int sb = (int)(h % KNB);
+          if (h >= KNB && !mbar_wait(&b_empty[sb], (uint32_t)((h / KNB - 1) & 1), abort_flag, gerr, 41)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&b_full[sb], KB_STAGE);
+          for (int u = 0; u < SK; ++u)
+            tma_load_3d(sB + sb * KB_STAGE + u * (KBN * KC * 2), &tb, &b_full[sb], c * KC, ct * KBN, u * batch + b);
+          last_b = h;
+          for (int t = 0; t < SK; ++t) {
+            const long ga = h * SK + t;
+            const int sa = (int)(ga % KNA);
+            if (ga >= KNA && !mbar_wait(&a_empty[sa], (uint32_t)((ga / KNA - 1) & 1), abort_flag, gerr, 42)) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(&a_full[sa], KA_STAGE);
+            tma_load_3d(sA + sa * KA_STAGE, &ta, &a_full[sa], c * KC, rb * BM, t * batch + b);
+            last_a = ga;
+          }
+        }
+    }
+    for (long gg = (last_a - KNA + 1 > 0 ? last_a - KNA + 1 : 0); gg <= last_a; ++gg)
+      mbar_drain(&a_full[gg % KNA], (uint32_t)((gg / KNA) & 1), gerr, 43);
+    for (long gg = (last_b - KNB + 1 > 0 ? last_b - KNB + 1 : 0); gg <= last_b; ++gg)
+      mbar_drain(&b_full[gg % KNB], (uint32_t)((gg / KNB) & 1), gerr, 44);
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA --
+    long h = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      const int cc = item % nch;
+      const int ct1 = min(nct, (cc + 1) * tpc);
+      for (int ct = cc * tpc; ct < ct1 && ok; ++ct)
+        for (int c = 0; c < nkc; ++c) {
+          const int sb = (int)(h % KNB), buf = (int)(h & 1);
+          if (!mbar_wait(&b_full[sb], (uint32_t)((h / KNB) & 1), abort_flag, gerr, 45) ||
+              (h >= 2 && !mbar_wait(&acc_empty[buf], (uint32_t)(((h >> 1) - 1) & 1), abort_flag, gerr, 46))) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t dbase = tmem + (uint32_t)(buf * K_ACC);
+          const uint64_t bd = sdesc_sw128(sm_u32(sB + sb * KB_STAGE));
+          bool issued = false;
+#pragma unroll
+          for (int t = 0; t < SK; ++t) {
+            const long ga = h * SK + t;
+            const int sa = (int)(ga % KNA);
+            if (!mbar_wait(&a_full[sa], (uint32_t)((ga / KNA) & 1), abort_flag, gerr, 47)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t idesc = idesc_bf16_n((SK - t) * KBN);
+            const uint64_t ad = sdesc_sw128(sm_u32(sA + sa * KA_STAGE));
+#pragma unroll
+            for (int kk = 0; kk < KC / 16; ++kk)
+              mma_bf16(dbase + (uint32_t)(t * KBN), ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                       (t > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(&a_empty[sa]);
+            issued = true;
+          }
+          if (!ok) {
+            if (issued) {
+              mma_commit(&acc_full[buf]);
+              ++h;
+            }
+            break;
+          }
+          mma_commit(&b_empty[sb]);
+          mma_commit(&acc_full[buf]);
+          ++h;
+        }
+    }
+    if (h > 0) mbar_drain(&acc_full[(h - 1) & 1], (uint32_t)(((h - 1) >> 1) & 1), gerr, 48);
+  } else if (warp >= 2) {
+    // ------------------------------------------------------- epilogue --
+    // Warp w reads TMEM lanes 32 (w % 4) .. +31 and columns c0 .. c0+15 of
+    // every tile, c0 = 16 ((w - 2) / 4).
+    const int q = warp & 3, c0 = ((warp - 2) >> 2) * 16;
+    const bool neg = alpha < 0.0;
+    long h = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      const int cc = item % nch, rb = (item / nch) % nrb, b = item / (nch * nrb);
+      const int ct1 = min(nct, (cc + 1) * tpc);
+      const int r = rb * BM + q * 32 + lane;
+      const bool rv = r < R;
+      const int es = rv ? __ldg(sexp + (long)b * R + r) - 7 * (SK + 1) : 0;
+      double *crow = CX ? reinterpret_cast<double *>(C + (long)b * sc + (r >> 1)) + (r & 1)
+                        : reinterpret_cast<double *>(C + (long)b * sc + r);
+      const long cstride = CX ? 2L * ldc : ldc;  // doubles between columns
+      for (int ct = cc * tpc; ct < ct1 && ok; ++ct) {
+        const int col0 = ct * KBN + c0;
+        const int tcol = (col0 + (lane & 15) < n) ? __ldg(texp + (long)b * n + col0 + (lane & 15)) : 0;
+        unsigned long long hi[16], lo[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0ull;
+        for (int c = 0; c < nkc; ++c, ++h) {
+          const int buf = (int)(h & 1);
+          int okw = 0;
+          if (lane == 0) okw = mbar_wait(&acc_full[buf], (uint32_t)((h >> 1) & 1), abort_flag, gerr, 49) ? 1 : 0;
+          if (__shfl_sync(0xffffffffu, okw, 0) == 0) {
+            ok = false;
+            break;
+          }
+          __syncwarp();
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          add_chunk<0>(hi, lo, tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * K_ACC + c0));
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(&acc_empty[buf])) : "memory");
+        }
+        if (!ok) break;
+        // value = (hi 2^28 + lo) 2^{es+et}: top = hi + floor(lo / 2^28) and
+        // rem = lo mod 2^28 are exact; top converts with one rounding, and
+        // one fused multiply-add joins them
+        const unsigned long long bias = (unsigned long long)nkc * quad_bias();
+        int et[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) et[j] = __shfl_sync(0xffffffffu, tcol, j);
+        const bool fast = __reduce_min_sync(0xffffffffu, es) + __reduce_min_sync(0xffffffffu, tcol) >= -1022 &&
+                          __reduce_max_sync(0xffffffffu, es) + __reduce_max_sync(0xffffffffu, tcol) <= 995;
+#pragma unroll
+        for (int j0 = 0; j0 < 16; j0 += 8) {
+          double cur[8];  // C of these 8 columns, loaded ahead of their conversions
+          if constexpr (BETA) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              cur[j] = (rv && col0 + j0 + j < n) ? crow[(long)(col0 + j0 + j) * cstride] : 0.0;
+          }
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int j = j0 + jj;
+          const long long hs = (long long)(hi[j] - bias), ls = (long long)(lo[j] - bias);
+          const long long top = hs + (ls >> 28);
+          const long long rem = ls & ((1LL << 28) - 1);
+          const int E = es + et[j];
+          double p28, p0;
+          if (fast) {
+            p28 = __longlong_as_double((long long)(E + 28 + 1023) << 52);
+            p0 = __longlong_as_double((long long)(E + 1023) << 52);
+          } else {
+            p28 = ldexp(1.0, E + 28);
+            p0 = ldexp(1.0, E);
+          }
+          double v = fma(__ll2double_rn(top), p28, __ll2double_rn(rem) * p0);
+          if (neg) v = -v;
+          if (rv && col0 + j < n) crow[(long)(col0 + j) * cstride] = BETA ? cur[jj] + v : v;
+        }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS) : "memory");
+}
+
+// 3-D map over [planes][rows][Kp] bf16, box (KC, box_rows, 1).
+static int make_map_k(CUtensorMap *map, const void *ptr, long rows, long Kp, int planes, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled unavailable");
+    return -4;
+  }
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2};
+  cuuint32_t box[3] = {(cuuint32_t)KC, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return -4;
+  }
+  return 0;
+}
+
+template <class T>
+static int gemm_sliced_k_launch(cudaStream_t st, const SlicedOp &a, const SlicedOp &b, int batch, double alpha,
+                                int beta_one, T *C, long ldc, long sc, int *gerr) {
+  if (a.Kp != b.Kp || a.Kp % KC) {
+    set_error("sliced GEMM: operand K layouts differ");
+    return -4;
+  }
+  CUtensorMap ta, tb;
+  if (int rc = make_map_k(&ta, a.slices, a.rows, a.Kp, SK * batch, BM)) return rc;
+  if (int rc = make_map_k(&tb, b.slices, b.rows, b.Kp, SK * batch, KBN)) return rc;
+  static bool attr = false;
+  if (!attr) {
+    GBF_CUDA(cudaFuncSetAttribute(gemm_sliced_k_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  K_SMEM));
+    GBF_CUDA(cudaFuncSetAttribute(gemm_sliced_k_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  K_SMEM));
+    attr = true;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int base_items = ceil_div(a.rows, (long)BM) * batch, nct = ceil_div(b.rows, KBN);
+  const int want = std::max(1, std::min(nct, ceil_div(2 * sms, base_items)));
+  const int tpc = ceil_div(nct, want), nch = ceil_div(nct, tpc);
+  const int items = base_items * nch;
+  const int nkc = (int)(a.Kp / KC);
+  dim3 grid(std::min(items, sms));
+  if (beta_one)
+    gemm_sliced_k_kernel<T, true><<<grid, KTHREADS, K_SMEM, st>>>(ta, tb, (int)a.rows, (int)b.rows, batch, nkc, nch,
+                                                                   tpc, a.exps, b.exps, alpha, C, ldc, sc, gerr);
+  else
+    gemm_sliced_k_kernel<T, false><<<grid, KTHREADS, K_SMEM, st>>>(ta, tb, (int)a.rows, (int)b.rows, batch, nkc,
+                                                                    nch, tpc, a.exps, b.exps, alpha, C, ldc, sc, gerr);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+
+
+}  // namespace tc
+
+long sliced_kp(int k, bool cplx) {
+  const long kr = cplx ? 2L * k : (long)k;
+  return (kr + tc::KC - 1) / tc::KC * tc::KC;
+}
+size_t sliced_op_bytes(long rows, long Kp, int batch) {
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  return al((size_t)tc::SK * batch * rows * Kp * 2) + al((size_t)batch * rows * 4);
+}
+
+template <class T>
+int slice_rows(cudaStream_t st, char op, int m, int k, const T *A, long lda, long sa, int batch, void *buf,
+               SlicedOp *out) {
+  constexpr bool CX = tc::is_cplx<T>::v;
+  const long R = CX ? 2L * m : m, Kp = sliced_kp(k, CX);
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  out->slices = buf;
+  out->exps = (const int *)((char *)buf + al((size_t)tc::SK * batch * R * Kp * 2));
+  out->rows = R;
+  out->Kp = Kp;
+  const int slot = prof_begin(st);
+  tc::slice_rows_kernel<T><<<dim3(ceil_div(m, 8), batch), 256, 0, st>>>(
+      op, m, k, A, lda, sa, batch, (int)Kp, (__nv_bfloat16 *)buf, const_cast<int *>(out->exps));
+  prof_end(st, slot, 0.0);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+
+template <class T>
+int slice_cols(cudaStream_t st, char op, int k, int n, const T *B, long ldb, long sb, int batch, void *buf,
+               SlicedOp *out) {
+  constexpr bool CX = tc::is_cplx<T>::v;
+  const long Kp = sliced_kp(k, CX);
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  out->slices = buf;
+  out->exps = (const int *)((char *)buf + al((size_t)tc::SK * batch * n * Kp * 2));
+  out->rows = n;
+  out->Kp = Kp;
+  const int slot = prof_begin(st);
+  tc::slice_cols_kernel<T><<<dim3(ceil_div(n, 8), batch), 256, 0, st>>>(
+      op, k, n, B, ldb, sb, batch, (int)Kp, (__nv_bfloat16 *)buf, const_cast<int *>(out->exps));
+  prof_end(st, slot, 0.0);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+
+template <class T>
+int gemm_sliced_ops(cudaStream_t st, const SlicedOp &a, const SlicedOp &b, int batch, double alpha, int beta_one,
+                    T *C, long ldc, long sc, int *gerr) {
+  if (alpha != 1.0 && alpha != -1.0) {
+    set_error("sliced GEMM: alpha must be +1 or -1");
+    return -4;
+  }
+  if (a.rows <= 0 || b.rows <= 0 || batch <= 0) return 0;
+  const int slot = prof_begin(st);
+  const int rc = tc::gemm_sliced_k_launch<T>(st, a, b, batch, alpha, beta_one, C, ldc, sc, gerr);
+  // useful FP64 flops (padded K): the real embedding's 2 R n Kp equals 8 m n k for complex data
+  prof_end(st, slot, 2.0 * a.rows * (double)b.rows * a.Kp * batch);
+  return rc;
+}
+
+size_t gemm_sliced_k_work(bool cplx, int m, int n, int k, int batch) {
+  const long Kp = sliced_kp(k, cplx);
+  return sliced_op_bytes(cplx ? 2L * m : m, Kp, batch) + sliced_op_bytes(n, Kp, batch);
+}
+
+template <class T>
+int gemm_sliced_k(cudaStream_t st, char opa, char opb, int m, int n, int k, double alpha, const T *A, long lda,
+                  long sa, const T *B, long ldb, long sb, int beta_one, T *C, long ldc, long sc, int batch, void *work,
+                  size_t work_bytes, int *gerr) {
+  constexpr bool CX = tc::is_cplx<T>::v;
+  if (m <= 0 || n <= 0 || batch <= 0) return 0;
+  if (k < 1) {
+    set_error("sliced GEMM: k must be positive");
+    return -4;
+  }
+  if (gemm_sliced_k_work(CX, m, n, k, batch) > work_bytes) {
+    set_error("sliced GEMM: workspace too small");
+    return -4;
+  }
+  const long Kp = sliced_kp(k, CX);
+  SlicedOp a, b;
+  if (int rc = slice_rows<T>(st, opa, m, k, A, lda, sa, batch, work, &a)) return rc;
+  if (int rc = slice_cols<T>(st, opb, k, n, B, ldb, sb, batch,
+                             (char *)work + sliced_op_bytes(CX ? 2L * m : m, Kp, batch), &b))
+    return rc;
+  return gemm_sliced_ops<T>(st, a, b, batch, alpha, beta_one, C, ldc, sc, gerr);
+}
+
+#define GBF_SLICED_INST(T)                                                                                   \
+  template int slice_rows<T>(cudaStream_t, char, int, int, const T *, long, long, int, void *, SlicedOp *);  \
+  template int slice_cols<T>(cudaStream_t, char, int, int, const T *, long, long, int, void *, SlicedOp *);  \
+  template int gemm_sliced_ops<T>(cudaStream_t, const SlicedOp &, const SlicedOp &, int, double, int, T *,  \
+                                  long, long, int *);                                                        \
+  template int gemm_sliced_k<T>(cudaStream_t, char, char, int, int, int, double, const T *, long, long,      \
+                                const T *, long, long, int, T *, long, long, int, void *, size_t, int *);
+GBF_SLICED_INST(double)
+GBF_SLICED_INST(zd)
+#undef GBF_SLICED_INST
+
+namespace tc {
 }  // namespace tc
 
 size_t zgemm_sliced_work(int m, int n, int batch, int S) {
@@ -1093,4 +1676,26 @@ extern "C" int gbf_zgemm_sliced_noalloc(void *stream, int prec, int S, char opa,
     return -5;
   }
   return 0;
+}
+
+// Verification entry (C ABI) of the sliced GEMM for any k: dC = alpha op(dA)
+// op(dB) + beta dC on FP64 data, real (cplx 0) or complex interleaved
+// (cplx 1), op in {'N','T','C'}, alpha = +-1, beta in {0, 1}, batches
+// strided by sa/sb/sc elements.  dWork >= gbf_gemm_sliced_work bytes; dErr
+// one device int.
+extern "C" size_t gbf_gemm_sliced_work(int cplx, int m, int n, int k, int batch) {
+  return gbf::gemm_sliced_k_work(cplx != 0, m, n, k, batch);
+}
+extern "C" int gbf_gemm_sliced(void *stream, int cplx, char opa, char opb, int m, int n, int k, double alpha,
+                               const void *dA, long lda, long sa, const void *dB, long ldb, long sb, int beta,
+                               void *dC, long ldc, long sc, int batch, void *dWork, size_t work_bytes, int *dErr) {
+  cudaStream_t st = (cudaStream_t)stream;
+  GBF_CUDA(cudaMemsetAsync(dErr, 0, sizeof(int), st));
+  int rc = cplx ? gbf::gemm_sliced_k<gbf::zd>(st, opa, opb, m, n, k, alpha, (const gbf::zd *)dA, lda, sa,
+                                               (const gbf::zd *)dB, ldb, sb, beta, (gbf::zd *)dC, ldc, sc, batch,
+                                               dWork, work_bytes, dErr)
+                : gbf::gemm_sliced_k<double>(st, opa, opb, m, n, k, alpha, (const double *)dA, lda, sa,
+                                             (const double *)dB, ldb, sb, beta, (double *)dC, ldc, sc, batch, dWork,
+                                             work_bytes, dErr);
+  return rc;
 }

@@ -59,3 +59,38 @@ def test_zgemm_sliced(gbf, S, prec, m, n, k, batch, opa, opb, alpha, beta):
         tol = max(tol, 1e-6 * k)   # FP32 output rounding
     for gt, rf in zip(got, ref):
         assert (gt - rf).abs().max().item() <= tol * (1 + rf.abs().max().item()), (gt - rf).abs().max().item()
+
+
+@pytest.mark.parametrize("cplx", [0, 1])
+@pytest.mark.parametrize("m,n,k,batch", [(1, 1, 1, 1), (37, 33, 7, 2), (200, 100, 100, 1), (300, 70, 257, 2),
+                                         (130, 300, 1000, 1)])
+@pytest.mark.parametrize("opa,opb", [("N", "N"), ("T", "N"), ("C", "N"), ("N", "C")])
+@pytest.mark.parametrize("alpha,beta", [(-1.0, 1), (1.0, 0)])
+def test_gemm_sliced_any_k(gbf, cplx, m, n, k, batch, opa, opb, alpha, beta):
+    """FP64-class sliced GEMM for any k against an FP64 product: error within a
+    few units of k * 2^-53 * max|A| max|B| (8 digits: 56 bits per operand)."""
+    import torch
+
+    g = torch.Generator(device="cuda").manual_seed(11 * m + 5 * n + k + cplx)
+
+    def rnd(r, c):
+        x = torch.randn((r, c), device="cuda", dtype=torch.float64, generator=g)
+        if cplx:
+            x = torch.complex(x, torch.randn((r, c), device="cuda", dtype=torch.float64, generator=g))
+        return x
+
+    As = [rnd(m, k) if opa == "N" else rnd(k, m) for _ in range(batch)]
+    Bs = [rnd(k, n) if opb == "N" else rnd(n, k) for _ in range(batch)]
+    Cs = [rnd(m, n) for _ in range(batch)]
+    A, B, Cd = colmajor_batch(torch, As), colmajor_batch(torch, Bs), colmajor_batch(torch, Cs)
+    op = {"N": lambda x: x, "T": lambda x: x.t(), "C": lambda x: x.conj().t()}
+    ref = [alpha * (op[opa](a) @ op[opb](b)) + beta * c for a, b, c in zip(As, Bs, Cs)]
+    rc = gbf.gemm_sliced(opa, opb, A, B, Cd, alpha=alpha, beta=beta)
+    torch.cuda.synchronize()
+    assert rc == 0, gbf.last_error()
+    kr = (2 if cplx else 1) * k
+    for i in range(batch):
+        got = Cd[i].t()
+        scale = As[i].abs().max().item() * Bs[i].abs().max().item()
+        tol = 4 * kr * 2.0 ** -53 * scale + 2.0 ** -52 * ref[i].abs().max().item()
+        assert (got - ref[i]).abs().max().item() <= tol, ((got - ref[i]).abs().max().item(), tol)
