@@ -253,6 +253,8 @@ template <class TQ, class TL> struct WS {
   size_t tcw_bytes;
   int *tc_err;
   void *pja, *pjb, *pjq;  // sliced operands of the projections: A, B (rows), Q / Y (columns)
+  void *kw;               // any-k sliced updates of the recursive solves
+  size_t kw_bytes;
 
   void layout(Bump &b, int n, int m0, int ne, int bs, bool herm, bool hasB, bool needAf, bool needBf,
               int ksplit, int tcS, bool proj) {
@@ -314,6 +316,8 @@ template <class TQ, class TL> struct WS {
     tcw_bytes = tcS ? std::max(zgemm_sliced_work(n, n, ne, tcS), zgemm_sliced_work(n, m0, ne, tcS)) : 0;
     tcw = tcS ? (void *)b.take<char>(tcw_bytes) : nullptr;
     tc_err = b.take<int>(4);
+    kw_bytes = tcS ? solve_kwork_bytes(n, m0, bs, ne) : 0;
+    kw = tcS ? (void *)b.take<char>(kw_bytes) : nullptr;
     pja = pjb = pjq = nullptr;
     if (proj) {
       const bool cx = sizeof(TQ) == sizeof(zd);
@@ -391,6 +395,8 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
   tcx.bytes = ws.tcw_bytes;
   tcx.gerr = ws.tc_err;
   tcx.S = tcS;
+  tcx.kwork = ws.kw;
+  tcx.kbytes = ws.kw_bytes;
   TcScope tc_scope(tcS ? &tcx : nullptr);
   if (ensure_hbuf(h, (size_t)std::max(m0, ne) + 64)) return out.info = -1;
   h->f_prec = -1;

@@ -158,7 +158,12 @@ struct TcCtx {
   size_t bytes = 0;
   int *gerr = nullptr;
   int S = 0;
+  void *kwork = nullptr;  // workspace of the any-k sliced GEMMs of the recursive solves
+  size_t kbytes = 0;
 };
+// Workspace bytes of the recursive solves' any-k sliced updates for n x n
+// factors, nrhs right-hand sides, block size bs (node groups of 2).
+size_t solve_kwork_bytes(int n, int nrhs, int bs, int ne);
 extern thread_local TcCtx *g_tc;
 struct TcScope {
   TcCtx *prev;

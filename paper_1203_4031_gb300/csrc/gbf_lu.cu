@@ -18,6 +18,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "gbf_common.cuh"
 
@@ -509,6 +510,70 @@ int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T 
 }
 
 // ---------------------------------------------------------------- solves --
+size_t solve_kwork_bytes(int n, int nrhs, int bs, int ne) {
+  const int nblk = ceil_div(n, bs);
+  const int half = std::min(n, (nblk - nblk / 2) * bs);  // largest update: rows and K at most this
+  return gemm_sliced_k_work(true, half, nrhs, half, std::min(ne, 2));
+}
+
+// C[e] -= op(A[e]) Y[e] for all nodes e with the any-k sliced GEMM, nodes
+// grouped so that each group's slices fit the workspace.
+template <class T>
+static int sliced_update(cudaStream_t st, char opa, int m, int k, int nrhs, const T *A, long lda, long sa,
+                         const T *Y, long ldy, long sy, T *C, long ldc, long sc, int ne) {
+  const size_t per = gemm_sliced_k_work(true, m, nrhs, k, 1);
+  const int g = (int)std::max<size_t>(1, std::min<size_t>(ne, g_tc->kbytes / std::max<size_t>(per, 1)));
+  for (int e0 = 0; e0 < ne; e0 += g) {
+    const int gb = std::min(g, ne - e0);
+    const int rc = gemm_sliced_k<T>(st, opa, 'N', m, nrhs, k, -1.0, A + (long)e0 * sa, lda, sa, Y + (long)e0 * sy,
+                                    ldy, sy, 1, C + (long)e0 * sc, ldc, sc, gb, g_tc->kwork, g_tc->kbytes, g_tc->gerr);
+    if (rc) return rc;
+  }
+  return 0;
+}
+
+// Recursive triangular solves (FP64 factors on the tensor-core engine): the
+// block range [b0, b1) splits in halves; the off-diagonal update between
+// them is one any-k GEMM (K up to n/2), the leaves multiply by the inverted
+// diagonal blocks.  Same operations as the blocked sweep, regrouped so that
+// almost all the work sits in a few large-K products.
+//   kind 0: L (unit lower), forward      kind 1: U (upper), backward
+//   kind 2: U^H (lower), forward         kind 3: L^H (unit upper), backward
+template <class T>
+static int trsv_rec(cudaStream_t st, int kind, int n, int ne, int nrhs, const T *S, const T *Dinv, int bs, T *Y,
+                    int b0, int b1) {
+  using X = tr<T>;
+  const long nn = (long)n * n, ny = (long)n * nrhs, sblk = (long)ceil_div(n, bs) * bs * bs;
+  const T one = X::one(), zero = X::zero(), m1 = X::sub(X::zero(), X::one());
+  if (b1 - b0 == 1) {
+    const int r0 = b0 * bs, bsz = std::min(bs, n - r0);
+    return gemm<T>(st, kind >= 2 ? 'C' : 'N', 'N', bsz, nrhs, bsz, one, Dinv + (long)b0 * bs * bs, bs, sblk,
+                   Y + r0, n, ny, zero, Y + r0, n, ny, ne);
+  }
+  const int mid = b0 + (b1 - b0) / 2;
+  const int r0 = b0 * bs, rm = mid * bs, r1 = std::min(n, b1 * bs);
+  const bool forward = (kind == 0 || kind == 2);
+  int rc;
+  if ((rc = trsv_rec<T>(st, kind, n, ne, nrhs, S, Dinv, bs, Y, forward ? b0 : mid, forward ? mid : b1))) return rc;
+  // the update: rows of the second half from the solved first half
+  const T *A;
+  char op;
+  int m, k, rdst, rsrc;
+  switch (kind) {
+    case 0: A = S + rm + (long)r0 * n; op = 'N'; m = r1 - rm; k = rm - r0; rdst = rm; rsrc = r0; break;
+    case 1: A = S + r0 + (long)rm * n; op = 'N'; m = rm - r0; k = r1 - rm; rdst = r0; rsrc = rm; break;
+    case 2: A = S + r0 + (long)rm * n; op = 'C'; m = r1 - rm; k = rm - r0; rdst = rm; rsrc = r0; break;
+    default: A = S + rm + (long)r0 * n; op = 'C'; m = rm - r0; k = r1 - rm; rdst = r0; rsrc = rm; break;
+  }
+  if (k > 32) {
+    rc = sliced_update<T>(st, op, m, k, nrhs, A, n, nn, Y + rsrc, n, ny, Y + rdst, n, ny, ne);
+  } else {
+    rc = gemm<T>(st, op, 'N', m, nrhs, k, m1, A, n, nn, Y + rsrc, n, ny, one, Y + rdst, n, ny, ne);
+  }
+  if (rc) return rc;
+  return trsv_rec<T>(st, kind, n, ne, nrhs, S, Dinv, bs, Y, forward ? mid : b0, forward ? b1 : mid);
+}
+
 template <class T>
 int getrs_inplace(cudaStream_t st, int trans, int n, int ne, int nrhs, const T *S, const T *Linv,
                   const T *Uinv, int bs, T *Y, T *) {
@@ -521,6 +586,16 @@ int getrs_inplace(cudaStream_t st, int trans, int n, int ne, int nrhs, const T *
   const T m1 = X::sub(X::zero(), X::one());
   const T zero = X::zero();
   int rc;
+  if constexpr (std::is_same<T, zd>::value) {
+    if (g_tc && g_tc->kwork) {
+      if (!trans) {
+        if ((rc = trsv_rec<T>(st, 0, n, ne, nrhs, S, Linv, bs, Y, 0, nblk))) return rc;
+        return trsv_rec<T>(st, 1, n, ne, nrhs, S, Uinv, bs, Y, 0, nblk);
+      }
+      if ((rc = trsv_rec<T>(st, 2, n, ne, nrhs, S, Uinv, bs, Y, 0, nblk))) return rc;
+      return trsv_rec<T>(st, 3, n, ne, nrhs, S, Linv, bs, Y, 0, nblk);
+    }
+  }
   auto blk = [&](int b) { return std::min(bs, n - b * bs); };
   if (!trans) {
     // L (unit lower): Y_b <- Linv_b Y_b ; Y_below -= L_{below,b} Y_b
