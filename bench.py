@@ -174,7 +174,7 @@ def run_gbf(args):
         ms = e0.elapsed_time(e1)
         launches = g.launch_count() - l0
         cl = clocks.stop() if clocks else None
-        prof = None
+        prof = tc = None
         if profile:
             import ctypes as C
 
@@ -185,6 +185,9 @@ def run_gbf(args):
                 nl, t, fl = C.c_longlong(), C.c_double(), C.c_double()
                 L.gbf_profile_read(c, C.byref(nl), C.byref(t), C.byref(fl))
                 prof[L.gbf_profile_name(c).decode()] = (nl.value, t.value, fl.value)
+            nl, t, fl, tf = C.c_longlong(), C.c_double(), C.c_double(), C.c_double()
+            L.gbf_profile_tc(C.byref(nl), C.byref(t), C.byref(fl), C.byref(tf))
+            tc = (nl.value, t.value, fl.value, tf.value)
             L.gbf_profile(0)
         r = rs[-1]
         if any(x["info"] != 0 for x in rs):
@@ -196,7 +199,7 @@ def run_gbf(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dist.all_reduce(tot, op=dist.ReduceOp.SUM)
         return dict(ms=t.item(), pairs=tot.item(), M=r["M"], ok=ok, worst=worst, loop=r["loop"],
-                    launches=launches, prof=prof, clocks=cl)
+                    launches=launches, prof=prof, tc=tc, clocks=cl)
 
     if args.only == "mixed":
         mx = timed(1, args.steps, args.warmup)
@@ -209,17 +212,19 @@ def run_gbf(args):
     # profiled step gives the per-category kernel times
     clocks = ClockSampler(local)
     fp = timed(0, args.steps, args.warmup, clocks=clocks)
-    fp["prof"] = timed(0, 1, 0, profile=True)["prof"]
+    pr = timed(0, 1, 0, profile=True)
+    fp["prof"], fp["tc"] = pr["prof"], pr["tc"]
     value = fp["pairs"] / (fp["ms"] / 1e3)
     mixed = None
     if not args.no_mixed and args.only is None:
         mx = timed(1, args.steps, args.warmup)
-        mx["prof"] = timed(1, 1, 0, profile=True)["prof"]
+        pr = timed(1, 1, 0, profile=True)
+        mx["prof"], mx["tc"] = pr["prof"], pr["tc"]
         mixed = {"value": mx["pairs"] / (mx["ms"] / 1e3), "ms_per_step": mx["ms"] / args.steps,
                  "M": mx["M"], "loops": mx["loop"], "max_rel_residual": mx["worst"],
                  "gpu_launches": mx["launches"], "dtype": "c32 factor/solve + f64 correction",
                  "kernels_ms": {k: round(v[1], 3) for k, v in mx["prof"].items()},
-                 "roofline": roofline(mx["prof"], "mixed")}
+                 "roofline": roofline(mx["prof"], mx["tc"], "mixed")}
 
     # end to end through the host-pointer C entry (pinned host buffers)
     e2e = None
@@ -259,7 +264,7 @@ def run_gbf(args):
                        "l2": "inputs A,B (2 x 134 MB) exceed L2 (129 MB)"},
             "max_rel_residual": fp["worst"], "gpu_launches": fp["launches"],
             "kernels_ms": {k: round(v[1], 3) for k, v in fp["prof"].items()},
-            "roofline": roofline(fp["prof"], "fp64"),
+            "roofline": roofline(fp["prof"], fp["tc"], "fp64"),
             "clocks": fp["clocks"], "e2e": e2e, "mixed": mixed, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -276,30 +281,39 @@ def measured_peaks():
         return {}
 
 
-def roofline(prof, path):
-    """Dominant category by device time.  The factor/solve GEMMs run on the
-    tensor cores as sliced products (S digits: S(S+1)/2 bf16 digit-pair
-    GEMMs of the real 2m x n x 2k embedding, i.e. S(S+1)/2 x the complex
-    flop count); they are rated against the measured bf16 tensor peak with
-    the bf16 flops they issue, and the complex flops they deliver are
-    reported beside ("useful").  The FP64 projection / reduced eigensolver
-    run on the FP64 ALUs (nominal 1.25 TFLOP/s)."""
-    name, (nl, ms, fl) = max(prof.items(), key=lambda kv: kv[1][1])
-    if ms <= 0:
-        return None
-    useful = fl / (ms / 1e3)
-    if name in ("lu_update_gemm", "solve_gemm"):
-        S = 7 if path == "fp64" else 3
-        issued = useful * S * (S + 1) / 2
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+# the sliced GEMM kernel on the solve shape 4096 x 300 x 32, 8 nodes (the
+# capture in profiles/), or None when the kernel changed since it was taken
+SLICED_TRAFFIC_BYTES = None
+
+
+def roofline(prof, tc, path):
+    """Dominant kernel by device time.  The FP64 factor / solve / projection
+    products run as sliced tensor-core GEMMs (zgemm_sliced_kernel for k <= 32,
+    7 digits; gemm_sliced_k_kernel for any k, 8 digits): their work is the
+    digit-pair bf16 products they issue (S(S+1)/2 products of each padded
+    128 x 32 x 64 tile), rated against the measured bf16 tensor peak; the
+    FP64 flops they deliver are reported beside as "useful".  The other
+    kernels run on the FP64 ALUs (nominal 1.25 TFLOP/s)."""
+    tn, tms, tfl, ttf = tc
+    other = {k: v for k, v in prof.items() if k not in ("lu_update_gemm", "solve_gemm")}
+    oname, (onl, oms, ofl) = max(other.items(), key=lambda kv: kv[1][1])
+    if tms > 0 and tms >= oms:
         pk = measured_peaks().get("bf16_tflops_sustained", 1721.2) * 1e12
-        return {"kernel": name + " (sliced tcgen05)", "bound": "tensor", "achieved": issued / 1e12,
-                "peak": pk / 1e12, "unit": "TFLOP/s", "frac": issued / pk, "traffic": None,
-                "useful_complex_tflops": useful / 1e12, "digits": S, "launches": nl,
-                "avg_launch_ms": ms / max(nl, 1),
+        ach = ttf / (tms / 1e3)
+        return {"kernel": "sliced tensor-core GEMMs (zgemm_sliced_kernel, gemm_sliced_k_kernel)",
+                "bound": "tensor", "achieved": ach / 1e12, "peak": pk / 1e12, "unit": "TFLOP/s",
+                "frac": ach / pk, "traffic": SLICED_TRAFFIC_BYTES,
+                "useful_fp64_tflops": tfl / (tms / 1e3) / 1e12, "launches": tn,
+                "avg_launch_ms": tms / max(tn, 1), "ms_per_step": tms,
                 "peak_source": "measured bf16 sustained (MEASURED_PEAKS.json), of measured"}
-    return {"kernel": name, "bound": "alu", "achieved": useful / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
-            "unit": "TFLOP/s", "frac": useful / FP64_PEAK_NOMINAL, "traffic": None, "launches": nl,
-            "avg_launch_ms": ms / max(nl, 1), "peak_source": "nominal FP64 1.25 TFLOP/s (GB300 table)"}
+    if oms <= 0:
+        return None
+    useful = ofl / (oms / 1e3)
+    return {"kernel": oname, "bound": "alu", "achieved": useful / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
+            "unit": "TFLOP/s", "frac": useful / FP64_PEAK_NOMINAL, "traffic": None, "launches": onl,
+            "avg_launch_ms": oms / max(onl, 1), "ms_per_step": oms,
+            "peak_source": "nominal FP64 1.25 TFLOP/s (GB300 table), of fallback nominal"}
 
 
 # ------------------------------------------------------------- CPU oracle --

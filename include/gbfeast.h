@@ -85,6 +85,11 @@ int gbf_profile(int enable);
 int gbf_profile_categories(void);
 const char *gbf_profile_name(int cat);
 int gbf_profile_read(int cat, long long *launches, double *ms, double *flops);
+/* The sliced tensor-core GEMM kernels alone (all categories, slicing
+ * excluded): timed launches, milliseconds, useful flops (as above) and the
+ * bf16 tensor-core flops they issue (digit-pair products over the padded
+ * tiles).  Returns 0 or -4. */
+int gbf_profile_tc(long long *launches, double *ms, double *flops, double *tensor_flops);
 
 /* Handle for the current CUDA device.  Returns 0, or -1 (allocation) / -4. */
 int gbf_create(gbf_handle *h);

@@ -146,6 +146,9 @@ struct CatScope {
 bool prof_on();
 int prof_begin(cudaStream_t st);                      // slot or -1
 void prof_end(cudaStream_t st, int slot, double flops);
+// same for a sliced tensor-core GEMM kernel: useful flops and issued bf16 tensor flops
+void prof_end_tc(cudaStream_t st, int slot, double flops, double tensor_flops);
+void prof_set_flops(int slot, double flops);  // flops known only after the launch
 
 // ------------------------------------------------------------------ GEMM --
 // Tensor-core engine for complex GEMMs with k <= 32 (LU trailing updates and

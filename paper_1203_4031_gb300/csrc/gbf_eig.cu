@@ -93,11 +93,12 @@ int heev_jacobi(cudaStream_t st, int m, T *A, double *w, T *V, T *work, double *
   permute_cols_kernel<T><<<gp, 128, 0, st>>>(m, m, rank, V, m, work, m);
   GBF_LAUNCHED();
   GBF_CUDA(cudaMemcpyAsync(V, work, sizeof(T) * (size_t)m * m, cudaMemcpyDeviceToDevice, st));
-  if (sweeps_out) {
-    GBF_CUDA(cudaMemcpyAsync(hflag, iwork + 2 * m + maxsw, sizeof(int), cudaMemcpyDeviceToHost, st));
-    GBF_CUDA(cudaStreamSynchronize(st));
-    *sweeps_out = *hflag;
-  }
+  GBF_CUDA(cudaMemcpyAsync(hflag, iwork + 2 * m + maxsw, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GBF_CUDA(cudaStreamSynchronize(st));
+  if (sweeps_out) *sweeps_out = *hflag;
+  // per round every entry of A (up to 4 multiply-adds) and V (2) is rewritten
+  const int P = m + (m & 1);
+  prof_set_flops(slot, (double)(*hflag + 1) * (P - 1) * (double)m * m * (tr<T>::cplx ? 4.0 : 1.0) * 12.0);
   GBF_CUDA(cudaGetLastError());
   return 0;
 }

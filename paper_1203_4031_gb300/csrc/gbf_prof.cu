@@ -15,6 +15,8 @@ struct Rec {
   cudaEvent_t a, b;
   int cat;
   double flops;
+  int tc;          // 1: a sliced tensor-core GEMM kernel
+  double tflops;   // bf16 tensor flops it issues
 };
 std::mutex mu;
 bool enabled = false;
@@ -43,7 +45,7 @@ bool prof_on() { return enabled; }
 int prof_begin(cudaStream_t st) {
   if (!enabled) return -1;
   std::lock_guard<std::mutex> lk(mu);
-  Rec r{get_event(), get_event(), g_cat, 0.0};
+  Rec r{get_event(), get_event(), g_cat, 0.0, 0, 0.0};
   if (!r.a || !r.b) return -1;
   cudaEventRecord(r.a, st);
   recs.push_back(r);
@@ -55,6 +57,22 @@ void prof_end(cudaStream_t st, int slot, double flops) {
   std::lock_guard<std::mutex> lk(mu);
   if (slot >= (int)recs.size()) return;
   recs[slot].flops = flops;
+  cudaEventRecord(recs[slot].b, st);
+}
+
+void prof_set_flops(int slot, double flops) {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (slot < (int)recs.size()) recs[slot].flops = flops;
+}
+
+void prof_end_tc(cudaStream_t st, int slot, double flops, double tensor_flops) {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (slot >= (int)recs.size()) return;
+  recs[slot].flops = flops;
+  recs[slot].tc = 1;
+  recs[slot].tflops = tensor_flops;
   cudaEventRecord(recs[slot].b, st);
 }
 }  // namespace gbf
@@ -92,5 +110,26 @@ extern "C" int gbf_profile_read(int cat, long long *launches, double *ms, double
   if (launches) *launches = n;
   if (ms) *ms = t;
   if (flops) *flops = f;
+  return 0;
+}
+
+extern "C" int gbf_profile_tc(long long *launches, double *ms, double *flops, double *tensor_flops) {
+  std::lock_guard<std::mutex> lk(mu);
+  long long n = 0;
+  double t = 0.0, f = 0.0, tf = 0.0;
+  for (auto &r : recs) {
+    if (!r.tc) continue;
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return -4;
+    float x = 0.f;
+    if (cudaEventElapsedTime(&x, r.a, r.b) != cudaSuccess) return -4;
+    ++n;
+    t += x;
+    f += r.flops;
+    tf += r.tflops;
+  }
+  if (launches) *launches = n;
+  if (ms) *ms = t;
+  if (flops) *flops = f;
+  if (tensor_flops) *tensor_flops = tf;
   return 0;
 }

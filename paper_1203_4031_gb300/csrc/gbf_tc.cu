@@ -920,8 +920,10 @@ static int zgemm_sliced_run(cudaStream_t st, char opa, char opb, int m, int n, i
   __nv_bfloat16 *Bs = (__nv_bfloat16 *)(w + al(a_bytes));
   int *sg = (int *)(w + al(a_bytes) + al(b_bytes));
   int *tg = (int *)(w + al(a_bytes) + al(b_bytes) + al(s_bytes));
+  const int sslot = prof_begin(st);
   slice_a_kernel<T, S><<<dim3(ceil_div(m, 8), batch), 256, 0, st>>>(opa, m, k, A, lda, sa, batch, As, sg);
   slice_b_kernel<T, S><<<dim3(ceil_div(n, 8), batch), 256, 0, st>>>(opb, k, n, B, ldb, sb, batch, Bs, tg);
+  prof_end(st, sslot, 0.0);
   g_launches.fetch_add(2, std::memory_order_relaxed);
   CUtensorMap ta, tb;
   if (int rc = make_map_rows(&ta, As, rows, S * batch, BM)) return rc;
@@ -944,12 +946,16 @@ static int zgemm_sliced_run(cudaStream_t st, char opa, char opb, int m, int n, i
   const int tpc = ceil_div(nct, want), nch = ceil_div(nct, tpc);  // no chunk is empty
   const int items = base_items * nch;
   dim3 grid(std::min(items, sms));
+  const int slot = prof_begin(st);
   if (beta_one)
     zgemm_sliced_kernel<T, S, true><<<grid, ZTHREADS, zlay<S>::SMEM, st>>>(ta, tb, m, n, batch, nch, tpc, sg, tg,
                                                                             alpha, C, ldc, sc, gerr);
   else
     zgemm_sliced_kernel<T, S, false><<<grid, ZTHREADS, zlay<S>::SMEM, st>>>(ta, tb, m, n, batch, nch, tpc, sg, tg,
                                                                              alpha, C, ldc, sc, gerr);
+  // issued: S(S+1)/2 digit-pair products of 128 x 32 x 64 per (row block, column tile)
+  prof_end_tc(st, slot, 8.0 * m * (double)n * k * batch,
+              2.0 * BM * ZBN * ZK * (S * (S + 1) / 2) * (double)base_items * nct);
   GBF_LAUNCHED();
   GBF_CUDA(cudaGetLastError());
   return 0;
@@ -1493,8 +1499,11 @@ int gemm_sliced_ops(cudaStream_t st, const SlicedOp &a, const SlicedOp &b, int b
   if (a.rows <= 0 || b.rows <= 0 || batch <= 0) return 0;
   const int slot = prof_begin(st);
   const int rc = tc::gemm_sliced_k_launch<T>(st, a, b, batch, alpha, beta_one, C, ldc, sc, gerr);
-  // useful FP64 flops (padded K): the real embedding's 2 R n Kp equals 8 m n k for complex data
-  prof_end(st, slot, 2.0 * a.rows * (double)b.rows * a.Kp * batch);
+  // useful FP64 flops (padded K): the real embedding's 2 R n Kp equals 8 m n k for complex data;
+  // issued: 36 digit-pair products of 128 x 32 x Kp per (row block, column tile)
+  const double tiles = (double)ceil_div(a.rows, (long)tc::BM) * ceil_div(b.rows, (long)tc::KBN) * batch;
+  prof_end_tc(st, slot, 2.0 * a.rows * (double)b.rows * a.Kp * batch,
+              2.0 * tc::BM * tc::KBN * (double)a.Kp * (tc::SK * (tc::SK + 1) / 2) * tiles);
   return rc;
 }
 

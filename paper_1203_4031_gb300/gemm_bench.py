@@ -1,0 +1,79 @@
+"""Times one sliced tensor-core GEMM shape through the C ABI (the kernels the
+FP64 factorisation, solves and projections run on), for profiling a single
+kernel in isolation:
+
+  python -m paper_1203_4031_gb300.gemm_bench --kind k32 --m 4096 --n 300 --k 32 --batch 8
+  python -m paper_1203_4031_gb300.gemm_bench --kind anyk --cplx 1 --m 2048 --n 300 --k 2048
+
+k32: gbf_zgemm_sliced (k <= 32, 7 digits, complex FP64), C -= A B.
+anyk: gbf_gemm_sliced (any k, 8 digits, real or complex FP64), C -= op(A) B with
+op(A) = A^T read from an (m x k)-transposed store, as the projections use it.
+Prints the time per call (CUDA events, after warm-up) and the useful FP64
+rate; inputs are seeded normal values resident on the device."""
+import argparse
+
+import torch
+
+from . import _ptr, _stream_ptr, last_error, lib
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kind", choices=["k32", "anyk"], default="k32")
+    ap.add_argument("--cplx", type=int, default=1)
+    ap.add_argument("--m", type=int, default=4096)
+    ap.add_argument("--n", type=int, default=300)
+    ap.add_argument("--k", type=int, default=32)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    a = ap.parse_args(argv)
+    L = lib()
+    g = torch.Generator(device="cuda").manual_seed(1)
+    cplx = 1 if a.kind == "k32" else a.cplx
+    dt = torch.complex128 if cplx else torch.float64
+    m, n, k, bt = a.m, a.n, a.k, a.batch
+
+    def rnd(*shape):
+        x = torch.randn(shape, device="cuda", dtype=torch.float64, generator=g)
+        if cplx:
+            x = torch.complex(x, torch.randn(shape, device="cuda", dtype=torch.float64, generator=g))
+        return x
+
+    st = torch.cuda.current_stream()
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    C = rnd(bt, n, m)
+    if a.kind == "k32":
+        A, B = rnd(bt, k, m), rnd(bt, n, k)   # column-major m x k and k x n
+        work = torch.empty(L.gbf_zgemm_sliced_work(m, n, bt, 7), dtype=torch.uint8, device="cuda")
+
+        def run():
+            return L.gbf_zgemm_sliced(_stream_ptr(st), 0, 7, b"N", b"N", m, n, k, -1.0, _ptr(A), m, m * k, _ptr(B),
+                                      k, k * n, 1, _ptr(C), m, m * n, bt, _ptr(work), work.numel(), _ptr(err))
+    else:
+        A, B = rnd(bt, m, k), rnd(bt, n, k)   # column-major k x m (op T) and k x n
+        work = torch.empty(L.gbf_gemm_sliced_work(cplx, m, n, k, bt), dtype=torch.uint8, device="cuda")
+
+        def run():
+            return L.gbf_gemm_sliced(_stream_ptr(st), cplx, b"T", b"N", m, n, k, -1.0, _ptr(A), k, m * k, _ptr(B),
+                                     k, k * n, 1, _ptr(C), m, m * n, bt, _ptr(work), work.numel(), _ptr(err))
+    for _ in range(a.warmup):
+        if run() != 0:
+            raise RuntimeError(last_error())
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(a.reps):
+        run()
+    e1.record(st)
+    torch.cuda.synchronize()
+    if err.item() != 0:
+        raise RuntimeError(f"bounded wait timed out (code {err.item()})")
+    ms = e0.elapsed_time(e1) / max(a.reps, 1)
+    flops = (8.0 if cplx else 2.0) * m * n * k * bt
+    print(f"{a.kind} cplx={cplx} m={m} n={n} k={k} batch={bt}: {ms * 1e3:.1f} us per call "
+          f"(slicing included), {flops / ms / 1e9:.2f} useful FP64 TFLOP/s")
+
+
+if __name__ == "__main__":
+    main()
