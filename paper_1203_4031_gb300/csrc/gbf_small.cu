@@ -154,41 +154,57 @@ __device__ inline int jpartner(int x, int P, int r) {
   return p < 0 ? p + P - 1 : p;
 }
 
-// Rotation of the pair (x, partner) from a = A[p][p], d = A[q][q],
-// b = A[p][q] (p < q).  Out: c, beta (coefficient of the partner row), px
-// (= x when not rotated) and the new diagonal entry of x.
-template <class T>
-__device__ void jrot_vals(int x, int p, int m, double a, double d, T b, double fro, double &c, T &beta, int &px,
-                          double &nd) {
-  using X = tr<T>;
-  c = 1.0;
-  beta = X::zero();
-  px = x;
-  const int pp = min(x, p);
-  nd = (x == pp) ? a : d;
-  if (p >= m || x >= m) return;
-  const double ab = absS(b);
-  if (ab == 0.0 || ab <= 0.5 * EPS_J * sqrt(fabs(a)) * sqrt(fabs(d)) || ab <= 1e-18 * fro) return;
-  const T ph = scS(b, 1.0 / ab);
-  const double tau = (d - a) / (2.0 * ab);
-  const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-  c = 1.0 / sqrt(1.0 + t * t);
-  const double s = t * c;
-  px = p;
-  if (x == pp) {
-    beta = scS(ph, -s);
-    nd = a - t * ab;
-  } else {
-    beta = scS(X::conj(ph), s);
-    nd = d + t * ab;
-  }
-}
-
 template <class T> struct JParams {
   double *cc, *nd;
   T *bb;
   int *pp;
 };
+
+// Rotation of the pair lo < hi from a = A[lo][lo], d = A[hi][hi], b =
+// A[lo][hi], written for both members: c (same for both), beta (coefficient
+// of the partner column), partner (= self when not rotated) and the new
+// diagonal entry.  Rotation angle from tau = (d - a) / (2|b|): t = sign(tau)
+// / (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c; no rotation
+// when |b| is at rounding level of sqrt(|a d|) or of the Frobenius norm.
+// The expensive operations are few: |b|^-1 by one reciprocal square root,
+// the threshold tests on squares, t by one square root and one division, c
+// by one reciprocal square root.
+template <class T>
+__device__ void jrot_pair(int lo, int hi, int m, double a, double d, T b, double fro, JParams<T> &pn) {
+  using X = tr<T>;
+  double c = 1.0;
+  T blo = X::zero(), bhi = X::zero();
+  int plo = lo, phi = hi;
+  double ndlo = a, ndhi = d;
+  const double b2 = X::re(X::mul(b, X::conj(b)));  // |b|^2
+  if (hi < m && b2 > 0.0 && b2 > 0.25 * EPS_J * EPS_J * fabs(a) * fabs(d) && b2 > 1e-36 * fro * fro) {
+    const double iab = rsqrt(b2);  // 1 / |b|
+    const double ab = b2 * iab;
+    const T ph = scS(b, iab);
+    const double tau = 0.5 * (d - a) * iab;
+    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+    c = rsqrt(1.0 + t * t);
+    const double sn = t * c;
+    blo = scS(ph, -sn);
+    bhi = scS(X::conj(ph), sn);
+    plo = hi;
+    phi = lo;
+    ndlo = a - t * ab;
+    ndhi = d + t * ab;
+  }
+  pn.cc[lo] = c;
+  pn.bb[lo] = blo;
+  pn.pp[lo] = plo;
+  pn.nd[lo] = ndlo;
+  if (hi < m) {
+    pn.cc[hi] = c;
+    pn.bb[hi] = bhi;
+    pn.pp[hi] = phi;
+    pn.nd[hi] = ndhi;
+  }
+}
+
+
 
 // Entry (i, j) of J^H A J for the rotations in prm.
 template <class T>
@@ -253,42 +269,43 @@ __global__ void jacobi_coop_kernel(int m, int maxsw, T *A, T *V, T *work, double
   for (long t = tid; t < maxsw; t += nthr) flags[t] = 0;
   grid.sync();
   const double fro = *frop;
-  // rotations of round 0 from the input matrix
-  for (long x = tid; x < m; x += nthr) {
-    const int p = jpartner((int)x, P, 0);
-    const int lo = min((int)x, p), hi = max((int)x, p);
-    double a = 0.0, d = 0.0;
-    T b = X::zero();
-    if (p < m) {
-      a = X::re(A[lo + (long)lo * m]);
-      d = X::re(A[hi + (long)hi * m]);
-      b = A[lo + (long)hi * m];
+  // rotations of round 0 from the input matrix (pair s: players x, y)
+  for (long s = tid; s < P / 2; s += nthr) {
+    int x, y;
+    if (s == 0) {
+      x = 0;
+      y = P - 1;
     } else {
-      a = d = X::re(A[x + x * (long)m]);
+      x = (int)s;
+      y = (int)((P - 1 - s) % (P - 1));
     }
-    double c, nd;
-    T be;
-    int px;
-    jrot_vals<T>((int)x, p, m, a, d, b, fro, c, be, px, nd);
-    prm[0].cc[x] = c;
-    prm[0].bb[x] = be;
-    prm[0].pp[x] = px;
-    prm[0].nd[x] = nd;
+    const int lo = min(x, y), hi = max(x, y);
+    if (hi < m)
+      jrot_pair<T>(lo, hi, m, X::re(A[lo + (long)lo * m]), X::re(A[hi + (long)hi * m]), A[lo + (long)hi * m], fro,
+                   prm[0]);
+    else if (lo < m)
+      jrot_pair<T>(lo, hi, m, X::re(A[lo + (long)lo * m]), 0.0, X::zero(), fro, prm[0]);
   }
   grid.sync();
   T *Ac = A, *An = A2, *Vc = V, *Vn = V2;
+  // warps per block that form rotations (one pair each), the rest update
+  const int npw = min((P / 2 + (int)gridDim.x - 1) / (int)gridDim.x, (int)(blockDim.x >> 5) - 1);
+  const long wid = (long)blockIdx.x * (blockDim.x - 32 * npw) + (long)threadIdx.x - 32 * npw;
+  const long nw = (long)gridDim.x * (blockDim.x - 32 * npw);
   int cur = 0, done_sweeps = -1;
   for (int sw = 0; sw < maxsw; ++sw) {
     for (int r = 0; r < P - 1; ++r) {
       const JParams<T> &pc = prm[cur];
       // next round's rotations, from this round's result
       const int rn = (r + 1 < P - 1) ? r + 1 : 0;
-      // pairs of the next round are spread over blocks first (their FP64
-      // divisions and square roots then run on different SMs' FP64 units)
-      // (lane 0 of warp w of block b takes pair b + gridDim.x * w)
-      const int sidx = (threadIdx.x & 31) ? -1 : (int)blockIdx.x + (int)gridDim.x * (int)(threadIdx.x >> 5);
-      if (sidx >= 0 && sidx < P / 2) {
-        const int s = sidx;
+      // pairs of the next round are spread over blocks (their FP64 square
+      // roots and divisions then run on different SMs' FP64 units): warp
+      // w < npw of block b takes pair b + gridDim.x * w; lanes 0, 1, 2 read
+      // the pair's entries a, d, b of this round's result, lane 0 forms the
+      // rotation
+      const int lane = threadIdx.x & 31;
+      const int sidx = (int)blockIdx.x + (int)gridDim.x * (int)(threadIdx.x >> 5);
+      for (int s = sidx; (int)(threadIdx.x >> 5) < npw && lane < 3 && s < P / 2; s += (int)gridDim.x * npw) {
         int x, y;
         if (s == 0) {
           x = rn;
@@ -299,31 +316,30 @@ __global__ void jacobi_coop_kernel(int m, int maxsw, T *A, T *V, T *work, double
         }
         const int lo = min(x, y), hi = max(x, y);
         JParams<T> &pn = prm[cur ^ 1];
-        if (hi < m) {
-          const double a = X::re(jelem<T>(lo, lo, m, Ac, pc));
-          const double d = X::re(jelem<T>(hi, hi, m, Ac, pc));
-          const T b = jelem<T>(lo, hi, m, Ac, pc);
-          double c, nd;
-          T be;
-          int px;
-          jrot_vals<T>(lo, hi, m, a, d, b, fro, c, be, px, nd);
-          pn.cc[lo] = c;
-          pn.bb[lo] = be;
-          pn.pp[lo] = px;
-          pn.nd[lo] = nd;
-          jrot_vals<T>(hi, lo, m, a, d, b, fro, c, be, px, nd);
-          pn.cc[hi] = c;
-          pn.bb[hi] = be;
-          pn.pp[hi] = px;
-          pn.nd[hi] = nd;
-        } else if (lo < m) {  // partner is the padding player: no rotation
-          pn.cc[lo] = 1.0;
-          pn.bb[lo] = X::zero();
-          pn.pp[lo] = lo;
-          pn.nd[lo] = 0.0;
+        T v = X::zero();
+        if (hi < m) v = jelem<T>(lane == 1 ? hi : lo, lane == 0 ? lo : hi, m, Ac, pc);
+        else if (lane == 0 && lo < m) v = jelem<T>(lo, lo, m, Ac, pc);
+        const unsigned msk = 0x7u;
+        T vd, vb;
+        if constexpr (tr<T>::cplx) {
+          vd.x = __shfl_sync(msk, v.x, 1);
+          vd.y = __shfl_sync(msk, v.y, 1);
+          vb.x = __shfl_sync(msk, v.x, 2);
+          vb.y = __shfl_sync(msk, v.y, 2);
+        } else {
+          vd = __shfl_sync(msk, v, 1);
+          vb = __shfl_sync(msk, v, 2);
+        }
+        if (lane == 0) {
+          if (hi < m)
+            jrot_pair<T>(lo, hi, m, X::re(v), X::re(vd), vb, fro, pn);
+          else if (lo < m)
+            jrot_pair<T>(lo, hi, m, X::re(v), 0.0, X::zero(), fro, pn);
         }
       }
-      for (long t = tid; t < 2 * mm; t += nthr) {
+      // entries of this round: warps npw.. of every block (warps below npw
+      // form the next round's rotations meanwhile)
+      for (long t = ((int)threadIdx.x >= 32 * npw) ? wid : 2 * mm; t < 2 * mm; t += nw) {
         if (t < mm) {
           An[t] = jelem<T>((int)(t % m), (int)(t / m), m, Ac, pc);
         } else {
@@ -351,7 +367,7 @@ __global__ void jacobi_coop_kernel(int m, int maxsw, T *A, T *V, T *work, double
       if (i >= j) continue;
       const double b = absS(Ac[t]);
       const double a = fabs(X::re(Ac[i + (long)i * m])), d = fabs(X::re(Ac[j + (long)j * m]));
-      if (b > 0.0 && b > 0.5 * EPS_J * sqrt(a) * sqrt(d) && b > 1e-18 * fro) viol = 1;
+      if (b > 0.0 && b * b > 0.25 * EPS_J * EPS_J * a * d && b > 1e-18 * fro) viol = 1;
     }
     viol = __syncthreads_or(viol);
     if (viol && threadIdx.x == 0) atomicOr(&flags[sw], 1);
