@@ -552,37 +552,41 @@ __device__ __forceinline__ double i64_scaled(long long x, int E, unsigned long l
   return x == 0 ? 0.0 : __longlong_as_double((long long)((bits) ^ (sgn ^ (sx << 63))));
 }
 
-// Reads the weight sums a = A, A+1 of 16 columns from TMEM (this warp's 32
-// lanes; column of weight a at taddr + a ZBN) and adds them into x.
-template <int S, int A>
-__device__ __forceinline__ void combine_weights(unsigned long long *x, uint32_t taddr) {
-  if constexpr (A < S) {
-    constexpr bool two = A + 1 < S;
-    uint32_t r0[16], r1[16];
-    const uint32_t t0 = taddr + (uint32_t)(A * ZBN);
+// 32 lanes x EC consecutive TMEM columns (EC = 8 or 16) into registers.
+template <int EC>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t *r) {
+  if constexpr (EC == 16) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
         "[%16];"
-        : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3]), "=r"(r0[4]), "=r"(r0[5]), "=r"(r0[6]), "=r"(r0[7]),
-          "=r"(r0[8]), "=r"(r0[9]), "=r"(r0[10]), "=r"(r0[11]), "=r"(r0[12]), "=r"(r0[13]), "=r"(r0[14]),
-          "=r"(r0[15])
-        : "r"(t0));
-    if constexpr (two)
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-          "[%16];"
-          : "=r"(r1[0]), "=r"(r1[1]), "=r"(r1[2]), "=r"(r1[3]), "=r"(r1[4]), "=r"(r1[5]), "=r"(r1[6]),
-            "=r"(r1[7]), "=r"(r1[8]), "=r"(r1[9]), "=r"(r1[10]), "=r"(r1[11]), "=r"(r1[12]), "=r"(r1[13]),
-            "=r"(r1[14]), "=r"(r1[15])
-          : "r"(t0 + (uint32_t)ZBN));
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+  } else {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+  }
+}
+
+// Reads the weight sums a = A, A+1 of EC columns from TMEM (this warp's 32
+// lanes; column of weight a at taddr + a ZBN) and adds them into x.
+template <int S, int A, int EC>
+__device__ __forceinline__ void combine_weights(unsigned long long *x, uint32_t taddr) {
+  if constexpr (A < S) {
+    constexpr bool two = A + 1 < S;
+    uint32_t r0[EC], r1[EC];
+    const uint32_t t0 = taddr + (uint32_t)(A * ZBN);
+    tmem_ld<EC>(t0, r0);
+    if constexpr (two) tmem_ld<EC>(t0 + (uint32_t)ZBN, r1);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     constexpr int w0 = 7 * (S - 1 - A);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
+    for (int j = 0; j < EC; ++j) {
       x[j] = add_shifted<w0>(x[j], __float_as_uint(__uint_as_float(r0[j]) + 12582912.0f));
       if constexpr (two) x[j] = add_shifted<w0 - 7>(x[j], __float_as_uint(__uint_as_float(r1[j]) + 12582912.0f));
     }
-    combine_weights<S, A + 2>(x, taddr);
+    combine_weights<S, A + 2, EC>(x, taddr);
   }
 }
 
@@ -597,10 +601,12 @@ __device__ __forceinline__ void combine_weights(unsigned long long *x, uint32_t 
 //   warps 2-5:           epilogue of tile g while tile g+1 is loaded and
 //                        multiplied.
 // g counts the tiles this CTA has processed; buffer = g % 2, use = g / 2.
-constexpr int ZTHREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int ZEC = 8;                      // columns per epilogue warp
+constexpr int ZEW = 4 * (ZBN / ZEC);        // epilogue warps (4 lane quarters x column groups)
+constexpr int ZTHREADS = 64 + 32 * ZEW;     // warp 0 TMA, warp 1 MMA, the rest epilogue
 
 template <class T, int S, bool BETA>
-__global__ void __launch_bounds__(ZTHREADS, 1)
+__global__ void __maxnreg__(96)
     zgemm_sliced_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int m,
                         int n, int batch, int nch, int tpc, const int *__restrict__ sexp, const int *__restrict__ texp, double alpha,
                         T *C, long ldc, long sc, int *gerr) {
@@ -632,7 +638,7 @@ __global__ void __launch_bounds__(ZTHREADS, 1)
     }
     for (int j = 0; j < 2; ++j) {
       mbar_init(&acc_full[j], 1);
-      mbar_init(&acc_empty[j], 8);  // one arrival per epilogue warp
+      mbar_init(&acc_empty[j], ZEW);  // one arrival per epilogue warp
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -739,17 +745,17 @@ __global__ void __launch_bounds__(ZTHREADS, 1)
   } else if (warp >= 2) {
     // ------------------------------------------------------- epilogue --
     // Warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of the tile) and
-    // columns half*16 .. +15 of each tile, half = (w - 2) / 4.  Per tile it
-    // waits for the accumulators, copies its S x 16 sums out of TMEM, frees
+    // columns g*ZEC .. +ZEC-1 of each tile, g = (w - 2) / 4.  Per tile it
+    // waits for the accumulators, copies its S x ZEC sums out of TMEM, frees
     // the buffer for the MMA of tile g + 2, issues the loads of C for its
     // next tile, and then combines and stores this tile.
     // Weight sums s_a (a = 0..S-1, weight 2^{-7(a+2)}) are combined exactly as
     // x = sum_a s_a 2^{7(S-1-a)} in 64-bit integers (|x| < 2^63: |s_0| <= 2^20
     // and |s_a| < 2^22); the entry is alpha sigma_i tau_j 2^{-7(S+1)} x.
-    const int q = warp & 3, c0 = ((warp - 2) >> 2) * 16;
+    const int q = warp & 3, c0 = ((warp - 2) >> 2) * ZEC;
     const bool neg = alpha < 0.0;
-    R cnext[16];
-    int tnext = 0;   // lane j < 16: exponent of column col0 + j, for shuffles
+    R cnext[ZEC];
+    int tnext = 0;   // lane j: exponent of column col0 + j % ZEC, for shuffles
     int esnext = 0;  // exponent of this lane's row
     // first column of (item, ct) handled by this thread's warp, its row, batch
     auto tile_of = [&](int item, int ct, int &rr, int &b, int &col0) {
@@ -762,13 +768,13 @@ __global__ void __launch_bounds__(ZTHREADS, 1)
       int rr, b, col0;
       tile_of(item, ct, rr, b, col0);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) cnext[j] = (R)0;
-      tnext = (col0 + (lane & 15) < n) ? __ldg(texp + (long)b * n + col0 + (lane & 15)) : 0;
+      for (int j = 0; j < ZEC; ++j) cnext[j] = (R)0;
+      tnext = (col0 + (lane % ZEC) < n) ? __ldg(texp + (long)b * n + col0 + (lane % ZEC)) : 0;
       esnext = (rr < rows) ? __ldg(sexp + (long)b * rows + rr) : 0;
       if (BETA && rr < rows) {
         const R *crow = reinterpret_cast<const R *>(C + (long)b * sc + (rr >> 1)) + (rr & 1);
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
+        for (int j = 0; j < ZEC; ++j)
           if (col0 + j < n) cnext[j] = crow[2L * (col0 + j) * ldc];
       }
     };
@@ -785,10 +791,10 @@ __global__ void __launch_bounds__(ZTHREADS, 1)
       if (__shfl_sync(0xffffffffu, okw, 0) == 0) break;
       __syncwarp();
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      unsigned long long x[16];
+      unsigned long long x[ZEC];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) x[j] = 0ull - acc_bias<S>();
-      combine_weights<S, 0>(x, tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * ACC + c0));
+      for (int j = 0; j < ZEC; ++j) x[j] = 0ull - acc_bias<S>();
+      combine_weights<S, 0, ZEC>(x, tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * ACC + c0));
       // accumulator buffer free for the MMA of tile g + 2
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -797,9 +803,9 @@ __global__ void __launch_bounds__(ZTHREADS, 1)
       // this tile's C entries and scales (loaded during the previous tile),
       // then the loads for the next tile of this CTA, which overlap the work
       // below
-      R cur[16];
+      R cur[ZEC];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) cur[j] = cnext[j];
+      for (int j = 0; j < ZEC; ++j) cur[j] = cnext[j];
       const int tcur = tnext, escur = esnext;
       int nitem = item, nct0 = ct + 1;
       if (nct0 >= ct1) {
@@ -819,19 +825,19 @@ __global__ void __launch_bounds__(ZTHREADS, 1)
                         __reduce_max_sync(0xffffffffu, es) + __reduce_max_sync(0xffffffffu, tcur) <= 960;
       R *crow = reinterpret_cast<R *>(C + (long)b * sc + (rr >> 1)) + (rr & 1);
       const unsigned long long sgn = neg ? 0x8000000000000000ull : 0ull;
-      int et[16];
+      int et[ZEC];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) et[j] = __shfl_sync(0xffffffffu, tcur, j);
+      for (int j = 0; j < ZEC; ++j) et[j] = __shfl_sync(0xffffffffu, tcur, j);
       // the product entry is rounded once to FP64 (exactly scaled), then added
       // to C with one more rounding
-      if (fast && __all_sync(0xffffffffu, rv) && col0 + 15 < n) {
-        // whole 32 x 16 block in range: straight-line code, so the 16
+      if (fast && __all_sync(0xffffffffu, rv) && col0 + ZEC - 1 < n) {
+        // whole 32 x ZEC block in range: straight-line code, so the ZEC
         // independent conversions interleave
-        double v[16];
+        double v[ZEC];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = i64_scaled((long long)x[j], es + et[j], sgn);
+        for (int j = 0; j < ZEC; ++j) v[j] = i64_scaled((long long)x[j], es + et[j], sgn);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < ZEC; ++j) {
           if constexpr (BETA)
             crow[2L * (col0 + j) * ldc] = (R)((double)cur[j] + v[j]);
           else
@@ -839,7 +845,7 @@ __global__ void __launch_bounds__(ZTHREADS, 1)
         }
       } else {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < ZEC; ++j) {
           const int col = col0 + j;
           if (rv && col < n) {
             double v;
