@@ -316,8 +316,8 @@ template <class TQ, class TL> struct WS {
     tcw_bytes = tcS ? std::max(zgemm_sliced_work(n, n, ne, tcS), zgemm_sliced_work(n, m0, ne, tcS)) : 0;
     tcw = tcS ? (void *)b.take<char>(tcw_bytes) : nullptr;
     tc_err = b.take<int>(4);
-    kw_bytes = tcS ? solve_kwork_bytes(n, m0, bs, ne) : 0;
-    kw = tcS ? (void *)b.take<char>(kw_bytes) : nullptr;
+    kw_bytes = (tcS && sizeof(TL) == sizeof(zd)) ? solve_kwork_bytes(n, m0, bs, ne) : 0;
+    kw = kw_bytes ? (void *)b.take<char>(kw_bytes) : nullptr;
     pja = pjb = pjq = nullptr;
     if (proj) {
       const bool cx = sizeof(TQ) == sizeof(zd);
@@ -377,7 +377,10 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
   const bool needBf = hasB && q.uplo != 'F';
   const int ksplit = pick_ksplit(m0, n);
   // complex GEMMs of the FP64 factorisation and solves: tensor cores
-  // (sliced, 7 digits) unless fpm(44) = 1; FP32 factors use CUDA cores
+  // (sliced, 7 digits) unless fpm(44) = 1.  FP32 factors stay on CUDA cores:
+  // the 4-digit (FP32-class) sliced product is exact only relative to each
+  // row's largest entry, which loses small entries that FP32 keeps, and at
+  // these sizes it is slower than the FP32 CUDA-core GEMM
   const int tcS = (fpm[43] == 0 && bs <= 32 && sizeof(TL) == sizeof(zd)) ? 7 : 0;
   // the n x n products of the projections (A Q, B Q, B Y): sliced tensor-core
   // GEMMs with A and B sliced once per call, unless fpm(44) = 1

@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <mutex>
 
 #include "gbf_common.cuh"
@@ -819,46 +820,67 @@ __global__ void __maxnreg__(96)
       tile_of(item, ct, rr, b, col0);
       const bool rv = rr < rows;
       // entry = +-2^{es+et} x (row scale es, column scale et); the warp checks
-      // once per tile that every exponent stays in the integer path's range
+      // once per tile that every exponent stays in the fast path's range
       const int es = rv ? escur - 7 * (S + 1) : 0;
-      const bool fast = __reduce_min_sync(0xffffffffu, es) + __reduce_min_sync(0xffffffffu, tcur) >= -1022 &&
-                        __reduce_max_sync(0xffffffffu, es) + __reduce_max_sync(0xffffffffu, tcur) <= 960;
+      const int emn = __reduce_min_sync(0xffffffffu, es) + __reduce_min_sync(0xffffffffu, tcur);
+      const int emx = __reduce_max_sync(0xffffffffu, es) + __reduce_max_sync(0xffffffffu, tcur);
       R *crow = reinterpret_cast<R *>(C + (long)b * sc + (rr >> 1)) + (rr & 1);
-      const unsigned long long sgn = neg ? 0x8000000000000000ull : 0ull;
       int et[ZEC];
 #pragma unroll
       for (int j = 0; j < ZEC; ++j) et[j] = __shfl_sync(0xffffffffu, tcur, j);
-      // the product entry is rounded once to FP64 (exactly scaled), then added
-      // to C with one more rounding
-      if (fast && __all_sync(0xffffffffu, rv) && col0 + ZEC - 1 < n) {
-        // whole 32 x ZEC block in range: straight-line code, so the ZEC
-        // independent conversions interleave
-        double v[ZEC];
-#pragma unroll
-        for (int j = 0; j < ZEC; ++j) v[j] = i64_scaled((long long)x[j], es + et[j], sgn);
-#pragma unroll
-        for (int j = 0; j < ZEC; ++j) {
-          if constexpr (BETA)
-            crow[2L * (col0 + j) * ldc] = (R)((double)cur[j] + v[j]);
-          else
-            crow[2L * (col0 + j) * ldc] = (R)v[j];
-        }
-      } else {
+      const bool full = __all_sync(0xffffffffu, rv) && col0 + ZEC - 1 < n;
+      if constexpr (std::is_same<R, float>::value) {
+        // FP32 output: x rounded once to FP32, scaled exactly by +-2^E (a
+        // normal power), added to C by one fused multiply-add
+        const bool fast = emn >= -126 && emx <= 127;
+        const float sg = neg ? -1.0f : 1.0f;
 #pragma unroll
         for (int j = 0; j < ZEC; ++j) {
           const int col = col0 + j;
-          if (rv && col < n) {
-            double v;
-            if (fast) {
-              v = i64_scaled((long long)x[j], es + et[j], sgn);
-            } else {
-              v = ldexp(__ll2double_rn((long long)x[j]), es + et[j]);
-              if (neg) v = -v;
-            }
+          if (full || (rv && col < n)) {
+            const float xf = __ll2float_rn((long long)x[j]);
+            const float p2 = sg * (fast ? __int_as_float((es + et[j] + 127) << 23) : ldexpf(1.0f, es + et[j]));
             if constexpr (BETA)
-              crow[2L * col * ldc] = (R)((double)cur[j] + v);
+              crow[2L * col * ldc] = fmaf(xf, p2, (float)cur[j]);
             else
-              crow[2L * col * ldc] = (R)v;
+              crow[2L * col * ldc] = xf * p2;
+          }
+        }
+      } else {
+        // FP64 output: the product entry is rounded once to FP64 (exactly
+        // scaled), then added to C with one more rounding
+        const bool fast = emn >= -1022 && emx <= 960;
+        const unsigned long long sgn = neg ? 0x8000000000000000ull : 0ull;
+        if (fast && full) {
+          // whole 32 x ZEC block in range: straight-line code, so the ZEC
+          // independent conversions interleave
+          double v[ZEC];
+#pragma unroll
+          for (int j = 0; j < ZEC; ++j) v[j] = i64_scaled((long long)x[j], es + et[j], sgn);
+#pragma unroll
+          for (int j = 0; j < ZEC; ++j) {
+            if constexpr (BETA)
+              crow[2L * (col0 + j) * ldc] = (R)((double)cur[j] + v[j]);
+            else
+              crow[2L * (col0 + j) * ldc] = (R)v[j];
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < ZEC; ++j) {
+            const int col = col0 + j;
+            if (rv && col < n) {
+              double v;
+              if (fast) {
+                v = i64_scaled((long long)x[j], es + et[j], sgn);
+              } else {
+                v = ldexp(__ll2double_rn((long long)x[j]), es + et[j]);
+                if (neg) v = -v;
+              }
+              if constexpr (BETA)
+                crow[2L * col * ldc] = (R)((double)cur[j] + v);
+              else
+                crow[2L * col * ldc] = (R)v;
+            }
           }
         }
       }
@@ -1569,10 +1591,13 @@ int zgemm_sliced(cudaStream_t st, int S, char opa, char opb, int m, int n, int k
   if (S == 7)
     return tc::zgemm_sliced_run<T, 7>(st, opa, opb, m, n, k, alpha, A, lda, sa, B, ldb, sb, beta_one, C, ldc, sc,
                                       batch, work, work_bytes, gerr);
+  if (S == 4)
+    return tc::zgemm_sliced_run<T, 4>(st, opa, opb, m, n, k, alpha, A, lda, sa, B, ldb, sb, beta_one, C, ldc, sc,
+                                      batch, work, work_bytes, gerr);
   if (S == 3)
     return tc::zgemm_sliced_run<T, 3>(st, opa, opb, m, n, k, alpha, A, lda, sa, B, ldb, sb, beta_one, C, ldc, sc,
                                       batch, work, work_bytes, gerr);
-  set_error("sliced GEMM: S must be 3 or 7");
+  set_error("sliced GEMM: S must be 3, 4 or 7");
   return -4;
 }
 template int zgemm_sliced<zd>(cudaStream_t, int, char, char, int, int, int, double, const zd *, long, long,
