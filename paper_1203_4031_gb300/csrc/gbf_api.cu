@@ -253,6 +253,7 @@ template <class TQ, class TL> struct WS {
   size_t tcw_bytes;
   int *tc_err;
   void *pja, *pjb, *pjq;  // sliced operands of the projections: A, B (rows), Q / Y (columns)
+  void *pjh, *pjx, *pjw;  // Q^H (rows), Q / AQ / BQ (rows, for X = Q W), W (columns)
   void *kw;               // any-k sliced updates of the recursive solves
   size_t kw_bytes;
 
@@ -318,13 +319,17 @@ template <class TQ, class TL> struct WS {
     tc_err = b.take<int>(4);
     kw_bytes = (tcS && sizeof(TL) == sizeof(zd)) ? solve_kwork_bytes(n, m0, bs, ne) : 0;
     kw = kw_bytes ? (void *)b.take<char>(kw_bytes) : nullptr;
-    pja = pjb = pjq = nullptr;
+    pja = pjb = pjq = pjh = pjx = pjw = nullptr;
     if (proj) {
       const bool cx = sizeof(TQ) == sizeof(zd);
       const long Kp = sliced_kp(n, cx), R = cx ? 2L * n : n;
+      const long Km = sliced_kp(m0, cx), Rm = cx ? 2L * m0 : m0;
       pja = b.take<char>(sliced_op_bytes(R, Kp, 1));
       pjb = hasB ? (void *)b.take<char>(sliced_op_bytes(R, Kp, 1)) : nullptr;
       pjq = b.take<char>(sliced_op_bytes(m0, Kp, 1));
+      pjh = b.take<char>(sliced_op_bytes(Rm, Kp, 1));
+      pjx = b.take<char>(sliced_op_bytes(R, Km, 1));
+      pjw = b.take<char>(sliced_op_bytes(m0, Km, 1));
     }
   }
 };
@@ -539,8 +544,17 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
     }
     // split-K chunks, capped by the workspace sized for (ksplit, m0)
     const int ks = std::max(1, std::min(pick_ksplit(m, n), (int)(((size_t)ksplit * m0 * m0) / ((size_t)m * m))));
-    CK(gemm<TQ>(st, 'C', 'N', m, m, n, one, ws.Q, n, 0, ws.AQ, n, 0, zero, ws.Aq, m, 0, 1, ks, ws.kwork));
-    CK(gemm<TQ>(st, 'C', 'N', m, m, n, one, ws.Q, n, 0, BQ, n, 0, zero, ws.Bq, m, 0, 1, ks, ws.kwork));
+    if (proj) {  // Q^H sliced once for both products
+      SlicedOp opQh, opM;
+      CK(slice_rows<TQ>(st, 'C', m, n, ws.Q, n, 0, 1, ws.pjh, &opQh));
+      CK(slice_cols<TQ>(st, 'N', n, m, ws.AQ, n, 0, 1, ws.pjq, &opM));
+      CK(gemm_sliced_ops<TQ>(st, opQh, opM, 1, 1.0, 0, ws.Aq, m, 0, ws.tc_err));
+      CK(slice_cols<TQ>(st, 'N', n, m, BQ, n, 0, 1, ws.pjq, &opM));
+      CK(gemm_sliced_ops<TQ>(st, opQh, opM, 1, 1.0, 0, ws.Bq, m, 0, ws.tc_err));
+    } else {
+      CK(gemm<TQ>(st, 'C', 'N', m, m, n, one, ws.Q, n, 0, ws.AQ, n, 0, zero, ws.Aq, m, 0, 1, ks, ws.kwork));
+      CK(gemm<TQ>(st, 'C', 'N', m, m, n, one, ws.Q, n, 0, BQ, n, 0, zero, ws.Bq, m, 0, 1, ks, ws.kwork));
+    }
     CK(rr_prepare<TQ>(st, m, ws.Aq, ws.Bq, ws.s, ws.flag, ws.As, ws.Bs));
     // B-orthonormal basis T of span(Q) (scaled): CholeskyQR passes on the
     // scaled Q^H B Q (T <- T L^{-H}, G <- T^H Bs T, until ||G - I||_F is at
@@ -612,12 +626,26 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
     CK(gemm<TQ>(st, 'N', 'N', m, mk, mk, one, ws.Tm, m, 0, ws.U, mk, 0, zero, ws.W, m, 0, 1));
     CK(scale_rows<TQ>(st, m, mk, ws.s, ws.W));
     }
-    CK(gemm<TQ>(st, 'N', 'N', n, mk, m, one, ws.Q, n, 0, ws.W, m, 0, zero, ws.Xu, n, 0, 1));
-    CK(gemm<TQ>(st, 'N', 'N', n, mk, m, one, ws.AQ, n, 0, ws.W, m, 0, zero, ws.AXu, n, 0, 1));
     const TQ *BXu = ws.Xu;
-    if (hasB) {
-      CK(gemm<TQ>(st, 'N', 'N', n, mk, m, one, ws.BQ, n, 0, ws.W, m, 0, zero, ws.BXu, n, 0, 1));
-      BXu = ws.BXu;
+    if (proj) {  // X, AX, BX = (Q, AQ, BQ) W with W sliced once
+      SlicedOp opW, opM;
+      CK(slice_cols<TQ>(st, 'N', m, mk, ws.W, m, 0, 1, ws.pjw, &opW));
+      CK(slice_rows<TQ>(st, 'N', n, m, ws.Q, n, 0, 1, ws.pjx, &opM));
+      CK(gemm_sliced_ops<TQ>(st, opM, opW, 1, 1.0, 0, ws.Xu, n, 0, ws.tc_err));
+      CK(slice_rows<TQ>(st, 'N', n, m, ws.AQ, n, 0, 1, ws.pjx, &opM));
+      CK(gemm_sliced_ops<TQ>(st, opM, opW, 1, 1.0, 0, ws.AXu, n, 0, ws.tc_err));
+      if (hasB) {
+        CK(slice_rows<TQ>(st, 'N', n, m, ws.BQ, n, 0, 1, ws.pjx, &opM));
+        CK(gemm_sliced_ops<TQ>(st, opM, opW, 1, 1.0, 0, ws.BXu, n, 0, ws.tc_err));
+        BXu = ws.BXu;
+      }
+    } else {
+      CK(gemm<TQ>(st, 'N', 'N', n, mk, m, one, ws.Q, n, 0, ws.W, m, 0, zero, ws.Xu, n, 0, 1));
+      CK(gemm<TQ>(st, 'N', 'N', n, mk, m, one, ws.AQ, n, 0, ws.W, m, 0, zero, ws.AXu, n, 0, 1));
+      if (hasB) {
+        CK(gemm<TQ>(st, 'N', 'N', n, mk, m, one, ws.BQ, n, 0, ws.W, m, 0, zero, ws.BXu, n, 0, 1));
+        BXu = ws.BXu;
+      }
     }
     CK(ritz_residual<TQ>(st, n, mk, ws.AXu, BXu, ws.lam, alpha, ws.resu));
     // spurious pairs: from loop 1 on, Y = Xc holds the previous B-orthonormal Ritz vectors
