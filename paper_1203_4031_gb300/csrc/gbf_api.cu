@@ -256,6 +256,7 @@ template <class TQ, class TL> struct WS {
   void *pjh, *pjx, *pjw;  // Q^H (rows), Q / AQ / BQ (rows, for X = Q W), W (columns)
   void *kw;               // any-k sliced updates of the recursive solves
   size_t kw_bytes;
+  TL *dinv_l, *dinv_u;    // 128 x 128 diagonal-block inverses (recursive solves' leaves)
 
   void layout(Bump &b, int n, int m0, int ne, int bs, bool herm, bool hasB, bool needAf, bool needBf,
               int ksplit, int tcS, bool proj) {
@@ -319,6 +320,9 @@ template <class TQ, class TL> struct WS {
     tc_err = b.take<int>(4);
     kw_bytes = (tcS && sizeof(TL) == sizeof(zd)) ? solve_kwork_bytes(n, m0, bs, ne) : 0;
     kw = kw_bytes ? (void *)b.take<char>(kw_bytes) : nullptr;
+    const bool big = kw_bytes && bs == 32 && n % 128 == 0;
+    dinv_l = big ? b.take<TL>((size_t)ne * n * 128) : nullptr;
+    dinv_u = big ? b.take<TL>((size_t)ne * n * 128) : nullptr;
     pja = pjb = pjq = pjh = pjx = pjw = nullptr;
     if (proj) {
       const bool cx = sizeof(TQ) == sizeof(zd);
@@ -405,6 +409,8 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
   tcx.S = tcS;
   tcx.kwork = ws.kw;
   tcx.kbytes = ws.kw_bytes;
+  tcx.dinv_l = ws.dinv_l;
+  tcx.dinv_u = ws.dinv_u;
   TcScope tc_scope(tcS ? &tcx : nullptr);
   if (ensure_hbuf(h, (size_t)std::max(m0, ne) + 64)) return out.info = -1;
   h->f_prec = -1;

@@ -163,6 +163,8 @@ struct TcCtx {
   int S = 0;
   void *kwork = nullptr;  // workspace of the any-k sliced GEMMs of the recursive solves
   size_t kbytes = 0;
+  void *dinv_l = nullptr;  // inverses of the 128 x 128 diagonal blocks of L and U (FP64
+  void *dinv_u = nullptr;  // factors, n a multiple of 128): the recursive solves' leaves
 };
 // Workspace bytes of the recursive solves' any-k sliced updates for n x n
 // factors, nrhs right-hand sides, block size bs (node groups of 2).

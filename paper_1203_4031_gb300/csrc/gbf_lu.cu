@@ -458,6 +458,77 @@ __global__ void tri_inverse_kernel(int n, int bs, int nblk, const T *S, T *Linv,
   for (int i = 0; i < bs; ++i) ui[i + (long)j * bs] = x[i];
 }
 
+// 128 x 128 diagonal blocks of L^-1 and U^-1 with their four 32 x 32
+// diagonal sub-blocks copied from the 32-block inverses and zeros elsewhere
+// (the off-diagonal sub-blocks are filled by block doubling below).
+template <class T>
+__global__ void big_diag_init_kernel(int nb32, int nb128, const T *Linv, const T *Uinv, T *L128, T *U128) {
+  const int b = blockIdx.x, e = blockIdx.y;
+  T *l = L128 + ((long)e * nb128 + b) * 128 * 128;
+  T *u = U128 + ((long)e * nb128 + b) * 128 * 128;
+  for (int t = threadIdx.x; t < 128 * 128; t += blockDim.x) {
+    const int i = t % 128, j = t / 128;
+    T lv = tr<T>::zero(), uv = tr<T>::zero();
+    if (i / 32 == j / 32) {
+      const long src = ((long)e * nb32 + b * 4 + i / 32) * 32 * 32 + (i % 32) + (long)(j % 32) * 32;
+      lv = Linv[src];
+      uv = Uinv[src];
+    }
+    l[t] = lv;
+    u[t] = uv;
+  }
+}
+
+// Copies, for every node e and 128-block b, the h x h sub-block of S at
+// (r + ro, r + co), r = 128 b, into out[(e nb128 + b)] (h x h, ld h).
+template <class T>
+__global__ void gather_sub_kernel(int n, int nb128, int h, int ro, int co, const T *S, T *out) {
+  const int b = blockIdx.x, e = blockIdx.y;
+  const T *src = S + (long)e * n * n + (long)(b * 128 + ro) + (long)(b * 128 + co) * n;
+  T *dst = out + ((long)e * nb128 + b) * h * h;
+  for (int t = threadIdx.x; t < h * h; t += blockDim.x) dst[t] = src[(t % h) + (long)(t / h) * n];
+}
+
+// Inverses of the 128 x 128 diagonal blocks (n a multiple of 128, bs = 32),
+// by doubling: for L = [A 0; C D], L^-1 = [A^-1 0; -D^-1 C A^-1 D^-1]; for
+// U = [A C; 0 D], U^-1 = [A^-1 -A^-1 C D^-1; 0 D^-1]; 32 -> 64 -> 128.  All
+// nodes and blocks in each batched product (the C blocks are gathered
+// first); tmp holds 2 x ne x n/128 x 64 x 64 entries.
+template <class T>
+static int build_big_inverses(cudaStream_t st, int n, int ne, const T *S, const T *Linv, const T *Uinv, T *L128,
+                              T *U128, T *tmp) {
+  using X = tr<T>;
+  const int nb32 = n / 32, nb128 = n / 128, nb = ne * nb128;
+  const long blk = 128L * 128, sq = 64L * 64;
+  const T one = X::one(), zero = X::zero(), m1 = X::sub(X::zero(), X::one());
+  T *tc = tmp, *tp = tmp + (long)nb * sq;
+  big_diag_init_kernel<T><<<dim3(nb128, ne), 256, 0, st>>>(nb32, nb128, Linv, Uinv, L128, U128);
+  GBF_LAUNCHED();
+  int rc;
+  for (int h = 32; h <= 64; h *= 2)             // half size: 32 (-> 64 blocks), 64 (-> 128)
+    for (int off = 0; off < 128; off += 2 * h) {  // the (2h)-blocks inside each 128-block
+      // L: tp = C A^-1, X = -D^-1 tp  (C = S[off+h.., off..], X at (off+h, off))
+      gather_sub_kernel<T><<<dim3(nb128, ne), 256, 0, st>>>(n, nb128, h, off + h, off, S, tc);
+      GBF_LAUNCHED();
+      if ((rc = gemm<T>(st, 'N', 'N', h, h, h, one, tc, h, (long)h * h, L128 + off + (long)off * 128, 128, blk, zero,
+                        tp, h, (long)h * h, nb)))
+        return rc;
+      if ((rc = gemm<T>(st, 'N', 'N', h, h, h, m1, L128 + (off + h) + (long)(off + h) * 128, 128, blk, tp, h,
+                        (long)h * h, zero, L128 + (off + h) + (long)off * 128, 128, blk, nb)))
+        return rc;
+      // U: tp = C D^-1, X = -A^-1 tp  (C = S[off.., off+h..], X at (off, off+h))
+      gather_sub_kernel<T><<<dim3(nb128, ne), 256, 0, st>>>(n, nb128, h, off, off + h, S, tc);
+      GBF_LAUNCHED();
+      if ((rc = gemm<T>(st, 'N', 'N', h, h, h, one, tc, h, (long)h * h, U128 + (off + h) + (long)(off + h) * 128,
+                        128, blk, zero, tp, h, (long)h * h, nb)))
+        return rc;
+      if ((rc = gemm<T>(st, 'N', 'N', h, h, h, m1, U128 + off + (long)off * 128, 128, blk, tp, h, (long)h * h, zero,
+                        U128 + off + (long)(off + h) * 128, 128, blk, nb)))
+        return rc;
+    }
+  return 0;
+}
+
 template <class T>
 int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T *Linv, T *Uinv, int bs,
                   int *sing, T *) {
@@ -506,6 +577,14 @@ int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T 
   tri_inverse_kernel<T><<<g, bs, 0, st>>>(n, bs, nblk, S, Linv, Uinv);
   GBF_LAUNCHED();
   GBF_CUDA(cudaGetLastError());
+  if constexpr (std::is_same<T, zd>::value) {
+    if (g_tc && g_tc->dinv_l && bs == 32 && n % 128 == 0) {
+      CatScope cat_inv(CAT_LU_SWAP);
+      // the product buffer: the solves' workspace is free at this point
+      return build_big_inverses<T>(st, n, ne, S, Linv, Uinv, (T *)g_tc->dinv_l, (T *)g_tc->dinv_u,
+                                   (T *)g_tc->kwork);
+    }
+  }
   return 0;
 }
 
@@ -513,7 +592,12 @@ int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T 
 size_t solve_kwork_bytes(int n, int nrhs, int bs, int ne) {
   const int nblk = ceil_div(n, bs);
   const int half = std::min(n, (nblk - nblk / 2) * bs);  // largest update: rows and K at most this
-  return gemm_sliced_k_work(true, half, nrhs, half, std::min(ne, 2));
+  size_t b = gemm_sliced_k_work(true, half, nrhs, half, std::min(ne, 2));
+  if (bs == 32 && n % 128 == 0) {  // 128-row leaves (all nodes) and the doubling products
+    b = std::max(b, gemm_sliced_k_work(true, 128, nrhs, 128, ne));
+    b = std::max(b, (size_t)2 * ne * (n / 128) * 64 * 64 * sizeof(zd));
+  }
+  return b;
 }
 
 // C[e] -= op(A[e]) Y[e] for all nodes e with the any-k sliced GEMM, nodes
@@ -549,6 +633,14 @@ static int trsv_rec(cudaStream_t st, int kind, int n, int ne, int nrhs, const T 
     const int r0 = b0 * bs, bsz = std::min(bs, n - r0);
     return gemm<T>(st, kind >= 2 ? 'C' : 'N', 'N', bsz, nrhs, bsz, one, Dinv + (long)b0 * bs * bs, bs, sblk,
                    Y + r0, n, ny, zero, Y + r0, n, ny, ne);
+  }
+  if (b1 - b0 == 4 && bs == 32 && b0 % 4 == 0 && n % 128 == 0 && g_tc && g_tc->dinv_l) {
+    // a 128-row leaf: one product with the inverted 128 x 128 diagonal block
+    const T *D = (const T *)((kind == 0 || kind == 3) ? g_tc->dinv_l : g_tc->dinv_u);
+    const long nb128 = n / 128;
+    return gemm_sliced_k<T>(st, kind >= 2 ? 'C' : 'N', 'N', 128, nrhs, 128, 1.0, D + (long)(b0 / 4) * 128 * 128,
+                            128, nb128 * 128 * 128, Y + (long)b0 * bs, n, ny, 0, Y + (long)b0 * bs, n, ny, ne,
+                            g_tc->kwork, g_tc->kbytes, g_tc->gerr);
   }
   const int mid = b0 + (b1 - b0) / 2;
   const int r0 = b0 * bs, rm = mid * bs, r1 = std::min(n, b1 * bs);
