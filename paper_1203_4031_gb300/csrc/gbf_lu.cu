@@ -12,9 +12,10 @@
 //                  then the row permutation and inverted bs x bs diagonal
 //                  blocks of L and U (reused by every solve of every FEAST
 //                  iteration, since the factors are kept: fpm(10)=1 style).
-//   getrs_inplace  blocked triangular solves in which every step is a GEMM:
-//                  Y_b <- inv(T_bb) Y_b, then the trailing update.  trans=1
-//                  gives S^H Y = R from the same factors (case 21).
+//   getrs_inplace  triangular solves in which every step is a GEMM: leaves
+//                  Y_b <- inv(T_bb) Y_b and updates, recursive (large-K
+//                  updates) on the tensor-core engine, blocked otherwise.
+//                  trans=1 gives S^H Y = R from the same factors (case 21).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -634,13 +635,15 @@ static int trsv_rec(cudaStream_t st, int kind, int n, int ne, int nrhs, const T 
     return gemm<T>(st, kind >= 2 ? 'C' : 'N', 'N', bsz, nrhs, bsz, one, Dinv + (long)b0 * bs * bs, bs, sblk,
                    Y + r0, n, ny, zero, Y + r0, n, ny, ne);
   }
-  if (b1 - b0 == 4 && bs == 32 && b0 % 4 == 0 && n % 128 == 0 && g_tc && g_tc->dinv_l) {
-    // a 128-row leaf: one product with the inverted 128 x 128 diagonal block
-    const T *D = (const T *)((kind == 0 || kind == 3) ? g_tc->dinv_l : g_tc->dinv_u);
-    const long nb128 = n / 128;
-    return gemm_sliced_k<T>(st, kind >= 2 ? 'C' : 'N', 'N', 128, nrhs, 128, 1.0, D + (long)(b0 / 4) * 128 * 128,
-                            128, nb128 * 128 * 128, Y + (long)b0 * bs, n, ny, 0, Y + (long)b0 * bs, n, ny, ne,
-                            g_tc->kwork, g_tc->kbytes, g_tc->gerr);
+  if constexpr (std::is_same<T, zd>::value) {
+    if (b1 - b0 == 4 && bs == 32 && b0 % 4 == 0 && n % 128 == 0 && g_tc && g_tc->dinv_l) {
+      // a 128-row leaf: one product with the inverted 128 x 128 diagonal block
+      const T *D = (const T *)((kind == 0 || kind == 3) ? g_tc->dinv_l : g_tc->dinv_u);
+      const long nb128 = n / 128;
+      return gemm_sliced_k<T>(st, kind >= 2 ? 'C' : 'N', 'N', 128, nrhs, 128, 1.0, D + (long)(b0 / 4) * 128 * 128,
+                              128, nb128 * 128 * 128, Y + (long)b0 * bs, n, ny, 0, Y + (long)b0 * bs, n, ny, ne,
+                              g_tc->kwork, g_tc->kbytes, g_tc->gerr);
+    }
   }
   const int mid = b0 + (b1 - b0) / 2;
   const int r0 = b0 * bs, rm = mid * bs, r1 = std::min(n, b1 * bs);
@@ -657,11 +660,14 @@ static int trsv_rec(cudaStream_t st, int kind, int n, int ne, int nrhs, const T 
     case 2: A = S + r0 + (long)rm * n; op = 'C'; m = r1 - rm; k = rm - r0; rdst = rm; rsrc = r0; break;
     default: A = S + rm + (long)r0 * n; op = 'C'; m = rm - r0; k = r1 - rm; rdst = r0; rsrc = rm; break;
   }
-  if (k > 32) {
-    rc = sliced_update<T>(st, op, m, k, nrhs, A, n, nn, Y + rsrc, n, ny, Y + rdst, n, ny, ne);
-  } else {
-    rc = gemm<T>(st, op, 'N', m, nrhs, k, m1, A, n, nn, Y + rsrc, n, ny, one, Y + rdst, n, ny, ne);
+  bool done = false;
+  if constexpr (std::is_same<T, zd>::value) {
+    if (k > 32 && g_tc && g_tc->kwork) {  // FP64 factors on the tensor-core engine
+      rc = sliced_update<T>(st, op, m, k, nrhs, A, n, nn, Y + rsrc, n, ny, Y + rdst, n, ny, ne);
+      done = true;
+    }
   }
+  if (!done) rc = gemm<T>(st, op, 'N', m, nrhs, k, m1, A, n, nn, Y + rsrc, n, ny, one, Y + rdst, n, ny, ne);
   if (rc) return rc;
   return trsv_rec<T>(st, kind, n, ne, nrhs, S, Dinv, bs, Y, forward ? mid : b0, forward ? b1 : mid);
 }
@@ -678,6 +684,8 @@ int getrs_inplace(cudaStream_t st, int trans, int n, int ne, int nrhs, const T *
   const T m1 = X::sub(X::zero(), X::one());
   const T zero = X::zero();
   int rc;
+  // FP64 factors on the tensor-core engine: recursive (large-K products);
+  // otherwise the blocked chain, which suits the CUDA-core GEMM better
   if constexpr (std::is_same<T, zd>::value) {
     if (g_tc && g_tc->kwork) {
       if (!trans) {
