@@ -274,7 +274,7 @@ template <class TQ, class TL> struct WS {
     pos = b.take<int>(m0);
     spur = b.take<int>(m0);
     nin = b.take<int>(4);
-    iwork = b.take<int>(3 * m0 + 96);
+    iwork = b.take<int>(5 * m0 + 96);
     flag = b.take<int>(4);
     Af = needAf ? b.take<TQ>(nn) : nullptr;
     Bf = needBf ? b.take<TQ>(nn) : nullptr;
@@ -1159,13 +1159,13 @@ static int heev_impl(gbf_handle h, cudaStream_t st, int m, T *A, double *w, T *V
   Bump sz(nullptr);
   sz.take<T>(2 * (size_t)m * m + 2 * m);
   sz.take<double>(8 + 4 * m);
-  sz.take<int>(3 * m + 96);
+  sz.take<int>(5 * m + 96);
   if (ensure_arena(h, sz.off + 4096)) return -1;
   h->f_prec = -1;
   Bump b(h->arena);
   T *work = b.take<T>(2 * (size_t)m * m + 2 * m);
   double *dwork = b.take<double>(8 + 4 * m);
-  int *iwork = b.take<int>(3 * m + 96);
+  int *iwork = b.take<int>(5 * m + 96);
   int sweeps = 0;
   const int rc = heev_jacobi<T>(st, m, A, w, V, work, dwork, iwork, h->hflag, &sweeps);
   if (rc) return rc;

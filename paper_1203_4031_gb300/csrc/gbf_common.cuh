@@ -251,7 +251,7 @@ int scatter_perm(cudaStream_t st, int n, int ne, int nrhs, const int *perm, cons
 // ------------------------------------------------------------ eig (eig.cu) --
 // Hermitian (T = zd) or real symmetric (T = double) Jacobi eigensolver of an
 // m x m matrix A (ld m, overwritten); w ascending (device), V eigenvectors.
-// work: 2 m^2 + 2m T; dwork: >= 4m + 8 doubles; iwork: >= 3m + 96 ints (device);
+// work: 2 m^2 + 2m T; dwork: >= 4m + 8 doubles; iwork: >= 5m + 96 ints (device);
 // hflag: pinned host int used to read the per-sweep convergence flag.
 template <class T>
 int heev_jacobi(cudaStream_t st, int m, T *A, double *w, T *V, T *work, double *dwork, int *iwork, int *hflag,

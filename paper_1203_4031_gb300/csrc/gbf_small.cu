@@ -147,13 +147,6 @@ int trinv_lower(cudaStream_t st, int m, const T *L, T *Linv) {
 // -------------------------------------------------------------- Jacobi --
 constexpr double EPS_J = 2.220446049250313e-16;
 
-__device__ inline int jpartner(int x, int P, int r) {
-  if (x == P - 1) return r;
-  if (x == r) return P - 1;
-  int p = (2 * r - x) % (P - 1);
-  return p < 0 ? p + P - 1 : p;
-}
-
 template <class T> struct JParams {
   double *cc, *nd;
   T *bb;
@@ -232,10 +225,9 @@ __device__ inline T jelem(int i, int j, int m, const T *A, const JParams<T> &prm
 // pair s of the NEXT round and that pair's rotation (double-buffered
 // parameters), so rounds need a single barrier.
 template <class T>
-__global__ void jacobi_coop_kernel(int m, int maxsw, T *A, T *V, T *work, double *dw, int *iw) {
+__global__ void __launch_bounds__(512, 1) jacobi_coop_kernel(int m, int maxsw, T *A, T *V, T *work, double *dw, int *iw) {
   using X = tr<T>;
   cg::grid_group grid = cg::this_grid();
-  const int P = m + (m & 1);
   const long nthr = (long)gridDim.x * blockDim.x;
   const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long mm = (long)m * m;
@@ -249,6 +241,9 @@ __global__ void jacobi_coop_kernel(int m, int maxsw, T *A, T *V, T *work, double
   }
   double *frop = dw + 4 * m;
   int *flags = iw + 2 * m, *sweeps_out = iw + 2 * m + maxsw;
+  // active indices (deflation): flag per index, sorted list, count; after
+  // iw[2m + maxsw + 8 .. + m) (the caller's ranking space)
+  int *act_flag = iw + 3 * m + maxsw + 8, *act = act_flag + m, *nact = act + m;
   __shared__ double red[32];
   if (blockIdx.x == 0) {
     double s = 0.0;
@@ -263,62 +258,77 @@ __global__ void jacobi_coop_kernel(int m, int maxsw, T *A, T *V, T *work, double
       double tot = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
       *frop = sqrt(tot);
+      *nact = m;
     }
   }
   for (long t = tid; t < mm; t += nthr) V[t] = ((t % m) == (t / m)) ? X::one() : X::zero();
   for (long t = tid; t < maxsw; t += nthr) flags[t] = 0;
-  grid.sync();
-  const double fro = *frop;
-  // rotations of round 0 from the input matrix (pair s: players x, y)
-  for (long s = tid; s < P / 2; s += nthr) {
-    int x, y;
-    if (s == 0) {
-      x = 0;
-      y = P - 1;
-    } else {
-      x = (int)s;
-      y = (int)((P - 1 - s) % (P - 1));
-    }
-    const int lo = min(x, y), hi = max(x, y);
-    if (hi < m)
-      jrot_pair<T>(lo, hi, m, X::re(A[lo + (long)lo * m]), X::re(A[hi + (long)hi * m]), A[lo + (long)hi * m], fro,
-                   prm[0]);
-    else if (lo < m)
-      jrot_pair<T>(lo, hi, m, X::re(A[lo + (long)lo * m]), 0.0, X::zero(), fro, prm[0]);
+  for (long t = tid; t < m; t += nthr) {
+    act[t] = (int)t;
+    act_flag[t] = 0;
   }
   grid.sync();
+  const double fro = *frop;
   T *Ac = A, *An = A2, *Vc = V, *Vn = V2;
-  // warps per block that form rotations (one pair each), the rest update
-  const int npw = min((P / 2 + (int)gridDim.x - 1) / (int)gridDim.x, (int)(blockDim.x >> 5) - 1);
-  const long wid = (long)blockIdx.x * (blockDim.x - 32 * npw) + (long)threadIdx.x - 32 * npw;
-  const long nw = (long)gridDim.x * (blockDim.x - 32 * npw);
   int cur = 0, done_sweeps = -1;
+  const int lane = threadIdx.x & 31;
+  // the matrix index of player x of a round over Pa players (Pa - 1 is the
+  // padding player when the active count is odd)
+  auto player = [&](int x, int ma) { return x < ma ? act[x] : m; };
   for (int sw = 0; sw < maxsw; ++sw) {
-    for (int r = 0; r < P - 1; ++r) {
+    // Each sweep pairs only the active indices: those with an off-diagonal
+    // entry above the rotation threshold after the previous sweep (all in
+    // sweep 0).  An index outside the set keeps the identity rotation; its
+    // entries with active indices are at rounding level and stay there.
+    const int ma = *nact;
+    const int Pa = ma + (ma & 1);
+    // warps per block that form rotations (one pair each), the rest update
+    const int npw = min((Pa / 2 + (int)gridDim.x - 1) / (int)gridDim.x, (int)(blockDim.x >> 5) - 1);
+    const long wid = (long)blockIdx.x * (blockDim.x - 32 * npw) + (long)threadIdx.x - 32 * npw;
+    const long nw = (long)gridDim.x * (blockDim.x - 32 * npw);
+    // identity rotations everywhere, then the active pairs of round 0
+    for (long t = tid; t < m; t += nthr)
+      for (int b = 0; b < 2; ++b) {
+        prm[b].cc[t] = 1.0;
+        prm[b].bb[t] = X::zero();
+        prm[b].pp[t] = (int)t;
+        prm[b].nd[t] = 0.0;
+      }
+    grid.sync();
+    for (long s = tid; s < Pa / 2; s += nthr) {
+      const int x = (s == 0) ? 0 : (int)s;
+      const int y = (s == 0) ? Pa - 1 : (int)((Pa - 1 - s) % (Pa - 1));
+      const int ix = player(x, ma), iy = player(y, ma);
+      const int lo = min(ix, iy), hi = max(ix, iy);
+      if (hi < m)
+        jrot_pair<T>(lo, hi, m, X::re(Ac[lo + (long)lo * m]), X::re(Ac[hi + (long)hi * m]), Ac[lo + (long)hi * m],
+                     fro, prm[cur]);
+    }
+    grid.sync();
+    for (int r = 0; r < Pa - 1; ++r) {
       const JParams<T> &pc = prm[cur];
-      // next round's rotations, from this round's result
-      const int rn = (r + 1 < P - 1) ? r + 1 : 0;
-      // pairs of the next round are spread over blocks (their FP64 square
-      // roots and divisions then run on different SMs' FP64 units): warp
-      // w < npw of block b takes pair b + gridDim.x * w; lanes 0, 1, 2 read
-      // the pair's entries a, d, b of this round's result, lane 0 forms the
-      // rotation
-      const int lane = threadIdx.x & 31;
+      JParams<T> &pn = prm[cur ^ 1];
+      // pairs of the next round (none after the last round of the sweep)
+      // are spread over blocks (their FP64 square roots and divisions then
+      // run on different SMs' FP64 units): warp w < npw of block b takes
+      // pair b + gridDim.x * w; lanes 0, 1, 2 read the pair's entries a, d,
+      // b of this round's result, lane 0 forms the rotation
+      const int rn = r + 1;
       const int sidx = (int)blockIdx.x + (int)gridDim.x * (int)(threadIdx.x >> 5);
-      for (int s = sidx; (int)(threadIdx.x >> 5) < npw && lane < 3 && s < P / 2; s += (int)gridDim.x * npw) {
+      for (int s = sidx; rn < Pa - 1 && (int)(threadIdx.x >> 5) < npw && lane < 3 && s < Pa / 2;
+           s += (int)gridDim.x * npw) {
         int x, y;
         if (s == 0) {
           x = rn;
-          y = P - 1;
+          y = Pa - 1;
         } else {
-          x = (rn + s) % (P - 1);
-          y = (rn - s + (P - 1)) % (P - 1);
+          x = (rn + s) % (Pa - 1);
+          y = (rn - s + (Pa - 1)) % (Pa - 1);
         }
-        const int lo = min(x, y), hi = max(x, y);
-        JParams<T> &pn = prm[cur ^ 1];
+        const int ix = player(x, ma), iy = player(y, ma);
+        const int lo = min(ix, iy), hi = max(ix, iy);
         T v = X::zero();
         if (hi < m) v = jelem<T>(lane == 1 ? hi : lo, lane == 0 ? lo : hi, m, Ac, pc);
-        else if (lane == 0 && lo < m) v = jelem<T>(lo, lo, m, Ac, pc);
         const unsigned msk = 0x7u;
         T vd, vb;
         if constexpr (tr<T>::cplx) {
@@ -330,11 +340,11 @@ __global__ void jacobi_coop_kernel(int m, int maxsw, T *A, T *V, T *work, double
           vd = __shfl_sync(msk, v, 1);
           vb = __shfl_sync(msk, v, 2);
         }
-        if (lane == 0) {
-          if (hi < m)
-            jrot_pair<T>(lo, hi, m, X::re(v), X::re(vd), vb, fro, pn);
-          else if (lo < m)
-            jrot_pair<T>(lo, hi, m, X::re(v), 0.0, X::zero(), fro, pn);
+        if (lane == 0 && hi < m) jrot_pair<T>(lo, hi, m, X::re(v), X::re(vd), vb, fro, pn);
+        if (lane == 0 && hi >= m && lo < m) {  // the padding player's partner: identity
+          pn.cc[lo] = 1.0;
+          pn.bb[lo] = X::zero();
+          pn.pp[lo] = lo;
         }
       }
       // entries of this round: warps npw.. of every block (warps below npw
@@ -360,14 +370,19 @@ __global__ void jacobi_coop_kernel(int m, int maxsw, T *A, T *V, T *work, double
       Vn = t1;
       cur ^= 1;
     }
-    // convergence: any pair still above the rotation threshold?
+    // convergence: pairs still above the rotation threshold; their indices
+    // form the next sweep's active set
     int viol = 0;
     for (long t = tid; t < mm; t += nthr) {
       const int i = (int)(t % m), j = (int)(t / m);
       if (i >= j) continue;
       const double b = absS(Ac[t]);
       const double a = fabs(X::re(Ac[i + (long)i * m])), d = fabs(X::re(Ac[j + (long)j * m]));
-      if (b > 0.0 && b * b > 0.25 * EPS_J * EPS_J * a * d && b > 1e-18 * fro) viol = 1;
+      if (b > 0.0 && b * b > 0.25 * EPS_J * EPS_J * a * d && b > 1e-18 * fro) {
+        viol = 1;
+        act_flag[i] = 1;
+        act_flag[j] = 1;
+      }
     }
     viol = __syncthreads_or(viol);
     if (viol && threadIdx.x == 0) atomicOr(&flags[sw], 1);
@@ -376,6 +391,17 @@ __global__ void jacobi_coop_kernel(int m, int maxsw, T *A, T *V, T *work, double
       done_sweeps = sw;
       break;
     }
+    // the sorted active list (one block), flags cleared for the next sweep
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      int c = 0;
+      for (int i = 0; i < m; ++i)
+        if (act_flag[i]) {
+          act[c++] = i;
+          act_flag[i] = 0;
+        }
+      *nact = c;
+    }
+    grid.sync();
   }
   if (Ac != A) {
     for (long t = tid; t < mm; t += nthr) {
