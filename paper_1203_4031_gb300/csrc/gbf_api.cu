@@ -56,6 +56,7 @@ struct gbf_context {
   double *hbuf = nullptr;     // pinned scratch
   size_t hbuf_cap = 0;
   cudaStream_t own = nullptr;  // stream of the host-pointer entries
+  AuxStreams aux;              // look-ahead side stream and events (created on first use)
   // factors kept by gbf_factor_dev
   int f_n = 0, f_ne = 0, f_prec = -1, f_bs = 32;
   size_t f_bytes = 0;
@@ -242,6 +243,22 @@ struct Res {
   int loop = 0, M = 0, m0 = 0, info = 0;
 };
 
+// The context's look-ahead stream and events, created once; null (no
+// look-ahead) if they cannot be made.
+static AuxStreams *ensure_aux(gbf_context *h) {
+  if (!h->aux.s) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&h->aux.s, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->aux.a, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->aux.b, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+  }
+  return &h->aux;
+}
+
 template <class TQ, class TL> struct WS {
   TL *S, *Linv, *Uinv, *Ysol, *Yadj, *Ytmp;
   int *ipiv, *perm, *sing, *pos, *nin, *iwork, *flag, *spur;
@@ -412,6 +429,7 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
   tcx.dinv_l = ws.dinv_l;
   tcx.dinv_u = ws.dinv_u;
   TcScope tc_scope(tcS ? &tcx : nullptr);
+  AuxScope aux_scope(ensure_aux(h));
   if (ensure_hbuf(h, (size_t)std::max(m0, ne) + 64)) return out.info = -1;
   h->f_prec = -1;
 
@@ -889,6 +907,9 @@ int gbf_destroy(gbf_handle h) {
   if (h->hflag) cudaFreeHost(h->hflag);
   if (h->hbuf) cudaFreeHost(h->hbuf);
   if (h->own) cudaStreamDestroy(h->own);
+  if (h->aux.s) cudaStreamDestroy(h->aux.s);
+  if (h->aux.a) cudaEventDestroy(h->aux.a);
+  if (h->aux.b) cudaEventDestroy(h->aux.b);
   delete h;
   return 0;
 }

@@ -170,6 +170,19 @@ struct TcCtx {
 // factors, nrhs right-hand sides, block size bs (node groups of 2).
 size_t solve_kwork_bytes(int n, int nrhs, int bs, int ne);
 extern thread_local TcCtx *g_tc;
+// Side stream (high priority) and two events of the calling context, for
+// the factorisation's look-ahead: panel k+1 runs there while the rest of
+// panel k's trailing update runs on the main stream.
+struct AuxStreams {
+  cudaStream_t s = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+};
+extern thread_local AuxStreams *g_aux;
+struct AuxScope {
+  AuxStreams *prev;
+  explicit AuxScope(AuxStreams *x) : prev(g_aux) { g_aux = x; }
+  ~AuxScope() { g_aux = prev; }
+};
 struct TcScope {
   TcCtx *prev;
   explicit TcScope(TcCtx *c) : prev(g_tc) { g_tc = c; }

@@ -12,6 +12,7 @@
 namespace gbf {
 
 thread_local TcCtx *g_tc = nullptr;
+thread_local AuxStreams *g_aux = nullptr;
 
 template <class T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))

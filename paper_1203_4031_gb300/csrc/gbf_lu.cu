@@ -536,15 +536,33 @@ int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T 
   using X = tr<T>;
   const int nb = std::min(bs, MAX_NB);
   const long nn = (long)n * n;
-  for (int k = 0; k < n; k += nb) {
+  T m1 = X::zero();
+  m1 = X::sub(m1, X::one());
+  auto panel = [&](cudaStream_t s, int k) {
     const int w = std::min(nb, n - k);
     CatScope cat_panel(CAT_LU_PANEL);
-    const int slot = prof_begin(st);
-    if (launch_cluster_panel<T>(st, n, ne, k, w, S, ipiv, sing)) {
-      lu_panel_kernel<T><<<ne, PANEL_THREADS, 0, st>>>(n, k, w, S, ipiv, sing);
+    const int slot = prof_begin(s);
+    if (launch_cluster_panel<T>(s, n, ne, k, w, S, ipiv, sing)) {
+      lu_panel_kernel<T><<<ne, PANEL_THREADS, 0, s>>>(n, k, w, S, ipiv, sing);
       GBF_LAUNCHED();
     }
-    prof_end(st, slot, 0.0);
+    prof_end(s, slot, 0.0);
+  };
+  // trailing update of panel k on the columns [c0, c1) (rows below the panel)
+  auto update = [&](int k, int c0, int c1) -> int {
+    const int w = std::min(nb, n - k);
+    if (c1 <= c0 || n - k - w <= 0) return 0;
+    CatScope cat_update(CAT_LU_UPDATE);
+    return gemm<T>(st, 'N', 'N', n - k - w, c1 - c0, w, m1, S + (k + w) + (long)k * n, n, nn, S + k + (long)c0 * n,
+                   n, nn, X::one(), S + (k + w) + (long)c0 * n, n, nn, ne);
+  };
+  // Look-ahead: the next panel depends only on its own columns, so once
+  // they are updated it runs on the side stream while the main stream
+  // updates the remaining columns; the next swap step waits for both.
+  AuxStreams *ax = g_aux;
+  panel(st, 0);
+  for (int k = 0; k < n; k += nb) {
+    const int w = std::min(nb, n - k);
     if (n - w > 0) {
       CatScope cat_swap(CAT_LU_SWAP);
       const int slot2 = prof_begin(st);
@@ -560,15 +578,21 @@ int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T 
       GBF_LAUNCHED();
       prof_end(st, slot2, 0.0);
     }
-    const int rest = n - k - w;
-    if (rest > 0) {
-      CatScope cat_update(CAT_LU_UPDATE);
-      T m1 = X::zero();
-      m1 = X::sub(m1, X::one());
-      int rc = gemm<T>(st, 'N', 'N', rest, rest, w, m1, S + (k + w) + (long)k * n, n, nn,
-                       S + k + (long)(k + w) * n, n, nn, X::one(), S + (k + w) + (long)(k + w) * n, n, nn,
-                       ne);
-      if (rc) return rc;
+    const int kn = k + w;  // next panel
+    if (kn >= n) break;
+    const int wn = std::min(nb, n - kn);
+    int rc;
+    if (ax) {
+      if ((rc = update(k, kn, kn + wn))) return rc;
+      GBF_CUDA(cudaEventRecord(ax->a, st));
+      GBF_CUDA(cudaStreamWaitEvent(ax->s, ax->a, 0));
+      panel(ax->s, kn);
+      GBF_CUDA(cudaEventRecord(ax->b, ax->s));
+      if ((rc = update(k, kn + wn, n))) return rc;
+      GBF_CUDA(cudaStreamWaitEvent(st, ax->b, 0));
+    } else {
+      if ((rc = update(k, kn, n))) return rc;
+      panel(st, kn);
     }
   }
   perm_from_ipiv_kernel<<<ne, 256, 0, st>>>(n, ipiv, perm);
