@@ -45,6 +45,10 @@ def parse():
                     help="time one path only (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving and batched samples")
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--batch-problems", type=int, default=24)
     return ap.parse_args()
 
 
@@ -248,6 +252,13 @@ def run_gbf(args):
                "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": (n * m0 + 2 * m0) * 8,
                "steps": ks, "api": "gbf_dsygv (host pointers, pinned)"}
 
+    serving = batched = None
+    if not args.no_serve and args.only is None and world == 1:
+        from paper_1203_4031_gb300 import workloads as W
+
+        serving = run_serving(g, torch, W, args.serve_requests, args.serve_rate)
+        batched = run_batched(g, torch, W, args.batch_problems)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(p, fp["M"])
@@ -265,12 +276,75 @@ def run_gbf(args):
             "max_rel_residual": fp["worst"], "gpu_launches": fp["launches"],
             "kernels_ms": {k: round(v[1], 3) for k, v in fp["prof"].items()},
             "roofline": roofline(fp["prof"], fp["tc"], "fp64"),
-            "clocks": fp["clocks"], "e2e": e2e, "mixed": mixed, "cpu_baseline": cpu,
+            "clocks": fp["clocks"], "e2e": e2e, "mixed": mixed, "serving": serving, "batched": batched,
+            "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     h.close()
     if dist:
         dist.destroy_process_group()
+
+
+def run_serving(g, torch, W, n_req, rate, budget=120e9, nworkers=4):
+    """Config-5 serving sample: n_req requests from the serving workload
+    (Poisson arrivals at `rate`/s, n log-uniform in [128, 4096], real
+    generalized or complex Hermitian 50/50, intervals holding 8-64), submitted
+    at their arrival times to gbf_server (HBM budget `budget`); latency =
+    the server's queue + run time per request; eigenpairs/s over the span
+    from the first arrival to the last completion.  Matrices are built on the
+    device before the clock starts."""
+    reqs = W.serving_requests(count=n_req, nmin=128, nmax=4096, rate=rate)
+    probs = []
+    for rq in reqs:
+        A, B, a, b = W.serving_matrices(rq)
+        f = g.gbf_init()
+        f[2] = 10
+        probs.append((rq, g.DeviceProblem(A, B, a, b, rq["m0"], fpm=f)))
+    torch.cuda.synchronize()
+    srv = g.Server(budget, nworkers=nworkers)
+    t0 = time.perf_counter()
+    tickets = []
+    for rq, dp in probs:
+        dt = rq["t_arrival"] - reqs[0]["t_arrival"] - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(srv.submit(dp))
+    res = [srv.wait(t) for t in tickets]
+    span = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r.queue_ms + r.run_ms for r in res])
+    ok = all(r.info == 0 and r.M == rq["count"] for (rq, _), r in zip(probs, res))
+    return {"requests": n_req, "offered_rate_per_s": rate, "workers": nworkers, "hbm_budget_gb": budget / 1e9,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "eigenpairs_per_s": float(sum(r.M for r in res) / span),
+            "span_s": span, "peak_admitted_gb": st["peak"] / 1e9, "all_counts_exact": bool(ok),
+            "paths": "FP64 (tensor-core engine)",
+            "workload": "serving requests (config 5 distribution), bounded sample"}
+
+
+def run_batched(g, torch, W, count, nworkers=4):
+    """Config-4 sample: `count` independent real symmetric generalized problems
+    (n log-uniform in [64, 1024], intervals holding 10-40, M0 = 1.5 count)
+    solved by one gbf_batch_solve call, FP64 path; eigenpairs/s over the call."""
+    probs = []
+    for p in W.batched_generalized(count=count, nmin=64, nmax=1024):
+        A = g.fortran(torch.from_numpy(p.A).cuda())
+        B = g.fortran(torch.from_numpy(p.B).cuda())
+        probs.append((p, g.DeviceProblem(A, B, p.emin, p.emax, p.m0, fpm=p.apply_fpm(g.gbf_init()))))
+    g.batch_solve([dp for _, dp in probs[:2]], nworkers=nworkers)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, outs = g.batch_solve([dp for _, dp in probs], nworkers=nworkers)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    ok = rc == 0
+    for (p, dp), r in zip(probs, outs):
+        w = p.spectrum
+        ok = ok and r.info == 0 and r.M == int(((w >= p.emin) & (w <= p.emax)).sum())
+    return {"problems": count, "eigenpairs_per_s": sum(r.M for r in outs) / dt, "ms": dt * 1e3,
+            "workers": nworkers, "all_counts_exact": bool(ok),
+            "workload": "batched generalized problems (config 4 distribution), bounded sample, FP64 path"}
 
 
 def measured_peaks():
