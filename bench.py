@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--batch-problems", type=int, default=24)
+    ap.add_argument("--no-herm", action="store_true", help="skip the complex Hermitian n=8192 sample")
     return ap.parse_args()
 
 
@@ -252,12 +253,14 @@ def run_gbf(args):
                "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": (n * m0 + 2 * m0) * 8,
                "steps": ks, "api": "gbf_dsygv (host pointers, pinned)"}
 
-    serving = batched = None
+    serving = batched = herm = None
     if not args.no_serve and args.only is None and world == 1:
         from paper_1203_4031_gb300 import workloads as W
 
         serving = run_serving(g, torch, W, args.serve_requests, args.serve_rate)
         batched = run_batched(g, torch, W, args.batch_problems)
+        if not args.no_herm:
+            herm = run_hermitian(g, torch, W)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -277,6 +280,7 @@ def run_gbf(args):
             "kernels_ms": {k: round(v[1], 3) for k, v in fp["prof"].items()},
             "roofline": roofline(fp["prof"], fp["tc"], "fp64"),
             "clocks": fp["clocks"], "e2e": e2e, "mixed": mixed, "serving": serving, "batched": batched,
+            "hermitian_n8192": herm,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -321,6 +325,36 @@ def run_serving(g, torch, W, n_req, rate, budget=120e9, nworkers=4):
             "span_s": span, "peak_admitted_gb": st["peak"] / 1e9, "all_counts_exact": bool(ok),
             "paths": "FP64 (tensor-core engine)",
             "workload": "serving requests (config 5 distribution), bounded sample"}
+
+
+def run_hermitian(g, torch, W):
+    """Config 3: complex Hermitian standard problem n = 8192, Ne = 16, M0 = 240,
+    interval [0, 0.04]; mixed and FP64 paths, one warm-up and one timed solve
+    each; pairs pass the same 1e-10 residual gate and are checked against the
+    known spectrum."""
+    p = W.dense_complex_hermitian()
+    A = g.fortran(torch.from_numpy(np.ascontiguousarray(p.A)).cuda())
+    lam = p.spectrum
+    ref = lam[(lam >= p.emin) & (lam <= p.emax)]
+    h = g.Handle()
+    out = {"workload": f"{p.name}: U diag(lam) U^H, B = I, [0, 0.04] holding {len(ref)}, M0 = {p.m0}, Ne = 16"}
+    for name, prec in (("mixed", 1), ("fp64", 0)):
+        f = p.apply_fpm(g.gbf_init())
+        f[41] = prec
+        g.feast_dev(A, None, p.emin, p.emax, p.m0, fpm=f, handle=h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = g.feast_dev(A, None, p.emin, p.emax, p.m0, fpm=f, handle=h)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        M = r["M"]
+        ok, worst = gate_count(A, torch.eye(p.n, dtype=A.dtype, device=A.device), r["X"], r["E"].to(A.dtype), M,
+                               torch) if r["info"] == 0 else (0, float("nan"))
+        err = float(np.max(np.abs(r["E"][:M].cpu().numpy() - ref))) if M == len(ref) else float("nan")
+        out[name] = {"eigenpairs_per_s": ok / dt, "ms": dt * 1e3, "M": M, "loops": r["loop"], "info": r["info"],
+                     "max_rel_residual": worst, "max_abs_eig_err": err}
+    h.close()
+    return out
 
 
 def run_batched(g, torch, W, count, nworkers=4):
