@@ -213,7 +213,8 @@ int gbf_gemm_sliced(void *stream, int cplx, char opa, char opb, int m, int n, in
  * engine behind the FP64 factorisation and solves): dC = alpha op(dA)
  * op(dB) + beta dC for interleaved complex data (prec 0: FP64, 1: FP32),
  * op in 'N','T','C', op(A) m x k, op(B) k x n with k <= 32, alpha = +1 or
- * -1, beta 0 or 1, S = 7 (FP64-class), 4 (FP32-class: 28 bits) or 3 digits, batches
+ * -1, beta 0 or 1, S = 7 (FP64-class), 4 (28 bits) or 3 digits, or S = -3 (FP32 data:
+ * every entry split into three bf16 parts, part products summed in FP32), batches
  * strided by sa, sb, sc elements.  Every operand row of op(A) / column of
  * op(B) is scaled by a power of two and split into S base-2^7 integer
  * digits held exactly in bf16; digit products are summed exactly in FP32

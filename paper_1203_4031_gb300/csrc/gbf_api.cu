@@ -402,11 +402,11 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
   const bool needAf = q.uplo != 'F';
   const bool needBf = hasB && q.uplo != 'F';
   const int ksplit = pick_ksplit(m0, n);
-  // complex GEMMs of the FP64 factorisation and solves: tensor cores
-  // (sliced, 7 digits) unless fpm(44) = 1.  FP32 factors stay on CUDA cores:
-  // the 4-digit (FP32-class) sliced product is exact only relative to each
-  // row's largest entry, which loses small entries that FP32 keeps, and at
-  // these sizes it is slower than the FP32 CUDA-core GEMM
+  // complex GEMMs of the FP64 factorisation and solves on the tensor cores
+  // (7-digit sliced products, FP64-class) unless fpm(44) = 1.  FP32 factors
+  // stay on CUDA cores: both FP32-class tensor-core variants (4 digits; bf16
+  // three-part split with FP32 sums) were slower here, and one small complex
+  // Hermitian case did not converge with them
   const int tcS = (fpm[43] == 0 && bs <= 32 && sizeof(TL) == sizeof(zd)) ? 7 : 0;
   // the n x n products of the projections (A Q, B Q, B Y): sliced tensor-core
   // GEMMs with A and B sliced once per call, unless fpm(44) = 1

@@ -172,7 +172,7 @@ int gemm(cudaStream_t st, char opa, char opb, int m, int n, int k, T alpha, cons
     double a = 0.0;
     int b1 = 0;
     TcCtx *tcx = g_tc;
-    if (tcx && tcx->S > 0 && k >= 1 && k <= 32 && m >= 16 && n >= 16 && sliced_ok<T>(alpha, beta, a, b1) &&
+    if (tcx && tcx->S != 0 && k >= 1 && k <= 32 && m >= 16 && n >= 16 && sliced_ok<T>(alpha, beta, a, b1) &&
         zgemm_sliced_work(m, n, batch, tcx->S) <= tcx->bytes) {
       return zgemm_sliced<T>(st, tcx->S, opa, opb, m, n, k, a, A, lda, sa, B, ldb, sb, b1, C, ldc, sc, batch,
                              tcx->work, tcx->bytes, tcx->gerr);

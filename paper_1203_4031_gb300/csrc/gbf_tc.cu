@@ -429,7 +429,20 @@ __device__ __forceinline__ void int_digits(long long X, float *d) {
 // element (i, p).  Out: slices [S][batch][2m][ZK] bf16 holding rows
 // 2i = [Re | -Im] and 2i+1 = [Im | Re] of the scaled row, zero-padded to ZK;
 // sexp [batch][2m] = e, the row's scale 2^e.
-template <class T, int S>
+// SPLIT: instead of digits, each entry (FP32 data) is split into S bf16 parts
+// hi + mid + lo (each the bf16 rounding of what the previous parts leave),
+// unscaled (exponents 0): FP32-class products accumulated in FP32.
+template <int S>
+__device__ __forceinline__ void float_split(double v, float *d) {
+  float r = (float)v;
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+    d[t] = __bfloat162float(__float2bfloat16_rn(r));
+    r -= d[t];
+  }
+}
+
+template <class T, int S, bool SPLIT>
 __global__ void slice_a_kernel(char opa, int m, int k, const T *A, long lda, long sa, int batch,
                                __nv_bfloat16 *out, int *sexp) {
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), b = blockIdx.y, p = threadIdx.x & 31;
@@ -441,10 +454,15 @@ __global__ void slice_a_kernel(char opa, int m, int k, const T *A, long lda, lon
     re = (double)a.x;
     im = (opa == 'C') ? -(double)a.y : (double)a.y;
   }
-  const int e = scale_exp(warp_absmax_bits(re, im));
+  const int e = SPLIT ? 0 : scale_exp(warp_absmax_bits(re, im));
   float dr[S], di[S];
-  int_digits<S>(fixed_point<S>(re, e), dr);
-  int_digits<S>(fixed_point<S>(im, e), di);
+  if constexpr (SPLIT) {
+    float_split<S>(re, dr);
+    float_split<S>(im, di);
+  } else {
+    int_digits<S>(fixed_point<S>(re, e), dr);
+    int_digits<S>(fixed_point<S>(im, e), di);
+  }
   const long rows = 2L * m;
   for (int t = 0; t < S; ++t) {
     __nv_bfloat16 *o = out + (((long)t * batch + b) * rows) * ZK;
@@ -469,7 +487,7 @@ __global__ void slice_a_kernel(char opa, int m, int k, const T *A, long lda, lon
 // B side: one warp per column c of op(B) (k x n), lane p < k holds element
 // (p, c).  Out: slices [S][batch][n][ZK] bf16 holding [Re ; Im] of the scaled
 // column, zero-padded; texp [batch][n] = e, the column's scale 2^e.
-template <class T, int S>
+template <class T, int S, bool SPLIT>
 __global__ void slice_b_kernel(char opb, int k, int n, const T *B, long ldb, long sb, int batch,
                                __nv_bfloat16 *out, int *texp) {
   const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), b = blockIdx.y, p = threadIdx.x & 31;
@@ -481,10 +499,15 @@ __global__ void slice_b_kernel(char opb, int k, int n, const T *B, long ldb, lon
     re = (double)v.x;
     im = (opb == 'C') ? -(double)v.y : (double)v.y;
   }
-  const int e = scale_exp(warp_absmax_bits(re, im));
+  const int e = SPLIT ? 0 : scale_exp(warp_absmax_bits(re, im));
   float dr[S], di[S];
-  int_digits<S>(fixed_point<S>(re, e), dr);
-  int_digits<S>(fixed_point<S>(im, e), di);
+  if constexpr (SPLIT) {
+    float_split<S>(re, dr);
+    float_split<S>(im, di);
+  } else {
+    int_digits<S>(fixed_point<S>(re, e), dr);
+    int_digits<S>(fixed_point<S>(im, e), di);
+  }
   for (int t = 0; t < S; ++t) {
     __nv_bfloat16 *o = out + (((long)t * batch + b) * n + c) * ZK;
     if (p < k) {
@@ -501,13 +524,14 @@ __host__ __device__ constexpr uint32_t idesc_bf16_n(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-template <int S> struct zlay {
+template <int S, bool SPLIT = false> struct zlay {
   // A slices of one 128-row block (resident per work item) + a ring of NB
   // stages of the B slices of one 32-column tile, as deep as fits in 227 KB
   static constexpr int FIXED = S * ZA_TILE + 1024 + 256;
   static constexpr int NB = (FIXED + 4 * S * ZB_TILE <= 232448) ? 4 : (FIXED + 3 * S * ZB_TILE <= 232448) ? 3 : 2;
   static constexpr int SMEM = FIXED + NB * S * ZB_TILE;
-  static constexpr int ACC_COLS = S * ZBN;  // one accumulator buffer (S weights x ZBN)
+  // one accumulator buffer: S weights x ZBN (digits) or one sum (split)
+  static constexpr int ACC_COLS = SPLIT ? ZBN : S * ZBN;
   static constexpr int COLS = (2 * ACC_COLS <= 64) ? 64 : (2 * ACC_COLS <= 128) ? 128 : (2 * ACC_COLS <= 256) ? 256 : 512;
 };
 
@@ -606,7 +630,7 @@ constexpr int ZEC = 8;                      // columns per epilogue warp
 constexpr int ZEW = 4 * (ZBN / ZEC);        // epilogue warps (4 lane quarters x column groups)
 constexpr int ZTHREADS = 64 + 32 * ZEW;     // warp 0 TMA, warp 1 MMA, the rest epilogue
 
-template <class T, int S, bool BETA>
+template <class T, int S, bool BETA, bool SPLIT>
 __global__ void __maxnreg__(96)
     zgemm_sliced_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int m,
                         int n, int batch, int nch, int tpc, const int *__restrict__ sexp, const int *__restrict__ texp, double alpha,
@@ -614,7 +638,7 @@ __global__ void __maxnreg__(96)
   using R = typename cplx_io<T>::R;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  constexpr int NB = zlay<S>::NB;
+  constexpr int NB = zlay<S, SPLIT>::NB;
   unsigned char *sA = base;                 // S x [128][64]
   unsigned char *sB = base + S * ZA_TILE;   // NB x S x [32][64]
   uint64_t *bars = reinterpret_cast<uint64_t *>(base + S * ZA_TILE + NB * S * ZB_TILE);
@@ -627,8 +651,8 @@ __global__ void __maxnreg__(96)
   const int rows = 2 * m;
   const int nrb = (rows + BM - 1) / BM, nct = (n + ZBN - 1) / ZBN;
   const int items = nch * nrb * batch;
-  constexpr uint32_t NCOLS = zlay<S>::COLS;
-  constexpr int ACC = zlay<S>::ACC_COLS;
+  constexpr uint32_t NCOLS = zlay<S, SPLIT>::COLS;
+  constexpr int ACC = zlay<S, SPLIT>::ACC_COLS;
 
   if (threadIdx.x == 0) {
     for (int t = 0; t < S; ++t) mbar_init(&a_full[t], 1);
@@ -710,24 +734,51 @@ __global__ void __maxnreg__(96)
         // its first k-step initialises the buffer.  On an item's first tile
         // each A slice is waited for just before its MMAs.
         const uint32_t dbase = tmem + (uint32_t)(buf * ACC);
-        const uint64_t bd = sdesc_sw128(sm_u32(sB + st * S * ZB_TILE));
         bool issued = false;
-#pragma unroll
-        for (int t = 0; t < S; ++t) {
+        if constexpr (SPLIT) {
+          // float split: every part product (t, u), t + u <= S-1, into the
+          // one accumulator, the smallest weights first
           if (ct == ct0) {
-            if (!mbar_wait(&a_full[t], it_local & 1, abort_flag, gerr, 25)) {
-              ok = false;
-              break;
-            }
+            for (int t = 0; t < S && ok; ++t)
+              if (!mbar_wait(&a_full[t], it_local & 1, abort_flag, gerr, 25)) ok = false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           }
-          const uint32_t idesc = idesc_bf16_n((S - t) * ZBN);
-          const uint64_t ad = sdesc_sw128(sm_u32(sA + t * ZA_TILE));
+          if (ok) {
+            constexpr uint32_t idesc = idesc_bf16_n(ZBN);
+            bool first = true;
 #pragma unroll
-          for (int kk = 0; kk < ZK / 16; ++kk)
-            mma_bf16(dbase + (uint32_t)(t * ZBN), ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
-                     (t > 0 || kk > 0) ? 1u : 0u);
-          issued = true;
+            for (int w = S - 1; w >= 0; --w)
+#pragma unroll
+              for (int t = 0; t <= w; ++t) {
+                const uint64_t ad = sdesc_sw128(sm_u32(sA + t * ZA_TILE));
+                const uint64_t bd = sdesc_sw128(sm_u32(sB + (st * S + (w - t)) * ZB_TILE));
+#pragma unroll
+                for (int kk = 0; kk < ZK / 16; ++kk)
+                  mma_bf16(dbase, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                           (first && kk == 0) ? 0u : 1u);
+                first = false;
+                issued = true;
+              }
+          }
+        } else {
+          const uint64_t bd = sdesc_sw128(sm_u32(sB + st * S * ZB_TILE));
+#pragma unroll
+          for (int t = 0; t < S; ++t) {
+            if (ct == ct0) {
+              if (!mbar_wait(&a_full[t], it_local & 1, abort_flag, gerr, 25)) {
+                ok = false;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
+            const uint32_t idesc = idesc_bf16_n((S - t) * ZBN);
+            const uint64_t ad = sdesc_sw128(sm_u32(sA + t * ZA_TILE));
+#pragma unroll
+            for (int kk = 0; kk < ZK / 16; ++kk)
+              mma_bf16(dbase + (uint32_t)(t * ZBN), ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                       (t > 0 || kk > 0) ? 1u : 0u);
+            issued = true;
+          }
         }
         if (!ok) {
           if (issued) {  // track the MMAs already issued for the drain below
@@ -793,9 +844,15 @@ __global__ void __maxnreg__(96)
       __syncwarp();
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       unsigned long long x[ZEC];
+      uint32_t fs[ZEC];  // split mode: the FP32 sums
+      if constexpr (SPLIT) {
+        tmem_ld<ZEC>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * ACC + c0), fs);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      } else {
 #pragma unroll
-      for (int j = 0; j < ZEC; ++j) x[j] = 0ull - acc_bias<S>();
-      combine_weights<S, 0, ZEC>(x, tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * ACC + c0));
+        for (int j = 0; j < ZEC; ++j) x[j] = 0ull - acc_bias<S>();
+        combine_weights<S, 0, ZEC>(x, tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * ACC + c0));
+      }
       // accumulator buffer free for the MMA of tile g + 2
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -829,7 +886,20 @@ __global__ void __maxnreg__(96)
 #pragma unroll
       for (int j = 0; j < ZEC; ++j) et[j] = __shfl_sync(0xffffffffu, tcur, j);
       const bool full = __all_sync(0xffffffffu, rv) && col0 + ZEC - 1 < n;
-      if constexpr (std::is_same<R, float>::value) {
+      if constexpr (SPLIT) {
+        // float split: the accumulator is the product entry itself (FP32)
+#pragma unroll
+        for (int j = 0; j < ZEC; ++j) {
+          const int col = col0 + j;
+          if (full || (rv && col < n)) {
+            const float v = neg ? -__uint_as_float(fs[j]) : __uint_as_float(fs[j]);
+            if constexpr (BETA)
+              crow[2L * col * ldc] = (R)((float)cur[j] + v);
+            else
+              crow[2L * col * ldc] = (R)v;
+          }
+        }
+      } else if constexpr (std::is_same<R, float>::value) {
         // FP32 output: x rounded once to FP32, scaled exactly by +-2^E (a
         // normal power), added to C by one fused multiply-add
         const bool fast = emn >= -126 && emx <= 127;
@@ -923,7 +993,7 @@ static int make_map_rows(CUtensorMap *map, const void *ptr, long rows, int plane
   return 0;
 }
 
-template <class T, int S>
+template <class T, int S, bool SPLIT>
 static int zgemm_sliced_run(cudaStream_t st, char opa, char opb, int m, int n, int k, double alpha, const T *A,
                             long lda, long sa, const T *B, long ldb, long sb, int beta_one, T *C, long ldc, long sc,
                             int batch, void *work, size_t work_bytes, int *gerr) {
@@ -949,8 +1019,8 @@ static int zgemm_sliced_run(cudaStream_t st, char opa, char opb, int m, int n, i
   int *sg = (int *)(w + al(a_bytes) + al(b_bytes));
   int *tg = (int *)(w + al(a_bytes) + al(b_bytes) + al(s_bytes));
   const int sslot = prof_begin(st);
-  slice_a_kernel<T, S><<<dim3(ceil_div(m, 8), batch), 256, 0, st>>>(opa, m, k, A, lda, sa, batch, As, sg);
-  slice_b_kernel<T, S><<<dim3(ceil_div(n, 8), batch), 256, 0, st>>>(opb, k, n, B, ldb, sb, batch, Bs, tg);
+  slice_a_kernel<T, S, SPLIT><<<dim3(ceil_div(m, 8), batch), 256, 0, st>>>(opa, m, k, A, lda, sa, batch, As, sg);
+  slice_b_kernel<T, S, SPLIT><<<dim3(ceil_div(n, 8), batch), 256, 0, st>>>(opb, k, n, B, ldb, sb, batch, Bs, tg);
   prof_end(st, sslot, 0.0);
   g_launches.fetch_add(2, std::memory_order_relaxed);
   CUtensorMap ta, tb;
@@ -958,10 +1028,10 @@ static int zgemm_sliced_run(cudaStream_t st, char opa, char opb, int m, int n, i
   if (int rc = make_map_rows(&tb, Bs, n, S * batch, ZBN)) return rc;
   static bool attr = false;
   if (!attr) {
-    GBF_CUDA(cudaFuncSetAttribute(zgemm_sliced_kernel<T, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  zlay<S>::SMEM));
-    GBF_CUDA(cudaFuncSetAttribute(zgemm_sliced_kernel<T, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  zlay<S>::SMEM));
+    GBF_CUDA(cudaFuncSetAttribute(zgemm_sliced_kernel<T, S, true, SPLIT>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, zlay<S, SPLIT>::SMEM));
+    GBF_CUDA(cudaFuncSetAttribute(zgemm_sliced_kernel<T, S, false, SPLIT>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, zlay<S, SPLIT>::SMEM));
     attr = true;
   }
   int dev = 0, sms = 0;
@@ -976,10 +1046,10 @@ static int zgemm_sliced_run(cudaStream_t st, char opa, char opb, int m, int n, i
   dim3 grid(std::min(items, sms));
   const int slot = prof_begin(st);
   if (beta_one)
-    zgemm_sliced_kernel<T, S, true><<<grid, ZTHREADS, zlay<S>::SMEM, st>>>(ta, tb, m, n, batch, nch, tpc, sg, tg,
+    zgemm_sliced_kernel<T, S, true, SPLIT><<<grid, ZTHREADS, zlay<S, SPLIT>::SMEM, st>>>(ta, tb, m, n, batch, nch, tpc, sg, tg,
                                                                             alpha, C, ldc, sc, gerr);
   else
-    zgemm_sliced_kernel<T, S, false><<<grid, ZTHREADS, zlay<S>::SMEM, st>>>(ta, tb, m, n, batch, nch, tpc, sg, tg,
+    zgemm_sliced_kernel<T, S, false, SPLIT><<<grid, ZTHREADS, zlay<S, SPLIT>::SMEM, st>>>(ta, tb, m, n, batch, nch, tpc, sg, tg,
                                                                              alpha, C, ldc, sc, gerr);
   // issued: S(S+1)/2 digit-pair products of 128 x 32 x 64 per (row block, column tile)
   prof_end_tc(st, slot, 8.0 * m * (double)n * k * batch,
@@ -1578,6 +1648,7 @@ namespace tc {
 }  // namespace tc
 
 size_t zgemm_sliced_work(int m, int n, int batch, int S) {
+  S = S < 0 ? -S : S;
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
   return al((size_t)S * batch * 2L * m * tc::ZK * 2) + al((size_t)S * batch * n * tc::ZK * 2) +
          al((size_t)batch * 2L * m * 8) + al((size_t)batch * n * 8);
@@ -1589,15 +1660,18 @@ int zgemm_sliced(cudaStream_t st, int S, char opa, char opb, int m, int n, int k
                  size_t work_bytes, int *gerr) {
   if (m <= 0 || n <= 0 || batch <= 0) return 0;
   if (S == 7)
-    return tc::zgemm_sliced_run<T, 7>(st, opa, opb, m, n, k, alpha, A, lda, sa, B, ldb, sb, beta_one, C, ldc, sc,
-                                      batch, work, work_bytes, gerr);
+    return tc::zgemm_sliced_run<T, 7, false>(st, opa, opb, m, n, k, alpha, A, lda, sa, B, ldb, sb, beta_one, C, ldc,
+                                             sc, batch, work, work_bytes, gerr);
   if (S == 4)
-    return tc::zgemm_sliced_run<T, 4>(st, opa, opb, m, n, k, alpha, A, lda, sa, B, ldb, sb, beta_one, C, ldc, sc,
-                                      batch, work, work_bytes, gerr);
+    return tc::zgemm_sliced_run<T, 4, false>(st, opa, opb, m, n, k, alpha, A, lda, sa, B, ldb, sb, beta_one, C, ldc,
+                                             sc, batch, work, work_bytes, gerr);
   if (S == 3)
-    return tc::zgemm_sliced_run<T, 3>(st, opa, opb, m, n, k, alpha, A, lda, sa, B, ldb, sb, beta_one, C, ldc, sc,
-                                      batch, work, work_bytes, gerr);
-  set_error("sliced GEMM: S must be 3, 4 or 7");
+    return tc::zgemm_sliced_run<T, 3, false>(st, opa, opb, m, n, k, alpha, A, lda, sa, B, ldb, sb, beta_one, C, ldc,
+                                             sc, batch, work, work_bytes, gerr);
+  if (S == -3)  // FP32 entries split into three bf16 parts, FP32 accumulation
+    return tc::zgemm_sliced_run<T, 3, true>(st, opa, opb, m, n, k, alpha, A, lda, sa, B, ldb, sb, beta_one, C, ldc,
+                                            sc, batch, work, work_bytes, gerr);
+  set_error("sliced GEMM: S must be 3, 4, 7 or -3");
   return -4;
 }
 template int zgemm_sliced<zd>(cudaStream_t, int, char, char, int, int, int, double, const zd *, long, long,

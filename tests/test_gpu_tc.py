@@ -28,7 +28,7 @@ def colmajor_batch(torch, mats):
     return torch.stack([x.t().contiguous() for x in mats])
 
 
-@pytest.mark.parametrize("S,prec", [(7, 0), (3, 1), (3, 0), (4, 1)])
+@pytest.mark.parametrize("S,prec", [(7, 0), (3, 1), (3, 0), (4, 1), (-3, 1)])
 @pytest.mark.parametrize("m,n,k,batch", [(1, 1, 1, 1), (37, 33, 7, 2), (200, 100, 32, 1), (1000, 300, 32, 3),
                                          (65, 129, 17, 2)])
 @pytest.mark.parametrize("opa,opb", [("N", "N"), ("C", "N"), ("T", "C")])
