@@ -924,16 +924,23 @@ __global__ void __maxnreg__(96)
         if (fast && full) {
           // whole 32 x ZEC block in range: straight-line code, so the ZEC
           // independent conversions interleave
+          // Odd columns go through the FP64 unit (conversion, then a fused
+          // multiply-add by +-2^E into C), even columns through the integer
+          // construction and one FP64 add: the two pipes share the work.
           double v[ZEC];
 #pragma unroll
-          for (int j = 0; j < ZEC; ++j) v[j] = i64_scaled((long long)x[j], es + et[j], sgn);
-#pragma unroll
           for (int j = 0; j < ZEC; ++j) {
-            if constexpr (BETA)
-              crow[2L * (col0 + j) * ldc] = (R)((double)cur[j] + v[j]);
-            else
-              crow[2L * (col0 + j) * ldc] = (R)v[j];
+            if (j & 1) {
+              const double p2 = __longlong_as_double(((long long)(es + et[j] + 1023) << 52) | (long long)sgn);
+              v[j] = BETA ? fma(__ll2double_rn((long long)x[j]), p2, (double)cur[j])
+                          : __ll2double_rn((long long)x[j]) * p2;
+            } else {
+              v[j] = i64_scaled((long long)x[j], es + et[j], sgn);
+              if constexpr (BETA) v[j] += (double)cur[j];
+            }
           }
+#pragma unroll
+          for (int j = 0; j < ZEC; ++j) crow[2L * (col0 + j) * ldc] = (R)v[j];
         } else {
 #pragma unroll
           for (int j = 0; j < ZEC; ++j) {
