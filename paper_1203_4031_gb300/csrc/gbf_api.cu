@@ -271,6 +271,8 @@ template <class TQ, class TL> struct WS {
   int *tc_err;
   void *pja, *pjb, *pjq;  // sliced operands of the projections: A, B (rows), Q / Y (columns)
   void *pjh, *pjx, *pjw;  // Q^H (rows), Q / AQ / BQ (rows, for X = Q W), W (columns)
+  void *rrw;              // both operands of the M0 x M0 x M0 reduced-space products
+  size_t rrw_bytes;
   void *kw;               // any-k sliced updates of the recursive solves
   size_t kw_bytes;
   TL *dinv_l, *dinv_u;    // 128 x 128 diagonal-block inverses (recursive solves' leaves)
@@ -340,7 +342,8 @@ template <class TQ, class TL> struct WS {
     const bool big = kw_bytes && bs == 32 && n % 128 == 0;
     dinv_l = big ? b.take<TL>((size_t)ne * n * 128) : nullptr;
     dinv_u = big ? b.take<TL>((size_t)ne * n * 128) : nullptr;
-    pja = pjb = pjq = pjh = pjx = pjw = nullptr;
+    pja = pjb = pjq = pjh = pjx = pjw = rrw = nullptr;
+    rrw_bytes = 0;
     if (proj) {
       const bool cx = sizeof(TQ) == sizeof(zd);
       const long Kp = sliced_kp(n, cx), R = cx ? 2L * n : n;
@@ -352,6 +355,8 @@ template <class TQ, class TL> struct WS {
       pjx = b.take<char>(sliced_op_bytes(R, Km, 1));
       pjw = b.take<char>(sliced_op_bytes(m0, Km, 1));
     }
+    rrw_bytes = proj ? gemm_sliced_k_work(sizeof(TQ) == sizeof(zd), m0, m0, m0, 1) : 0;
+    rrw = proj ? (void *)b.take<char>(rrw_bytes) : nullptr;
   }
 };
 
@@ -491,6 +496,16 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
     return gemm_sliced_ops<TQ>(st, opM, opY, 1, 1.0, 0, out_, n, 0, ws.tc_err);
   };
 
+  // M0-sized products of the reduced space (B-orthonormalisation, reduced
+  // matrix, W): any-k sliced GEMM on the tensor-core engine
+  auto rr_gemm = [&](char opa, char opb, int mm, int nn2, int kk, const TQ *A_, int lda_, const TQ *B_, int ldb_,
+                     TQ *C_, int ldc_) -> int {
+    if (proj)
+      return gemm_sliced_k<TQ>(st, opa, opb, mm, nn2, kk, 1.0, A_, lda_, 0, B_, ldb_, 0, 0, C_, ldc_, 0, 1, ws.rrw,
+                               ws.rrw_bytes, ws.tc_err);
+    return gemm<TQ>(st, opa, opb, mm, nn2, kk, XQ::one(), A_, lda_, 0, B_, ldb_, 0, XQ::zero(), C_, ldc_, 0, 1);
+  };
+
   // initial subspace into Xc
   if (fpm[4] == 1) {
     copy_cols_kernel<TQ><<<dim3(ceil_div(n, 256), m0), 256, 0, st>>>(n, m0, (const TQ *)q.X, n, ws.Xc, n);
@@ -603,12 +618,12 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
           copy_t_kernel<TQ><<<dim3(ceil_div(m, 256), m), 256, 0, st>>>(m, Li, ws.Tm);
           GBF_LAUNCHED();
         } else {
-          CK(gemm<TQ>(st, 'N', 'C', m, m, m, one, ws.Tm, m, 0, Li, m, 0, zero, Tn, m, 0, 1));
+          CK(rr_gemm('N', 'C', m, m, m, ws.Tm, m, Li, m, Tn, m));
           GBF_CUDA(cudaMemcpyAsync(ws.Tm, Tn, sizeof(TQ) * (size_t)m * m, cudaMemcpyDeviceToDevice, st));
         }
         // G = T^H Bs T
-        CK(gemm<TQ>(st, 'N', 'N', m, m, m, one, ws.Bs, m, 0, ws.Tm, m, 0, zero, Tn, m, 0, 1));
-        CK(gemm<TQ>(st, 'C', 'N', m, m, m, one, ws.Tm, m, 0, Tn, m, 0, zero, G, m, 0, 1));
+        CK(rr_gemm('N', 'N', m, m, m, ws.Bs, m, ws.Tm, m, Tn, m));
+        CK(rr_gemm('C', 'N', m, m, m, ws.Tm, m, Tn, m, G, m));
         CK(ns_prep<TQ>(st, m, G, (TQ *)nullptr, ws.dwork + 4));
         GBF_CUDA(cudaMemcpyAsync(hd, ws.dwork + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
         GBF_CUDA(cudaMemcpyAsync(h->hflag, ws.flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
@@ -643,11 +658,11 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
     {
     CatScope cat_red(CAT_REDUCED);
     if (!ns_done) CK(make_t<TQ>(st, m, mk, first, ws.V, ws.d, ws.Tm));
-    CK(gemm<TQ>(st, 'N', 'N', m, mk, m, one, ws.As, m, 0, ws.Tm, m, 0, zero, ws.Ctmp, m, 0, 1));
-    CK(gemm<TQ>(st, 'C', 'N', mk, mk, m, one, ws.Tm, m, 0, ws.Ctmp, m, 0, zero, ws.Cm, mk, 0, 1));
+    CK(rr_gemm('N', 'N', m, mk, m, ws.As, m, ws.Tm, m, ws.Ctmp, m));
+    CK(rr_gemm('C', 'N', mk, mk, m, ws.Tm, m, ws.Ctmp, m, ws.Cm, mk));
     CK(hermitize<TQ>(st, mk, ws.Cm, ws.Cs));
     CK(heev_jacobi<TQ>(st, mk, ws.Cs, ws.lam, ws.U, ws.jwork, ws.dwork, ws.iwork, h->hflag, &sw_c));
-    CK(gemm<TQ>(st, 'N', 'N', m, mk, mk, one, ws.Tm, m, 0, ws.U, mk, 0, zero, ws.W, m, 0, 1));
+    CK(rr_gemm('N', 'N', m, mk, mk, ws.Tm, m, ws.U, mk, ws.W, m));
     CK(scale_rows<TQ>(st, m, mk, ws.s, ws.W));
     }
     const TQ *BXu = ws.Xu;
