@@ -113,6 +113,21 @@ def workload():
     return W.dense_real_generalized()
 
 
+def combine_ranks(ms, pairs, dist, device):
+    """Whole-job figures over the ranks (independent replicas, no data-path
+    collective): the slowest rank's time (max) and the pairs of all ranks
+    (sum).  `dist` is torch.distributed (nccl on GPUs, gloo in the CPU test)
+    or None for one rank."""
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    tot = torch.tensor([float(pairs)], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    return t.item(), tot.item()
+
+
 def gate_count(A, B, X, E, M, torch):
     """Pairs (of the first M) with ||Ax - lBx||_2 / (||A||_1 ||x||_2) <= 1e-10."""
     Xm = X[:, :M]
@@ -198,12 +213,8 @@ def run_gbf(args):
         if any(x["info"] != 0 for x in rs):
             raise RuntimeError(f"timed solve failed: {[x['info'] for x in rs]}")
         ok, worst = gate_count(A, B, r["X"], r["E"], r["M"], torch)
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        tot = torch.tensor([ok * steps], dtype=torch.float64, device=dev)
-        if dist:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        return dict(ms=t.item(), pairs=tot.item(), M=r["M"], ok=ok, worst=worst, loop=r["loop"],
+        ms_all, pairs_all = combine_ranks(ms, ok * steps, dist, dev)
+        return dict(ms=ms_all, pairs=pairs_all, M=r["M"], ok=ok, worst=worst, loop=r["loop"],
                     launches=launches, prof=prof, tc=tc, clocks=cl)
 
     if args.only == "mixed":
@@ -246,10 +257,8 @@ def run_gbf(args):
             rh = g.feast_host(a_np, b_np, p.emin, p.emax, m0, fpm=fpm_for(0))
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0
-        tt = torch.tensor([dt], dtype=torch.float64, device=dev)
-        if dist:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": (rh["M"] * ks * world) / tt.item(), "unit": "eigenpairs/s",
+        dt_all, _ = combine_ranks(dt, 0, dist, dev)
+        e2e = {"value": (rh["M"] * ks * world) / dt_all, "unit": "eigenpairs/s",
                "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": (n * m0 + 2 * m0) * 8,
                "steps": ks, "api": "gbf_dsygv (host pointers, pinned)"}
 
