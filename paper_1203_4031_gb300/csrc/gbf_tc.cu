@@ -1528,8 +1528,10 @@ static int gemm_sliced_k_launch(cudaStream_t st, const SlicedOp &a, const Sliced
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int base_items = ceil_div(a.rows, (long)BM) * batch, nct = ceil_div(b.rows, KBN);
-  const int want = std::max(1, std::min(nct, ceil_div(2 * sms, base_items)));
-  const int tpc = ceil_div(nct, want), nch = ceil_div(nct, tpc);
+  // one work item per tile: every tile streams its own A chunks, so finer
+  // items cost no traffic and balance the last round; consecutive items are
+  // the column tiles of one row block (its A chunks shared in L2)
+  const int tpc = 1, nch = nct;
   const int items = base_items * nch;
   const int nkc = (int)(a.Kp / KC);
   dim3 grid(std::min(items, sms));
