@@ -148,7 +148,6 @@ template <> bool is_zero<cf>(cf v) { return v.x == 0.f && v.y == 0.f; }
 
 // real scalar +-1 / 0-1 tests for the sliced tensor-core path
 template <class T> static bool sliced_ok(T alpha, T beta, double &a, int &b);
-template <> bool sliced_ok<double>(double, double, double &, int &) { return false; }
 template <> bool sliced_ok<zd>(zd alpha, zd beta, double &a, int &b) {
   if (alpha.y != 0.0 || (alpha.x != 1.0 && alpha.x != -1.0) || beta.y != 0.0 || (beta.x != 0.0 && beta.x != 1.0))
     return false;
