@@ -167,7 +167,7 @@ struct TcCtx {
   void *dinv_u = nullptr;  // factors, n a multiple of 128): the recursive solves' leaves
 };
 // Workspace bytes of the recursive solves' any-k sliced updates for n x n
-// factors, nrhs right-hand sides, block size bs (node groups of 2).
+// factors, nrhs right-hand sides, block size bs (node groups of up to 8).
 size_t solve_kwork_bytes(int n, int nrhs, int bs, int ne);
 extern thread_local TcCtx *g_tc;
 // Side stream (high priority) and two events of the calling context, for

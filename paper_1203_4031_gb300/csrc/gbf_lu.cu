@@ -617,7 +617,7 @@ int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T 
 size_t solve_kwork_bytes(int n, int nrhs, int bs, int ne) {
   const int nblk = ceil_div(n, bs);
   const int half = std::min(n, (nblk - nblk / 2) * bs);  // largest update: rows and K at most this
-  size_t b = gemm_sliced_k_work(true, half, nrhs, half, std::min(ne, 2));
+  size_t b = gemm_sliced_k_work(true, half, nrhs, half, std::min(ne, 8));
   if (bs == 32 && n % 128 == 0) {  // 128-row leaves (all nodes) and the doubling products
     b = std::max(b, gemm_sliced_k_work(true, 128, nrhs, 128, ne));
     b = std::max(b, (size_t)2 * ne * (n / 128) * 64 * 64 * sizeof(zd));

@@ -1085,7 +1085,7 @@ constexpr int KC = 64;                      // real K positions per chunk
 constexpr int KBN = 32;                     // columns per tile
 constexpr int KA_STAGE = BM * KC * 2;       // one A slice of one chunk (16 KB)
 constexpr int KB_STAGE = SK * KBN * KC * 2; // all B slices of one chunk (32 KB)
-constexpr int KNA = 9, KNB = 2;             // ring depths (A: more than one chunk in flight)
+constexpr int KNA = 10, KNB = 2;            // ring depths (A: more than one chunk in flight)
 constexpr int K_SMEM = KNA * KA_STAGE + KNB * KB_STAGE + 1024 + 512;
 constexpr int K_ACC = SK * KBN;             // TMEM columns of one accumulator buffer
 constexpr int KTHREADS = 320;               // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
