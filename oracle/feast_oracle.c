@@ -34,7 +34,10 @@
  *     convergence test and goes to the end of E/X with res = -1;
  *   - info 1 as soon as no Ritz value is inside; info 3 when every one of the
  *     M0 requested Ritz values is inside and M0 < N;
- *   - epsout = 1 at loop 0 (the hello-world output prints 1.0 at loop 0).
+ *   - epsout = 1 at loop 0 (the hello-world output prints 1.0 at loop 0);
+ *   - stochastic estimate (fpm(14)=2): Rademacher probes (fpm(5)=0) or the
+ *     input X as probes (fpm(5)=1); res(j) = running mean over probes 1..j,
+ *     M = res(M0) rounded to nearest and clamped at 0, X = the probes.
  *
  * Arithmetic: C99 double complex, compiled with -fcx-limited-range (textbook
  * complex multiply/divide without the Annex G inf/NaN recovery).
@@ -554,9 +557,13 @@ int ora_feast(int kind, int n, const zc *A, int lda, const zc *B, int ldb,
             goto cleanup;
         }
 
-        /* initial subspace Y (n x m0): input X (fpm(5)=1) or SplitMix64 */
+        /* initial subspace Y (n x m0): input X (fpm(5)=1) or SplitMix64;
+         * for the stochastic estimate (fpm(14)=2) the generated columns are
+         * Rademacher probes, +1 or -1 by the top bit of SplitMix64 */
         if (fpm[4] == 1) {
             memcpy(Y, X, sizeof(zc) * nm);
+        } else if (fpm[13] == 2) {
+            for (size_t i = 0; i < nm; ++i) Y[i] = (ora_splitmix64(ORA_SEED, i) >> 63) ? -1.0 : 1.0;
         } else {
             for (size_t i = 0; i < nm; ++i)
                 Y[i] = kind ? (u11(ORA_SEED, 2 * i) + I * u11(ORA_SEED, 2 * i + 1)) : u11(ORA_SEED, i);
@@ -612,6 +619,30 @@ int ora_feast(int kind, int n, const zc *A, int lda, const zc *B, int ldb,
                 zc s = 0.0;
                 for (int e = 0; e < ne; ++e) s += Qe[(size_t)e * n * m + i];
                 Q[i] = s;
+            }
+            if (fpm[13] == 2) {
+                /* stochastic count ("Stochastic estimate" section, after Di
+                 * Napoli, Polizzi & Saad): Q = f(B^-1 A) Y is the filtered
+                 * probe block, and for a probe y with independent +-1
+                 * entries E[y^H f(B^-1 A) y] = trace f(B^-1 A), which is the
+                 * eigenvalue count in the interval when f is the indicator.
+                 * res(j) = mean of Re(y_i^H q_i) over the first j probes;
+                 * M = that mean over all M0 probes, rounded (not below 0);
+                 * X returns the probes Y. */
+                double s = 0.0;
+                for (int j = 0; j < m0; ++j) {
+                    double t = 0.0;
+                    for (int i = 0; i < n; ++i) t += creal(conj(Y[IX(i, j, n)]) * Q[IX(i, j, n)]);
+                    s += t;
+                    res[j] = s / (j + 1);
+                    E[j] = 0.0;
+                }
+                double mh = floor(res[m0 - 1] + 0.5);
+                *M = mh > 0.0 ? (int)mh : 0;
+                memcpy(X, Y, sizeof(zc) * nm);
+                *loop = 0;
+                info = 5;
+                goto cleanup;
             }
             if (fpm[13] == 1) { /* return the subspace after one contour */
                 memset(X, 0, sizeof(zc) * nm);
