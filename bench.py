@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--batch-problems", type=int, default=24)
     ap.add_argument("--no-herm", action="store_true", help="skip the complex Hermitian n=8192 sample")
+    ap.add_argument("--no-stoch", action="store_true", help="skip the stochastic-count sample (fpm(14)=2)")
     return ap.parse_args()
 
 
@@ -262,6 +263,10 @@ def run_gbf(args):
                "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": (n * m0 + 2 * m0) * 8,
                "steps": ks, "api": "gbf_dsygv (host pointers, pinned)"}
 
+    stoch = None
+    if not args.no_stoch and args.only is None and world == 1:
+        stoch = run_stochastic(g, torch, p, A, B, h, stream)
+
     serving = batched = herm = None
     if not args.no_serve and args.only is None and world == 1:
         from paper_1203_4031_gb300 import workloads as W
@@ -289,7 +294,7 @@ def run_gbf(args):
             "kernels_ms": {k: round(v[1], 3) for k, v in fp["prof"].items()},
             "roofline": roofline(fp["prof"], fp["tc"], "fp64"),
             "clocks": fp["clocks"], "e2e": e2e, "mixed": mixed, "serving": serving, "batched": batched,
-            "hermitian_n8192": herm,
+            "hermitian_n8192": herm, "stochastic_count": stoch,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -334,6 +339,35 @@ def run_serving(g, torch, W, n_req, rate, budget=120e9, nworkers=4):
             "span_s": span, "peak_admitted_gb": st["peak"] / 1e9, "all_counts_exact": bool(ok),
             "paths": "FP64 (tensor-core engine)",
             "workload": "serving requests (config 5 distribution), bounded sample"}
+
+
+def run_stochastic(g, torch, p, A, B, h, stream, reps=3):
+    """Stochastic eigenvalue count (fpm(14)=2) on the resident n=4096
+    generalized problem (200 eigenvalues inside): one contour over M0 +-1
+    probes, no Rayleigh-Ritz.  Device time per estimate (CUDA events, two
+    warm-ups, `reps` timed calls) for the settings the guide suggests (few
+    nodes, FP32 factors, small M0) and an FP64 one."""
+    out = {"workload": f"{p.name}: estimate of the count in [-{p.emax:.6g},{p.emax:.6g}] (exact 200)"}
+    for name, ne, m0, prec in (("ne3_m16_mixed", 3, 16, 1), ("ne3_m64_mixed", 3, 64, 1),
+                               ("ne8_m64_fp64", 8, 64, 0)):
+        f = p.apply_fpm(g.gbf_init())
+        f[1], f[13], f[41] = ne, 2, prec
+        E = torch.zeros(m0, dtype=torch.float64, device=A.device)
+        res = torch.zeros(m0, dtype=torch.float64, device=A.device)
+        X = torch.zeros((m0, p.n), dtype=A.dtype, device=A.device).t()
+        for _ in range(2):
+            r = g.feast_dev(A, B, p.emin, p.emax, m0, fpm=f, E=E, X=X, res=res, handle=h, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            r = g.feast_dev(A, B, p.emin, p.emax, m0, fpm=f, E=E, X=X, res=res, handle=h, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"ms": e0.elapsed_time(e1) / reps, "M": r["M"], "info": r["info"],
+                     "mean": float(r["res"][m0 - 1].item()), "ne": ne, "m0": m0,
+                     "dtype": "c32 factor/solve" if prec else "f64"}
+    return out
 
 
 def run_hermitian(g, torch, W):

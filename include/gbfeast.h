@@ -37,7 +37,8 @@
  *    M0 holds the subspace size kept after B-orthonormalisation (the "new
  *    suitable M0"); entries past it are zero.
  *  - Return value == *info, codes of Table "tab_info": 202 bad N, 201 bad M0,
- *    200 Emin >= Emax, 100+i bad fpm(i), 4 subspace returned (fpm(14)=1),
+ *    200 Emin >= Emax, 100+i bad fpm(i), 5 stochastic count returned
+ *    (fpm(14)=2), 4 subspace returned (fpm(14)=1),
  *    3 M0 too small (every Ritz value inside and M0 < N), 2 no convergence
  *    within fpm(4) loops, 1 no eigenvalue in the interval, 0 success,
  *    -1 allocation failure, -2 inner solver failure (zero pivot or
@@ -48,6 +49,14 @@
  *    counter-based SplitMix64 generator (Steele, Lea & Flood 2014) with seed
  *    0x3C6EF372FE94F82B, value i (column-major linear index; complex: real
  *    part 2i, imaginary part 2i+1).
+ *  - Stochastic eigenvalue count, fpm(14)=2 (guide section "Stochastic
+ *    estimate"): one contour filters M0 probe vectors Y into Q = f(B^-1 A) Y
+ *    and returns res[j] = mean over probes 0..j of Re(y^H q) (an unbiased
+ *    estimate of trace f, the eigenvalue count of the interval), M = res[M0-1]
+ *    rounded to nearest within [0, N], E = 0, X = the probes, loop 0, info 5.
+ *    Probes: X on entry when fpm(5)=1, else +1/-1 by the top bit of the same
+ *    SplitMix64 value i (column-major index; complex: real probes).  A few
+ *    nodes (fpm(2) ~ 3) and fpm(42)=1 suffice for the estimate.
  *  - Memory: the library owns its workspace (stored factorisations for all
  *    nodes, as fpm(10)=1 in the guide, subspace blocks, reduced matrices);
  *    it lives in the handle and is reused across calls.  Inputs are read

@@ -37,7 +37,7 @@
  *   - epsout = 1 at loop 0 (the hello-world output prints 1.0 at loop 0);
  *   - stochastic estimate (fpm(14)=2): Rademacher probes (fpm(5)=0) or the
  *     input X as probes (fpm(5)=1); res(j) = running mean over probes 1..j,
- *     M = res(M0) rounded to nearest and clamped at 0, X = the probes.
+ *     M = res(M0) rounded to nearest and clamped to [0, N], X = the probes.
  *
  * Arithmetic: C99 double complex, compiled with -fcx-limited-range (textbook
  * complex multiply/divide without the Annex G inf/NaN recovery).
@@ -627,7 +627,7 @@ int ora_feast(int kind, int n, const zc *A, int lda, const zc *B, int ldb,
                  * entries E[y^H f(B^-1 A) y] = trace f(B^-1 A), which is the
                  * eigenvalue count in the interval when f is the indicator.
                  * res(j) = mean of Re(y_i^H q_i) over the first j probes;
-                 * M = that mean over all M0 probes, rounded (not below 0);
+                 * M = that mean over all M0 probes, rounded, within [0, N];
                  * X returns the probes Y. */
                 double s = 0.0;
                 for (int j = 0; j < m0; ++j) {
@@ -638,7 +638,7 @@ int ora_feast(int kind, int n, const zc *A, int lda, const zc *B, int ldb,
                     E[j] = 0.0;
                 }
                 double mh = floor(res[m0 - 1] + 0.5);
-                *M = mh > 0.0 ? (int)mh : 0;
+                *M = mh > 0.0 ? (mh < n ? (int)mh : n) : 0;
                 memcpy(X, Y, sizeof(zc) * nm);
                 *loop = 0;
                 info = 5;

@@ -506,10 +506,12 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
     return gemm<TQ>(st, opa, opb, mm, nn2, kk, XQ::one(), A_, lda_, 0, B_, ldb_, 0, XQ::zero(), C_, ldc_, 0, 1);
   };
 
-  // initial subspace into Xc
+  // initial subspace into Xc (the probes of the stochastic count when fpm(14)=2)
   if (fpm[4] == 1) {
     copy_cols_kernel<TQ><<<dim3(ceil_div(n, 256), m0), 256, 0, st>>>(n, m0, (const TQ *)q.X, n, ws.Xc, n);
     GBF_LAUNCHED();
+  } else if (fpm[13] == 2) {
+    CK(rademacher_probes<TQ>(st, (long)n * m0, SUBSPACE_SEED, ws.Xc));
   } else {
     CK(random_subspace<TQ>(st, (long)n * m0, SUBSPACE_SEED, ws.Xc));
   }
@@ -551,6 +553,23 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
     CK(accumulate<TL, TQ>(st, n, m, ne, ws.w, ws.Ysol, herm ? ws.Yadj : nullptr, rc_form ? ws.Xc : nullptr,
                           rc_form ? ws.f : nullptr, ws.Q));
 
+    if (fpm[13] == 2) {
+      // stochastic count (guide section "Stochastic estimate"): Q = f(B^-1 A) Y
+      // for +-1 probes Y, so the mean of Re(y^H q) estimates trace f = the
+      // count; res(j) = running mean, M = res(M0) rounded, within [0, N],
+      // X = the probes, E = 0, info 5
+      CK(probe_running_mean<TQ>(st, n, m0, ws.Xc, ws.Q, q.res));
+      copy_cols_kernel<TQ><<<dim3(ceil_div(n, 256), m0), 256, 0, st>>>(n, m0, ws.Xc, n, (TQ *)q.X, n);
+      GBF_LAUNCHED();
+      GBF_CUDA(cudaMemsetAsync(q.E, 0, sizeof(double) * m0, st));
+      GBF_CUDA(cudaMemcpyAsync(h->hbuf, q.res + (m0 - 1), sizeof(double), cudaMemcpyDeviceToHost, st));
+      GBF_CUDA(cudaStreamSynchronize(st));
+      const double mh = std::floor(h->hbuf[0] + 0.5);
+      out.M = mh > 0.0 ? (int)std::min(mh, (double)n) : 0;
+      out.loop = 0;
+      out.m0 = m0;
+      return out.info = 5;
+    }
     if (fpm[13] == 1) {  // return the subspace after one contour
       GBF_CUDA(cudaMemsetAsync(q.X, 0, sizeof(TQ) * (size_t)n * m0, st));
       copy_cols_kernel<TQ><<<dim3(ceil_div(n, 256), m), 256, 0, st>>>(n, m, ws.Q, n, (TQ *)q.X, n);

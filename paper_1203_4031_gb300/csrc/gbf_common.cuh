@@ -301,6 +301,10 @@ template <class TY, class TQ>
 int accumulate(cudaStream_t st, int n, int m, int ne, const zd *w, const TY *Y, const TY *Yadj, const TQ *X0,
                const double *f, TQ *Q);
 template <class TQ> int random_subspace(cudaStream_t st, long count, uint64_t seed, TQ *Y);
+// Stochastic eigenvalue count (fpm(14)=2): +-1 probes from the same counter
+// generator, and res(j) = mean over probes 1..j of Re(y^H q) (device res).
+template <class TQ> int rademacher_probes(cudaStream_t st, long count, uint64_t seed, TQ *Y);
+template <class TQ> int probe_running_mean(cudaStream_t st, int n, int m, const TQ *Y, const TQ *Q, double *res);
 template <class T> int ns_prep(cudaStream_t st, int m, const T *P, T *Tn, double *norm);
 
 }  // namespace gbf

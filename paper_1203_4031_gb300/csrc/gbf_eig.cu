@@ -375,6 +375,45 @@ __global__ void random_subspace_kernel(long count, uint64_t seed, TQ *Y) {
   const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (t < count) Y[t] = rand_entry<TQ>(seed, (uint64_t)t);
 }
+// Rademacher probes of the stochastic count: +1 or -1 by the top bit of the
+// generator at the column-major index (real part only for complex types).
+template <class TQ>
+__global__ void rademacher_kernel(long count, uint64_t seed, TQ *Y) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t < count) {
+    TQ v = tr<TQ>::zero();
+    reinterpret_cast<double *>(&v)[0] = (splitmix64_at(seed, (uint64_t)t) >> 63) ? -1.0 : 1.0;
+    Y[t] = v;
+  }
+}
+
+// Stochastic count, one block per probe column j: t_j = Re(y_j^H q_j) with a
+// fixed-order FP64 tree (each thread strides the rows, then a shared-memory
+// halving), so the result does not depend on scheduling.
+constexpr int PROBE_THREADS = 256;
+template <class TQ>
+__global__ void __launch_bounds__(PROBE_THREADS) probe_form_kernel(int n, const TQ *Y, const TQ *Q, double *t) {
+  __shared__ double red[PROBE_THREADS];
+  const TQ *y = Y + (size_t)blockIdx.x * n, *q = Q + (size_t)blockIdx.x * n;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += PROBE_THREADS) acc += tr<TQ>::re(tr<TQ>::mul(tr<TQ>::conj(y[i]), q[i]));
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = PROBE_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) t[blockIdx.x] = red[0];
+}
+// res(j) = (t_1 + ... + t_j) / j, in place; one thread (m is the probe count).
+__global__ void running_mean_kernel(int m, double *res) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int j = 0; j < m; ++j) {
+    s += res[j];
+    res[j] = s / (j + 1);
+  }
+}
 
 // ------------------------------------------------------------ launchers --
 #define L1D(count) ceil_div((long)(count), 256), 256, 0, st
@@ -465,6 +504,23 @@ int random_subspace(cudaStream_t st, long count, uint64_t seed, TQ *Y) {
   return 0;
 }
 
+template <class TQ>
+int rademacher_probes(cudaStream_t st, long count, uint64_t seed, TQ *Y) {
+  rademacher_kernel<TQ><<<L1D(count)>>>(count, seed, Y);
+  GBF_LAUNCHED();
+  return 0;
+}
+template <class TQ>
+int probe_running_mean(cudaStream_t st, int n, int m, const TQ *Y, const TQ *Q, double *res) {
+  if (m < 1) return 0;
+  probe_form_kernel<TQ><<<m, PROBE_THREADS, 0, st>>>(n, Y, Q, res);
+  GBF_LAUNCHED();
+  running_mean_kernel<<<1, 32, 0, st>>>(m, res);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+
 #define EIG_INST(T)                                                                                         \
   template int heev_jacobi<T>(cudaStream_t, int, T *, double *, T *, T *, double *, int *, int *, int *);   \
   template int rr_prepare<T>(cudaStream_t, int, const T *, const T *, double *, int *, T *, T *);           \
@@ -476,6 +532,8 @@ int random_subspace(cudaStream_t st, long count, uint64_t seed, TQ *Y) {
   template int permute_cols<T>(cudaStream_t, int, int, const int *, const T *, T *);                        \
   template int eig_residual<T>(cudaStream_t, int, int, const T *, const T *, const double *, T *);          \
   template int random_subspace<T>(cudaStream_t, long, uint64_t, T *);                                \
+  template int rademacher_probes<T>(cudaStream_t, long, uint64_t, T *);                              \
+  template int probe_running_mean<T>(cudaStream_t, int, int, const T *, const T *, double *);        \
   template int spurious_flags<T>(cudaStream_t, int, int, const T *, const double *, double, double,        \
                                  const double *, int, int *);                                             \
   template int ns_prep<T>(cudaStream_t, int, const T *, T *, double *);

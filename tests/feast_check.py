@@ -9,6 +9,8 @@ Acceptance gates (the readings recorded in the design notes):
 """
 import numpy as np
 
+from paper_1203_4031_gb300 import workloads as W
+
 TOL_E = 1e-10
 TOL_R = 1e-10
 
@@ -51,3 +53,36 @@ def vector_alignment(B, Xg, Xr, E, gap_tol=1e-6):
     simple[:-1] &= ~close
     simple[1:] &= ~close
     return float(ov[simple].min()) if simple.any() else 1.0
+
+
+# ---- stochastic count (fpm(14)=2) inputs: probes and a gapped pencil ----
+SEED = 0x3C6EF372FE94F82B   # the documented seed of generated subspaces / probes
+
+
+def rademacher(n, m, seed=SEED):
+    """+1 / -1 by the top bit of SplitMix64 at the column-major index."""
+    bits = W.splitmix64(seed, np.arange(n * m, dtype=np.uint64)) >> np.uint64(63)
+    return np.where(bits.reshape(m, n).T == 1, -1.0, 1.0)
+
+
+def gapped_pencil(n, inside, herm, gen, seed):
+    """A, B with a B-orthonormal eigenbasis V and eigenvalues: `inside` of
+    them in [-0.5, 0.5], the rest with |lambda| in [2, 6]; interval [-1, 1]."""
+    r = np.random.default_rng(seed)
+    cplx = (lambda s: r.standard_normal(s) + 1j * r.standard_normal(s)) if herm else r.standard_normal
+    U, _ = np.linalg.qr(cplx((n, n)))
+    lam = np.concatenate([r.uniform(-0.5, 0.5, inside),
+                          r.choice([-1.0, 1.0], n - inside) * r.uniform(2.0, 6.0, n - inside)])
+    if gen:
+        G = cplx((n, n))
+        B = G @ G.conj().T / n + np.eye(n)
+        L = np.linalg.cholesky(B)
+        V = np.linalg.solve(L.conj().T, U)            # V^H B V = I
+        A = B @ V @ np.diag(lam) @ V.conj().T @ B     # A V = B V diag(lam)
+    else:
+        B, V = None, U
+        A = U @ np.diag(lam) @ U.conj().T
+    A = np.asfortranarray(0.5 * (A + A.conj().T))
+    if B is not None:
+        B = np.asfortranarray(0.5 * (B + B.conj().T))
+    return A, B, V, lam
