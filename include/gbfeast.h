@@ -24,10 +24,11 @@
  *                    R = A X - B X Lambda (see gbf_dsygv), so the subspace
  *                    reaches FP64 accuracy.
  *        fpm(43) LU panel width / diagonal block size (0 = default 32).
- *        fpm(44) engine of the complex FP64 GEMMs of the factorisation
- *                and the solves: 0 = tensor cores (default; exact bf16
- *                digit products, 7 digits, see gbf_zgemm_sliced), 1 =
- *                CUDA-core FMA.  FP32 factors (fpm(42)=1) use CUDA cores.
+ *        fpm(44) engine of the complex GEMMs of the factorisation and the
+ *                solves: 0 = tensor cores (default; FP64 factors: exact
+ *                bf16 digit products, 7 digits; FP32 factors (fpm(42)=1):
+ *                3xTF32 products; see gbf_zgemm_sliced S = 7 and S = 1),
+ *                1 = CUDA-core FMA.
  *  - Outputs follow Table "tab_common": E[M0] eigenvalues (first M inside the
  *    interval, ascending, then the remaining Ritz values ascending), X (N x
  *    M0, ld N) B-orthonormal Ritz vectors in the same order, res[M0] relative
@@ -223,7 +224,10 @@ int gbf_gemm_sliced(void *stream, int cplx, char opa, char opb, int m, int n, in
  * op(dB) + beta dC for interleaved complex data (prec 0: FP64, 1: FP32),
  * op in 'N','T','C', op(A) m x k, op(B) k x n with k <= 32, alpha = +1 or
  * -1, beta 0 or 1, S = 7 (FP64-class), 4 (28 bits) or 3 digits, or S = -3 (FP32 data:
- * every entry split into three bf16 parts, part products summed in FP32), batches
+ * every entry split into three bf16 parts, part products summed in FP32), or
+ * S = 1 (prec 1 only, the FP32-factor engine: every entry split into two
+ * TF32 parts hi + lo and each product formed as lo hi + hi lo + hi hi by
+ * kind::tf32 MMAs into an FP32 accumulator, about 2^-22 relative), batches
  * strided by sa, sb, sc elements.  Every operand row of op(A) / column of
  * op(B) is scaled by a power of two and split into S base-2^7 integer
  * digits held exactly in bf16; digit products are summed exactly in FP32

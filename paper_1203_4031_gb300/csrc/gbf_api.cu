@@ -412,7 +412,9 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
   // stay on CUDA cores: both FP32-class tensor-core variants (4 digits; bf16
   // three-part split with FP32 sums) were slower here, and one small complex
   // Hermitian case did not converge with them
-  const int tcS = (fpm[43] == 0 && bs <= 32 && sizeof(TL) == sizeof(zd)) ? 7 : 0;
+  // tensor-core engine: 7-digit sliced products for FP64 factors, 3xTF32
+  // for FP32 factors (k <= 32 needs the block size <= 32)
+  const int tcS = (fpm[43] == 0 && bs <= 32) ? (sizeof(TL) == sizeof(zd) ? 7 : 1) : 0;
   // the n x n products of the projections (A Q, B Q, B Y): sliced tensor-core
   // GEMMs with A and B sliced once per call, unless fpm(44) = 1
   const bool proj = fpm[43] == 0;
@@ -898,7 +900,7 @@ static size_t footprint_t(const gbf_problem *p) {
   const int bs = p->fpm[42] ? p->fpm[42] : 32;
   WS<TQ, TL> ws;
   Bump b(nullptr);
-  const int tcS = (p->fpm[43] == 0 && bs <= 32 && sizeof(TL) == sizeof(zd)) ? 7 : 0;
+  const int tcS = (p->fpm[43] == 0 && bs <= 32) ? (sizeof(TL) == sizeof(zd) ? 7 : 1) : 0;
   ws.layout(b, p->n, p->m0, ne, bs, p->kind == 1, p->dB != nullptr, p->uplo != 'F',
             p->dB != nullptr && p->uplo != 'F', pick_ksplit(p->m0, p->n), tcS, p->fpm[43] == 0);
   return b.off + 4096;
@@ -1062,7 +1064,7 @@ static int factor_impl(gbf_handle h, cudaStream_t st, int kind, char uplo, int n
   sz.take<int>((size_t)ne * n);
   sz.take<int>(ne);
   sz.take<zd>(ne);
-  const int tcS = sizeof(TL) == sizeof(zd) ? 7 : 0;
+  const int tcS = sizeof(TL) == sizeof(zd) ? 7 : 1;  // sliced FP64 / 3xTF32 FP32
   const size_t tcb = tcS ? zgemm_sliced_work(n, n, ne, tcS) : 0;
   sz.take<char>(tcb);
   sz.take<int>(4);
@@ -1126,7 +1128,7 @@ static int solve_impl(gbf_handle h, cudaStream_t st, int trans, int nrhs, const 
   int *perm = b.take<int>((size_t)ne * n);
   b.take<int>(ne);
   b.take<zd>(ne);
-  const int tcS = sizeof(TL) == sizeof(zd) ? 7 : 0;
+  const int tcS = sizeof(TL) == sizeof(zd) ? 7 : 1;  // sliced FP64 / 3xTF32 FP32
   b.take<char>(tcS ? zgemm_sliced_work(n, n, ne, tcS) : 0);
   int *tc_err = b.take<int>(4);
   const size_t base = b.off;

@@ -154,8 +154,9 @@ void prof_set_flops(int slot, double flops);  // flops known only after the laun
 // Tensor-core engine for complex GEMMs with k <= 32 (LU trailing updates and
 // solve steps): while a TcScope is active on this thread, gemm<zd> / gemm<cf>
 // calls that fit (k <= 32, alpha = +-1, beta in {0, 1}, m and n large
-// enough) run as sliced tcgen05 GEMMs with S digits (7: FP64-class for zd,
-// 3: FP32-class for cf) using the scope's workspace and error word.
+// enough) run on the tensor cores using the scope's workspace and error
+// word: S = 7 sliced digits (FP64-class) for zd, S = 1 3xTF32 products
+// (FP32-class) for cf.
 struct TcCtx {
   void *work = nullptr;
   size_t bytes = 0;

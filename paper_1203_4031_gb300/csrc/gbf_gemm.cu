@@ -7,6 +7,8 @@
 // a TM x TN register block whose rows/columns are interleaved with stride
 // BM/TM and BN/TN so that global stores and shared-memory reads are unit
 // stride across a warp.
+#include <type_traits>
+
 #include "gbf_common.cuh"
 
 namespace gbf {
@@ -163,6 +165,8 @@ template <> bool sliced_ok<cf>(cf alpha, cf beta, double &a, int &b) {
   return true;
 }
 
+constexpr long TF32_MIN_ENTRIES = 8L << 20;
+
 template <class T>
 int gemm(cudaStream_t st, char opa, char opb, int m, int n, int k, T alpha, const T *A, long lda, long sa,
          const T *B, long ldb, long sb, T beta, T *C, long ldc, long sc, int batch, int ksplit, T *work) {
@@ -171,7 +175,15 @@ int gemm(cudaStream_t st, char opa, char opb, int m, int n, int k, T alpha, cons
     double a = 0.0;
     int b1 = 0;
     TcCtx *tcx = g_tc;
-    if (tcx && tcx->S != 0 && k >= 1 && k <= 32 && m >= 16 && n >= 16 && sliced_ok<T>(alpha, beta, a, b1) &&
+    // S = 1 (3xTF32) serves the FP32 factors, the digit counts the FP64 ones.
+    // 3xTF32 adds a splitting launch and writes C at the memory rate, while
+    // the FP32 CUDA-core kernel at k = 32 is bound by its FMA rate: the
+    // tensor cores pay off once C holds a few million entries (the large
+    // trailing updates and the solves of large problems).
+    const bool tf32 = tcx && tcx->S == 1;
+    const bool kind_ok = tcx && (tf32 == std::is_same<T, cf>::value) &&
+                         (!tf32 || (long)m * n * batch >= TF32_MIN_ENTRIES);
+    if (kind_ok && tcx->S != 0 && k >= 1 && k <= 32 && m >= 16 && n >= 16 && sliced_ok<T>(alpha, beta, a, b1) &&
         zgemm_sliced_work(m, n, batch, tcx->S) <= tcx->bytes) {
       return zgemm_sliced<T>(st, tcx->S, opa, opb, m, n, k, a, A, lda, sa, B, ldb, sb, b1, C, ldc, sc, batch,
                              tcx->work, tcx->bytes, tcx->gerr);

@@ -1067,6 +1067,416 @@ static int zgemm_sliced_run(cudaStream_t st, char opa, char opb, int m, int n, i
 }
 
 // ===================================================================
+// FP32-complex GEMM on the tensor cores, k <= 32 (the shifted LU's trailing
+// updates and the blocked triangular solves of the FP32 factors):
+//   C = alpha op(A) op(B) + beta C,  C complex FP32, alpha in {+1, -1},
+//   beta in {0, 1}.
+// Complex operands use the real embedding of the sliced kernels (rows
+// 2i = (Re, -Im), 2i+1 = (Im, Re) of op(A) against columns (Re, Im) of
+// op(B); K' = 2k <= 64).  Every real entry x is split into two TF32 numbers,
+// hi = x rounded to TF32 (11 significant bits) and lo = x - hi rounded to
+// TF32, and each product is formed as lo_a hi_b + hi_a lo_b + hi_a hi_b by
+// three kind::tf32 MMAs into one FP32 TMEM accumulator ("3xTF32": the
+// dropped lo_a lo_b and the rounding of lo leave a relative error of about
+// 2^-22 per product, FP32-class).
+// The kernel is the persistent layout of zgemm_sliced_kernel: per work item
+// (column chunk, 128-row block, batch) the A planes stay resident in shared
+// memory (hi and lo, 2 K-chunks of 32 FP32 = 64 KB) while 64-column B tiles
+// (32 KB) stream through a 4-deep TMA ring; two 64-column TMEM accumulators
+// let the epilogue of tile g (16 warps: 4 lane quarters x 4 groups of 16
+// columns) overlap the MMAs of tile g + 1; C of the next tile is prefetched.
+// ===================================================================
+constexpr int TF_BN = 64;                         // output columns per tile (MMA N)
+constexpr int TF_KC = 32;                         // FP32 per K-chunk (one 128-byte swizzle row)
+constexpr int TF_A_BOX = BM * TF_KC * 4;          // 16 KB: one (plane, chunk) of an A tile
+constexpr int TF_B_BOX = TF_BN * TF_KC * 4;       // 8 KB: one (plane, chunk) of a B tile
+constexpr int TF_A_TILE = 4 * TF_A_BOX;           // hi/lo x 2 chunks
+constexpr int TF_B_TILE = 4 * TF_B_BOX;
+constexpr int TF_NB = 4;                          // B ring depth
+constexpr int TF_SMEM = TF_A_TILE + TF_NB * TF_B_TILE + 1024 + 256;
+constexpr int TF_EC = 16;                         // columns per epilogue warp
+constexpr int TF_EW = 4 * (TF_BN / TF_EC);        // epilogue warps
+constexpr int TF_THREADS = 64 + 32 * TF_EW;
+constexpr uint32_t TF_COLS = 2 * TF_BN;           // TMEM columns (two accumulators)
+
+// Instruction descriptor, kind::tf32: FP32 accumulate, TF32 A and B, both
+// K-major, M = 128, N = TF_BN.
+__host__ __device__ constexpr uint32_t idesc_tf32() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TF_BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
+// x rounded to the nearest TF32 value (ties away from zero): the low 13
+// mantissa bits cleared after adding half of their range.  Finite inputs.
+__device__ __forceinline__ float tf32_rn(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+__device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
+  hi = tf32_rn(x);
+  lo = tf32_rn(x - hi);
+}
+
+// Planes layout [plane (0 hi, 1 lo)][batch][chunk][rows][32] FP32.
+__device__ __forceinline__ long tf_idx(int plane, int b, int batch, int q, long rows, long r) {
+  return ((((long)plane * batch + b) * 2 + (q >> 5)) * rows + r) * TF_KC + (q & 31);
+}
+
+// A side: one warp per complex row i of op(A) (m x k), lane p < k holds
+// element (i, p); writes embedded rows 2i, 2i+1 (positions 2k..63 zero).
+template <class T>
+__device__ __forceinline__ void tf32_split_a(int i, int b, char opa, int m, int k, const T *A, long lda, long sa,
+                                             int batch, float *out) {
+  const int p = threadIdx.x & 31;
+  if (i >= m) return;  // warp-uniform
+  const T *Ab = A + (long)b * sa;
+  float re = 0.f, im = 0.f;
+  if (p < k) {
+    const T a = (opa == 'N') ? Ab[i + (long)p * lda] : Ab[p + (long)i * lda];
+    re = (float)a.x;
+    im = (opa == 'C') ? -(float)a.y : (float)a.y;
+  }
+  const long rows = 2L * m, r0 = 2L * i, r1 = r0 + 1;
+  float rh, rl, ih, il;
+  tf32_split(re, rh, rl);
+  tf32_split(im, ih, il);
+  if (p < k) {
+    out[tf_idx(0, b, batch, p, rows, r0)] = rh;
+    out[tf_idx(1, b, batch, p, rows, r0)] = rl;
+    out[tf_idx(0, b, batch, k + p, rows, r0)] = -ih;
+    out[tf_idx(1, b, batch, k + p, rows, r0)] = -il;
+    out[tf_idx(0, b, batch, p, rows, r1)] = ih;
+    out[tf_idx(1, b, batch, p, rows, r1)] = il;
+    out[tf_idx(0, b, batch, k + p, rows, r1)] = rh;
+    out[tf_idx(1, b, batch, k + p, rows, r1)] = rl;
+  }
+  for (int q = 2 * k + p; q < 2 * TF_KC; q += 32)
+    for (int pl = 0; pl < 2; ++pl) {
+      out[tf_idx(pl, b, batch, q, rows, r0)] = 0.f;
+      out[tf_idx(pl, b, batch, q, rows, r1)] = 0.f;
+    }
+}
+
+// B side: one warp per column c of op(B) (k x n), lane p < k holds element
+// (p, c); writes the column (Re ; Im) as one K-major row.
+template <class T>
+__device__ __forceinline__ void tf32_split_b(int c, int b, char opb, int k, int n, const T *B, long ldb, long sb,
+                                             int batch, float *out) {
+  const int p = threadIdx.x & 31;
+  if (c >= n) return;  // warp-uniform
+  const T *Bb = B + (long)b * sb;
+  float re = 0.f, im = 0.f;
+  if (p < k) {
+    const T v = (opb == 'N') ? Bb[p + (long)c * ldb] : Bb[c + (long)p * ldb];
+    re = (float)v.x;
+    im = (opb == 'C') ? -(float)v.y : (float)v.y;
+  }
+  float rh, rl, ih, il;
+  tf32_split(re, rh, rl);
+  tf32_split(im, ih, il);
+  if (p < k) {
+    out[tf_idx(0, b, batch, p, n, c)] = rh;
+    out[tf_idx(1, b, batch, p, n, c)] = rl;
+    out[tf_idx(0, b, batch, k + p, n, c)] = ih;
+    out[tf_idx(1, b, batch, k + p, n, c)] = il;
+  }
+  for (int q = 2 * k + p; q < 2 * TF_KC; q += 32) {
+    out[tf_idx(0, b, batch, q, n, c)] = 0.f;
+    out[tf_idx(1, b, batch, q, n, c)] = 0.f;
+  }
+}
+
+// Both operands in one launch: blocks [0, ablocks) split rows of op(A),
+// the rest columns of op(B); 8 warps per block, blockIdx.y = batch.
+template <class T>
+__global__ void tf32_split_kernel(char opa, char opb, int m, int n, int k, const T *A, long lda, long sa,
+                                  const T *B, long ldb, long sb, int batch, int ablocks, float *Ap, float *Bp) {
+  const int w = threadIdx.x >> 5;
+  if ((int)blockIdx.x < ablocks)
+    tf32_split_a<T>(blockIdx.x * 8 + w, blockIdx.y, opa, m, k, A, lda, sa, batch, Ap);
+  else
+    tf32_split_b<T>((blockIdx.x - ablocks) * 8 + w, blockIdx.y, opb, k, n, B, ldb, sb, batch, Bp);
+}
+
+template <bool BETA>
+__global__ void __launch_bounds__(TF_THREADS, 1)
+    ctf32_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int m, int n,
+                 int batch, int nch, int tpc, float alpha, cf *C, long ldc, long sc, int *gerr) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char *sA = base;               // [plane][chunk][128][32] FP32
+  unsigned char *sB = base + TF_A_TILE;   // TF_NB x [plane][chunk][64][32]
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + TF_A_TILE + TF_NB * TF_B_TILE);
+  uint64_t *a_full = bars, *a_empty = bars + 1;
+  uint64_t *b_full = bars + 2, *b_empty = b_full + TF_NB;
+  uint64_t *acc_full = b_empty + TF_NB, *acc_empty = acc_full + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rows = 2 * m;
+  const int nrb = (rows + BM - 1) / BM, nct = (n + TF_BN - 1) / TF_BN;
+  const int items = nch * nrb * batch;
+
+  if (threadIdx.x == 0) {
+    mbar_init(a_full, 1);
+    mbar_init(a_empty, 1);
+    for (int j = 0; j < TF_NB; ++j) {
+      mbar_init(&b_full[j], 1);
+      mbar_init(&b_empty[j], 1);
+    }
+    for (int j = 0; j < 2; ++j) {
+      mbar_init(&acc_full[j], 1);
+      mbar_init(&acc_empty[j], TF_EW);  // one arrival per epilogue warp
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_u32(tmem_slot)),
+                 "r"(TF_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ TMA --
+    int g = 0, it_local = 0, last_b = -1;
+    bool ok = true;
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it_local) {
+      const int cc = item % nch, rb = (item / nch) % nrb, b = item / (nch * nrb);
+      const int ct1 = min(nct, (cc + 1) * tpc);
+      if (it_local > 0 && !mbar_wait(a_empty, (it_local - 1) & 1, abort_flag, gerr, 41)) {
+        ok = false;
+        break;
+      }
+      mbar_expect_tx(a_full, TF_A_TILE);
+      for (int pc = 0; pc < 4; ++pc)  // (plane, chunk) = (pc / 2, pc % 2)
+        tma_load_3d(sA + pc * TF_A_BOX, &ta, a_full, 0, rb * BM, ((pc >> 1) * batch + b) * 2 + (pc & 1));
+      for (int ct = cc * tpc; ct < ct1; ++ct, ++g) {
+        const int st = g % TF_NB, use = g / TF_NB;
+        if (use > 0 && !mbar_wait(&b_empty[st], (use - 1) & 1, abort_flag, gerr, 42)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&b_full[st], TF_B_TILE);
+        for (int pc = 0; pc < 4; ++pc)
+          tma_load_3d(sB + st * TF_B_TILE + pc * TF_B_BOX, &tb, &b_full[st], 0, ct * TF_BN,
+                      ((pc >> 1) * batch + b) * 2 + (pc & 1));
+        last_b = g;
+      }
+    }
+    if (it_local > 0) mbar_drain(a_full, (it_local - 1) & 1, gerr, 43);
+    for (int gg = (last_b - TF_NB + 1 > 0 ? last_b - TF_NB + 1 : 0); gg <= last_b; ++gg)
+      mbar_drain(&b_full[gg % TF_NB], (gg / TF_NB) & 1, gerr, 44);
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA --
+    constexpr uint32_t idesc = idesc_tf32();
+    int g = 0, it_local = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it_local) {
+      const int cc = item % nch;
+      const int ct0 = cc * tpc, ct1 = min(nct, ct0 + tpc);
+      for (int ct = ct0; ct < ct1; ++ct, ++g) {
+        const int st = g % TF_NB, buf = g & 1;
+        if ((ct == ct0 && !mbar_wait(a_full, it_local & 1, abort_flag, gerr, 45)) ||
+            !mbar_wait(&b_full[st], (g / TF_NB) & 1, abort_flag, gerr, 46) ||
+            (g >= 2 && !mbar_wait(&acc_empty[buf], ((g >> 1) - 1) & 1, abort_flag, gerr, 47))) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(buf * TF_BN);
+        const unsigned char *sb = sB + st * TF_B_TILE;
+        // (a plane, b plane): lo hi, hi lo, then hi hi (smaller terms first)
+#pragma unroll
+        for (int pr = 0; pr < 3; ++pr) {
+          const int pa = (pr == 0) ? 1 : 0, pb = (pr == 1) ? 1 : 0;
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const uint64_t ad = sdesc_sw128(sm_u32(sA + (pa * 2 + c) * TF_A_BOX));
+            const uint64_t bd = sdesc_sw128(sm_u32(sb + (pb * 2 + c) * TF_B_BOX));
+#pragma unroll
+            for (int kk = 0; kk < TF_KC / 8; ++kk)  // 8 TF32 (32 bytes) per MMA
+              mma_tf32(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                       (pr == 0 && c == 0 && kk == 0) ? 0u : 1u);
+          }
+        }
+        mma_commit(&b_empty[st]);
+        mma_commit(&acc_full[buf]);
+      }
+      if (ok) mma_commit(a_empty);
+    }
+    if (g > 0) mbar_drain(&acc_full[(g - 1) & 1], ((g - 1) >> 1) & 1, gerr, 48);
+  } else if (warp >= 2) {
+    // ------------------------------------------------------- epilogue --
+    // Warp w: TMEM lanes 32 (w % 4) .. +31 (embedded rows), columns
+    // c0 .. c0 + 15 of each tile, c0 = 16 ((w - 2) / 4).  Embedded row rr is
+    // the real (rr even) or imaginary (rr odd) part of complex row rr / 2.
+    const int q = warp & 3, c0 = ((warp - 2) >> 2) * TF_EC;
+    float cnext[TF_EC];
+    auto load_c = [&](int item, int ct) {
+      const int rb = (item / nch) % nrb, b = item / (nch * nrb);
+      const int rr = rb * BM + q * 32 + lane, col0 = ct * TF_BN + c0;
+#pragma unroll
+      for (int j = 0; j < TF_EC; ++j) cnext[j] = 0.f;
+      if (BETA && rr < rows) {
+        const float *crow = reinterpret_cast<const float *>(C + (long)b * sc + (rr >> 1)) + (rr & 1);
+#pragma unroll
+        for (int j = 0; j < TF_EC; ++j)
+          if (col0 + j < n) cnext[j] = crow[2L * (col0 + j) * ldc];
+      }
+    };
+    int item = blockIdx.x, ct = 0, ct1 = 0;
+    if (item < items) {
+      ct = (item % nch) * tpc;
+      ct1 = min(nct, ct + tpc);
+      load_c(item, ct);
+    }
+    for (int g = 0; item < items; ++g) {
+      const int buf = g & 1, use = g >> 1;
+      int okw = 0;
+      if (lane == 0) okw = mbar_wait(&acc_full[buf], use & 1, abort_flag, gerr, 49) ? 1 : 0;
+      if (__shfl_sync(0xffffffffu, okw, 0) == 0) break;
+      __syncwarp();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t acc[TF_EC];
+      tmem_ld<TF_EC>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TF_BN + c0), acc);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(&acc_empty[buf])) : "memory");
+      float cur[TF_EC];
+#pragma unroll
+      for (int j = 0; j < TF_EC; ++j) cur[j] = cnext[j];
+      int nitem = item, nct0 = ct + 1;
+      if (nct0 >= ct1) {
+        nitem = item + gridDim.x;
+        if (nitem < items) nct0 = (nitem % nch) * tpc;
+      }
+      if (nitem < items) load_c(nitem, nct0);
+      const int rb = (item / nch) % nrb, b = item / (nch * nrb);
+      const int rr = rb * BM + q * 32 + lane, col0 = ct * TF_BN + c0;
+      if (rr < rows) {
+        float *crow = reinterpret_cast<float *>(C + (long)b * sc + (rr >> 1)) + (rr & 1);
+#pragma unroll
+        for (int j = 0; j < TF_EC; ++j)
+          if (col0 + j < n) {
+            const float v = __uint_as_float(acc[j]);
+            crow[2L * (col0 + j) * ldc] = BETA ? fmaf(alpha, v, cur[j]) : alpha * v;
+          }
+      }
+      if (nitem != item) {
+        item = nitem;
+        if (item < items) {
+          ct = nct0;
+          ct1 = min(nct, ct + tpc);
+        }
+      } else {
+        ct = nct0;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TF_COLS) : "memory");
+}
+
+// 3-D map over [planes x batch x chunks][rows][32] FP32 with a box of
+// (32, box_rows, 1), 128-byte swizzle.
+static int make_map_tf32(CUtensorMap *map, const void *ptr, long rows, int planes, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled unavailable");
+    return -4;
+  }
+  cuuint64_t dims[3] = {(cuuint64_t)TF_KC, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)TF_KC * 4, (cuuint64_t)rows * TF_KC * 4};
+  cuuint32_t box[3] = {(cuuint32_t)TF_KC, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return -4;
+  }
+  return 0;
+}
+
+static size_t ctf32_work(int m, int n, int batch) {
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  return al((size_t)2 * batch * 2 * (2L * m) * TF_KC * 4) + al((size_t)2 * batch * 2 * (long)n * TF_KC * 4);
+}
+
+static int ctf32_run(cudaStream_t st, char opa, char opb, int m, int n, int k, double alpha, const cf *A, long lda,
+                     long sa, const cf *B, long ldb, long sb, int beta_one, cf *C, long ldc, long sc, int batch,
+                     void *work, size_t work_bytes, int *gerr) {
+  if (k < 1 || k > TF_KC) {
+    set_error("3xTF32 GEMM: k must be in [1, 32]");
+    return -4;
+  }
+  if (alpha != 1.0 && alpha != -1.0) {
+    set_error("3xTF32 GEMM: alpha must be +1 or -1");
+    return -4;
+  }
+  const long rows = 2L * m;
+  if (ctf32_work(m, n, batch) > work_bytes) {
+    set_error("3xTF32 GEMM: workspace too small");
+    return -4;
+  }
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  float *Ap = (float *)work;
+  float *Bp = (float *)((char *)work + al((size_t)2 * batch * 2 * rows * TF_KC * 4));
+  const int sslot = prof_begin(st);
+  const int ablocks = ceil_div(m, 8);
+  tf32_split_kernel<cf><<<dim3(ablocks + ceil_div(n, 8), batch), 256, 0, st>>>(opa, opb, m, n, k, A, lda, sa, B, ldb,
+                                                                              sb, batch, ablocks, Ap, Bp);
+  prof_end(st, sslot, 0.0);
+  GBF_LAUNCHED();
+  CUtensorMap ta, tb;
+  if (int rc = make_map_tf32(&ta, Ap, rows, 4 * batch, BM)) return rc;
+  if (int rc = make_map_tf32(&tb, Bp, n, 4 * batch, TF_BN)) return rc;
+  static bool attr = false;
+  if (!attr) {
+    GBF_CUDA(cudaFuncSetAttribute(ctf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TF_SMEM));
+    GBF_CUDA(cudaFuncSetAttribute(ctf32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TF_SMEM));
+    attr = true;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int base_items = (int)ceil_div(rows, (long)BM) * batch, nct = ceil_div(n, TF_BN);
+  const int want = std::max(1, std::min(nct, ceil_div(4 * sms, base_items)));
+  const int tpc = ceil_div(nct, want), nch = ceil_div(nct, tpc);
+  const int items = base_items * nch;
+  dim3 grid(std::min(items, sms));
+  const int slot = prof_begin(st);
+  if (beta_one)
+    ctf32_kernel<true><<<grid, TF_THREADS, TF_SMEM, st>>>(ta, tb, m, n, batch, nch, tpc, (float)alpha, C, ldc, sc,
+                                                          gerr);
+  else
+    ctf32_kernel<false><<<grid, TF_THREADS, TF_SMEM, st>>>(ta, tb, m, n, batch, nch, tpc, (float)alpha, C, ldc, sc,
+                                                           gerr);
+  prof_end(st, slot, 8.0 * m * (double)n * k * batch);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+
+// ===================================================================
 // Sliced GEMM for any k (real or complex FP64 operands):
 //   C = alpha op(A) op(B) + beta C,  alpha in {+1, -1}, beta in {0, 1}.
 // Operands are sliced once into SK = 8 base-2^7 digits (56 bits relative to
@@ -1657,6 +2067,7 @@ namespace tc {
 }  // namespace tc
 
 size_t zgemm_sliced_work(int m, int n, int batch, int S) {
+  if (S == 1) return tc::ctf32_work(m, n, batch);
   S = S < 0 ? -S : S;
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
   return al((size_t)S * batch * 2L * m * tc::ZK * 2) + al((size_t)S * batch * n * tc::ZK * 2) +
@@ -1680,7 +2091,14 @@ int zgemm_sliced(cudaStream_t st, int S, char opa, char opb, int m, int n, int k
   if (S == -3)  // FP32 entries split into three bf16 parts, FP32 accumulation
     return tc::zgemm_sliced_run<T, 3, true>(st, opa, opb, m, n, k, alpha, A, lda, sa, B, ldb, sb, beta_one, C, ldc,
                                             sc, batch, work, work_bytes, gerr);
-  set_error("sliced GEMM: S must be 3, 4, 7 or -3");
+  if (S == 1) {  // complex FP32 operands and output: 3xTF32 products
+    if constexpr (std::is_same<T, cf>::value)
+      return tc::ctf32_run(st, opa, opb, m, n, k, alpha, A, lda, sa, B, ldb, sb, beta_one, C, ldc, sc, batch, work,
+                           work_bytes, gerr);
+    set_error("sliced GEMM: S = 1 (3xTF32) needs complex FP32 operands");
+    return -4;
+  }
+  set_error("sliced GEMM: S must be 1, 3, 4, 7 or -3");
   return -4;
 }
 template int zgemm_sliced<zd>(cudaStream_t, int, char, char, int, int, int, double, const zd *, long, long,

@@ -4,8 +4,11 @@ kernel in isolation:
 
   python -m paper_1203_4031_gb300.gemm_bench --kind k32 --m 4096 --n 300 --k 32 --batch 8
   python -m paper_1203_4031_gb300.gemm_bench --kind anyk --cplx 1 --m 2048 --n 300 --k 2048
+  python -m paper_1203_4031_gb300.gemm_bench --kind tf32 --m 4096 --n 4096 --k 32 --batch 2
 
 k32: gbf_zgemm_sliced (k <= 32, 7 digits, complex FP64), C -= A B.
+tf32: gbf_zgemm_sliced with S = 1 (k <= 32, complex FP32, 3xTF32 products),
+C -= A B: the engine of the FP32 factorisation's trailing updates.
 anyk: gbf_gemm_sliced (any k, 8 digits, real or complex FP64), C -= op(A) B with
 op(A) = A^T read from an (m x k)-transposed store, as the projections use it.
 Prints the time per call (CUDA events, after warm-up) and the useful FP64
@@ -19,7 +22,7 @@ from . import _ptr, _stream_ptr, last_error, lib
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kind", choices=["k32", "anyk"], default="k32")
+    ap.add_argument("--kind", choices=["k32", "anyk", "tf32"], default="k32")
     ap.add_argument("--cplx", type=int, default=1)
     ap.add_argument("--m", type=int, default=4096)
     ap.add_argument("--n", type=int, default=300)
@@ -30,7 +33,7 @@ def main(argv=None):
     a = ap.parse_args(argv)
     L = lib()
     g = torch.Generator(device="cuda").manual_seed(1)
-    cplx = 1 if a.kind == "k32" else a.cplx
+    cplx = 1 if a.kind in ("k32", "tf32") else a.cplx
     dt = torch.complex128 if cplx else torch.float64
     m, n, k, bt = a.m, a.n, a.k, a.batch
 
@@ -43,7 +46,15 @@ def main(argv=None):
     st = torch.cuda.current_stream()
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
     C = rnd(bt, n, m)
-    if a.kind == "k32":
+    if a.kind == "tf32":
+        A, B = rnd(bt, k, m).to(torch.complex64), rnd(bt, n, k).to(torch.complex64)
+        C = C.to(torch.complex64)
+        work = torch.empty(L.gbf_zgemm_sliced_work(m, n, bt, 1), dtype=torch.uint8, device="cuda")
+
+        def run():
+            return L.gbf_zgemm_sliced(_stream_ptr(st), 1, 1, b"N", b"N", m, n, k, -1.0, _ptr(A), m, m * k, _ptr(B),
+                                      k, k * n, 1, _ptr(C), m, m * n, bt, _ptr(work), work.numel(), _ptr(err))
+    elif a.kind == "k32":
         A, B = rnd(bt, k, m), rnd(bt, n, k)   # column-major m x k and k x n
         work = torch.empty(L.gbf_zgemm_sliced_work(m, n, bt, 7), dtype=torch.uint8, device="cuda")
 
@@ -71,8 +82,10 @@ def main(argv=None):
         raise RuntimeError(f"bounded wait timed out (code {err.item()})")
     ms = e0.elapsed_time(e1) / max(a.reps, 1)
     flops = (8.0 if cplx else 2.0) * m * n * k * bt
+    what = "FP32" if a.kind == "tf32" else "FP64"
+    cbytes = 2 * C.numel() * C.element_size()   # C read and written once
     print(f"{a.kind} cplx={cplx} m={m} n={n} k={k} batch={bt}: {ms * 1e3:.1f} us per call "
-          f"(slicing included), {flops / ms / 1e9:.2f} useful FP64 TFLOP/s")
+          f"(slicing included), {flops / ms / 1e9:.2f} useful {what} TFLOP/s, C traffic {cbytes / ms / 1e6:.0f} GB/s")
 
 
 if __name__ == "__main__":

@@ -28,7 +28,7 @@ def colmajor_batch(torch, mats):
     return torch.stack([x.t().contiguous() for x in mats])
 
 
-@pytest.mark.parametrize("S,prec", [(7, 0), (3, 1), (3, 0), (4, 1), (-3, 1)])
+@pytest.mark.parametrize("S,prec", [(7, 0), (3, 1), (3, 0), (4, 1), (-3, 1), (1, 1)])
 @pytest.mark.parametrize("m,n,k,batch", [(1, 1, 1, 1), (37, 33, 7, 2), (200, 100, 32, 1), (1000, 300, 32, 3),
                                          (65, 129, 17, 2)])
 @pytest.mark.parametrize("opa,opb", [("N", "N"), ("C", "N"), ("T", "C")])
@@ -54,6 +54,7 @@ def test_zgemm_sliced(gbf, S, prec, m, n, k, batch, opa, opb, alpha, beta):
     torch.cuda.synchronize()
     assert rc == 0, gbf.last_error()
     got = [Cd[i].t().to(torch.complex128) for i in range(batch)]
+    # S = 1: 3xTF32 products (about 2^-22 relative each) accumulated in FP32
     tol = (4e-14 if S == 7 else 2e-6) * k
     if prec == 1:
         tol = max(tol, 1e-6 * k)   # FP32 output rounding
@@ -94,3 +95,16 @@ def test_gemm_sliced_any_k(gbf, cplx, m, n, k, batch, opa, opb, alpha, beta):
         scale = As[i].abs().max().item() * Bs[i].abs().max().item()
         tol = 4 * kr * 2.0 ** -53 * scale + 2.0 ** -52 * ref[i].abs().max().item()
         assert (got - ref[i]).abs().max().item() <= tol, ((got - ref[i]).abs().max().item(), tol)
+
+
+def test_tf32_engine_needs_complex_fp32(gbf):
+    """S = 1 (3xTF32) is the FP32-factor engine: an FP64 call is refused
+    before anything is launched."""
+    import torch
+
+    A = torch.zeros((1, 8, 32), dtype=torch.complex128, device="cuda")
+    B = torch.zeros((1, 32, 8), dtype=torch.complex128, device="cuda")
+    C = torch.zeros((1, 32, 32), dtype=torch.complex128, device="cuda")
+    rc = gbf.zgemm_sliced("N", "N", A, B, C, alpha=1.0, beta=0, S=1)
+    torch.cuda.synchronize()
+    assert rc != 0 and "3xTF32" in gbf.last_error()

@@ -30,6 +30,7 @@ CALLS = [
     # (seed, m, n, k, batch, opa, opb, alpha, beta, S, complex dtype)
     (11, 300, 200, 32, 2, "N", "C", -1.0, 1, 7, "complex128"),
     (12, 129, 65, 17, 1, "C", "N", 1.0, 0, 3, "complex64"),
+    (13, 150, 90, 32, 2, "N", "N", -1.0, 1, 1, "complex64"),
 ]
 
 
