@@ -271,8 +271,12 @@ def run_gbf(args):
     if not args.no_serve and args.only is None and world == 1:
         from paper_1203_4031_gb300 import workloads as W
 
-        serving = run_serving(g, torch, W, args.serve_requests, args.serve_rate)
-        batched = run_batched(g, torch, W, args.batch_problems)
+        # config 5 is quoted on the mixed path with the FP64 run beside it;
+        # config 4 on both
+        serving = {name: run_serving(g, torch, W, args.serve_requests, args.serve_rate, prec=pr)
+                   for name, pr in (("mixed", 1), ("fp64", 0))}
+        batched = {name: run_batched(g, torch, W, args.batch_problems, prec=pr)
+                   for name, pr in (("fp64", 0), ("mixed", 1))}
         if not args.no_herm:
             herm = run_hermitian(g, torch, W)
 
@@ -303,7 +307,7 @@ def run_gbf(args):
         dist.destroy_process_group()
 
 
-def run_serving(g, torch, W, n_req, rate, budget=120e9, nworkers=4):
+def run_serving(g, torch, W, n_req, rate, budget=120e9, nworkers=4, prec=0):
     """Config-5 serving sample: n_req requests from the serving workload
     (Poisson arrivals at `rate`/s, n log-uniform in [128, 4096], real
     generalized or complex Hermitian 50/50, intervals holding 8-64), submitted
@@ -317,6 +321,7 @@ def run_serving(g, torch, W, n_req, rate, budget=120e9, nworkers=4):
         A, B, a, b = W.serving_matrices(rq)
         f = g.gbf_init()
         f[2] = 10
+        f[41] = prec
         probs.append((rq, g.DeviceProblem(A, B, a, b, rq["m0"], fpm=f)))
     torch.cuda.synchronize()
     srv = g.Server(budget, nworkers=nworkers)
@@ -337,7 +342,7 @@ def run_serving(g, torch, W, n_req, rate, budget=120e9, nworkers=4):
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "max_ms": float(lat.max()), "eigenpairs_per_s": float(sum(r.M for r in res) / span),
             "span_s": span, "peak_admitted_gb": st["peak"] / 1e9, "all_counts_exact": bool(ok),
-            "paths": "FP64 (tensor-core engine)",
+            "paths": "FP32 factors + FP64 correction (3xTF32 updates)" if prec else "FP64 (tensor-core engine)",
             "workload": "serving requests (config 5 distribution), bounded sample"}
 
 
@@ -400,7 +405,7 @@ def run_hermitian(g, torch, W):
     return out
 
 
-def run_batched(g, torch, W, count, nworkers=4):
+def run_batched(g, torch, W, count, nworkers=4, prec=0):
     """Config-4 sample: `count` independent real symmetric generalized problems
     (n log-uniform in [64, 1024], intervals holding 10-40, M0 = 1.5 count)
     solved by one gbf_batch_solve call, FP64 path; eigenpairs/s over the call."""
@@ -408,7 +413,9 @@ def run_batched(g, torch, W, count, nworkers=4):
     for p in W.batched_generalized(count=count, nmin=64, nmax=1024):
         A = g.fortran(torch.from_numpy(p.A).cuda())
         B = g.fortran(torch.from_numpy(p.B).cuda())
-        probs.append((p, g.DeviceProblem(A, B, p.emin, p.emax, p.m0, fpm=p.apply_fpm(g.gbf_init()))))
+        f = p.apply_fpm(g.gbf_init())
+        f[41] = prec
+        probs.append((p, g.DeviceProblem(A, B, p.emin, p.emax, p.m0, fpm=f)))
     g.batch_solve([dp for _, dp in probs[:2]], nworkers=nworkers)  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -421,7 +428,8 @@ def run_batched(g, torch, W, count, nworkers=4):
         ok = ok and r.info == 0 and r.M == int(((w >= p.emin) & (w <= p.emax)).sum())
     return {"problems": count, "eigenpairs_per_s": sum(r.M for r in outs) / dt, "ms": dt * 1e3,
             "workers": nworkers, "all_counts_exact": bool(ok),
-            "workload": "batched generalized problems (config 4 distribution), bounded sample, FP64 path"}
+            "workload": "batched generalized problems (config 4 distribution), bounded sample, "
+                        + ("mixed path" if prec else "FP64 path")}
 
 
 def measured_peaks():
