@@ -94,3 +94,20 @@ def test_driver_argument_validation_without_gpu():
         f = base.copy()
         f[idx] = bad
         assert g.feast_host(A, None, 0.5, 3.5, 5, fpm=f)["info"] == code, (idx, bad)
+
+
+def test_tensor_core_workspace_sizes():
+    """Workspace sizes are host arithmetic on the operand layouts: S digit
+    planes of bf16 (64 per embedded row) plus one 8-byte scale slot per row
+    and column for the sliced engine; for S = 1 (3xTF32), hi and lo planes
+    of 2 K-chunks x 32 FP32 per embedded row of A and per column of B."""
+    L = g.load()
+    L.gbf_zgemm_sliced_work.restype = C.c_size_t
+    L.gbf_zgemm_sliced_work.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
+    al = lambda v: (v + 255) & ~255  # noqa: E731
+    for m, n, b in [(1, 1, 1), (300, 200, 2), (4096, 4096, 8), (8191, 241, 16)]:
+        assert L.gbf_zgemm_sliced_work(m, n, b, 1) == al(2 * b * 2 * 2 * m * 32 * 4) + al(2 * b * 2 * n * 32 * 4)
+        for S in (7, 4, 3, -3):
+            s = abs(S)
+            assert L.gbf_zgemm_sliced_work(m, n, b, S) == (al(s * b * 2 * m * 64 * 2) + al(s * b * n * 64 * 2)
+                                                            + al(b * 2 * m * 8) + al(b * n * 8))
