@@ -1,3 +1,14 @@
+// Tensor-core engine for sm_103a (tcgen05 + TMA + TMEM).  This file holds:
+//   * tc_gemm_kernel: the bf16 building block described below;
+//   * zgemm_sliced_kernel: k <= 32 complex products from exact bf16 digit
+//     products (FP64-class for the FP64 factors' LU updates and solve steps);
+//   * ctf32_kernel: k <= 32 complex FP32 products as 3xTF32 (the FP32
+//     factors' large updates);
+//   * gemm_sliced_k_kernel: any-k FP64-class sliced products (projections,
+//     the recursive solves' large-K updates, reduced-space products);
+//   * the slicing / splitting kernels that lay the operands out K-major for
+//     the TMA boxes, the host launchers and the C-ABI verification entries.
+//
 // Tensor-core GEMM building block for sm_103a (tcgen05 + TMA + TMEM):
 //   C[b] (M x N, FP32, column-major, ldc) = A[b] (M x K) * B[b]^T (N x K)
 // with A and B bf16, both K-major (row r holds its K values contiguously,
