@@ -2,9 +2,9 @@
 FP64 factorisation, solves and projections run on), for profiling a single
 kernel in isolation:
 
-  python -m paper_1203_4031_gb300.gemm_bench --kind k32 --m 4096 --n 300 --k 32 --batch 8
-  python -m paper_1203_4031_gb300.gemm_bench --kind anyk --cplx 1 --m 2048 --n 300 --k 2048
-  python -m paper_1203_4031_gb300.gemm_bench --kind tf32 --m 4096 --n 4096 --k 32 --batch 2
+  python gemm_bench.py --kind k32 --m 4096 --n 300 --k 32 --batch 8
+  python gemm_bench.py --kind anyk --cplx 1 --m 2048 --n 300 --k 2048
+  python gemm_bench.py --kind tf32 --m 4096 --n 4096 --k 32 --batch 2
 
 k32: gbf_zgemm_sliced (k <= 32, 7 digits, complex FP64), C -= A B.
 tf32: gbf_zgemm_sliced with S = 1 (k <= 32, complex FP32, 3xTF32 products),
@@ -14,10 +14,13 @@ op(A) = A^T read from an (m x k)-transposed store, as the projections use it.
 Prints the time per call (CUDA events, after warm-up) and the useful FP64
 rate; inputs are seeded normal values resident on the device."""
 import argparse
+import os
+import sys
 
 import torch
 
-from . import _ptr, _stream_ptr, last_error, lib
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+from paper_1203_4031_gb300 import _ptr, _stream_ptr, last_error, lib  # noqa: E402
 
 
 def main(argv=None):

@@ -171,6 +171,60 @@ int gbf_zhegv_dev(gbf_handle h, void *stream, char uplo, int n, const double *dA
                   double *dX, int *M, double *dres, int *info, const double *Zne, const double *Wne);
 
 /* ---------------------------------------------------------------------
+ * Node sharding across processes (one GPU each): the guide's second level
+ * of parallelism ("Using the FEAST-MPI version"; "Single search interval
+ * and FEAST-MPI": the contour nodes of one interval are spread over the
+ * ranks, each factors and solves only its own shifted systems, and the
+ * filtered subspace is summed over the ranks once per iteration).
+ *
+ * Shard `rank` of `nranks` holds the nodes [rank*c, min(Ne, (rank+1)*c)),
+ * c = ceil(Ne / nranks) (gbf_shard_nodes; a shard may hold none), keeps
+ * only those factorisations, and solves only those systems.  The exchange
+ * step is one all-gather per FEAST iteration of the node solution blocks
+ * (and of the adjoint blocks for complex Hermitian problems), after which
+ * every shard forms Q with the same node-ordered sum and runs the
+ * Rayleigh-Ritz step itself (replicated, deterministic), so every shard
+ * returns the same E, X, res, M, loop, bit for bit, and these equal what
+ * the unsharded gbf_dsygv_dev / gbf_zhegv_dev return for the same inputs.
+ *
+ * The collective is the caller's (e.g. NCCL through torch.distributed):
+ *  - allgather(user, stream, dbuf, chunk_bytes): dbuf is a device buffer
+ *    of nranks chunks of chunk_bytes; on entry chunk `rank` holds this
+ *    shard's blocks (written by work queued on `stream`); on return every
+ *    chunk must hold its shard's blocks for all work queued on `stream`
+ *    after the call.  Return 0, or nonzero to fail the solve with -4.
+ *  - agree(user, code): host-side; *code holds this shard's status (0 or a
+ *    negative info); on return it must hold the minimum over all shards.
+ *    Called after the factorisation and once per iteration, so an error on
+ *    any shard ends the solve on every shard at the same point.
+ * All shards must call with the same arguments (A, B, fpm, interval, M0,
+ * nodes); dA, dB are each shard's own copies.  nranks = 1 is the unsharded
+ * solve.  Errors: -122 for a missing or inconsistent shard description;
+ * otherwise those of gbf_dsygv_dev.
+ * ------------------------------------------------------------------- */
+typedef struct {
+  int rank;    /* 0 <= rank < nranks */
+  int nranks;  /* number of shards */
+  int (*allgather)(void *user, void *stream, void *dbuf, size_t chunk_bytes);
+  int (*agree)(void *user, int *code);
+  void *user;  /* passed back to both callbacks */
+} gbf_shard;
+
+/* Nodes of shard `rank` of `nranks` for Ne = ne: *first, *count; returns the
+ * chunk size c (node blocks per shard in the exchanged buffer), or
+ * -101 / -102 / -103 for a bad ne / rank / nranks. */
+int gbf_shard_nodes(int ne, int rank, int nranks, int *first, int *count);
+
+int gbf_dsygv_dev_shard(gbf_handle h, void *stream, char uplo, int n, const double *dA, int lda, const double *dB,
+                        int ldb, int *fpm, double *epsout, int *loop, double emin, double emax, int *M0, double *dE,
+                        double *dX, int *M, double *dres, int *info, const double *Zne, const double *Wne,
+                        const gbf_shard *sh);
+int gbf_zhegv_dev_shard(gbf_handle h, void *stream, char uplo, int n, const double *dA, int lda, const double *dB,
+                        int ldb, int *fpm, double *epsout, int *loop, double emin, double emax, int *M0, double *dE,
+                        double *dX, int *M, double *dres, int *info, const double *Zne, const double *Wne,
+                        const gbf_shard *sh);
+
+/* ---------------------------------------------------------------------
  * Step-level entry points (device pointers) exposing single rows of the
  * hot path for verification and for callers that drive the iteration
  * themselves (the RCI pattern of Fig. "fig_rci").
@@ -240,10 +294,10 @@ int gbf_zgemm_sliced(void *stream, int prec, int S, char opa, char opb, int m, i
                      long ldc, long sc, int batch, void *dWork, size_t work_bytes, int *dErr);
 
 /* gbf_zgemm_sliced without any device allocation, for callers that cannot
- * allocate device memory during the call (their memory belongs to another
- * allocator, they cannot afford the device-wide synchronisation of
- * cudaMalloc/cudaFree, or they will record the sequence into a graph).
- * The guide has no counterpart.  Same operation, arguments and return codes
+ * allocate device memory during the call: their device memory belongs to
+ * another allocator (a framework's caching pool that holds the whole
+ * budget), or they cannot afford the device-wide synchronisation that
+ * cudaMalloc/cudaFree imply.  The guide has no counterpart.  Same operation, arguments and return codes
  * as gbf_zgemm_sliced, but the scratch (digit slices, scales, error word) is
  * a fixed 16 MiB device array inside the library, which every GPU that loads
  * the library keeps until the process exits.  Limits and rules:
@@ -256,7 +310,8 @@ int gbf_zgemm_sliced(void *stream, int prec, int S, char opa, char opb, int m, i
  *  - every call shares the one array and it keeps the last call's contents
  *    (the call clears what must start at zero): calls whose work overlaps on
  *    the GPU (other streams, other threads) race and must not be issued;
- *  - the call returns after its stream has finished it. */
+ *  - the call reads the error word back and synchronises `stream` before
+ *    it returns, so it returns after its stream has finished the work. */
 size_t gbf_zgemm_sliced_noalloc_max(void);
 int gbf_zgemm_sliced_noalloc(void *stream, int prec, int S, char opa, char opb, int m, int n, int k, double alpha,
                              const void *dA, long lda, long sa, const void *dB, long ldb, long sb, int beta, void *dC,

@@ -50,6 +50,9 @@ def load(build: bool = True):
            ip, vp, ip, vp, vp]
     L.gbf_dsygv_dev.argtypes = dev
     L.gbf_zhegv_dev.argtypes = dev
+    L.gbf_dsygv_dev_shard.argtypes = dev + [vp]
+    L.gbf_zhegv_dev_shard.argtypes = dev + [vp]
+    L.gbf_shard_nodes.argtypes = [C.c_int, C.c_int, C.c_int, ip, ip]
     L.gbf_factor_dev.argtypes = [vp, vp, C.c_int, C.c_int, C.c_char, C.c_int, vp, C.c_int, vp, C.c_int, C.c_int, vp]
     L.gbf_solve_dev.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp]
     L.gbf_heev_dev.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp, vp]

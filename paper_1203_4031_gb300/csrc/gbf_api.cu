@@ -237,6 +237,7 @@ struct Req {
   double *E;
   void *X;
   double *res;
+  const gbf_shard *sh;  // node sharding across processes, or null
 };
 struct Res {
   double epsout = 1.0;
@@ -277,19 +278,23 @@ template <class TQ, class TL> struct WS {
   size_t kw_bytes;
   TL *dinv_l, *dinv_u;    // 128 x 128 diagonal-block inverses (recursive solves' leaves)
 
-  void layout(Bump &b, int n, int m0, int ne, int bs, bool herm, bool hasB, bool needAf, bool needBf,
-              int ksplit, int tcS, bool proj) {
+  // ne: quadrature nodes; nf: nodes factored and solved here (all of them,
+  // or this shard's share); slots: node solution blocks (ne, or nranks x the
+  // share size so the blocks can be exchanged in equal chunks)
+  void layout(Bump &b, int n, int m0, int ne, int nf, int slots, int bs, bool herm, bool hasB, bool needAf,
+              bool needBf, int ksplit, int tcS, bool proj) {
     const size_t nn = (size_t)n * n, nm = (size_t)n * m0, mm = (size_t)m0 * m0;
     const int nblk = ceil_div(n, bs);
-    S = b.take<TL>((size_t)ne * nn);
-    Linv = b.take<TL>((size_t)ne * nblk * bs * bs);
-    Uinv = b.take<TL>((size_t)ne * nblk * bs * bs);
-    Ysol = b.take<TL>((size_t)ne * nm);
-    Yadj = herm ? b.take<TL>((size_t)ne * nm) : nullptr;
-    Ytmp = herm ? b.take<TL>((size_t)ne * nm) : nullptr;
-    ipiv = b.take<int>((size_t)ne * n);
-    perm = b.take<int>((size_t)ne * n);
-    sing = b.take<int>(ne);
+    const int nfa = std::max(nf, 1);
+    S = b.take<TL>((size_t)nfa * nn);
+    Linv = b.take<TL>((size_t)nfa * nblk * bs * bs);
+    Uinv = b.take<TL>((size_t)nfa * nblk * bs * bs);
+    Ysol = b.take<TL>((size_t)slots * nm);
+    Yadj = herm ? b.take<TL>((size_t)slots * nm) : nullptr;
+    Ytmp = herm ? b.take<TL>((size_t)nfa * nm) : nullptr;
+    ipiv = b.take<int>((size_t)nfa * n);
+    perm = b.take<int>((size_t)nfa * n);
+    sing = b.take<int>(nfa + 1);  // + the non-finite-input flag
     pos = b.take<int>(m0);
     spur = b.take<int>(m0);
     nin = b.take<int>(4);
@@ -334,14 +339,14 @@ template <class TQ, class TL> struct WS {
     w = b.take<zd>(ne);
     D = b.take<zd>((size_t)ne * m0);
     Dc = b.take<zd>((size_t)ne * m0);
-    tcw_bytes = tcS ? std::max(zgemm_sliced_work(n, n, ne, tcS), zgemm_sliced_work(n, m0, ne, tcS)) : 0;
+    tcw_bytes = tcS ? std::max(zgemm_sliced_work(n, n, nfa, tcS), zgemm_sliced_work(n, m0, nfa, tcS)) : 0;
     tcw = tcS ? (void *)b.take<char>(tcw_bytes) : nullptr;
     tc_err = b.take<int>(4);
-    kw_bytes = (tcS && sizeof(TL) == sizeof(zd)) ? solve_kwork_bytes(n, m0, bs, ne) : 0;
+    kw_bytes = (tcS && sizeof(TL) == sizeof(zd)) ? solve_kwork_bytes(n, m0, bs, nfa) : 0;
     kw = kw_bytes ? (void *)b.take<char>(kw_bytes) : nullptr;
     const bool big = kw_bytes && bs == 32 && n % 128 == 0;
-    dinv_l = big ? b.take<TL>((size_t)ne * n * 128) : nullptr;
-    dinv_u = big ? b.take<TL>((size_t)ne * n * 128) : nullptr;
+    dinv_l = big ? b.take<TL>((size_t)nfa * n * 128) : nullptr;
+    dinv_u = big ? b.take<TL>((size_t)nfa * n * 128) : nullptr;
     pja = pjb = pjq = pjh = pjx = pjw = rrw = nullptr;
     rrw_bytes = 0;
     if (proj) {
@@ -367,6 +372,38 @@ static int pick_ksplit(int m, int k) {
   return std::max(ks, 1);
 }
 
+// Share of the quadrature nodes of shard `rank` of `nranks`: the nodes are
+// dealt out in contiguous blocks of chunk = ceil(ne / nranks), so shard r
+// holds nodes [r chunk, min(ne, (r+1) chunk)) and every shard's node
+// solutions form one equal-sized chunk of the exchanged buffer.
+static void shard_share(int ne, int rank, int nranks, int *lo, int *cnt, int *chunk) {
+  const int c = ceil_div(ne, nranks);
+  const int a = std::min(ne, rank * c);
+  *lo = a;
+  *cnt = std::min(ne, a + c) - a;
+  *chunk = c;
+}
+
+// Combine a status code over all shards (the agreement callback returns the
+// minimum, so an error anywhere stops every shard at the same point).
+static int shard_agree(const gbf_shard *sh, int code) {
+  int c = code;
+  if (sh->agree(sh->user, &c) != 0) {
+    set_error("node sharding: the agreement callback failed");
+    return -4;
+  }
+  if (c != code && code == 0) set_error("node sharding: another shard stopped with info %d", c);
+  return c;
+}
+
+static int shard_allgather(const gbf_shard *sh, cudaStream_t st, void *buf, size_t chunk_bytes) {
+  if (sh->allgather(sh->user, (void *)st, buf, chunk_bytes) != 0) {
+    set_error("node sharding: the all-gather callback failed");
+    return -4;
+  }
+  return 0;
+}
+
 #define CK(...)                            \
   do {                                     \
     int rc_ = (__VA_ARGS__);               \
@@ -386,6 +423,14 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
   const bool mixed = fpm[41] == 1;
   const int ne = fpm[1];
   const int bs = fpm[42] ? fpm[42] : 32;
+  // nodes factored and solved here: all, or this shard's [nlo, nlo + nf)
+  const gbf_shard *sh = q.sh;
+  int nlo = 0, nf = ne, chunk = ne, slots = ne;
+  if (sh) {
+    shard_share(ne, sh->rank, sh->nranks, &nlo, &nf, &chunk);
+    slots = chunk * sh->nranks;
+  }
+  const int nfa = std::max(nf, 1);
   const double eps = pow(10.0, -fpm[2]);
   const double alpha = std::max(fabs(q.emin), fabs(q.emax));
   out = Res{};
@@ -421,10 +466,10 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
   WS<TQ, TL> ws;
   {
     Bump sizing(nullptr);
-    ws.layout(sizing, n, m0, ne, bs, herm, hasB, needAf, needBf, ksplit, tcS, proj);
+    ws.layout(sizing, n, m0, ne, nf, slots, bs, herm, hasB, needAf, needBf, ksplit, tcS, proj);
     if (ensure_arena(h, sizing.off + 4096)) return out.info = -1;
     Bump real(h->arena);
-    ws.layout(real, n, m0, ne, bs, herm, hasB, needAf, needBf, ksplit, tcS, proj);
+    ws.layout(real, n, m0, ne, nf, slots, bs, herm, hasB, needAf, needBf, ksplit, tcS, proj);
   }
   TcCtx tcx;
   tcx.work = ws.tcw;
@@ -442,7 +487,7 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
 
   GBF_CUDA(cudaMemcpyAsync(ws.z, zh.data(), sizeof(zd) * ne, cudaMemcpyHostToDevice, st));
   GBF_CUDA(cudaMemcpyAsync(ws.w, wh.data(), sizeof(zd) * ne, cudaMemcpyHostToDevice, st));
-  GBF_CUDA(cudaMemsetAsync(ws.sing, 0, sizeof(int) * ne, st));
+  GBF_CUDA(cudaMemsetAsync(ws.sing, 0, sizeof(int) * (nfa + 1), st));
   GBF_CUDA(cudaMemsetAsync(ws.tc_err, 0, sizeof(int) * 4, st));
   GBF_CUDA(cudaMemsetAsync(ws.flag, 0, sizeof(int) * 4, st));
 
@@ -465,22 +510,33 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
 
   // factor all nodes (kept for the whole iteration)
   CatScope cat_other(CAT_OTHER);
-  CK(form_shift<TL>(st, n, ne, ws.z, kind_of<TQ>::v, 'F', Af, lda, hasB ? (const void *)Bf : nullptr, ldb, ws.S));
-  CK(getrf_batched<TL>(st, n, ne, ws.S, ws.ipiv, ws.perm, ws.Linv, ws.Uinv, bs, ws.sing, nullptr));
+  if (nf > 0) {
+    CK(form_shift<TL>(st, n, nf, ws.z + nlo, kind_of<TQ>::v, 'F', Af, lda, hasB ? (const void *)Bf : nullptr, ldb,
+                      ws.S, ws.sing + nfa));
+    CK(getrf_batched<TL>(st, n, nf, ws.S, ws.ipiv, ws.perm, ws.Linv, ws.Uinv, bs, ws.sing, nullptr));
+  }
   {
     int *hs = (int *)h->hbuf;
-    GBF_CUDA(cudaMemcpyAsync(hs, ws.sing, sizeof(int) * ne, cudaMemcpyDeviceToHost, st));
-    GBF_CUDA(cudaMemcpyAsync(hs + ne, ws.tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GBF_CUDA(cudaMemcpyAsync(hs, ws.sing, sizeof(int) * (nfa + 1), cudaMemcpyDeviceToHost, st));
+    GBF_CUDA(cudaMemcpyAsync(hs + nfa + 1, ws.tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     GBF_CUDA(cudaStreamSynchronize(st));
-    if (hs[ne]) {
-      set_error("tensor-core GEMM: bounded wait timed out (code %d)", hs[ne]);
-      return out.info = -4;
+    int code = 0;
+    if (hs[nfa + 1]) {
+      set_error("tensor-core GEMM: bounded wait timed out (code %d)", hs[nfa + 1]);
+      code = -4;
+    } else if (hs[nfa]) {
+      set_error("A or B holds a non-finite entry (NaN or Inf)");
+      code = -2;
+    } else {
+      for (int e = 0; e < nf; ++e)
+        if (hs[e]) {
+          set_error("zero pivot in column %d of the shifted system of node %d", hs[e], nlo + e);
+          code = -2;
+          break;
+        }
     }
-    for (int e = 0; e < ne; ++e)
-      if (hs[e]) {
-        set_error("zero pivot in column %d of the shifted system of node %d", hs[e], e);
-        return out.info = -2;
-      }
+    if (sh) code = shard_agree(sh, code);
+    if (code) return out.info = code;
   }
 
   // rows of A and B (A^T = A, A^H = A: contiguous columns) sliced once
@@ -545,12 +601,25 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
     } else {
       rhs = ws.Xc;
     }
-    CK(gather_rhs<TL>(st, n, ne, m, ws.perm, kindR, rhs, n, scale, ws.Ysol));
-    CK(getrs_inplace<TL>(st, 0, n, ne, m, ws.S, ws.Linv, ws.Uinv, bs, ws.Ysol, nullptr));
-    if (herm) {
-      CK(gather_rhs<TL>(st, n, ne, m, nullptr, kindR, rhs, n, scalec, ws.Ytmp));
-      CK(getrs_inplace<TL>(st, 1, n, ne, m, ws.S, ws.Linv, ws.Uinv, bs, ws.Ytmp, nullptr));
-      CK(scatter_perm<TL>(st, n, ne, m, ws.perm, ws.Ytmp, ws.Yadj));
+    // this shard's nodes [nlo, nlo + nf) (all nodes without sharding)
+    const size_t nmc = (size_t)n * m;
+    if (nf > 0) {
+      TL *Yown = ws.Ysol + (size_t)nlo * nmc;
+      CK(gather_rhs<TL>(st, n, nf, m, ws.perm, kindR, rhs, n, scale ? scale + (size_t)nlo * m : nullptr, Yown));
+      CK(getrs_inplace<TL>(st, 0, n, nf, m, ws.S, ws.Linv, ws.Uinv, bs, Yown, nullptr));
+      if (herm) {
+        CK(gather_rhs<TL>(st, n, nf, m, nullptr, kindR, rhs, n, scalec ? scalec + (size_t)nlo * m : nullptr,
+                          ws.Ytmp));
+        CK(getrs_inplace<TL>(st, 1, n, nf, m, ws.S, ws.Linv, ws.Uinv, bs, ws.Ytmp, nullptr));
+        CK(scatter_perm<TL>(st, n, nf, m, ws.perm, ws.Ytmp, ws.Yadj + (size_t)nlo * nmc));
+      }
+    }
+    if (sh) {
+      // the exchange step: every shard receives every node's solution block,
+      // then all of them form the same Q with the node-ordered sum below
+      const size_t cb = (size_t)chunk * nmc * sizeof(TL);
+      CK(shard_allgather(sh, st, ws.Ysol, cb));
+      if (herm) CK(shard_allgather(sh, st, ws.Yadj, cb));
     }
     CK(accumulate<TL, TQ>(st, n, m, ne, ws.w, ws.Ysol, herm ? ws.Yadj : nullptr, rc_form ? ws.Xc : nullptr,
                           rc_form ? ws.f : nullptr, ws.Q));
@@ -720,9 +789,14 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
     GBF_CUDA(cudaMemcpyAsync(hs, ws.stats, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
     GBF_CUDA(cudaMemcpyAsync(h->hflag + 2, ws.tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     GBF_CUDA(cudaStreamSynchronize(st));
-    if (h->hflag[2]) {
-      set_error("tensor-core GEMM: bounded wait timed out (code %d)", h->hflag[2]);
-      return out.info = -4;
+    {
+      int code = 0;
+      if (h->hflag[2]) {
+        set_error("tensor-core GEMM: bounded wait timed out (code %d)", h->hflag[2]);
+        code = -4;
+      }
+      if (sh) code = shard_agree(sh, code);
+      if (code) return out.info = code;
     }
     const int nin = (int)hs[0];
     const double trace = hs[1], maxres = hs[2];
@@ -796,12 +870,13 @@ static gbf_context *default_ctx() {
 template <class TQ>
 static int run_dev(gbf_handle h, void *stream, char uplo, int n, const double *dA, int lda, const double *dB,
                    int ldb, int *fpm, double *epsout, int *loop, double emin, double emax, int *M0, double *dE,
-                   double *dX, int *M, double *dres, int *info, const double *Zne, const double *Wne) {
+                   double *dX, int *M, double *dres, int *info, const double *Zne, const double *Wne,
+                   const gbf_shard *sh = nullptr) {
   int code = validate(uplo, n, lda, dB != nullptr, ldb, fpm, emin, emax, M0 ? *M0 : 0);
   Res out;
   if (code == 0 && (!dA || !dE || !dX || !dres)) code = -103;
   if (code == 0) {
-    Req q{uplo, n, dA, lda, dB, ldb, fpm, emin, emax, *M0, Zne, Wne, dE, dX, dres};
+    Req q{uplo, n, dA, lda, dB, ldb, fpm, emin, emax, *M0, Zne, Wne, dE, dX, dres, sh};
     cudaStream_t st = (cudaStream_t)stream;
     if (fpm[41] == 1)
       code = feast_run<TQ, cf>(h, st, q, out);
@@ -901,7 +976,7 @@ static size_t footprint_t(const gbf_problem *p) {
   WS<TQ, TL> ws;
   Bump b(nullptr);
   const int tcS = (p->fpm[43] == 0 && bs <= 32) ? (sizeof(TL) == sizeof(zd) ? 7 : 1) : 0;
-  ws.layout(b, p->n, p->m0, ne, bs, p->kind == 1, p->dB != nullptr, p->uplo != 'F',
+  ws.layout(b, p->n, p->m0, ne, ne, ne, bs, p->kind == 1, p->dB != nullptr, p->uplo != 'F',
             p->dB != nullptr && p->uplo != 'F', pick_ksplit(p->m0, p->n), tcS, p->fpm[43] == 0);
   return b.off + 4096;
 }
@@ -1045,6 +1120,53 @@ int gbf_zhegv_dev(gbf_handle h, void *stream, char uplo, int n, const double *dA
   if (!h) return -4;
   return run_dev<zd>(h, stream, uplo, n, dA, lda, dB, ldb, fpm, epsout, loop, emin, emax, M0, dE, dX, M, dres,
                      info, Zne, Wne);
+}
+
+int gbf_shard_nodes(int ne, int rank, int nranks, int *first, int *count) {
+  if (ne < 1) return -101;
+  if (nranks < 1) return -103;
+  if (rank < 0 || rank >= nranks) return -102;
+  int lo = 0, cnt = 0, chunk = 0;
+  shard_share(ne, rank, nranks, &lo, &cnt, &chunk);
+  if (first) *first = lo;
+  if (count) *count = cnt;
+  return chunk;
+}
+
+static int check_shard(const gbf_shard *sh) {
+  if (!sh) return -122;
+  if (sh->nranks < 1 || sh->rank < 0 || sh->rank >= sh->nranks || !sh->allgather || !sh->agree) {
+    set_error("gbf_shard: need 0 <= rank < nranks and both callbacks");
+    return -122;
+  }
+  return 0;
+}
+
+int gbf_dsygv_dev_shard(gbf_handle h, void *stream, char uplo, int n, const double *dA, int lda, const double *dB,
+                        int ldb, int *fpm, double *epsout, int *loop, double emin, double emax, int *M0, double *dE,
+                        double *dX, int *M, double *dres, int *info, const double *Zne, const double *Wne,
+                        const gbf_shard *sh) {
+  if (int rc = check_shard(sh)) {
+    if (info) *info = rc;
+    return rc;
+  }
+  if (!h) h = default_ctx();
+  if (!h) return -4;
+  return run_dev<double>(h, stream, uplo, n, dA, lda, dB, ldb, fpm, epsout, loop, emin, emax, M0, dE, dX, M, dres,
+                         info, Zne, Wne, sh);
+}
+int gbf_zhegv_dev_shard(gbf_handle h, void *stream, char uplo, int n, const double *dA, int lda, const double *dB,
+                        int ldb, int *fpm, double *epsout, int *loop, double emin, double emax, int *M0, double *dE,
+                        double *dX, int *M, double *dres, int *info, const double *Zne, const double *Wne,
+                        const gbf_shard *sh) {
+  if (int rc = check_shard(sh)) {
+    if (info) *info = rc;
+    return rc;
+  }
+  if (!h) h = default_ctx();
+  if (!h) return -4;
+  return run_dev<zd>(h, stream, uplo, n, dA, lda, dB, ldb, fpm, epsout, loop, emin, emax, M0, dE, dX, M, dres,
+                     info, Zne, Wne, sh);
 }
 
 }  // extern "C"

@@ -7,6 +7,7 @@
 #include <stdio.h>
 
 #include <atomic>
+#include <mutex>
 
 namespace gbf {
 
@@ -123,6 +124,25 @@ void set_error(const char *fmt, ...);
 
 inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
 
+// Runs f() (which returns 0 or an error code) once per device for the
+// device current on the calling thread: kernel attributes such as the
+// dynamic shared-memory limit are per device, so a process-wide flag would
+// leave a second device without them.  Thread-safe; ordinals >= 64 run f()
+// on every call.
+template <class F>
+int once_per_device(std::atomic<unsigned long long> &mask, F f) {
+  int dev = 0;
+  GBF_CUDA(cudaGetDevice(&dev));
+  const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+  if (bit && (mask.load(std::memory_order_acquire) & bit)) return 0;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (bit && (mask.load(std::memory_order_acquire) & bit)) return 0;
+  if (int rc = f()) return rc;
+  mask.fetch_or(bit, std::memory_order_acq_rel);
+  return 0;
+}
+
 // -------------------------------------------------------------- profiling --
 // Optional per-category timing of launches (gbf_profile): a CUDA event pair
 // on the launching stream around each instrumented launch, with the
@@ -232,9 +252,10 @@ int gemm(cudaStream_t st, char opa, char opb, int m, int n, int k, T alpha, cons
 // ------------------------------------------------------ LU / solve (lu.cu) --
 // Form S_e = z_e B - A for all nodes (B == nullptr: B = I) in type T.
 // kindA: 0 real input (double), 1 complex input (zd). uplo: 'F','L','U'.
+// bad (may be null): set to 1 when a referenced entry of A or B is not finite.
 template <class T>
 int form_shift(cudaStream_t st, int n, int ne, const zd *z, int kindA, char uplo, const void *A,
-               long lda, const void *B, long ldb, T *S);
+               long lda, const void *B, long ldb, T *S, int *bad = nullptr);
 
 // Blocked right-looking LU with partial pivoting of ne matrices (stride n*n,
 // ld n).  ipiv 0-based absolute rows (ne x n).  perm receives the final row

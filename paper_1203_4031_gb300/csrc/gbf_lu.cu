@@ -38,7 +38,7 @@ template <> __device__ inline cf cinv<cf>(cf a) {
 template <class T>
 __global__ void form_shift_kernel(int n, int ne, const zd *__restrict__ z, int kindA, char uplo,
                                   const void *__restrict__ Av, long lda, const void *__restrict__ Bv,
-                                  long ldb, T *__restrict__ S) {
+                                  long ldb, T *__restrict__ S, int *bad) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (i >= n) return;
@@ -62,6 +62,7 @@ __global__ void form_shift_kernel(int n, int ne, const zd *__restrict__ z, int k
       b.y = 0.0;
     }
   }
+  if (bad && !(isfinite(a.x) && isfinite(a.y) && isfinite(b.x) && isfinite(b.y))) *bad = 1;
   const long nn = (long)n * n;
   const long off = i + (long)j * n;
   for (int e = 0; e < ne; ++e) {
@@ -73,9 +74,9 @@ __global__ void form_shift_kernel(int n, int ne, const zd *__restrict__ z, int k
 
 template <class T>
 int form_shift(cudaStream_t st, int n, int ne, const zd *z, int kindA, char uplo, const void *A, long lda,
-               const void *B, long ldb, T *S) {
+               const void *B, long ldb, T *S, int *bad) {
   dim3 grid(ceil_div(n, 256), n);
-  form_shift_kernel<T><<<grid, 256, 0, st>>>(n, ne, z, kindA, uplo, A, lda, B, ldb, S);
+  form_shift_kernel<T><<<grid, 256, 0, st>>>(n, ne, z, kindA, uplo, A, lda, B, ldb, S, bad);
   GBF_LAUNCHED();
   GBF_CUDA(cudaGetLastError());
   return 0;
@@ -317,12 +318,13 @@ template <class T>
 static int launch_cluster_panel(cudaStream_t st, int n, int ne, int k, int w, T *S, int *ipiv, int *sing) {
   const int rowsp = n - k;
   const size_t cap = 200 * 1024;
-  static bool attr_done = false;
-  if (!attr_done) {
+  static std::atomic<unsigned long long> attr_done{0};
+  once_per_device(attr_done, [&]() -> int {
     cudaFuncSetAttribute(lu_panel_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     cudaFuncSetAttribute(lu_panel_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    attr_done = true;
-  }
+    cudaGetLastError();
+    return 0;
+  });
   int C0 = 1;
   while (C0 < 16 && C0 * 256 < rowsp) C0 *= 2;
   // largest C first (more SMs per panel), smaller clusters when the GPU
@@ -568,12 +570,13 @@ int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T 
       const int slot2 = prof_begin(st);
       dim3 g(ceil_div(n - w, SWAP_COLS), ne);
       const size_t sm = (size_t)w * w * sizeof(T) + (size_t)w * sizeof(int);
-      static bool attr_set = false;
-      if (!attr_set) {
-        GBF_CUDA(cudaFuncSetAttribute(laswp_trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(MAX_NB * MAX_NB * sizeof(T) + MAX_NB * sizeof(int))));
-        attr_set = true;
-      }
+      static std::atomic<unsigned long long> attr_set{0};
+      if (int rc = once_per_device(attr_set, [&]() -> int {
+            GBF_CUDA(cudaFuncSetAttribute(laswp_trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(MAX_NB * MAX_NB * sizeof(T) + MAX_NB * sizeof(int))));
+            return 0;
+          }))
+        return rc;
       laswp_trsm_kernel<T><<<g, SWAP_COLS, sm, st>>>(n, k, w, S, ipiv);
       GBF_LAUNCHED();
       prof_end(st, slot2, 0.0);
@@ -819,7 +822,7 @@ int scatter_perm(cudaStream_t st, int n, int ne, int nrhs, const int *perm, cons
 
 #define GBF_INST(T)                                                                                        \
   template int form_shift<T>(cudaStream_t, int, int, const zd *, int, char, const void *, long, const void *, \
-                             long, T *);                                                                   \
+                             long, T *, int *);                                                            \
   template int getrf_batched<T>(cudaStream_t, int, int, T *, int *, int *, T *, T *, int, int *, T *);       \
   template int getrs_inplace<T>(cudaStream_t, int, int, int, int, const T *, const T *, const T *, int, T *,  \
                                 T *);                                                                      \

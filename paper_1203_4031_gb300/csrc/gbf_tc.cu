@@ -294,11 +294,12 @@ static int launch(cudaStream_t st, int M, int N, int K, int batch, const void *A
   CUtensorMap ta, tb;
   if (int rc = make_map(&ta, A, M, K, batch)) return rc;
   if (int rc = make_map(&tb, B, N, K, batch)) return rc;
-  static bool attr = false;
-  if (!attr) {
-    GBF_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  if (int rc = once_per_device(attr_done, [&]() -> int {
+      GBF_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        return 0;
+      }))
+    return rc;
   dim3 grid(ceil_div(M, BM), ceil_div(N, BN), batch);
   tc_gemm_kernel<MODE><<<grid, THREADS, SMEM_BYTES, st>>>(ta, tb, M, N, K, C, C64, ldc, sc, scale, gerr);
   GBF_LAUNCHED();
@@ -1044,14 +1045,15 @@ static int zgemm_sliced_run(cudaStream_t st, char opa, char opb, int m, int n, i
   CUtensorMap ta, tb;
   if (int rc = make_map_rows(&ta, As, rows, S * batch, BM)) return rc;
   if (int rc = make_map_rows(&tb, Bs, n, S * batch, ZBN)) return rc;
-  static bool attr = false;
-  if (!attr) {
-    GBF_CUDA(cudaFuncSetAttribute(zgemm_sliced_kernel<T, S, true, SPLIT>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, zlay<S, SPLIT>::SMEM));
-    GBF_CUDA(cudaFuncSetAttribute(zgemm_sliced_kernel<T, S, false, SPLIT>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, zlay<S, SPLIT>::SMEM));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  if (int rc = once_per_device(attr_done, [&]() -> int {
+      GBF_CUDA(cudaFuncSetAttribute(zgemm_sliced_kernel<T, S, true, SPLIT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, zlay<S, SPLIT>::SMEM));
+      GBF_CUDA(cudaFuncSetAttribute(zgemm_sliced_kernel<T, S, false, SPLIT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, zlay<S, SPLIT>::SMEM));
+        return 0;
+      }))
+    return rc;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1460,12 +1462,13 @@ static int ctf32_run(cudaStream_t st, char opa, char opb, int m, int n, int k, d
   CUtensorMap ta, tb;
   if (int rc = make_map_tf32(&ta, Ap, rows, 4 * batch, BM)) return rc;
   if (int rc = make_map_tf32(&tb, Bp, n, 4 * batch, TF_BN)) return rc;
-  static bool attr = false;
-  if (!attr) {
-    GBF_CUDA(cudaFuncSetAttribute(ctf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TF_SMEM));
-    GBF_CUDA(cudaFuncSetAttribute(ctf32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TF_SMEM));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  if (int rc = once_per_device(attr_done, [&]() -> int {
+      GBF_CUDA(cudaFuncSetAttribute(ctf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TF_SMEM));
+      GBF_CUDA(cudaFuncSetAttribute(ctf32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TF_SMEM));
+        return 0;
+      }))
+    return rc;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1937,14 +1940,15 @@ static int gemm_sliced_k_launch(cudaStream_t st, const SlicedOp &a, const Sliced
   CUtensorMap ta, tb;
   if (int rc = make_map_k(&ta, a.slices, a.rows, a.Kp, SK * batch, BM)) return rc;
   if (int rc = make_map_k(&tb, b.slices, b.rows, b.Kp, SK * batch, KBN)) return rc;
-  static bool attr = false;
-  if (!attr) {
-    GBF_CUDA(cudaFuncSetAttribute(gemm_sliced_k_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  K_SMEM));
-    GBF_CUDA(cudaFuncSetAttribute(gemm_sliced_k_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  K_SMEM));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  if (int rc = once_per_device(attr_done, [&]() -> int {
+      GBF_CUDA(cudaFuncSetAttribute(gemm_sliced_k_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    K_SMEM));
+      GBF_CUDA(cudaFuncSetAttribute(gemm_sliced_k_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    K_SMEM));
+        return 0;
+      }))
+    return rc;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -2155,9 +2159,10 @@ extern "C" int gbf_zgemm_sliced(void *stream, int prec, int S, char opa, char op
 //
 // For callers that must not allocate device memory during the call: code
 // whose device memory is owned by another allocator (a framework's caching
-// pool holding the whole budget), latency-critical paths that cannot afford
-// the device-wide synchronisation cudaMalloc/cudaFree imply, and sequences
-// that will later be recorded into a CUDA graph.  The scratch this GEMM needs
+// pool holding the whole budget), and latency-critical paths that cannot
+// afford the device-wide synchronisation cudaMalloc/cudaFree imply.  The
+// call reads its error word back and synchronises its stream before it
+// returns.  The scratch this GEMM needs
 // (digit slices, scales, error word) lives in the file-scope array below,
 // which every GPU that loads this library holds until the process exits.
 // ===================================================================

@@ -164,6 +164,15 @@ def test_info_codes_on_gpu(gbf):
     Aneg = np.diag(np.r_[1.0, 2.0, -3.0, np.arange(4.0, 11.0)])
     Bbad = np.diag(np.r_[1.0, 1.0, -1.0, np.ones(7)])
     assert gbf.feast_host(Aneg, Bbad, 0.5, 3.5, 6)["info"] == -3
+    # non-finite entries: the inner solver reports -2 (Table tab_info)
+    for bad in (np.nan, np.inf, -np.inf):
+        An = A.copy()
+        An[2, 6] = An[6, 2] = bad
+        assert gbf.feast_host(An, None, 0.5, 3.5, 5)["info"] == -2
+        Bn = np.eye(10)
+        Bn[3, 3] = bad
+        for prec in (0, 1):
+            assert gbf.feast_host(A, Bn, 0.5, 3.5, 5, fpm=fpm_for(gbf, prec))["info"] == -2
 
 
 @pytest.mark.parametrize("uplo", ["L", "U"])

@@ -3,8 +3,8 @@ times (device-pointer driver, inputs resident on the GPU):
   * n=4096 real symmetric generalized (M0=300, Ne=8): M against the Sylvester
     inertia count and the oracle's eigenvalues (stored by
     tests/golden/make_golden.py from the oracle alone), per-pair residuals;
-  * n=8192 complex Hermitian (M0=240, Ne=16, mixed path): eigenvalues against
-    the generated spectrum (A = U diag(lam) U^H exactly), residuals.
+  * n=8192 complex Hermitian (M0=240, Ne=16, mixed and FP64 paths): eigenvalues
+    against the generated spectrum (A = U diag(lam) U^H exactly), residuals.
 """
 import json
 import os
@@ -56,20 +56,21 @@ def test_real_generalized_4096(gbf, cfg2, prec, engine):
     assert rel.max() < TOL_R
     G = X.t() @ (B @ X)
     assert (G - torch.eye(M, dtype=G.dtype, device=G.device)).abs().max().item() < 1e-10
-    if os.path.exists(GOLD):
-        gold = json.load(open(GOLD))
-        assert gold["M"] == M and gold["sylvester_count"] == M
-        assert compare_eigs(E.cpu().numpy(), np.array(gold["E"]), p.emin, p.emax) < TOL_E
+    with open(GOLD) as f:
+        gold = json.load(f)
+    assert gold["M"] == M and gold["sylvester_count"] == M
+    assert compare_eigs(E.cpu().numpy(), np.array(gold["E"]), p.emin, p.emax) < TOL_E
     h.close()
 
 
-def test_complex_hermitian_8192_mixed(gbf):
+@pytest.mark.parametrize("prec", [1, 0])
+def test_complex_hermitian_8192(gbf, prec):
     import torch
 
     p = W.dense_complex_hermitian()
     A = gbf.fortran(torch.from_numpy(np.ascontiguousarray(p.A)).cuda())
     fpm = p.apply_fpm(gbf.gbf_init())
-    fpm[41] = 1
+    fpm[41] = prec
     h = gbf.Handle()
     r = gbf.feast_dev(A, None, p.emin, p.emax, p.m0, fpm=fpm, handle=h)
     torch.cuda.synchronize()
