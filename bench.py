@@ -407,7 +407,8 @@ def run_serving(g, torch, W, pool, n_req, rate, budget=120e9, nworkers=4, prec=0
     (rate None: all at once, the saturation run), submitted at their arrival
     times to gbf_server (HBM admission budget `budget`); latency = queue +
     run time per request; eigenpairs/s and requests/s over the span from the
-    first arrival to the last completion."""
+    first arrival to the last completion.  A request whose workspace exceeds
+    the whole budget is rejected (info -1) and counted apart."""
     arr = W.serving_requests(count=n_req, nmin=128, nmax=4096, rate=rate or 1.0)
     probs = [pool.problem(i, prec) for i in range(n_req)]
     torch.cuda.synchronize()
@@ -425,12 +426,13 @@ def run_serving(g, torch, W, pool, n_req, rate, budget=120e9, nworkers=4, prec=0
     st = srv.stats()
     srv.close()
     lat = np.array([r.queue_ms + r.run_ms for r in res])
-    ok = all(r.info == 0 and r.M == rq["count"] for (rq, _), r in zip(probs, res))
+    rejected = sum(1 for r in res if r.info == -1)
+    ok = all((r.info == 0 and r.M == rq["count"]) or r.info == -1 for (rq, _), r in zip(probs, res))
     return {"requests": n_req, "offered_rate_per_s": rate, "workers": nworkers, "hbm_budget_gb": budget / 1e9,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "max_ms": float(lat.max()), "eigenpairs_per_s": float(sum(r.M for r in res) / span),
             "requests_per_s": n_req / span, "span_s": span, "peak_admitted_gb": st["peak"] / 1e9,
-            "all_counts_exact": bool(ok)}
+            "rejected": rejected, "all_counts_exact": bool(ok)}
 
 
 def run_serving_suite(g, torch, W, args):
@@ -453,7 +455,10 @@ def run_serving_suite(g, torch, W, args):
             nr = args.serve_requests if (name == "mixed" and ld == 0.7) else side
             runs[f"load_{ld}"] = run_serving(g, torch, W, pool, nr, ld * cap, prec=prec)
         if name == "mixed":
-            runs["load_0.7_budget_2gb"] = run_serving(g, torch, W, pool, side, 0.7 * cap, budget=2e9, prec=prec)
+            # a budget that holds the largest request with little to spare, so
+            # that admission binds while every request still fits
+            big = 1.25 * max(pool.problem(i, prec)[1].bytes() for i in range(len(pool.descs)))
+            runs["load_0.7_tight_budget"] = run_serving(g, torch, W, pool, side, 0.7 * cap, budget=big, prec=prec)
         runs["paths"] = ("FP32 factors + FP64 correction (3xTF32 updates)" if prec
                          else "FP64 (tensor-core engine)")
         out[name] = runs

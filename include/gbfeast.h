@@ -241,9 +241,13 @@ int gbf_factor_dev(gbf_handle h, void *stream, int kind, int prec, char uplo, in
  * n x nrhs (ld n); dY: complex ne x n x nrhs (node-major, ld n), FP64
  * interleaved whatever prec the factors were made in. */
 int gbf_solve_dev(gbf_handle h, void *stream, int trans, int nrhs, const double *dRHS, double *dY);
-/* Reduced dense eigensolver of the Rayleigh-Ritz step (cyclic Jacobi):
- * dA (m x m, ld m; real if kind 0, complex interleaved if kind 1) is
- * overwritten; dW[m] ascending eigenvalues; dV (m x m) eigenvectors. */
+/* Reduced dense eigensolver of the Rayleigh-Ritz step, the one the FEAST
+ * loop runs: Householder tridiagonalisation in one thread-block cluster,
+ * bisection for the eigenvalues, inverse iteration for the eigenvectors of
+ * the tridiagonal matrix, back-transformation (cyclic Jacobi for m = 1, for
+ * m above 1024 or when no cluster shape fits).  dA (m x m, ld m; real if
+ * kind 0, complex interleaved if kind 1; full storage) may be overwritten;
+ * dW[m] ascending eigenvalues; dV (m x m) orthonormal eigenvectors. */
 int gbf_heev_dev(gbf_handle h, void *stream, int kind, int m, double *dA, double *dW, double *dV);
 
 /* Tensor-core building block (tcgen05 + TMA + TMEM, sm_103a): dC (FP32,
@@ -292,6 +296,22 @@ size_t gbf_zgemm_sliced_work(int m, int n, int batch, int S);
 int gbf_zgemm_sliced(void *stream, int prec, int S, char opa, char opb, int m, int n, int k, double alpha,
                      const void *dA, long lda, long sa, const void *dB, long ldb, long sb, int beta, void *dC,
                      long ldc, long sc, int batch, void *dWork, size_t work_bytes, int *dErr);
+
+/* 3xTF32 complex FP32 GEMM for any k on the tensor cores (verification entry
+ * of the engine behind the FP32 factors' recursive solves in the mixed
+ * path, fpm(42)=1): dC = alpha op(dA) op(dB) + beta dC for interleaved
+ * complex FP32 data (numpy complex64), op in 'N','T','C', op(A) m x k,
+ * op(B) k x n, k >= 1, alpha = +1 or -1, beta 0 or 1, batches strided by
+ * sa, sb, sc elements.  Every FP32 value of the real embedding is split
+ * into TF32 parts hi + lo and each product is formed as lo hi + hi lo +
+ * hi hi by kind::tf32 MMAs into one FP32 accumulator over the whole K
+ * (about 2^-22 relative per product).  dWork: gbf_cgemm_tf32_work bytes;
+ * dErr: one device int.  Returns 0, -4 (CUDA error / bad argument), -5 (an
+ * in-kernel bounded wait timed out).  No counterpart in the guide. */
+size_t gbf_cgemm_tf32_work(int m, int n, int k, int batch);
+int gbf_cgemm_tf32(void *stream, char opa, char opb, int m, int n, int k, double alpha, const void *dA, long lda,
+                   long sa, const void *dB, long ldb, long sb, int beta, void *dC, long ldc, long sc, int batch,
+                   void *dWork, size_t work_bytes, int *dErr);
 
 /* gbf_zgemm_sliced without any device allocation, for callers that cannot
  * allocate device memory during the call: their device memory belongs to

@@ -77,6 +77,11 @@ def load(build: bool = True):
     L.gbf_gemm_sliced.argtypes = [vp, C.c_int, C.c_char, C.c_char, C.c_int, C.c_int, C.c_int, C.c_double, vp,
                                   C.c_long, C.c_long, vp, C.c_long, C.c_long, C.c_int, vp, C.c_long, C.c_long,
                                   C.c_int, vp, C.c_size_t, vp]
+    L.gbf_cgemm_tf32_work.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
+    L.gbf_cgemm_tf32_work.restype = C.c_size_t
+    L.gbf_cgemm_tf32.argtypes = [vp, C.c_char, C.c_char, C.c_int, C.c_int, C.c_int, C.c_double, vp, C.c_long,
+                                 C.c_long, vp, C.c_long, C.c_long, C.c_int, vp, C.c_long, C.c_long, C.c_int, vp,
+                                 C.c_size_t, vp]
     L.gbf_zgemm_sliced_noalloc_max.restype = C.c_size_t
     L.gbf_zgemm_sliced_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_char, C.c_char, C.c_int, C.c_int, C.c_int,
                                            C.c_double, vp, C.c_long, C.c_long, vp, C.c_long, C.c_long, C.c_int, vp,
@@ -520,3 +525,24 @@ def zgemm_sliced_noalloc(opa, opb, A, B, C_, alpha=1.0, beta=0, S=7, stream=None
     return lib().gbf_zgemm_sliced_noalloc(_stream_ptr(stream), prec, S, opa.encode(), opb.encode(), m, n, k,
                                           float(alpha), _ptr(A), am, am * ak, _ptr(B), bk, bk * bn, int(beta),
                                           _ptr(C_), C_.shape[2], C_.shape[1] * C_.shape[2], bt)
+
+
+def cgemm_tf32(opa, opb, A, B, C_, alpha=1.0, beta=0, stream=None):
+    """gbf_cgemm_tf32 (any k, complex FP32, 3xTF32) on column-major complex64
+    CUDA tensors packed as for zgemm_sliced.  C_ is updated in place; returns
+    the code."""
+    import torch
+
+    bt = A.shape[0]
+    am, ak = A.shape[2], A.shape[1]
+    bk, bn = B.shape[2], B.shape[1]
+    m = am if opa == "N" else ak
+    k = ak if opa == "N" else am
+    n = bn if opb == "N" else bk
+    work = torch.empty(lib().gbf_cgemm_tf32_work(m, n, k, bt), dtype=torch.uint8, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device)
+    return lib().gbf_cgemm_tf32(_stream_ptr(stream), opa.encode(), opb.encode(), m, n, k, float(alpha), _ptr(A), am,
+                                am * ak, _ptr(B), bk, bk * bn, int(beta), _ptr(C_), C_.shape[2],
+                                C_.shape[1] * C_.shape[2], bt, _ptr(work), work.numel(), _ptr(err))

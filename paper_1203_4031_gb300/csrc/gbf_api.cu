@@ -274,6 +274,8 @@ template <class TQ, class TL> struct WS {
   void *pjh, *pjx, *pjw;  // Q^H (rows), Q / AQ / BQ (rows, for X = Q W), W (columns)
   void *rrw;              // both operands of the M0 x M0 x M0 reduced-space products
   size_t rrw_bytes;
+  void *trw;              // reduced eigensolver (tridiagonal route)
+  size_t trw_bytes;
   void *kw;               // any-k sliced updates of the recursive solves
   size_t kw_bytes;
   TL *dinv_l, *dinv_u;    // 128 x 128 diagonal-block inverses (recursive solves' leaves)
@@ -342,9 +344,10 @@ template <class TQ, class TL> struct WS {
     tcw_bytes = tcS ? std::max(zgemm_sliced_work(n, n, nfa, tcS), zgemm_sliced_work(n, m0, nfa, tcS)) : 0;
     tcw = tcS ? (void *)b.take<char>(tcw_bytes) : nullptr;
     tc_err = b.take<int>(4);
-    kw_bytes = (tcS && sizeof(TL) == sizeof(zd)) ? solve_kwork_bytes(n, m0, bs, nfa) : 0;
+    kw_bytes = !tcS ? 0 : (sizeof(TL) == sizeof(zd) ? solve_kwork_bytes(n, m0, bs, nfa)
+                                                     : solve_kwork_bytes_cf(n, m0, bs, nfa));
     kw = kw_bytes ? (void *)b.take<char>(kw_bytes) : nullptr;
-    const bool big = kw_bytes && bs == 32 && n % 128 == 0;
+    const bool big = kw_bytes && sizeof(TL) == sizeof(zd) && bs == 32 && n % 128 == 0;
     dinv_l = big ? b.take<TL>((size_t)nfa * n * 128) : nullptr;
     dinv_u = big ? b.take<TL>((size_t)nfa * n * 128) : nullptr;
     pja = pjb = pjq = pjh = pjx = pjw = rrw = nullptr;
@@ -362,6 +365,8 @@ template <class TQ, class TL> struct WS {
     }
     rrw_bytes = proj ? gemm_sliced_k_work(sizeof(TQ) == sizeof(zd), m0, m0, m0, 1) : 0;
     rrw = proj ? (void *)b.take<char>(rrw_bytes) : nullptr;
+    trw_bytes = heev_tridiag_work(m0, sizeof(TQ) == sizeof(zd));
+    trw = b.take<char>(trw_bytes);
   }
 };
 
@@ -751,7 +756,14 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
     CK(rr_gemm('N', 'N', m, mk, m, ws.As, m, ws.Tm, m, ws.Ctmp, m));
     CK(rr_gemm('C', 'N', mk, mk, m, ws.Tm, m, ws.Ctmp, m, ws.Cm, mk));
     CK(hermitize<TQ>(st, mk, ws.Cm, ws.Cs));
-    CK(heev_jacobi<TQ>(st, mk, ws.Cs, ws.lam, ws.U, ws.jwork, ws.dwork, ws.iwork, h->hflag, &sw_c));
+    {
+      // tridiagonal route (one cluster); cyclic Jacobi when it declines
+      const int trc = heev_tridiag<TQ>(st, mk, ws.Cs, ws.lam, ws.U, ws.trw, ws.trw_bytes);
+      if (trc == 1)
+        CK(heev_jacobi<TQ>(st, mk, ws.Cs, ws.lam, ws.U, ws.jwork, ws.dwork, ws.iwork, h->hflag, &sw_c));
+      else
+        CK(trc);
+    }
     CK(rr_gemm('N', 'N', m, mk, mk, ws.Tm, m, ws.U, mk, ws.W, m));
     CK(scale_rows<TQ>(st, m, mk, ws.s, ws.W));
     }
@@ -807,9 +819,9 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
     out.epsout = eout;
     out.m0 = mk;
     if (fpm[0] == 1)  // runtime comments (fpm(1)): one line per loop, as the guide's output
-      fprintf(stderr, "%d\t%d\t%.15e\t%.15e\t%.15e\t(M0 %d; B-orth: %s %d; reduced sweeps %d)\n", k, nin,
+      fprintf(stderr, "%d\t%d\t%.15e\t%.15e\t%.15e\t(M0 %d; B-orth: %s %d; reduced: %s %d)\n", k, nin,
               trace, eout, maxres, mk, ns_done ? "CholeskyQR passes" : "Jacobi sweeps",
-              ns_done ? ns_it : sw_b + 1, sw_c + 1);
+              ns_done ? ns_it : sw_b + 1, sw_c == -2 ? "tridiagonal" : "Jacobi sweeps", sw_c + 1);
     int info = -99;
     if (!finite) {
       set_error("non-finite Ritz values or residuals");
@@ -1258,6 +1270,11 @@ static int solve_impl(gbf_handle h, cudaStream_t st, int trans, int nrhs, const 
   TL *Y2 = b.take<TL>(ny);
   const size_t tcb = tcS ? zgemm_sliced_work(n, nrhs, ne, tcS) : 0;
   void *tcw = b.take<char>(tcb);
+  // the recursive solves of the FEAST loop (large-K products on the tensor
+  // cores: sliced for FP64 factors, 3xTF32 for FP32 ones)
+  const size_t kwb = sizeof(TL) == sizeof(zd) ? solve_kwork_bytes(n, nrhs, bs, ne)
+                                              : solve_kwork_bytes_cf(n, nrhs, bs, ne);
+  void *kw = b.take<char>(kwb);
   if (b.off + 4096 > h->cap) {
     // grow while keeping the factors
     char *na = nullptr;
@@ -1278,6 +1295,8 @@ static int solve_impl(gbf_handle h, cudaStream_t st, int trans, int nrhs, const 
   tcx.bytes = tcb;
   tcx.gerr = tc_err;
   tcx.S = tcS;
+  tcx.kwork = kw;
+  tcx.kbytes = kwb;
   TcScope tc_scope(&tcx);
   int rc;
   if (!trans) {
@@ -1339,12 +1358,22 @@ static int heev_impl(gbf_handle h, cudaStream_t st, int m, T *A, double *w, T *V
   sz.take<T>(2 * (size_t)m * m + 2 * m);
   sz.take<double>(8 + 4 * m);
   sz.take<int>(5 * m + 96);
+  const size_t tb = heev_tridiag_work(m, tr<T>::cplx);
+  sz.take<char>(tb);
   if (ensure_arena(h, sz.off + 4096)) return -1;
   h->f_prec = -1;
   Bump b(h->arena);
   T *work = b.take<T>(2 * (size_t)m * m + 2 * m);
   double *dwork = b.take<double>(8 + 4 * m);
   int *iwork = b.take<int>(5 * m + 96);
+  void *tw = b.take<char>(tb);
+  // the solver of the FEAST loop (tridiagonal route), Jacobi when it declines
+  const int trc = heev_tridiag<T>(st, m, A, w, V, tw, tb);
+  if (trc != 1) {
+    if (trc) return trc;
+    GBF_CUDA(cudaStreamSynchronize(st));
+    return 0;
+  }
   int sweeps = 0;
   const int rc = heev_jacobi<T>(st, m, A, w, V, work, dwork, iwork, h->hflag, &sweeps);
   if (rc) return rc;

@@ -190,6 +190,8 @@ struct TcCtx {
 // Workspace bytes of the recursive solves' any-k sliced updates for n x n
 // factors, nrhs right-hand sides, block size bs (node groups of up to 8).
 size_t solve_kwork_bytes(int n, int nrhs, int bs, int ne);
+// The same for FP32 factors (3xTF32 any-k updates of the recursive solves).
+size_t solve_kwork_bytes_cf(int n, int nrhs, int bs, int ne);
 extern thread_local TcCtx *g_tc;
 // Side stream (high priority) and two events of the calling context, for
 // the factorisation's look-ahead: panel k+1 runs there while the rest of
@@ -234,6 +236,13 @@ int gemm_sliced_k(cudaStream_t st, char opa, char opb, int m, int n, int k, doub
                   long sa, const T *B, long ldb, long sb, int beta_one, T *C, long ldc, long sc, int batch, void *work,
                   size_t work_bytes, int *gerr);
 size_t zgemm_sliced_work(int m, int n, int batch, int S);
+// 3xTF32 complex FP32 GEMM for any k on the tensor cores (the FP32 factors'
+// large-K solve updates): C = alpha op(A) op(B) + beta C, alpha = +-1, beta
+// in {0, 1}; work: cgemm_tf32k_work bytes (the split TF32 planes).
+size_t cgemm_tf32k_work(int m, int n, int k, int batch);
+int cgemm_tf32k(cudaStream_t st, char opa, char opb, int m, int n, int k, double alpha, const cf *A, long lda, long sa,
+                const cf *B, long ldb, long sb, int beta_one, cf *C, long ldc, long sc, int batch, void *work,
+                size_t work_bytes, int *gerr);
 template <class T>
 int zgemm_sliced(cudaStream_t st, int S, char opa, char opb, int m, int n, int k, double alpha, const T *A, long lda,
                  long sa, const T *B, long ldb, long sb, int beta_one, T *C, long ldc, long sc, int batch, void *work,
@@ -291,6 +300,19 @@ int scatter_perm(cudaStream_t st, int n, int ne, int nrhs, const int *perm, cons
 template <class T>
 int heev_jacobi(cudaStream_t st, int m, T *A, double *w, T *V, T *work, double *dwork, int *iwork, int *hflag,
                 int *sweeps_out);
+
+// Reduced Hermitian eigensolver (tridiag.cu): Householder tridiagonalisation
+// in one thread-block cluster, bisection, inverse iteration, back-transform.
+// A (m x m, ld m, full storage) is not modified; w ascending, V (m x m, ld m)
+// eigenvectors.  work: heev_tridiag_work bytes.  Returns 0, 1 when it
+// declines (m outside 2..1024 or no cluster shape fits; nothing launched),
+// or -4.
+size_t heev_tridiag_work(int m, bool cplx);
+template <class T> int heev_tridiag(cudaStream_t st, int m, const T *A, double *w, T *V, void *work, size_t work_bytes);
+// Cholesky A = L L^H of an m x m Hermitian matrix (full storage, ld m, not
+// modified) in one thread-block cluster; fail = first non-positive pivot + 1.
+// Returns 0, or 1 when the cluster kernel cannot take m (nothing launched).
+template <class T> int chol_cluster(cudaStream_t st, int m, const T *A, T *L, int *fail);
 
 // Small dense FP64 kernels (small.cu): cooperative Cholesky (A = L L^H, A
 // overwritten as workspace, fail = first non-positive pivot + 1), inverse of

@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   __shared__ R sval[32];
   __shared__ int sidx[32];
   __shared__ T urow[MAX_NB];
+  __shared__ T s_inv;
   __shared__ int s_p, s_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -160,7 +161,11 @@ __global__ void __launch_bounds__(PANEL_THREADS)
     __syncthreads();
     for (int jj = tid; jj < w; jj += blockDim.x) urow[jj] = a[c + (long)(k + jj) * n];
     __syncthreads();
-    const T inv = cinv<T>(urow[j]);
+    // the pivot's reciprocal, formed once (a complex division is several FP64
+    // divisions; every thread forming it cost more than the rank-1 update)
+    if (tid == 0) s_inv = cinv<T>(urow[j]);
+    __syncthreads();
+    const T inv = s_inv;
     T *colc = a + (long)c * n;
     for (int r = c + 1 + tid; r < n; r += blockDim.x) {
       const T l = X::mul(colc[r], inv);
@@ -202,6 +207,7 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   int *cidx = reinterpret_cast<int *>(cval + 2);
   __shared__ Rt wv[32];
   __shared__ int wi[32];
+  __shared__ T s_inv;
   __shared__ int s_p, s_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int r0 = k + q * R;
@@ -291,10 +297,14 @@ __global__ void __launch_bounds__(PANEL_THREADS)
       ipiv[(long)e * n + c] = ok ? p : c;
       if (!ok && sing[e] == 0) sing[e] = c + 1;
     }
+    // the pivot's reciprocal, formed once per CTA (a complex division is
+    // several FP64 divisions; every thread forming it cost more than the
+    // rank-1 update)
+    if (tid == 32 && ok) s_inv = cinv<T>(urow[j]);
     __syncthreads();
     // 5. scale and rank-1 update of the local rows below c
     if (ok) {
-      const T inv = cinv<T>(urow[j]);
+      const T inv = s_inv;
       for (int rl = tid; rl < rows; rl += blockDim.x) {
         if (r0 + rl <= c) continue;
         const T l = X::mul(sl[(long)j * R + rl], inv);
@@ -628,6 +638,27 @@ size_t solve_kwork_bytes(int n, int nrhs, int bs, int ne) {
   return b;
 }
 
+size_t solve_kwork_bytes_cf(int n, int nrhs, int bs, int ne) {
+  const int nblk = ceil_div(n, bs);
+  const int half = std::min(n, (nblk - nblk / 2) * bs);
+  return cgemm_tf32k_work(half, nrhs, half, std::min(ne, 8));
+}
+
+// C[e] -= op(A[e]) Y[e] for all nodes e with the any-k 3xTF32 GEMM (FP32
+// factors), nodes grouped so that each group's TF32 planes fit the workspace.
+static int tf32_update(cudaStream_t st, char opa, int m, int k, int nrhs, const cf *A, long lda, long sa,
+                       const cf *Y, long ldy, long sy, cf *C, long ldc, long sc, int ne) {
+  const size_t per = cgemm_tf32k_work(m, nrhs, k, 1);
+  const int g = (int)std::max<size_t>(1, std::min<size_t>(ne, g_tc->kbytes / std::max<size_t>(per, 1)));
+  for (int e0 = 0; e0 < ne; e0 += g) {
+    const int gb = std::min(g, ne - e0);
+    const int rc = cgemm_tf32k(st, opa, 'N', m, nrhs, k, -1.0, A + (long)e0 * sa, lda, sa, Y + (long)e0 * sy, ldy, sy,
+                               1, C + (long)e0 * sc, ldc, sc, gb, g_tc->kwork, g_tc->kbytes, g_tc->gerr);
+    if (rc) return rc;
+  }
+  return 0;
+}
+
 // C[e] -= op(A[e]) Y[e] for all nodes e with the any-k sliced GEMM, nodes
 // grouped so that each group's slices fit the workspace.
 template <class T>
@@ -694,6 +725,12 @@ static int trsv_rec(cudaStream_t st, int kind, int n, int ne, int nrhs, const T 
       done = true;
     }
   }
+  if constexpr (std::is_same<T, cf>::value) {
+    if (k > 32 && g_tc && g_tc->kwork) {  // FP32 factors: 3xTF32 on the tensor cores
+      rc = tf32_update(st, op, m, k, nrhs, A, n, nn, Y + rsrc, n, ny, Y + rdst, n, ny, ne);
+      done = true;
+    }
+  }
   if (!done) rc = gemm<T>(st, op, 'N', m, nrhs, k, m1, A, n, nn, Y + rsrc, n, ny, one, Y + rdst, n, ny, ne);
   if (rc) return rc;
   return trsv_rec<T>(st, kind, n, ne, nrhs, S, Dinv, bs, Y, forward ? mid : b0, forward ? b1 : mid);
@@ -711,9 +748,10 @@ int getrs_inplace(cudaStream_t st, int trans, int n, int ne, int nrhs, const T *
   const T m1 = X::sub(X::zero(), X::one());
   const T zero = X::zero();
   int rc;
-  // FP64 factors on the tensor-core engine: recursive (large-K products);
-  // otherwise the blocked chain, which suits the CUDA-core GEMM better
-  if constexpr (std::is_same<T, zd>::value) {
+  // factors on the tensor-core engine (FP64: sliced; FP32: 3xTF32):
+  // recursive (large-K products); otherwise the blocked chain, which suits
+  // the CUDA-core GEMM better
+  if constexpr (std::is_same<T, zd>::value || std::is_same<T, cf>::value) {
     if (g_tc && g_tc->kwork) {
       if (!trans) {
         if ((rc = trsv_rec<T>(st, 0, n, ne, nrhs, S, Linv, bs, Y, 0, nblk))) return rc;

@@ -126,6 +126,9 @@ __global__ void trinv_lower_kernel(int m, const T *L, T *Linv) {
 
 template <class T>
 int chol_lower(cudaStream_t st, int m, T *A, T *L, int *fail) {
+  // one thread-block cluster (hardware barriers) when the matrix fits in its
+  // shared memory; the cooperative grid-wide form otherwise
+  if (chol_cluster<T>(st, m, A, L, fail) == 0) return 0;
   const int threads = 512;
   const int blocks = coop_grid((const void *)chol_coop_kernel<T>, threads, 0, m);
   if (blocks < 1) {

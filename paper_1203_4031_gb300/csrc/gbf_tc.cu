@@ -1491,6 +1491,319 @@ static int ctf32_run(cudaStream_t st, char opa, char opb, int m, int n, int k, d
 }
 
 // ===================================================================
+// 3xTF32 complex FP32 GEMM for any k (the FP32 factors' solves and updates
+// with large K):  C = alpha op(A) op(B) + beta C, alpha = +-1, beta 0 / 1.
+// Operands are split once per call into TF32 planes hi = rn(x), lo =
+// rn(x - hi) of the real embedding (row 2i = (Re, -Im), 2i+1 = (Im, Re) of
+// op(A) against column (Re, Im) of op(B)), laid out K-major in chunks of 32
+// FP32 with the real parts in chunks [0, nk) and the imaginary parts in
+// chunks [nk, 2 nk) (k padded to nk = ceil(k / 32) chunks).  Work item =
+// (128 embedded rows, 128 columns, batch), column tile fastest so that the
+// CTAs working at the same time share their A rows in L2; per K chunk one
+// stage of the TMA ring holds A hi, A lo (16 KB each) and B hi, B lo (16 KB
+// each) and the MMA thread issues lo hi, hi lo, hi hi (4 kind::tf32 MMAs of
+// K = 8 each) into an FP32 TMEM accumulator.  The tensor cores' FP32
+// accumulation loses accuracy roughly in proportion to the number of terms
+// (measured: 1e-6 relative at K = 64, 1e-4 at K = 8192), so an accumulator
+// covers only one group of TK_KG chunks (128 real positions); the epilogue
+// adds each group's sums into registers with FP32 round-to-nearest adds and
+// writes C once per item.  Two TMEM buffers (2 x 128 columns) let the
+// epilogue drain one group while the MMAs fill the next.  16 epilogue
+// warps: 4 lane quarters x 4 groups of 32 columns.  Bounded waits as in the
+// other kernels.
+// ===================================================================
+constexpr int TK_BN = 128;
+constexpr int TK_BOX = BM * TF_KC * 4;               // 16 KB: one plane of one chunk (A, or B with 128 rows)
+constexpr int TK_STAGE = 4 * TK_BOX;                 // A hi, A lo, B hi, B lo
+constexpr int TK_NS = 3;
+constexpr int TK_SMEM = TK_NS * TK_STAGE + 1024 + 256;
+constexpr int TK_EC = 32;
+constexpr int TK_KG = 4;                             // K chunks per TMEM accumulation group
+constexpr int TK_EW = 4 * (TK_BN / TK_EC);
+constexpr int TK_THREADS = 64 + 32 * TK_EW;
+constexpr uint32_t TK_COLS = 2 * TK_BN;
+
+__host__ __device__ constexpr uint32_t idesc_tf32_n(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+// Plane layout [plane (0 hi, 1 lo)][batch][chunk][rows][32] FP32.
+__device__ __forceinline__ long tk_idx(int plane, int b, int batch, int nch, int ch, long rows, long r, int kk) {
+  return (((((long)plane * batch + b) * nch + ch) * rows + r) * TF_KC) + kk;
+}
+
+// One block per 32 x 32 tile of op(X) (rows i0.., K positions p0..) of
+// batch blockIdx.z: read coalesced along the stored dimension through
+// shared memory, write the hi / lo planes of the embedded rows.  asA: rows
+// of op(A) (two embedded rows each), else columns of op(B).
+template <class T>
+__global__ void __launch_bounds__(256) tf32k_split_kernel(int asA, char op, int rows, int k, int nk, const T *X, long ld,
+                                                          long sx, int batch, float *out) {
+  __shared__ float sre[32][33], sim[32][33];
+  const int i0 = blockIdx.x * 32, p0 = blockIdx.y * 32, b = blockIdx.z;
+  const T *Xb = X + (long)b * sx;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows of 32 threads
+  // op(X)(i, p): op 'N' -> X[i + p ld] (asA) / X[p + i ld] (B side, column i
+  // of op(B) = column i of X); 'T' / 'C' the transposed access
+  const bool i_fast = asA ? (op == 'N') : (op != 'N');
+  for (int r = ty; r < 32; r += 8) {
+    const int a = i_fast ? (i0 + tx) : (i0 + r);  // index i
+    const int p = i_fast ? (p0 + r) : (p0 + tx);  // index p
+    float re = 0.f, im = 0.f;
+    if (a < rows && p < k) {
+      const bool trans = asA ? (op != 'N') : (op == 'N');
+      const T v = trans ? Xb[p + (long)a * ld] : Xb[a + (long)p * ld];
+      re = (float)v.x;
+      im = (op == 'C') ? -(float)v.y : (float)v.y;
+    }
+    const int li = a - i0, lp = p - p0;
+    sre[li][lp] = re;
+    sim[li][lp] = im;
+  }
+  __syncthreads();
+  const int ch = p0 / TF_KC;
+  const long orows = asA ? 2L * rows : (long)rows;
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + r;
+    if (i >= rows) continue;
+    float rh, rl, ih, il;
+    tf32_split(sre[r][tx], rh, rl);
+    tf32_split(sim[r][tx], ih, il);
+    if (asA) {
+      const long r0 = 2L * i, r1 = r0 + 1;
+      out[tk_idx(0, b, batch, 2 * nk, ch, orows, r0, tx)] = rh;
+      out[tk_idx(1, b, batch, 2 * nk, ch, orows, r0, tx)] = rl;
+      out[tk_idx(0, b, batch, 2 * nk, nk + ch, orows, r0, tx)] = -ih;
+      out[tk_idx(1, b, batch, 2 * nk, nk + ch, orows, r0, tx)] = -il;
+      out[tk_idx(0, b, batch, 2 * nk, ch, orows, r1, tx)] = ih;
+      out[tk_idx(1, b, batch, 2 * nk, ch, orows, r1, tx)] = il;
+      out[tk_idx(0, b, batch, 2 * nk, nk + ch, orows, r1, tx)] = rh;
+      out[tk_idx(1, b, batch, 2 * nk, nk + ch, orows, r1, tx)] = rl;
+    } else {
+      out[tk_idx(0, b, batch, 2 * nk, ch, orows, i, tx)] = rh;
+      out[tk_idx(1, b, batch, 2 * nk, ch, orows, i, tx)] = rl;
+      out[tk_idx(0, b, batch, 2 * nk, nk + ch, orows, i, tx)] = ih;
+      out[tk_idx(1, b, batch, 2 * nk, nk + ch, orows, i, tx)] = il;
+    }
+  }
+}
+
+template <bool BETA>
+__global__ void __launch_bounds__(TK_THREADS, 1)
+    ctf32k_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int m, int n,
+                  int batch, int nk, float alpha, cf *C, long ldc, long sc, int *gerr) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + TK_NS * TK_STAGE);
+  uint64_t *full = bars, *empty = bars + TK_NS;
+  uint64_t *acc_full = empty + TK_NS, *acc_empty = acc_full + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rows = 2 * m, nch = 2 * nk;
+  const int nrb = (rows + BM - 1) / BM, nct = (n + TK_BN - 1) / TK_BN;
+  const int items = nct * nrb * batch;
+
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < TK_NS; ++j) {
+      mbar_init(&full[j], 1);
+      mbar_init(&empty[j], 1);
+    }
+    for (int j = 0; j < 2; ++j) {
+      mbar_init(&acc_full[j], 1);
+      mbar_init(&acc_empty[j], TK_EW);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_u32(tmem_slot)),
+                 "r"(TK_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ TMA --
+    int g = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      const int ct = item % nct, rb = (item / nct) % nrb, b = item / (nct * nrb);
+      for (int ch = 0; ch < nch; ++ch, ++g) {
+        const int s = g % TK_NS, use = g / TK_NS;
+        if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, abort_flag, gerr, 61)) {
+          ok = false;
+          break;
+        }
+        unsigned char *st = base + s * TK_STAGE;
+        mbar_expect_tx(&full[s], TK_STAGE);
+        for (int pl = 0; pl < 2; ++pl) {
+          tma_load_3d(st + pl * TK_BOX, &ta, &full[s], 0, rb * BM, (pl * batch + b) * nch + ch);
+          tma_load_3d(st + (2 + pl) * TK_BOX, &tb, &full[s], 0, ct * TK_BN, (pl * batch + b) * nch + ch);
+        }
+      }
+    }
+    for (int gg = (g - TK_NS > 0 ? g - TK_NS : 0); gg < g; ++gg) mbar_drain(&full[gg % TK_NS], (gg / TK_NS) & 1, gerr, 62);
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA --
+    constexpr uint32_t idesc = idesc_tf32_n(TK_BN);
+    int g = 0, gq = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      for (int c0 = 0; c0 < nch && ok; c0 += TK_KG, ++gq) {
+        const int buf = gq & 1;
+        if (gq >= 2 && !mbar_wait(&acc_empty[buf], ((gq >> 1) - 1) & 1, abort_flag, gerr, 63)) {
+          ok = false;
+          break;
+        }
+        const uint32_t d = tmem + (uint32_t)(buf * TK_BN);
+        const int c1 = min(nch, c0 + TK_KG);
+        for (int ch = c0; ch < c1; ++ch, ++g) {
+          const int s = g % TK_NS;
+          if (!mbar_wait(&full[s], (g / TK_NS) & 1, abort_flag, gerr, 64)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const unsigned char *st = base + s * TK_STAGE;
+          // (a plane, b plane): lo hi, hi lo, hi hi
+#pragma unroll
+          for (int pr = 0; pr < 3; ++pr) {
+            const int pa = (pr == 0) ? 1 : 0, pb = (pr == 1) ? 1 : 0;
+            const uint64_t ad = sdesc_sw128(sm_u32(st + pa * TK_BOX));
+            const uint64_t bd = sdesc_sw128(sm_u32(st + (2 + pb) * TK_BOX));
+#pragma unroll
+            for (int kk = 0; kk < TF_KC / 8; ++kk)
+              mma_tf32(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                       (ch == c0 && pr == 0 && kk == 0) ? 0u : 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(&acc_full[buf]);
+      }
+    }
+    if (gq > 0) mbar_drain(&acc_full[(gq - 1) & 1], ((gq - 1) >> 1) & 1, gerr, 65);
+  } else if (warp >= 2) {
+    // ------------------------------------------------------- epilogue --
+    const int q = warp & 3, c0 = ((warp - 2) >> 2) * TK_EC;
+    int gq = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      const int ct = item % nct, rb = (item / nct) % nrb, b = item / (nct * nrb);
+      const int rr = rb * BM + q * 32 + lane, col0 = ct * TK_BN + c0;
+      // C of this tile while the MMAs run
+      float cold[TK_EC], sum[TK_EC];
+#pragma unroll
+      for (int j = 0; j < TK_EC; ++j) {
+        cold[j] = 0.f;
+        sum[j] = 0.f;
+      }
+      float *crow = nullptr;
+      if (rr < rows) {
+        crow = reinterpret_cast<float *>(C + (long)b * sc + (rr >> 1)) + (rr & 1);
+        if (BETA) {
+#pragma unroll
+          for (int j = 0; j < TK_EC; ++j)
+            if (col0 + j < n) cold[j] = crow[2L * (col0 + j) * ldc];
+        }
+      }
+      for (int k0 = 0; k0 < nch; k0 += TK_KG, ++gq) {
+        const int buf = gq & 1;
+        int okw = 0;
+        if (lane == 0) okw = mbar_wait(&acc_full[buf], (gq >> 1) & 1, abort_flag, gerr, 66) ? 1 : 0;
+        if (__shfl_sync(0xffffffffu, okw, 0) == 0) {
+          ok = false;
+          break;
+        }
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint32_t acc[TK_EC];
+        tmem_ld<16>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TK_BN + c0), acc);
+        tmem_ld<16>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TK_BN + c0 + 16), acc + 16);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(&acc_empty[buf])) : "memory");
+#pragma unroll
+        for (int j = 0; j < TK_EC; ++j) sum[j] += __uint_as_float(acc[j]);
+      }
+      if (ok && crow) {
+#pragma unroll
+        for (int j = 0; j < TK_EC; ++j)
+          if (col0 + j < n) crow[2L * (col0 + j) * ldc] = BETA ? fmaf(alpha, sum[j], cold[j]) : alpha * sum[j];
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TK_COLS) : "memory");
+}
+
+static size_t ctf32k_work(int m, int n, int k, int batch) {
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t nk = (size_t)ceil_div(k, TF_KC);
+  return al((size_t)2 * batch * 2 * nk * (2L * m) * TF_KC * 4) + al((size_t)2 * batch * 2 * nk * (long)n * TF_KC * 4);
+}
+
+static int ctf32k_run(cudaStream_t st, char opa, char opb, int m, int n, int k, double alpha, const cf *A, long lda,
+                      long sa, const cf *B, long ldb, long sb, int beta_one, cf *C, long ldc, long sc, int batch,
+                      void *work, size_t work_bytes, int *gerr) {
+  if (k < 1) {
+    set_error("3xTF32 GEMM: k must be >= 1");
+    return -4;
+  }
+  if (alpha != 1.0 && alpha != -1.0) {
+    set_error("3xTF32 GEMM: alpha must be +1 or -1");
+    return -4;
+  }
+  if (ctf32k_work(m, n, k, batch) > work_bytes) {
+    set_error("3xTF32 GEMM: workspace too small");
+    return -4;
+  }
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const int nk = ceil_div(k, TF_KC);
+  const long rows = 2L * m;
+  float *Ap = (float *)work;
+  float *Bp = (float *)((char *)work + al((size_t)2 * batch * 2 * nk * rows * TF_KC * 4));
+  const int sslot = prof_begin(st);
+  tf32k_split_kernel<cf><<<dim3(ceil_div(m, 32), nk, batch), 256, 0, st>>>(1, opa, m, k, nk, A, lda, sa, batch, Ap);
+  tf32k_split_kernel<cf><<<dim3(ceil_div(n, 32), nk, batch), 256, 0, st>>>(0, opb, n, k, nk, B, ldb, sb, batch, Bp);
+  prof_end(st, sslot, 0.0);
+  g_launches.fetch_add(2, std::memory_order_relaxed);
+  CUtensorMap ta, tb;
+  if (int rc = make_map_tf32(&ta, Ap, rows, 2 * batch * 2 * nk, BM)) return rc;
+  if (int rc = make_map_tf32(&tb, Bp, n, 2 * batch * 2 * nk, TK_BN)) return rc;
+  static std::atomic<unsigned long long> attr_done{0};
+  if (int rc = once_per_device(attr_done, [&]() -> int {
+        GBF_CUDA(cudaFuncSetAttribute(ctf32k_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_SMEM));
+        GBF_CUDA(cudaFuncSetAttribute(ctf32k_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_SMEM));
+        return 0;
+      }))
+    return rc;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int items = ceil_div(rows, BM) * ceil_div(n, TK_BN) * batch;
+  dim3 grid(std::min(items, sms));
+  const int slot = prof_begin(st);
+  if (beta_one)
+    ctf32k_kernel<true><<<grid, TK_THREADS, TK_SMEM, st>>>(ta, tb, m, n, batch, nk, (float)alpha, C, ldc, sc, gerr);
+  else
+    ctf32k_kernel<false><<<grid, TK_THREADS, TK_SMEM, st>>>(ta, tb, m, n, batch, nk, (float)alpha, C, ldc, sc, gerr);
+  prof_end(st, slot, 8.0 * m * (double)n * k * batch);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+
+// ===================================================================
 // Sliced GEMM for any k (real or complex FP64 operands):
 //   C = alpha op(A) op(B) + beta C,  alpha in {+1, -1}, beta in {0, 1}.
 // Operands are sliced once into SK = 8 base-2^7 digits (56 bits relative to
@@ -2116,6 +2429,16 @@ int zgemm_sliced(cudaStream_t st, int S, char opa, char opb, int m, int n, int k
   set_error("sliced GEMM: S must be 1, 3, 4, 7 or -3");
   return -4;
 }
+
+size_t cgemm_tf32k_work(int m, int n, int k, int batch) { return tc::ctf32k_work(m, n, k, batch); }
+
+int cgemm_tf32k(cudaStream_t st, char opa, char opb, int m, int n, int k, double alpha, const cf *A, long lda, long sa,
+                const cf *B, long ldb, long sb, int beta_one, cf *C, long ldc, long sc, int batch, void *work,
+                size_t work_bytes, int *gerr) {
+  if (m <= 0 || n <= 0 || batch <= 0) return 0;
+  return tc::ctf32k_run(st, opa, opb, m, n, k, alpha, A, lda, sa, B, ldb, sb, beta_one, C, ldc, sc, batch, work,
+                        work_bytes, gerr);
+}
 template int zgemm_sliced<zd>(cudaStream_t, int, char, char, int, int, int, double, const zd *, long, long,
                               const zd *, long, long, int, zd *, long, long, int, void *, size_t, int *);
 template int zgemm_sliced<cf>(cudaStream_t, int, char, char, int, int, int, double, const cf *, long, long,
@@ -2233,6 +2556,19 @@ extern "C" int gbf_zgemm_sliced_noalloc(void *stream, int prec, int S, char opa,
     return -5;
   }
   return 0;
+}
+
+// Verification entry (C ABI) of the 3xTF32 complex FP32 GEMM for any k.
+extern "C" size_t gbf_cgemm_tf32_work(int m, int n, int k, int batch) {
+  return gbf::cgemm_tf32k_work(m, n, std::max(k, 1), batch);
+}
+extern "C" int gbf_cgemm_tf32(void *stream, char opa, char opb, int m, int n, int k, double alpha, const void *dA,
+                              long lda, long sa, const void *dB, long ldb, long sb, int beta, void *dC, long ldc,
+                              long sc, int batch, void *dWork, size_t work_bytes, int *dErr) {
+  cudaStream_t st = (cudaStream_t)stream;
+  GBF_CUDA(cudaMemsetAsync(dErr, 0, sizeof(int), st));
+  return gbf::cgemm_tf32k(st, opa, opb, m, n, k, alpha, (const gbf::cf *)dA, lda, sa, (const gbf::cf *)dB, ldb, sb,
+                          beta, (gbf::cf *)dC, ldc, sc, batch, dWork, work_bytes, dErr);
 }
 
 // Verification entry (C ABI) of the sliced GEMM for any k: dC = alpha op(dA)

@@ -1,0 +1,722 @@
+// Reduced dense Hermitian eigensolver of the Rayleigh-Ritz step (FEAST v3.0
+// guide, "The FEAST Algorithm": the reduced eigenproblem Aq W = Bq W Lambda,
+// solved after B-orthonormalisation as a standard Hermitian problem C U = U
+// Lambda) and the Cholesky factor of the B-orthonormalisation, as
+// thread-block-cluster kernels.
+//
+// The M0 x M0 problems are small (M0 <= a few hundred) but their O(M0^3)
+// work is FP64, which runs at ~2 fused multiply-adds per clock per SM on this
+// GPU.  A cyclic Jacobi method costs ~6 M0^3 multiply-adds per sweep and
+// (in a grid-wide form) one grid barrier per round; the path here costs
+// ~M0^3 multiply-adds in all and keeps its M0-step recurrences inside one
+// cluster, whose barrier is a hardware barrier:
+//
+//   sytrd_cluster   Householder reduction C = Q T_c Q^H to a Hermitian
+//                   tridiagonal T_c (one cluster of up to 16 CTAs; the
+//                   matrix lives in distributed shared memory, rows dealt
+//                   cyclically to the CTAs; four cluster barriers per column)
+//   tridiag_prep    T_c = D T D^H with T real symmetric tridiagonal (D a
+//                   diagonal of unit phases), Gershgorin bounds
+//   stebz           every eigenvalue of T by bisection on its Sturm count
+//                   (the sign changes of the characteristic-polynomial
+//                   recurrence, rescaled against overflow), one thread each
+//   stein           eigenvectors of T by inverse iteration (tridiagonal LU
+//                   with partial pivoting of T - lambda I), three steps from
+//                   a fixed pseudo-random start; eigenvalues closer than
+//                   1e-10 ||T|| form a cluster whose vectors one thread
+//                   computes in turn, each orthogonalised against the
+//                   previous ones
+//   ormtr           U = Q D Z: the reflectors applied to D Z in reverse
+//                   order, a few columns per CTA
+//   chol_cluster    C = L L^H (lower), right-looking, the same cluster layout
+//
+// Householder reflector of step j (column j below the diagonal, x):
+//   H = I - tau v v^H with v = (1, x_2..x_k) / (ph (|x_1| + ||x||)),
+//   ph = x_1 / |x_1| (1 if x_1 = 0), tau = 1 + |x_1| / ||x||, so that
+//   H x = -ph ||x|| e_1 (H Hermitian and unitary); the trailing block
+//   becomes A - v w^H - w v^H with p = tau A v, w = p - (tau/2)(v^H p) v.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "gbf_common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace gbf {
+
+constexpr int TRD_THREADS = 512;
+constexpr int TRD_SMEM_CAP = 200 * 1024;
+
+__device__ inline double absq(double a) { return a * a; }
+__device__ inline double absq(zd a) { return a.x * a.x + a.y * a.y; }
+__device__ inline double scl(double a, double s) { return a * s; }
+__device__ inline zd scl(zd a, double s) { return zd{a.x * s, a.y * s}; }
+__device__ inline double shfl_x(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ inline zd shfl_x(zd v, int o) {
+  return zd{__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)};
+}
+template <class T> __device__ inline T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v = tr<T>::add(v, shfl_x(v, o));
+  return v;
+}
+
+// Deterministic CTA sum of one value per thread (fixed shuffle pattern, then
+// the warps' partials in warp order).  Every thread gets the result.
+template <class T> __device__ T cta_sum(T v, T *red) {
+  using X = tr<T>;
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  T s = X::zero();
+  for (int i = 0; i < nw; ++i) s = X::add(s, red[i]);
+  return s;
+}
+
+// The cluster kernels deal the rows of the m x m matrix cyclically to the C
+// CTAs of the cluster: row i lives in CTA i % C at local row i / C, stored
+// whole (m entries) in that CTA's shared memory.
+
+// ------------------------------------------------- tridiagonalisation --
+template <class T>
+__global__ void __launch_bounds__(TRD_THREADS, 1)
+    sytrd_cluster_kernel(int m, const T *__restrict__ A, long lda, T *__restrict__ Vr, double *__restrict__ tau,
+                         T *__restrict__ betac, double *__restrict__ dd) {
+  using X = tr<T>;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), q = (int)cl.block_rank();
+  const int rl = (m + C - 1) / C;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *L = reinterpret_cast<T *>(smem);  // [rl][m]
+  T *vown = L + (size_t)rl * m;        // [rl] this CTA's entries of v
+  T *wown = vown + rl;                 // [rl] p, then w
+  T *vfull = wown + rl;                // [m]
+  T *wfull = vfull + m;                // [m]
+  __shared__ double s_nrm;             // partial sum of |x_i|^2, i >= j+2 (own rows)
+  __shared__ T s_x0;                   // x_1 = A[j+1][j] (owner of row j+1)
+  __shared__ T s_pv;                   // partial v^H p (own rows)
+  __shared__ double s_tau, s_k;
+  __shared__ T s_sc;
+  __shared__ double red_d[32];
+  __shared__ T red_t[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+
+  for (long t = tid; t < (long)rl * m; t += blockDim.x) {
+    const int k = (int)(t / rl), il = (int)(t % rl);
+    const int i = il * C + q;
+    L[(long)il * m + k] = (i < m) ? A[i + (long)k * lda] : X::zero();
+  }
+  __syncthreads();
+
+  for (int j = 0; j < m - 1; ++j) {
+    // (a) this CTA's part of ||x_{2..}||^2 and, from the owner of row j+1, x_1
+    double part = 0.0;
+    for (int il = tid; il < rl; il += blockDim.x) {
+      const int i = il * C + q;
+      if (i >= j + 2 && i < m) part += absq(L[(long)il * m + j]);
+    }
+    part = cta_sum(part, red_d);
+    if (tid == 0) {
+      s_nrm = part;
+      if ((j + 1) % C == q) s_x0 = L[(long)((j + 1) / C) * m + j];
+    }
+    cl.sync();  // B1
+    // (b) the reflector, formed identically by every CTA: lane c of warp 0
+    // reads CTA c's partial (all remote reads in flight at once), then a
+    // fixed-pattern shuffle sum
+    if (warp == 0) {
+      double r = lane < C ? *cl.map_shared_rank(&s_nrm, lane) : 0.0;
+      const T x0 = *cl.map_shared_rank(&s_x0, (j + 1) % C);
+      const double rest = warp_sum(r);
+      double tj = 0.0;
+      T beta = x0, sc = X::zero();
+      if (rest > 0.0) {
+        const double a0 = sqrt(absq(x0));
+        const double nx = sqrt(a0 * a0 + rest);
+        const T ph = a0 > 0.0 ? scl(x0, 1.0 / a0) : X::one();
+        beta = scl(ph, -nx);
+        sc = scl(X::conj(ph), 1.0 / (a0 + nx));
+        tj = 1.0 + a0 / nx;
+      }
+      if (lane == 0) {
+        s_tau = tj;
+        s_sc = sc;
+        if (q == 0) {
+          tau[j] = tj;
+          betac[j] = beta;
+        }
+      }
+    }
+    __syncthreads();
+    const double tj = s_tau;
+    const T sc = s_sc;
+    for (int il = tid; il < rl; il += blockDim.x) {
+      const int i = il * C + q;
+      T v = X::zero();
+      if (i < m && i >= j + 1) {
+        v = (i == j + 1) ? X::one() : X::mul(L[(long)il * m + j], sc);
+        Vr[i + (long)j * m] = v;
+      }
+      vown[il] = v;
+    }
+    cl.sync();  // B2: every CTA's v visible
+    if (tj != 0.0) {
+      for (int k = j + 1 + tid; k < m; k += blockDim.x) vfull[k] = *cl.map_shared_rank(&vown[k / C], k % C);
+      __syncthreads();
+      // (c) p_i = tau sum_k A[i][k] v_k for the own rows i > j, one warp per row
+      T pv = X::zero();
+      for (int il = warp; il < rl; il += nw) {
+        const int i = il * C + q;
+        if (i < j + 1 || i >= m) continue;
+        const T *Li = L + (long)il * m;
+        T s = X::zero();
+        for (int k = j + 1 + lane; k < m; k += 32) s = X::fma(Li[k], vfull[k], s);
+        s = scl(warp_sum(s), tj);
+        if (lane == 0) {
+          wown[il] = s;
+          pv = X::fma(X::conj(vown[il]), s, pv);
+        }
+      }
+      pv = cta_sum(pv, red_t);
+      if (tid == 0) s_pv = pv;
+    }
+    cl.sync();  // B3
+    if (tj != 0.0) {
+      if (warp == 0) {
+        const T r = lane < C ? *cl.map_shared_rank(&s_pv, lane) : X::zero();
+        const T tot = warp_sum(r);
+        if (lane == 0) s_k = 0.5 * tj * X::re(tot);
+      }
+      __syncthreads();
+      const double kk = s_k;
+      for (int il = tid; il < rl; il += blockDim.x) {
+        const int i = il * C + q;
+        if (i >= j + 1 && i < m) wown[il] = X::sub(wown[il], scl(vown[il], kk));
+      }
+    }
+    cl.sync();  // B4: every CTA's w visible
+    if (tj != 0.0) {
+      for (int k = j + 1 + tid; k < m; k += blockDim.x) wfull[k] = *cl.map_shared_rank(&wown[k / C], k % C);
+      __syncthreads();
+      // (e) A[i][k] -= v_i conj(w_k) + w_i conj(v_k), own rows i > j, columns k > j
+      const int w = m - j - 1;
+      for (long t = tid; t < (long)rl * w; t += blockDim.x) {
+        const int il = (int)(t / w), k = j + 1 + (int)(t % w);
+        const int i = il * C + q;
+        if (i < j + 1 || i >= m) continue;
+        T a = L[(long)il * m + k];
+        a = X::sub(a, X::mul(vown[il], X::conj(wfull[k])));
+        a = X::sub(a, X::mul(wown[il], X::conj(vfull[k])));
+        L[(long)il * m + k] = a;
+      }
+    }
+    __syncthreads();
+  }
+  for (int il = tid; il < rl; il += blockDim.x) {
+    const int i = il * C + q;
+    if (i < m) dd[i] = X::re(L[(long)il * m + i]);
+  }
+  cl.sync();  // no CTA leaves while another may read its shared memory
+}
+
+// T_c (diagonal dd, subdiagonal betac) = D T D^H with T real (diagonal dd,
+// subdiagonal e = |betac|), D = diag(delta): delta_0 = 1, delta_{k+1} =
+// delta_k betac_k / |betac_k| (a prefix product of unit phases, formed by a
+// parallel scan).  Also e^2 and the Gershgorin interval [gl, gu] with tnorm
+// = max(|gl|, |gu|) in sc[0..2].  One block of PREP_THREADS >= m threads.
+constexpr int PREP_THREADS = 1024;
+template <class T>
+__global__ void __launch_bounds__(PREP_THREADS) tridiag_prep_kernel(int m, const double *dd, const T *betac, double *e,
+                                                                   double *e2, T *delta, double *sc) {
+  using X = tr<T>;
+  __shared__ T ph[PREP_THREADS];
+  __shared__ double mn[PREP_THREADS / 32], mx[PREP_THREADS / 32];
+  const int k = threadIdx.x;
+  double ek = 0.0;
+  T u = X::one();  // phase of betac_{k-1} (1 for k = 0)
+  if (k < m - 1) {
+    ek = sqrt(absq(betac[k]));
+    e[k] = ek;
+    e2[k] = ek * ek;
+  }
+  if (k >= 1 && k < m) {
+    const double a = sqrt(absq(betac[k - 1]));
+    if (a > 0.0) u = scl(betac[k - 1], 1.0 / a);
+  }
+  ph[k] = u;
+  __syncthreads();
+  for (int o = 1; o < PREP_THREADS; o <<= 1) {  // inclusive scan: delta_k = u_1 ... u_k
+    const T v = (k >= o) ? ph[k - o] : X::one();
+    __syncthreads();
+    ph[k] = X::mul(v, ph[k]);
+    __syncthreads();
+  }
+  if (k < m) delta[k] = ph[k];
+  double lo = 1e300, hi = -1e300;
+  if (k < m) {
+    const double r = (k > 0 ? sqrt(absq(betac[k - 1])) : 0.0) + ek;
+    lo = dd[k] - r;
+    hi = dd[k] + r;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if ((k & 31) == 0) {
+    mn[k >> 5] = lo;
+    mx[k >> 5] = hi;
+  }
+  __syncthreads();
+  if (k == 0) {
+    double gl = mn[0], gu = mx[0];
+    for (int w = 1; w < PREP_THREADS / 32; ++w) {
+      gl = fmin(gl, mn[w]);
+      gu = fmax(gu, mx[w]);
+    }
+    const double tn = fmax(fabs(gl), fabs(gu));
+    sc[0] = gl - 2.2e-16 * tn * 2 * m - 1e-300;
+    sc[1] = gu + 2.2e-16 * tn * 2 * m + 1e-300;
+    sc[2] = tn;
+  }
+}
+
+// ----------------------------------------------------------- bisection --
+// Number of eigenvalues of T below x: sign changes of 1, p_0, ..., p_{m-1},
+// p_k = (d_k - x) p_{k-1} - e_{k-1}^2 p_{k-2}, i.e. the negative pivots of
+// the LDL^T factorisation of T - x I.  A zero p_k counts as a sign change
+// (as a tiny negative pivot).  The pair (p_{k-1}, p_k) is rescaled by
+// powers of two whenever p_k leaves [2^-600, 2^600].  Three FP64
+// operations per step; signs, zero tests and exponents are read from the
+// bit patterns with integer operations (FP64 instructions are the scarce
+// resource on this GPU).
+__device__ inline int sgnb(double v) { return (int)((unsigned long long)__double_as_longlong(v) >> 63); }
+__device__ inline int expb(double v) { return (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FF); }
+__device__ inline bool zerob(double v) { return ((unsigned long long)__double_as_longlong(v) << 1) == 0ull; }
+
+__device__ inline int sturm_count(int m, const double *__restrict__ d, const double *__restrict__ e2, double x) {
+  double pm = 1.0, p = d[0] - x;
+  if (zerob(p)) p = -0x1p-1000;
+  int cnt = sgnb(p);
+  for (int k = 1; k < m; ++k) {
+    double pn = fma(d[k] - x, p, -(e2[k - 1] * pm));
+    if (zerob(pn)) pn = sgnb(p) ? 0x1p-1000 : -0x1p-1000;
+    cnt += sgnb(pn) ^ sgnb(p);
+    pm = p;
+    p = pn;
+    const int ex = expb(p);
+    if (ex > 1023 + 600) {
+      p *= 0x1p-600;
+      pm *= 0x1p-600;
+    } else if (ex < 1023 - 600 && expb(pm) < 1023 - 600) {
+      p *= 0x1p600;
+      pm *= 0x1p600;
+    }
+  }
+  return cnt;
+}
+
+// Eigenvalue k (ascending) lies in (lo, hi] with count(lo) <= k < count(hi).
+// One warp per eigenvalue: its 32 lanes count at 32 interior points of the
+// interval (multisection, 5 bits per round), until the interval is below
+// 1e-3 eps ||T|| or holds no interior double; hi is returned (so an isolated
+// eigenvalue that is a double, e.g. of a diagonal T, comes back exactly).
+constexpr int STEBZ_WARPS = 4;
+__global__ void __launch_bounds__(32 * STEBZ_WARPS) stebz_kernel(int m, const double *__restrict__ d,
+                                                               const double *__restrict__ e2,
+                                                               const double *__restrict__ sc, double *__restrict__ w) {
+  const int k = blockIdx.x * STEBZ_WARPS + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= m) return;  // warp-uniform
+  double lo = sc[0], hi = sc[1];
+  const double floor_w = 1e-3 * 2.220446049250313e-16 * sc[2];
+  for (int round = 0; round < 40; ++round) {
+    const double wd = hi - lo;
+    if (wd <= floor_w) break;
+    const double x = fma((double)(lane + 1), wd * (1.0 / 33.0), lo);
+    int c;
+    if (!(x > lo))
+      c = 0;  // count(lo) <= k
+    else if (!(x < hi))
+      c = 1;  // count(hi) > k
+    else
+      c = sturm_count(m, d, e2, x) > k;
+    const unsigned mask = __ballot_sync(0xffffffffu, c);
+    double nlo, nhi;
+    if (mask == 0u) {
+      nlo = __shfl_sync(0xffffffffu, x, 31);
+      nhi = hi;
+    } else {
+      const int f = __ffs(mask) - 1;
+      nhi = __shfl_sync(0xffffffffu, x, f);
+      const double xl = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
+      nlo = f > 0 ? xl : lo;
+    }
+    nlo = fmax(nlo, lo);
+    nhi = fmin(nhi, hi);
+    if (nlo == lo && nhi == hi) break;  // no interior double left
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) w[k] = hi;
+}
+
+// ---------------------------------------------------- inverse iteration --
+__device__ inline double unit_rand(uint64_t k, uint64_t i) {
+  uint64_t z = 0x9E3779B97F4A7C15ull * (k * 0x100000001B3ull + i + 1ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// Thread k (the first eigenvalue of its cluster) computes the eigenvectors
+// of eigenvalues k, k+1, ... of its cluster (consecutive eigenvalues within
+// 1e-10 tnorm of each other) into columns of Z (m x m, ld m).  Scratch per
+// thread: 5 m doubles at wk + 5 m k.
+__global__ void stein_kernel(int m, const double *__restrict__ d, const double *__restrict__ e,
+                             const double *__restrict__ sc, const double *__restrict__ w, double *__restrict__ Z,
+                             double *__restrict__ wk) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  const double tn = sc[2];
+  const double ctol = 1e-10 * tn;
+  if (k > 0 && w[k] - w[k - 1] <= ctol) return;  // not the first of its cluster
+  int kend = k + 1;
+  while (kend < m && w[kend] - w[kend - 1] <= ctol) ++kend;
+  double *a = wk + (size_t)5 * m * k;  // U diagonal
+  double *b = a + m;                   // U first superdiagonal
+  double *c2 = b + m;                  // U second superdiagonal
+  double *l = c2 + m;                  // multipliers
+  double *fl = l + m;                  // 1: rows i, i+1 swapped
+  const double tiny = 2.220446049250313e-16 * tn + 1e-300;
+  for (int kk = k; kk < kend; ++kk) {
+    const double lam = w[kk];
+    // LU with partial pivoting of T - lam I (tridiagonal; U gets a second
+    // superdiagonal from the swaps); zero pivots become eps tnorm
+    for (int i = 0; i < m; ++i) {
+      a[i] = d[i] - lam;
+      b[i] = (i < m - 1) ? e[i] : 0.0;
+      c2[i] = 0.0;
+    }
+    for (int i = 0; i < m - 1; ++i) {
+      const double sub = e[i];
+      if (fabs(a[i]) >= fabs(sub)) {
+        if (a[i] == 0.0) a[i] = tiny;
+        const double f = sub / a[i];
+        l[i] = f;
+        fl[i] = 0.0;
+        a[i + 1] -= f * b[i];
+      } else {
+        const double f = a[i] / sub;
+        a[i] = sub;
+        l[i] = f;
+        fl[i] = 1.0;
+        const double t = b[i];
+        b[i] = a[i + 1];
+        a[i + 1] = t - f * a[i + 1];
+        if (i < m - 2) {
+          c2[i] = b[i + 1];
+          b[i + 1] = -f * b[i + 1];
+        }
+      }
+    }
+    if (a[m - 1] == 0.0) a[m - 1] = tiny;
+    for (int i = 0; i < m; ++i) {  // pivots below eps tnorm raised to it; kept as reciprocals
+      const double v = (fabs(a[i]) < tiny) ? (a[i] < 0.0 ? -tiny : tiny) : a[i];
+      a[i] = 1.0 / v;
+    }
+    double *x = Z + (size_t)kk * m;
+    for (int i = 0; i < m; ++i) x[i] = unit_rand(kk, i);
+    for (int it = 0; it < 3; ++it) {
+      // x <- (T - lam I)^{-1} x
+      for (int i = 0; i < m - 1; ++i) {
+        if (fl[i] != 0.0) {
+          const double t = x[i];
+          x[i] = x[i + 1];
+          x[i + 1] = t - l[i] * x[i + 1];
+        } else {
+          x[i + 1] -= l[i] * x[i];
+        }
+      }
+      x[m - 1] *= a[m - 1];
+      if (m > 1) x[m - 2] = (x[m - 2] - b[m - 2] * x[m - 1]) * a[m - 2];
+      for (int i = m - 3; i >= 0; --i) x[i] = (x[i] - b[i] * x[i + 1] - c2[i] * x[i + 2]) * a[i];
+      // orthogonalise against the cluster's earlier vectors, normalise
+      for (int jj = k; jj < kk; ++jj) {
+        const double *y = Z + (size_t)jj * m;
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s = fma(y[i], x[i], s);
+        for (int i = 0; i < m; ++i) x[i] = fma(-s, y[i], x[i]);
+      }
+      // normalise: scale by a power of two near 1 / max|x| (exact), then by
+      // 1 / ||x||
+      int emx = 0;
+      for (int i = 0; i < m; ++i) emx = max(emx, expb(x[i]));
+      const double p2 = __longlong_as_double((long long)(2046 - min(emx, 2045)) << 52);
+      double nn = 0.0;
+      for (int i = 0; i < m; ++i) {
+        x[i] *= p2;
+        nn = fma(x[i], x[i], nn);
+      }
+      const double r = 1.0 / sqrt(nn);
+      for (int i = 0; i < m; ++i) x[i] *= r;
+    }
+  }
+}
+
+// ------------------------------------------------------ back-transform --
+// U = Q D Z, Q = H_0 H_1 ... H_{m-2}: every CTA takes OCOLS columns of D Z
+// into shared memory and applies H_{m-2}, ..., H_0 to them.  Few columns per
+// CTA spread the FP64 work over many SMs; the next reflector is read into
+// registers while the current one is applied.
+constexpr int OCOLS = 2;
+constexpr int OR_THREADS = 128;
+constexpr int OR_PER = 8;  // reflector entries a thread prefetches (m <= OR_THREADS * OR_PER)
+
+template <class T>
+__global__ void __launch_bounds__(OR_THREADS)
+    ormtr_kernel(int m, const T *__restrict__ Vr, const double *__restrict__ tau, const T *__restrict__ delta,
+                 const double *__restrict__ Z, T *__restrict__ U) {
+  using X = tr<T>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *Y = reinterpret_cast<T *>(smem);  // [OCOLS][m]
+  T *v = Y + (size_t)OCOLS * m;        // [m]
+  __shared__ T dots[OCOLS];
+  const int c0 = blockIdx.x * OCOLS;
+  const int nc = min(OCOLS, m - c0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int t = tid; t < nc * m; t += blockDim.x) {
+    const int c = t / m, i = t % m;
+    Y[(long)c * m + i] = scl(delta[i], Z[i + (long)(c0 + c) * m]);
+  }
+  T pre[OR_PER];
+  auto fetch = [&](int j) {
+#pragma unroll
+    for (int u = 0; u < OR_PER; ++u) {
+      const int i = j + 1 + tid + u * OR_THREADS;
+      pre[u] = (j >= 0 && i < m) ? Vr[i + (long)j * m] : X::zero();
+    }
+  };
+  fetch(m - 2);
+  for (int j = m - 2; j >= 0; --j) {
+    const double tj = tau[j];
+    __syncthreads();  // previous update done with v
+#pragma unroll
+    for (int u = 0; u < OR_PER; ++u) {
+      const int i = j + 1 + tid + u * OR_THREADS;
+      if (i < m) v[i] = pre[u];
+    }
+    __syncthreads();
+    fetch(j - 1);  // in flight while this reflector is applied
+    if (tj == 0.0) continue;  // uniform over the CTA
+    if (warp < nc) {
+      const T *y = Y + (long)warp * m;
+      T s = X::zero();
+      for (int i = j + 1 + lane; i < m; i += 32) s = X::fma(X::conj(v[i]), y[i], s);
+      s = warp_sum(s);
+      if (lane == 0) dots[warp] = scl(s, tj);
+    }
+    __syncthreads();
+    const int w = m - j - 1;
+    for (int t = tid; t < nc * w; t += blockDim.x) {
+      const int c = t / w, i = j + 1 + t % w;
+      Y[(long)c * m + i] = X::sub(Y[(long)c * m + i], X::mul(v[i], dots[c]));
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < nc * m; t += blockDim.x) {
+    const int c = t / m, i = t % m;
+    U[i + (long)(c0 + c) * m] = Y[(long)c * m + i];
+  }
+}
+
+// ------------------------------------------------------------- Cholesky --
+// A = L L^H (lower), right-looking; rows dealt cyclically to the cluster's
+// CTAs as above.  fail: first column whose pivot is not positive, + 1.
+// Two cluster barriers per column.
+template <class T>
+__global__ void __launch_bounds__(TRD_THREADS, 1)
+    chol_cluster_kernel(int m, const T *__restrict__ A, T *__restrict__ Lout, int *fail) {
+  using X = tr<T>;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), q = (int)cl.block_rank();
+  const int rl = (m + C - 1) / C;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *L = reinterpret_cast<T *>(smem);  // [rl][m]
+  T *lown = L + (size_t)rl * m;        // [rl] entries of column j (own rows)
+  T *lfull = lown + rl;                // [m]
+  __shared__ double s_piv;
+  const int tid = threadIdx.x;
+  for (long t = tid; t < (long)rl * m; t += blockDim.x) {
+    const int k = (int)(t / rl), il = (int)(t % rl);
+    const int i = il * C + q;
+    L[(long)il * m + k] = (i < m) ? A[i + (long)k * m] : X::zero();
+  }
+  __syncthreads();
+  int bad = 0;
+  for (int j = 0; j < m; ++j) {
+    if (tid == 0 && j % C == q) s_piv = X::re(L[(long)(j / C) * m + j]);
+    cl.sync();  // B1: pivot visible
+    const double piv = *cl.map_shared_rank(&s_piv, j % C);
+    if (!(piv > 0.0)) {  // uniform: every CTA reads the same pivot
+      if (tid == 0 && q == 0) *fail = j + 1;
+      bad = 1;
+      break;
+    }
+    const double r = sqrt(piv), ir = 1.0 / r;
+    for (int il = tid; il < rl; il += blockDim.x) {
+      const int i = il * C + q;
+      T l = X::zero();
+      if (i == j) {
+        l = cvt<T, double>(r);
+        L[(long)il * m + j] = l;
+      } else if (i > j && i < m) {
+        l = scl(L[(long)il * m + j], ir);
+        L[(long)il * m + j] = l;
+      }
+      lown[il] = l;
+    }
+    cl.sync();  // B2: column j of L visible
+    for (int k = j + 1 + tid; k < m; k += blockDim.x) lfull[k] = *cl.map_shared_rank(&lown[k / C], k % C);
+    __syncthreads();
+    const int w = m - j - 1;
+    for (long t = tid; t < (long)rl * w; t += blockDim.x) {
+      const int il = (int)(t / w), k = j + 1 + (int)(t % w);
+      const int i = il * C + q;
+      if (i < k || i >= m) continue;  // lower triangle of the trailing block
+      L[(long)il * m + k] = X::sub(L[(long)il * m + k], X::mul(lown[il], X::conj(lfull[k])));
+    }
+    __syncthreads();
+  }
+  if (!bad) {
+    for (long t = tid; t < (long)rl * m; t += blockDim.x) {
+      const int k = (int)(t / rl), il = (int)(t % rl);
+      const int i = il * C + q;
+      if (i < m) Lout[i + (long)k * m] = (k <= i) ? L[(long)il * m + k] : X::zero();
+    }
+  }
+  cl.sync();
+}
+
+// ------------------------------------------------------------ launchers --
+// Cluster size and per-CTA shared memory for an m x m matrix of T with
+// `extra` more vectors of T per CTA: the smallest power-of-two cluster
+// (>= 2, <= 16) whose slices fit, preferring ~20 rows per CTA.
+template <class T> static int cluster_shape(int m, int extra_rows, int extra_vecs, size_t *smem) {
+  int C = 2;
+  while (C < 16 && (m + C - 1) / C > 20) C *= 2;
+  for (; C <= 16; C *= 2) {
+    const int rl = (m + C - 1) / C;
+    const size_t b = ((size_t)rl * m + (size_t)extra_rows * rl + (size_t)extra_vecs * m) * sizeof(T) + 64;
+    if (b <= (size_t)TRD_SMEM_CAP) {
+      *smem = b;
+      return C;
+    }
+  }
+  return 0;
+}
+
+// Launches kern as one cluster of C CTAs; returns 1 (nothing launched) when
+// the cluster cannot be scheduled, so the caller can fall back.
+template <class K, class... Args>
+static int launch_cluster(K kern, int C, size_t smem, cudaStream_t st, Args... args) {
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TRD_SMEM_CAP) != cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, 1, 1);
+  cfg.blockDim = dim3(TRD_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t err = cudaLaunchKernelEx(&cfg, kern, args...);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  GBF_LAUNCHED();
+  return 0;
+}
+
+size_t heev_tridiag_work(int m, bool cplx) {
+  const size_t ts = cplx ? sizeof(zd) : sizeof(double);
+  const size_t mm = (size_t)m * m;
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  return al(mm * ts) + 3 * al(m * ts) + 5 * al(m * sizeof(double)) + al(8 * sizeof(double)) +
+         al(mm * sizeof(double)) + al(5 * mm * sizeof(double));
+}
+
+template <class T>
+int heev_tridiag(cudaStream_t st, int m, const T *A, double *w, T *V, void *work, size_t work_bytes) {
+  if (m < 2 || m > OR_THREADS * OR_PER) return 1;
+  if (heev_tridiag_work(m, tr<T>::cplx) > work_bytes) return 1;
+  size_t sm_t = 0;
+  const int C = cluster_shape<T>(m, 2, 2, &sm_t);
+  if (C == 0) return 1;
+  const size_t mm = (size_t)m * m;
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  char *p = (char *)work;
+  T *Vr = (T *)p;
+  p += al(mm * sizeof(T));
+  T *betac = (T *)p;
+  p += al(m * sizeof(T));
+  T *delta = (T *)p;
+  p += al(m * sizeof(T));
+  p += al(m * sizeof(T));
+  double *tau = (double *)p;
+  p += al(m * sizeof(double));
+  double *dd = (double *)p;
+  p += al(m * sizeof(double));
+  double *e = (double *)p;
+  p += al(m * sizeof(double));
+  double *e2 = (double *)p;
+  p += al(m * sizeof(double));
+  p += al(m * sizeof(double));
+  double *sc = (double *)p;
+  p += al(8 * sizeof(double));
+  double *Z = (double *)p;
+  p += al(mm * sizeof(double));
+  double *wk = (double *)p;
+  const int slot = prof_begin(st);
+  if (launch_cluster(sytrd_cluster_kernel<T>, C, sm_t, st, m, A, (long)m, Vr, tau, betac, dd)) return 1;
+  tridiag_prep_kernel<T><<<1, PREP_THREADS, 0, st>>>(m, dd, betac, e, e2, delta, sc);
+  GBF_LAUNCHED();
+  stebz_kernel<<<ceil_div(m, STEBZ_WARPS), 32 * STEBZ_WARPS, 0, st>>>(m, dd, e2, sc, w);
+  GBF_LAUNCHED();
+  stein_kernel<<<ceil_div(m, 32), 32, 0, st>>>(m, dd, e, sc, w, Z, wk);
+  GBF_LAUNCHED();
+  const size_t sm_o = ((size_t)OCOLS * m + m) * sizeof(T);
+  ormtr_kernel<T><<<ceil_div(m, OCOLS), OR_THREADS, sm_o, st>>>(m, Vr, tau, delta, Z, V);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  prof_end(st, slot, 0.0);
+  return 0;
+}
+
+// Cholesky of the M0 x M0 Hermitian A (full storage, ld m, not modified):
+// L (lower, ld m, strict upper part zero); *fail = first non-positive pivot
+// column + 1.  Returns 1 when the cluster kernel cannot take m.
+template <class T> int chol_cluster(cudaStream_t st, int m, const T *A, T *L, int *fail) {
+  size_t sm = 0;
+  const int C = cluster_shape<T>(m, 1, 1, &sm);
+  if (C == 0) return 1;
+  return launch_cluster(chol_cluster_kernel<T>, C, sm, st, m, A, L, fail);
+}
+
+#define TRD_INST(T)                                                                         \
+  template int heev_tridiag<T>(cudaStream_t, int, const T *, double *, T *, void *, size_t); \
+  template int chol_cluster<T>(cudaStream_t, int, const T *, T *, int *);
+TRD_INST(double)
+TRD_INST(zd)
+
+}  // namespace gbf

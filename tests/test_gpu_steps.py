@@ -64,6 +64,32 @@ def test_factor_and_solve(gbf, handle, n, cplx, gen, prec):
             assert err < tol, (e, trans, err)
 
 
+@pytest.mark.parametrize("n", [1000, 2048])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_factor_and_solve_large(gbf, handle, n, prec):
+    """Sizes where the solves recurse with large-K products on the tensor
+    cores (sliced for FP64 factors, 3xTF32 for FP32 ones), both solve
+    directions, against an FP64 dense solve of the same shifted systems."""
+    A = herm(n, True, seed=n)
+    rc = gbf.gbf_factor_dev(handle, cuda(A), None, ZNE, prec=prec)
+    assert rc == 0, gbf.last_error()
+    r = np.random.default_rng(9)
+    rhs = r.standard_normal((n, 40)) + 1j * r.standard_normal((n, 40))
+    # backward error ||S y - r|| / (||S|| ||y||) per column: a few units of
+    # the factors' rounding (FP64-class, or FP32 for prec 1) times sqrt(n)
+    tol = 1e-13 if prec == 0 else 2e-6
+    for trans in (0, 1):
+        Y, rc = gbf.gbf_solve_dev(handle, cuda(rhs), len(ZNE), trans=trans)
+        assert rc == 0, gbf.last_error()
+        Y = Y.cpu().numpy()
+        for e, z in enumerate(ZNE):
+            S = z * np.eye(n) - A
+            Sop = S.conj().T if trans else S
+            y = Y[e].T
+            bwd = np.linalg.norm(Sop @ y - rhs, axis=0) / (np.linalg.norm(Sop, 1) * np.linalg.norm(y, axis=0))
+            assert bwd.max() < tol, (e, trans, bwd.max())
+
+
 @pytest.mark.parametrize("uplo", ["L", "U"])
 def test_factor_uplo(gbf, handle, uplo):
     n = 45

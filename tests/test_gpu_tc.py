@@ -108,3 +108,38 @@ def test_tf32_engine_needs_complex_fp32(gbf):
     rc = gbf.zgemm_sliced("N", "N", A, B, C, alpha=1.0, beta=0, S=1)
     torch.cuda.synchronize()
     assert rc != 0 and "3xTF32" in gbf.last_error()
+
+
+@pytest.mark.parametrize("m,n,k,batch", [(1, 1, 1, 1), (37, 33, 7, 2), (200, 100, 100, 1), (300, 70, 257, 2),
+                                         (130, 300, 1000, 1), (2048, 300, 2048, 2)])
+@pytest.mark.parametrize("opa,opb", [("N", "N"), ("T", "N"), ("C", "N"), ("N", "C")])
+@pytest.mark.parametrize("alpha,beta", [(-1.0, 1), (1.0, 0)])
+def test_cgemm_tf32_any_k(gbf, m, n, k, batch, opa, opb, alpha, beta):
+    """3xTF32 complex FP32 GEMM for any k (the FP32 factors' recursive solve
+    updates) against an FP64 product of the same complex64 operands: each
+    product is exact to about 2^-22 relative and the FP32 accumulation over
+    the real embedding's 2k terms adds about sqrt(2k) 2^-24; the bound below
+    is a few units of 2k 2^-22 max|A| max|B| plus the FP32 rounding of C."""
+    import torch
+
+    g = torch.Generator(device="cuda").manual_seed(13 * m + 7 * n + k)
+
+    def rnd(r, c):
+        return torch.complex(torch.randn((r, c), device="cuda", dtype=torch.float32, generator=g),
+                             torch.randn((r, c), device="cuda", dtype=torch.float32, generator=g))
+
+    As = [rnd(m, k) if opa == "N" else rnd(k, m) for _ in range(batch)]
+    Bs = [rnd(k, n) if opb == "N" else rnd(n, k) for _ in range(batch)]
+    Cs = [rnd(m, n) for _ in range(batch)]
+    A, B, Cd = colmajor_batch(torch, As), colmajor_batch(torch, Bs), colmajor_batch(torch, Cs)
+    op = {"N": lambda x: x, "T": lambda x: x.t(), "C": lambda x: x.conj().t()}
+    w = torch.complex128
+    ref = [alpha * (op[opa](a.to(w)) @ op[opb](b.to(w))) + beta * c.to(w) for a, b, c in zip(As, Bs, Cs)]
+    rc = gbf.cgemm_tf32(opa, opb, A, B, Cd, alpha=alpha, beta=beta)
+    torch.cuda.synchronize()
+    assert rc == 0, gbf.last_error()
+    for i in range(batch):
+        got = Cd[i].t().to(w)
+        scale = As[i].abs().max().item() * Bs[i].abs().max().item()
+        tol = 4 * (2 * k) * 2.0 ** -22 * scale + 2.0 ** -23 * ref[i].abs().max().item()
+        assert (got - ref[i]).abs().max().item() <= tol, ((got - ref[i]).abs().max().item(), tol)
