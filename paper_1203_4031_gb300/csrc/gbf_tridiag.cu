@@ -80,6 +80,19 @@ template <class T> __device__ T cta_sum(T v, T *red) {
 // whole (m entries) in that CTA's shared memory.
 
 // ------------------------------------------------- tridiagonalisation --
+// Step j, with the rows of the trailing block dealt to the CTAs as above:
+//  (a) the owner of row j forms the reflector from that row (the matrix is
+//      Hermitian, so column j below the diagonal is the conjugate of row j
+//      right of it, and the owner holds all of it): v into its shared
+//      memory and into column j of Vr, tau and the new subdiagonal entry;
+//  -- cluster barrier --
+//  (b) every CTA copies v from the owner, forms p_i = tau sum_k A[i][k] v_k
+//      for its rows (one warp per row) and its part of v^H p;
+//  -- cluster barrier --
+//  (c) every CTA copies p and the parts of v^H p from all CTAs (summed in
+//      CTA order, so every CTA gets the same K = tau/2 Re(v^H p)), forms w =
+//      p - K v and updates its rows: A[i][k] -= v_i conj(w_k) + w_i conj(v_k).
+// Two cluster barriers per column; FP64 work as fused multiply-adds.
 template <class T>
 __global__ void __launch_bounds__(TRD_THREADS, 1)
     sytrd_cluster_kernel(int m, const T *__restrict__ A, long lda, T *__restrict__ Vr, double *__restrict__ tau,
@@ -90,14 +103,12 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
   const int rl = (m + C - 1) / C;
   extern __shared__ __align__(16) unsigned char smem[];
   T *L = reinterpret_cast<T *>(smem);  // [rl][m]
-  T *vown = L + (size_t)rl * m;        // [rl] this CTA's entries of v
-  T *wown = vown + rl;                 // [rl] p, then w
-  T *vfull = wown + rl;                // [m]
-  T *wfull = vfull + m;                // [m]
-  __shared__ double s_nrm;             // partial sum of |x_i|^2, i >= j+2 (own rows)
-  __shared__ T s_x0;                   // x_1 = A[j+1][j] (owner of row j+1)
-  __shared__ T s_pv;                   // partial v^H p (own rows)
-  __shared__ double s_tau, s_k;
+  T *pown = L + (size_t)rl * m;        // [rl] p of this CTA's rows
+  T *vpub = pown + rl;                 // [m] v, published by the owner of row j
+  T *vfull = vpub + m;                 // [m] copy of v
+  T *wfull = vfull + m;                // [m] p, then w
+  __shared__ T s_pv;                   // this CTA's part of v^H p
+  __shared__ double s_tau;             // published by the owner of row j
   __shared__ T s_sc;
   __shared__ double red_d[32];
   __shared__ T red_t[32];
@@ -111,61 +122,45 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
   __syncthreads();
 
   for (int j = 0; j < m - 1; ++j) {
-    // (a) this CTA's part of ||x_{2..}||^2 and, from the owner of row j+1, x_1
-    double part = 0.0;
-    for (int il = tid; il < rl; il += blockDim.x) {
-      const int i = il * C + q;
-      if (i >= j + 2 && i < m) part += absq(L[(long)il * m + j]);
-    }
-    part = cta_sum(part, red_d);
-    if (tid == 0) {
-      s_nrm = part;
-      if ((j + 1) % C == q) s_x0 = L[(long)((j + 1) / C) * m + j];
-    }
-    cl.sync();  // B1
-    // (b) the reflector, formed identically by every CTA: lane c of warp 0
-    // reads CTA c's partial (all remote reads in flight at once), then a
-    // fixed-pattern shuffle sum
-    if (warp == 0) {
-      double r = lane < C ? *cl.map_shared_rank(&s_nrm, lane) : 0.0;
-      const T x0 = *cl.map_shared_rank(&s_x0, (j + 1) % C);
-      const double rest = warp_sum(r);
-      double tj = 0.0;
-      T beta = x0, sc = X::zero();
-      if (rest > 0.0) {
-        const double a0 = sqrt(absq(x0));
-        const double nx = sqrt(a0 * a0 + rest);
-        const T ph = a0 > 0.0 ? scl(x0, 1.0 / a0) : X::one();
-        beta = scl(ph, -nx);
-        sc = scl(X::conj(ph), 1.0 / (a0 + nx));
-        tj = 1.0 + a0 / nx;
-      }
-      if (lane == 0) {
+    const int own = j % C;
+    if (q == own) {
+      // (a) x = conj(row j)[j+1 ..]; ||x_{2..}||^2 over this CTA's threads
+      const T *Lj = L + (long)(j / C) * m;
+      double part = 0.0;
+      for (int k = j + 2 + tid; k < m; k += blockDim.x) part += absq(Lj[k]);
+      const double rest = cta_sum(part, red_d);
+      if (tid == 0) {
+        const T x0 = X::conj(Lj[j + 1]);
+        double tj = 0.0;
+        T beta = x0, sc = X::zero();
+        if (rest > 0.0) {
+          const double a0 = sqrt(absq(x0));
+          const double nx = sqrt(a0 * a0 + rest);
+          const T ph = a0 > 0.0 ? scl(x0, 1.0 / a0) : X::one();
+          beta = scl(ph, -nx);
+          sc = scl(X::conj(ph), 1.0 / (a0 + nx));
+          tj = 1.0 + a0 / nx;
+        }
         s_tau = tj;
         s_sc = sc;
-        if (q == 0) {
-          tau[j] = tj;
-          betac[j] = beta;
-        }
+        tau[j] = tj;
+        betac[j] = beta;
       }
-    }
-    __syncthreads();
-    const double tj = s_tau;
-    const T sc = s_sc;
-    for (int il = tid; il < rl; il += blockDim.x) {
-      const int i = il * C + q;
-      T v = X::zero();
-      if (i < m && i >= j + 1) {
-        v = (i == j + 1) ? X::one() : X::mul(L[(long)il * m + j], sc);
-        Vr[i + (long)j * m] = v;
-      }
-      vown[il] = v;
-    }
-    cl.sync();  // B2: every CTA's v visible
-    if (tj != 0.0) {
-      for (int k = j + 1 + tid; k < m; k += blockDim.x) vfull[k] = *cl.map_shared_rank(&vown[k / C], k % C);
       __syncthreads();
-      // (c) p_i = tau sum_k A[i][k] v_k for the own rows i > j, one warp per row
+      const T sc = s_sc;
+      for (int k = j + 1 + tid; k < m; k += blockDim.x) {
+        const T v = (k == j + 1) ? X::one() : X::mul(X::conj(Lj[k]), sc);
+        vpub[k] = v;
+        Vr[k + (long)j * m] = v;
+      }
+    }
+    cl.sync();  // B1: the reflector is published
+    const double tj = *cl.map_shared_rank(&s_tau, own);
+    if (tj != 0.0) {  // uniform: every CTA reads the owner's tau
+      const T *vsrc = cl.map_shared_rank(vpub, own);
+      for (int k = j + 1 + tid; k < m; k += blockDim.x) vfull[k] = vsrc[k];
+      __syncthreads();
+      // (b) p_i for the own rows i > j, one warp per row
       T pv = X::zero();
       for (int il = warp; il < rl; il += nw) {
         const int i = il * C + q;
@@ -175,41 +170,42 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
         for (int k = j + 1 + lane; k < m; k += 32) s = X::fma(Li[k], vfull[k], s);
         s = scl(warp_sum(s), tj);
         if (lane == 0) {
-          wown[il] = s;
-          pv = X::fma(X::conj(vown[il]), s, pv);
+          pown[il] = s;
+          pv = X::fma(X::conj(vfull[i]), s, pv);
         }
       }
       pv = cta_sum(pv, red_t);
       if (tid == 0) s_pv = pv;
     }
-    cl.sync();  // B3
+    cl.sync();  // B2: every CTA's p and part of v^H p visible
     if (tj != 0.0) {
+      // (c) p from all CTAs, K (identical in every CTA: lane c of warp 0
+      // reads CTA c's part, fixed-pattern shuffle sum), w = p - K v
       if (warp == 0) {
         const T r = lane < C ? *cl.map_shared_rank(&s_pv, lane) : X::zero();
         const T tot = warp_sum(r);
-        if (lane == 0) s_k = 0.5 * tj * X::re(tot);
+        if (lane == 0) s_sc = tot;
       }
       __syncthreads();
-      const double kk = s_k;
-      for (int il = tid; il < rl; il += blockDim.x) {
-        const int i = il * C + q;
-        if (i >= j + 1 && i < m) wown[il] = X::sub(wown[il], scl(vown[il], kk));
+      const double kk = 0.5 * tj * X::re(s_sc);
+      for (int k = j + 1 + tid; k < m; k += blockDim.x) {
+        const T pk = *cl.map_shared_rank(&pown[k / C], k % C);
+        wfull[k] = X::sub(pk, scl(vfull[k], kk));
       }
-    }
-    cl.sync();  // B4: every CTA's w visible
-    if (tj != 0.0) {
-      for (int k = j + 1 + tid; k < m; k += blockDim.x) wfull[k] = *cl.map_shared_rank(&wown[k / C], k % C);
       __syncthreads();
-      // (e) A[i][k] -= v_i conj(w_k) + w_i conj(v_k), own rows i > j, columns k > j
-      const int w = m - j - 1;
-      for (long t = tid; t < (long)rl * w; t += blockDim.x) {
-        const int il = (int)(t / w), k = j + 1 + (int)(t % w);
+      // A[i][k] -= v_i conj(w_k) + w_i conj(v_k), own rows i > j, one warp
+      // per row, lanes over the columns k > j
+      for (int il = warp; il < rl; il += nw) {
         const int i = il * C + q;
         if (i < j + 1 || i >= m) continue;
-        T a = L[(long)il * m + k];
-        a = X::sub(a, X::mul(vown[il], X::conj(wfull[k])));
-        a = X::sub(a, X::mul(wown[il], X::conj(vfull[k])));
-        L[(long)il * m + k] = a;
+        T *Li = L + (long)il * m;
+        const T vi = X::neg(vfull[i]), wi = X::neg(wfull[i]);
+        for (int k = j + 1 + lane; k < m; k += 32) {
+          T a = Li[k];
+          a = X::fma(vi, X::conj(wfull[k]), a);
+          a = X::fma(wi, X::conj(vfull[k]), a);
+          Li[k] = a;
+        }
       }
     }
     __syncthreads();
@@ -322,7 +318,7 @@ __device__ inline int sturm_count(int m, const double *__restrict__ d, const dou
 // interval (multisection, 5 bits per round), until the interval is below
 // 1e-3 eps ||T|| or holds no interior double; hi is returned (so an isolated
 // eigenvalue that is a double, e.g. of a diagonal T, comes back exactly).
-constexpr int STEBZ_WARPS = 4;
+constexpr int STEBZ_WARPS = 1;
 __global__ void __launch_bounds__(32 * STEBZ_WARPS) stebz_kernel(int m, const double *__restrict__ d,
                                                                const double *__restrict__ e2,
                                                                const double *__restrict__ sc, double *__restrict__ w) {
@@ -373,97 +369,116 @@ __device__ inline double unit_rand(uint64_t k, uint64_t i) {
 
 // Thread k (the first eigenvalue of its cluster) computes the eigenvectors
 // of eigenvalues k, k+1, ... of its cluster (consecutive eigenvalues within
-// 1e-10 tnorm of each other) into columns of Z (m x m, ld m).  Scratch per
-// thread: 5 m doubles at wk + 5 m k.
-__global__ void stein_kernel(int m, const double *__restrict__ d, const double *__restrict__ e,
-                             const double *__restrict__ sc, const double *__restrict__ w, double *__restrict__ Z,
-                             double *__restrict__ wk) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+// 1e-10 tnorm of each other) into columns of Z (m x m, ld m).  Scratch: six
+// m-vectors per thread, interleaved across the 32 lanes of a warp (element
+// i of lane l at i * 32 + l) so that a warp's accesses are contiguous.
+__global__ void __launch_bounds__(32) stein_kernel(int m, const double *__restrict__ d, const double *__restrict__ e,
+                                                   const double *__restrict__ sc, const double *__restrict__ w,
+                                                   double *__restrict__ Z, double *__restrict__ wk) {
+  const int lane = threadIdx.x;
+  const int k = blockIdx.x * 32 + lane;
+  const size_t vs = (size_t)m * 32;
+  double *base = wk + (size_t)blockIdx.x * 6 * vs + lane;
+  double *a = base;            // U diagonal (then its reciprocals)
+  double *b = base + vs;       // U first superdiagonal
+  double *c2 = base + 2 * vs;  // U second superdiagonal
+  double *l = base + 3 * vs;   // multipliers
+  double *fl = base + 4 * vs;  // 1: rows i, i+1 swapped
+  double *x = base + 5 * vs;   // the iterate
+#define V(arr, i) arr[(size_t)(i) * 32]
   if (k >= m) return;
   const double tn = sc[2];
   const double ctol = 1e-10 * tn;
   if (k > 0 && w[k] - w[k - 1] <= ctol) return;  // not the first of its cluster
   int kend = k + 1;
   while (kend < m && w[kend] - w[kend - 1] <= ctol) ++kend;
-  double *a = wk + (size_t)5 * m * k;  // U diagonal
-  double *b = a + m;                   // U first superdiagonal
-  double *c2 = b + m;                  // U second superdiagonal
-  double *l = c2 + m;                  // multipliers
-  double *fl = l + m;                  // 1: rows i, i+1 swapped
   const double tiny = 2.220446049250313e-16 * tn + 1e-300;
   for (int kk = k; kk < kend; ++kk) {
     const double lam = w[kk];
     // LU with partial pivoting of T - lam I (tridiagonal; U gets a second
-    // superdiagonal from the swaps); zero pivots become eps tnorm
+    // superdiagonal from the swaps); pivots below eps tnorm become eps tnorm
     for (int i = 0; i < m; ++i) {
-      a[i] = d[i] - lam;
-      b[i] = (i < m - 1) ? e[i] : 0.0;
-      c2[i] = 0.0;
+      V(a, i) = d[i] - lam;
+      V(b, i) = (i < m - 1) ? e[i] : 0.0;
+      V(c2, i) = 0.0;
     }
     for (int i = 0; i < m - 1; ++i) {
       const double sub = e[i];
-      if (fabs(a[i]) >= fabs(sub)) {
-        if (a[i] == 0.0) a[i] = tiny;
-        const double f = sub / a[i];
-        l[i] = f;
-        fl[i] = 0.0;
-        a[i + 1] -= f * b[i];
+      double ai = V(a, i);
+      if (fabs(ai) >= fabs(sub)) {
+        if (ai == 0.0) ai = tiny;
+        const double f = sub / ai;
+        V(a, i) = ai;
+        V(l, i) = f;
+        V(fl, i) = 0.0;
+        V(a, i + 1) -= f * V(b, i);
       } else {
-        const double f = a[i] / sub;
-        a[i] = sub;
-        l[i] = f;
-        fl[i] = 1.0;
-        const double t = b[i];
-        b[i] = a[i + 1];
-        a[i + 1] = t - f * a[i + 1];
+        const double f = ai / sub;
+        V(a, i) = sub;
+        V(l, i) = f;
+        V(fl, i) = 1.0;
+        const double t = V(b, i);
+        V(b, i) = V(a, i + 1);
+        V(a, i + 1) = t - f * V(a, i + 1);
         if (i < m - 2) {
-          c2[i] = b[i + 1];
-          b[i + 1] = -f * b[i + 1];
+          V(c2, i) = V(b, i + 1);
+          V(b, i + 1) = -f * V(b, i + 1);
         }
       }
     }
-    if (a[m - 1] == 0.0) a[m - 1] = tiny;
-    for (int i = 0; i < m; ++i) {  // pivots below eps tnorm raised to it; kept as reciprocals
-      const double v = (fabs(a[i]) < tiny) ? (a[i] < 0.0 ? -tiny : tiny) : a[i];
-      a[i] = 1.0 / v;
+    for (int i = 0; i < m; ++i) {  // reciprocal pivots
+      const double ai = V(a, i);
+      const double v = (fabs(ai) < tiny) ? (ai < 0.0 ? -tiny : tiny) : ai;
+      V(a, i) = 1.0 / v;
     }
-    double *x = Z + (size_t)kk * m;
-    for (int i = 0; i < m; ++i) x[i] = unit_rand(kk, i);
+    for (int i = 0; i < m; ++i) V(x, i) = unit_rand(kk, i);
     for (int it = 0; it < 3; ++it) {
       // x <- (T - lam I)^{-1} x
       for (int i = 0; i < m - 1; ++i) {
-        if (fl[i] != 0.0) {
-          const double t = x[i];
-          x[i] = x[i + 1];
-          x[i + 1] = t - l[i] * x[i + 1];
+        if (V(fl, i) != 0.0) {
+          const double t = V(x, i);
+          V(x, i) = V(x, i + 1);
+          V(x, i + 1) = fma(-V(l, i), V(x, i + 1), t);
         } else {
-          x[i + 1] -= l[i] * x[i];
+          V(x, i + 1) = fma(-V(l, i), V(x, i), V(x, i + 1));
         }
       }
-      x[m - 1] *= a[m - 1];
-      if (m > 1) x[m - 2] = (x[m - 2] - b[m - 2] * x[m - 1]) * a[m - 2];
-      for (int i = m - 3; i >= 0; --i) x[i] = (x[i] - b[i] * x[i + 1] - c2[i] * x[i + 2]) * a[i];
+      double xn1 = V(x, m - 1) * V(a, m - 1), xn2 = 0.0;
+      V(x, m - 1) = xn1;
+      if (m > 1) {
+        xn2 = (V(x, m - 2) - V(b, m - 2) * xn1) * V(a, m - 2);
+        V(x, m - 2) = xn2;
+      }
+      for (int i = m - 3; i >= 0; --i) {
+        const double xi = (V(x, i) - V(b, i) * xn2 - V(c2, i) * xn1) * V(a, i);
+        V(x, i) = xi;
+        xn1 = xn2;
+        xn2 = xi;
+      }
       // orthogonalise against the cluster's earlier vectors, normalise
       for (int jj = k; jj < kk; ++jj) {
         const double *y = Z + (size_t)jj * m;
         double s = 0.0;
-        for (int i = 0; i < m; ++i) s = fma(y[i], x[i], s);
-        for (int i = 0; i < m; ++i) x[i] = fma(-s, y[i], x[i]);
+        for (int i = 0; i < m; ++i) s = fma(y[i], V(x, i), s);
+        for (int i = 0; i < m; ++i) V(x, i) = fma(-s, y[i], V(x, i));
       }
       // normalise: scale by a power of two near 1 / max|x| (exact), then by
       // 1 / ||x||
       int emx = 0;
-      for (int i = 0; i < m; ++i) emx = max(emx, expb(x[i]));
+      for (int i = 0; i < m; ++i) emx = max(emx, expb(V(x, i)));
       const double p2 = __longlong_as_double((long long)(2046 - min(emx, 2045)) << 52);
       double nn = 0.0;
       for (int i = 0; i < m; ++i) {
-        x[i] *= p2;
-        nn = fma(x[i], x[i], nn);
+        const double xi = V(x, i) * p2;
+        V(x, i) = xi;
+        nn = fma(xi, xi, nn);
       }
       const double r = 1.0 / sqrt(nn);
-      for (int i = 0; i < m; ++i) x[i] *= r;
+      for (int i = 0; i < m; ++i) V(x, i) *= r;
     }
+    for (int i = 0; i < m; ++i) Z[(size_t)kk * m + i] = V(x, i);
   }
+#undef V
 }
 
 // ------------------------------------------------------ back-transform --
@@ -534,8 +549,12 @@ __global__ void __launch_bounds__(OR_THREADS)
 
 // ------------------------------------------------------------- Cholesky --
 // A = L L^H (lower), right-looking; rows dealt cyclically to the cluster's
-// CTAs as above.  fail: first column whose pivot is not positive, + 1.
-// Two cluster barriers per column.
+// CTAs as above.  Column j of L is conj(row j) / sqrt(a_jj) right of the
+// diagonal, so the owner of row j forms and publishes the whole column (and
+// writes it to Lout); after one cluster barrier every CTA updates its rows
+// whole, A[i][k] -= l_i conj(l_k) for k > j (the row of the next pivot is
+// then complete in its owner).  fail: first column whose pivot is not
+// positive, + 1.  One cluster barrier per column.
 template <class T>
 __global__ void __launch_bounds__(TRD_THREADS, 1)
     chol_cluster_kernel(int m, const T *__restrict__ A, T *__restrict__ Lout, int *fail) {
@@ -545,57 +564,53 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
   const int rl = (m + C - 1) / C;
   extern __shared__ __align__(16) unsigned char smem[];
   T *L = reinterpret_cast<T *>(smem);  // [rl][m]
-  T *lown = L + (size_t)rl * m;        // [rl] entries of column j (own rows)
-  T *lfull = lown + rl;                // [m]
-  __shared__ double s_piv;
-  const int tid = threadIdx.x;
+  T *lpub = L + (size_t)rl * m;        // [m] column j of L, published by the owner of row j
+  T *lfull = lpub + m;                 // [m] copy
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (long t = tid; t < (long)rl * m; t += blockDim.x) {
     const int k = (int)(t / rl), il = (int)(t % rl);
     const int i = il * C + q;
     L[(long)il * m + k] = (i < m) ? A[i + (long)k * m] : X::zero();
   }
   __syncthreads();
-  int bad = 0;
   for (int j = 0; j < m; ++j) {
-    if (tid == 0 && j % C == q) s_piv = X::re(L[(long)(j / C) * m + j]);
-    cl.sync();  // B1: pivot visible
-    const double piv = *cl.map_shared_rank(&s_piv, j % C);
-    if (!(piv > 0.0)) {  // uniform: every CTA reads the same pivot
-      if (tid == 0 && q == 0) *fail = j + 1;
-      bad = 1;
+    const int own = j % C;
+    if (q == own) {
+      const T *Lj = L + (long)(j / C) * m;
+      const double piv = X::re(Lj[j]);
+      const bool ok = piv > 0.0;
+      if (tid == 0) s_fail = ok ? 0 : j + 1;
+      if (ok) {
+        const double r = sqrt(piv), ir = 1.0 / r;
+        for (int k = tid; k < m; k += blockDim.x) {
+          T l = X::zero();
+          if (k == j)
+            l = cvt<T, double>(r);
+          else if (k > j)
+            l = scl(X::conj(Lj[k]), ir);
+          if (k >= j) lpub[k] = l;
+          Lout[k + (long)j * m] = l;
+        }
+      }
+    }
+    cl.sync();  // column j of L published (or the failure)
+    const int f = *cl.map_shared_rank(&s_fail, own);
+    if (f) {  // uniform: every CTA reads the owner's flag
+      if (tid == 0 && q == 0) *fail = f;
       break;
     }
-    const double r = sqrt(piv), ir = 1.0 / r;
-    for (int il = tid; il < rl; il += blockDim.x) {
-      const int i = il * C + q;
-      T l = X::zero();
-      if (i == j) {
-        l = cvt<T, double>(r);
-        L[(long)il * m + j] = l;
-      } else if (i > j && i < m) {
-        l = scl(L[(long)il * m + j], ir);
-        L[(long)il * m + j] = l;
-      }
-      lown[il] = l;
-    }
-    cl.sync();  // B2: column j of L visible
-    for (int k = j + 1 + tid; k < m; k += blockDim.x) lfull[k] = *cl.map_shared_rank(&lown[k / C], k % C);
+    const T *lsrc = cl.map_shared_rank(lpub, own);
+    for (int k = j + 1 + tid; k < m; k += blockDim.x) lfull[k] = lsrc[k];
     __syncthreads();
-    const int w = m - j - 1;
-    for (long t = tid; t < (long)rl * w; t += blockDim.x) {
-      const int il = (int)(t / w), k = j + 1 + (int)(t % w);
+    for (int il = warp; il < rl; il += nw) {
       const int i = il * C + q;
-      if (i < k || i >= m) continue;  // lower triangle of the trailing block
-      L[(long)il * m + k] = X::sub(L[(long)il * m + k], X::mul(lown[il], X::conj(lfull[k])));
+      if (i <= j || i >= m) continue;
+      T *Li = L + (long)il * m;
+      const T li = X::neg(lfull[i]);
+      for (int k = j + 1 + lane; k < m; k += 32) Li[k] = X::fma(li, X::conj(lfull[k]), Li[k]);
     }
     __syncthreads();
-  }
-  if (!bad) {
-    for (long t = tid; t < (long)rl * m; t += blockDim.x) {
-      const int k = (int)(t / rl), il = (int)(t % rl);
-      const int i = il * C + q;
-      if (i < m) Lout[i + (long)k * m] = (k <= i) ? L[(long)il * m + k] : X::zero();
-    }
   }
   cl.sync();
 }
@@ -652,8 +667,9 @@ size_t heev_tridiag_work(int m, bool cplx) {
   const size_t ts = cplx ? sizeof(zd) : sizeof(double);
   const size_t mm = (size_t)m * m;
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t stein_b = (size_t)ceil_div(m, 32) * 6 * 32 * m * sizeof(double);
   return al(mm * ts) + 3 * al(m * ts) + 5 * al(m * sizeof(double)) + al(8 * sizeof(double)) +
-         al(mm * sizeof(double)) + al(5 * mm * sizeof(double));
+         al(mm * sizeof(double)) + al(stein_b);
 }
 
 template <class T>
@@ -661,7 +677,7 @@ int heev_tridiag(cudaStream_t st, int m, const T *A, double *w, T *V, void *work
   if (m < 2 || m > OR_THREADS * OR_PER) return 1;
   if (heev_tridiag_work(m, tr<T>::cplx) > work_bytes) return 1;
   size_t sm_t = 0;
-  const int C = cluster_shape<T>(m, 2, 2, &sm_t);
+  const int C = cluster_shape<T>(m, 1, 3, &sm_t);
   if (C == 0) return 1;
   const size_t mm = (size_t)m * m;
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
@@ -708,7 +724,7 @@ int heev_tridiag(cudaStream_t st, int m, const T *A, double *w, T *V, void *work
 // column + 1.  Returns 1 when the cluster kernel cannot take m.
 template <class T> int chol_cluster(cudaStream_t st, int m, const T *A, T *L, int *fail) {
   size_t sm = 0;
-  const int C = cluster_shape<T>(m, 1, 1, &sm);
+  const int C = cluster_shape<T>(m, 0, 2, &sm);
   if (C == 0) return 1;
   return launch_cluster(chol_cluster_kernel<T>, C, sm, st, m, A, L, fail);
 }
