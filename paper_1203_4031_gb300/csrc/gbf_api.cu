@@ -707,7 +707,7 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
         GBF_CUDA(cudaMemcpyAsync(Gw, G, sizeof(TQ) * (size_t)m * m, cudaMemcpyDeviceToDevice, st));
         GBF_CUDA(cudaMemsetAsync(ws.flag + 1, 0, sizeof(int), st));
         CK(chol_lower<TQ>(st, m, Gw, L, ws.flag + 1));
-        CK(trinv_lower<TQ>(st, m, L, Li));
+        CK(trinv_lower<TQ>(st, m, L, Li, ws.resu));
         if (pass == 0) {
           // T = L^{-H}
           copy_t_kernel<TQ><<<dim3(ceil_div(m, 256), m), 256, 0, st>>>(m, Li, ws.Tm);

@@ -318,7 +318,7 @@ template <class T> int chol_cluster(cudaStream_t st, int m, const T *A, T *L, in
 // overwritten as workspace, fail = first non-positive pivot + 1), inverse of
 // a lower triangular matrix, and the Jacobi eigensolver core.
 template <class T> int chol_lower(cudaStream_t st, int m, T *A, T *L, int *fail);
-template <class T> int trinv_lower(cudaStream_t st, int m, const T *L, T *Linv);
+template <class T> int trinv_lower(cudaStream_t st, int m, const T *L, T *Linv, double *rd /* m scratch */);
 template <class T> int jacobi_coop(cudaStream_t st, int m, int maxsw, T *A, T *V, T *work, double *dw, int *iw);
 
 // Rayleigh-Ritz glue (eig.cu).

@@ -83,6 +83,19 @@ int form_shift(cudaStream_t st, int n, int ne, const zd *z, int kindA, char uplo
 }
 
 // ---------------------------------------------------------------- panel --
+// Pivot comparison key of a magnitude |re| + |im| >= 0: its bit pattern as
+// an integer (ordered like the value for non-negative numbers), -1 for NaN
+// (never chosen).  The argmax then runs on the integer units: FP64
+// instructions are the scarce resource on this GPU.
+__device__ inline long long pivkey(double v) {
+  const long long b = __double_as_longlong(v);
+  return b > 0x7FF0000000000000LL ? -1LL : b;
+}
+__device__ inline long long pivkey(float v) {
+  const int b = __float_as_int(v);
+  return b > 0x7F800000 ? -1LL : (long long)b;
+}
+
 // One CTA per node factors columns [k, k+w) of rows [k, n).
 constexpr int PANEL_THREADS = 512;
 constexpr int MAX_NB = 64;
@@ -96,7 +109,7 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   const long nn = (long)n * n;
   T *a = S + e * nn;
   int *piv = ipiv + (long)e * n;
-  __shared__ R sval[32];
+  __shared__ long long sval[32];
   __shared__ int sidx[32];
   __shared__ T urow[MAX_NB];
   __shared__ T s_inv;
@@ -107,17 +120,17 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   for (int j = 0; j < w; ++j) {
     const int c = k + j;
     const T *col = a + (long)c * n;
-    R best = (R)-1;
+    long long best = -1;
     int bidx = n;
     for (int r = c + tid; r < n; r += blockDim.x) {
-      const R v = X::abs1(col[r]);
+      const long long v = pivkey(X::abs1(col[r]));
       if (v > best) {
         best = v;
         bidx = r;
       }
     }
     for (int off = 16; off > 0; off >>= 1) {
-      const R ov = __shfl_down_sync(0xffffffffu, best, off);
+      const long long ov = __shfl_down_sync(0xffffffffu, best, off);
       const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
       if (ov > best || (ov == best && oi < bidx)) {
         best = ov;
@@ -130,10 +143,10 @@ __global__ void __launch_bounds__(PANEL_THREADS)
     }
     __syncthreads();
     if (warp == 0) {
-      best = lane < nwarps ? sval[lane] : (R)-1;
+      best = lane < nwarps ? sval[lane] : -1;
       bidx = lane < nwarps ? sidx[lane] : n;
       for (int off = 16; off > 0; off >>= 1) {
-        const R ov = __shfl_down_sync(0xffffffffu, best, off);
+        const long long ov = __shfl_down_sync(0xffffffffu, best, off);
         const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
         if (ov > best || (ov == best && oi < bidx)) {
           best = ov;
@@ -141,7 +154,7 @@ __global__ void __launch_bounds__(PANEL_THREADS)
         }
       }
       if (lane == 0) {
-        const int ok = (best > (R)0) && (bidx < n);
+        const int ok = (best > 0) && (bidx < n);
         s_ok = ok;
         s_p = ok ? bidx : c;
         piv[c] = ok ? bidx : c;
@@ -203,9 +216,9 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   T *sl = reinterpret_cast<T *>(smem_raw);  // [w][R]
   T *urow = sl + (long)w * R;               // pivot row (old row p)
   T *xrow = urow + MAX_NB;                  // old row c (kept by the owner of p)
-  Rt *cval = reinterpret_cast<Rt *>(xrow + MAX_NB);
+  long long *cval = reinterpret_cast<long long *>(xrow + MAX_NB);
   int *cidx = reinterpret_cast<int *>(cval + 2);
-  __shared__ Rt wv[32];
+  __shared__ long long wv[32];
   __shared__ int wi[32];
   __shared__ T s_inv;
   __shared__ int s_p, s_ok;
@@ -220,19 +233,19 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   for (int j = 0; j < w; ++j) {
     const int c = k + j;
     // 1. local candidate
-    Rt best = (Rt)-1;
+    long long best = -1;
     int bidx = n;
     for (int rl = tid; rl < rows; rl += blockDim.x) {
       const int gr = r0 + rl;
       if (gr < c) continue;
-      const Rt v = X::abs1(sl[(long)j * R + rl]);
+      const long long v = pivkey(X::abs1(sl[(long)j * R + rl]));
       if (v > best) {
         best = v;
         bidx = gr;
       }
     }
     for (int off = 16; off > 0; off >>= 1) {
-      const Rt ov = __shfl_down_sync(0xffffffffu, best, off);
+      const long long ov = __shfl_down_sync(0xffffffffu, best, off);
       const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
       if (ov > best || (ov == best && oi < bidx)) {
         best = ov;
@@ -245,7 +258,7 @@ __global__ void __launch_bounds__(PANEL_THREADS)
     }
     __syncthreads();
     if (tid == 0) {
-      Rt b = (Rt)-1;
+      long long b = -1;
       int bi = n;
       for (int w2 = 0; w2 < nwarps; ++w2)
         if (wv[w2] > b || (wv[w2] == b && wi[w2] < bi)) {
@@ -258,14 +271,14 @@ __global__ void __launch_bounds__(PANEL_THREADS)
     cl.sync();  // (A) candidates visible; previous column's updates complete
     // 2. cluster argmax (every CTA reduces the same list in the same order)
     if (warp == 0) {
-      Rt b = (Rt)-1;
+      long long b = -1;
       int bi = n;
       if (lane < C) {
         b = *cl.map_shared_rank(cval, lane);
         bi = *cl.map_shared_rank(cidx, lane);
       }
       for (int off = 16; off > 0; off >>= 1) {
-        const Rt ov = __shfl_down_sync(0xffffffffu, b, off);
+        const long long ov = __shfl_down_sync(0xffffffffu, b, off);
         const int oi = __shfl_down_sync(0xffffffffu, bi, off);
         if (ov > b || (ov == b && oi < bi)) {
           b = ov;
@@ -273,7 +286,7 @@ __global__ void __launch_bounds__(PANEL_THREADS)
         }
       }
       if (lane == 0) {
-        const int ok = (b > (Rt)0) && (bi < n);
+        const int ok = (b > 0) && (bi < n);
         s_ok = ok;
         s_p = ok ? bi : c;
       }

@@ -95,8 +95,15 @@ __global__ void chol_coop_kernel(int m, T *A, T *L, int *fail) {
 
 // ------------------------------------------------- triangular inverse --
 // Linv = L^{-1} for lower triangular L; warp w of the grid computes column j.
+// rd: the reciprocals of L's (real, positive) diagonal, formed once by
+// recip_diag_kernel (FP64 divisions are costly; every column needs them).
 template <class T>
-__global__ void trinv_lower_kernel(int m, const T *L, T *Linv) {
+__global__ void recip_diag_kernel(int m, const T *L, double *rd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) rd[i] = 1.0 / tr<T>::re(L[i + (long)i * m]);
+}
+template <class T>
+__global__ void trinv_lower_kernel(int m, const T *L, const double *rd, T *Linv) {
   using X = tr<T>;
   const int lane = threadIdx.x & 31;
   const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -118,7 +125,7 @@ __global__ void trinv_lower_kernel(int m, const T *L, T *Linv) {
     }
     if (lane == 0) {
       T rhs = (i == j) ? X::sub(X::one(), s) : X::neg(s);
-      x[i] = X::mul(rhs, cvt<T, double>(1.0 / X::re(L[i + (long)i * m])));
+      x[i] = X::mul(rhs, cvt<T, double>(rd[i]));
     }
     __syncwarp();
   }
@@ -140,8 +147,10 @@ int chol_lower(cudaStream_t st, int m, T *A, T *L, int *fail) {
 }
 
 template <class T>
-int trinv_lower(cudaStream_t st, int m, const T *L, T *Linv) {
-  trinv_lower_kernel<T><<<ceil_div((long)m * 32, 256), 256, 0, st>>>(m, L, Linv);
+int trinv_lower(cudaStream_t st, int m, const T *L, T *Linv, double *rd) {
+  recip_diag_kernel<T><<<ceil_div(m, 256), 256, 0, st>>>(m, L, rd);
+  GBF_LAUNCHED();
+  trinv_lower_kernel<T><<<ceil_div((long)m * 32, 256), 256, 0, st>>>(m, L, rd, Linv);
   GBF_LAUNCHED();
   GBF_CUDA(cudaGetLastError());
   return 0;
@@ -429,7 +438,7 @@ int jacobi_coop(cudaStream_t st, int m, int maxsw, T *A, T *V, T *work, double *
 
 #define SMALL_INST(T)                                                                          \
   template int chol_lower<T>(cudaStream_t, int, T *, T *, int *);                             \
-  template int trinv_lower<T>(cudaStream_t, int, const T *, T *);                             \
+  template int trinv_lower<T>(cudaStream_t, int, const T *, T *, double *);                   \
   template int jacobi_coop<T>(cudaStream_t, int, int, T *, T *, T *, double *, int *);
 SMALL_INST(double)
 SMALL_INST(zd)

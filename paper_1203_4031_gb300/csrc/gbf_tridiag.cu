@@ -45,7 +45,7 @@ namespace cg = cooperative_groups;
 
 namespace gbf {
 
-constexpr int TRD_THREADS = 512;
+constexpr int TRD_THREADS = 640;
 constexpr int TRD_SMEM_CAP = 200 * 1024;
 
 __device__ inline double absq(double a) { return a * a; }
@@ -62,7 +62,9 @@ template <class T> __device__ inline T warp_sum(T v) {
 }
 
 // Deterministic CTA sum of one value per thread (fixed shuffle pattern, then
-// the warps' partials in warp order).  Every thread gets the result.
+// the warps' partials in warp order, added by one thread: FP64 instructions
+// are scarce, so the final sum is not repeated by every warp).  Every thread
+// gets the result (red[32] holds it).
 template <class T> __device__ T cta_sum(T v, T *red) {
   using X = tr<T>;
   v = warp_sum(v);
@@ -70,9 +72,13 @@ template <class T> __device__ T cta_sum(T v, T *red) {
   __syncthreads();
   if (lane == 0) red[warp] = v;
   __syncthreads();
-  T s = X::zero();
-  for (int i = 0; i < nw; ++i) s = X::add(s, red[i]);
-  return s;
+  if (threadIdx.x == 0) {
+    T s = X::zero();
+    for (int i = 0; i < nw; ++i) s = X::add(s, red[i]);
+    red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
 }
 
 // The cluster kernels deal the rows of the m x m matrix cyclically to the C
@@ -98,6 +104,7 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
     sytrd_cluster_kernel(int m, const T *__restrict__ A, long lda, T *__restrict__ Vr, double *__restrict__ tau,
                          T *__restrict__ betac, double *__restrict__ dd) {
   using X = tr<T>;
+  constexpr int NW = TRD_THREADS / 32;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks(), q = (int)cl.block_rank();
   const int rl = (m + C - 1) / C;
@@ -106,13 +113,11 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
   T *pown = L + (size_t)rl * m;        // [rl] p of this CTA's rows
   T *vpub = pown + rl;                 // [m] v, published by the owner of row j
   T *vfull = vpub + m;                 // [m] copy of v
-  T *wfull = vfull + m;                // [m] p, then w
-  __shared__ T s_pv;                   // this CTA's part of v^H p
+  T *wfull = vfull + m;                // [m] w
+  __shared__ T s_pvw[NW];              // each warp's part of v^H p
   __shared__ double s_tau;             // published by the owner of row j
   __shared__ T s_sc;
-  __shared__ double red_d[32];
-  __shared__ T red_t[32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (long t = tid; t < (long)rl * m; t += blockDim.x) {
     const int k = (int)(t / rl), il = (int)(t % rl);
@@ -124,27 +129,30 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
   for (int j = 0; j < m - 1; ++j) {
     const int own = j % C;
     if (q == own) {
-      // (a) x = conj(row j)[j+1 ..]; ||x_{2..}||^2 over this CTA's threads
+      // (a) x = conj(row j)[j+1 ..]: ||x_{2..}||^2 by warp 0 (fixed order),
+      // the reflector by its lane 0, v by the whole CTA
       const T *Lj = L + (long)(j / C) * m;
-      double part = 0.0;
-      for (int k = j + 2 + tid; k < m; k += blockDim.x) part += absq(Lj[k]);
-      const double rest = cta_sum(part, red_d);
-      if (tid == 0) {
-        const T x0 = X::conj(Lj[j + 1]);
-        double tj = 0.0;
-        T beta = x0, sc = X::zero();
-        if (rest > 0.0) {
-          const double a0 = sqrt(absq(x0));
-          const double nx = sqrt(a0 * a0 + rest);
-          const T ph = a0 > 0.0 ? scl(x0, 1.0 / a0) : X::one();
-          beta = scl(ph, -nx);
-          sc = scl(X::conj(ph), 1.0 / (a0 + nx));
-          tj = 1.0 + a0 / nx;
+      if (warp == 0) {
+        double part = 0.0;
+        for (int k = j + 2 + lane; k < m; k += 32) part += absq(Lj[k]);
+        const double rest = warp_sum(part);
+        if (lane == 0) {
+          const T x0 = X::conj(Lj[j + 1]);
+          double tj = 0.0;
+          T beta = x0, sc = X::zero();
+          if (rest > 0.0) {
+            const double a0 = sqrt(absq(x0));
+            const double nx = sqrt(a0 * a0 + rest);
+            const T ph = a0 > 0.0 ? scl(x0, 1.0 / a0) : X::one();
+            beta = scl(ph, -nx);
+            sc = scl(X::conj(ph), 1.0 / (a0 + nx));
+            tj = 1.0 + a0 / nx;
+          }
+          s_tau = tj;
+          s_sc = sc;
+          tau[j] = tj;
+          betac[j] = beta;
         }
-        s_tau = tj;
-        s_sc = sc;
-        tau[j] = tj;
-        betac[j] = beta;
       }
       __syncthreads();
       const T sc = s_sc;
@@ -160,29 +168,29 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
       const T *vsrc = cl.map_shared_rank(vpub, own);
       for (int k = j + 1 + tid; k < m; k += blockDim.x) vfull[k] = vsrc[k];
       __syncthreads();
-      // (b) p_i for the own rows i > j, one warp per row
+      // (b) p_i for the own rows i > j, one warp per row; each warp's part
+      // of v^H p to s_pvw (no CTA-wide reduction here: the cross-CTA sum
+      // below reads every warp's part)
       T pv = X::zero();
-      for (int il = warp; il < rl; il += nw) {
+      for (int il = warp; il < rl; il += NW) {
         const int i = il * C + q;
         if (i < j + 1 || i >= m) continue;
         const T *Li = L + (long)il * m;
         T s = X::zero();
         for (int k = j + 1 + lane; k < m; k += 32) s = X::fma(Li[k], vfull[k], s);
         s = scl(warp_sum(s), tj);
-        if (lane == 0) {
-          pown[il] = s;
-          pv = X::fma(X::conj(vfull[i]), s, pv);
-        }
+        if (lane == 0) pown[il] = s;
+        pv = X::fma(X::conj(vfull[i]), s, pv);
       }
-      pv = cta_sum(pv, red_t);
-      if (tid == 0) s_pv = pv;
+      if (lane == 0) s_pvw[warp] = pv;
     }
-    cl.sync();  // B2: every CTA's p and part of v^H p visible
+    cl.sync();  // B2: every CTA's p and parts of v^H p visible
     if (tj != 0.0) {
-      // (c) p from all CTAs, K (identical in every CTA: lane c of warp 0
-      // reads CTA c's part, fixed-pattern shuffle sum), w = p - K v
+      // (c) v^H p: warp 0 reads the C x NW parts (lane-parallel, then a
+      // fixed-pattern shuffle sum, the same in every CTA); w = p - K v
       if (warp == 0) {
-        const T r = lane < C ? *cl.map_shared_rank(&s_pv, lane) : X::zero();
+        T r = X::zero();
+        for (int t = lane; t < C * NW; t += 32) r = X::add(r, *cl.map_shared_rank(&s_pvw[t % NW], t / NW));
         const T tot = warp_sum(r);
         if (lane == 0) s_sc = tot;
       }
@@ -195,7 +203,7 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
       __syncthreads();
       // A[i][k] -= v_i conj(w_k) + w_i conj(v_k), own rows i > j, one warp
       // per row, lanes over the columns k > j
-      for (int il = warp; il < rl; il += nw) {
+      for (int il = warp; il < rl; il += NW) {
         const int i = il * C + q;
         if (i < j + 1 || i >= m) continue;
         T *Li = L + (long)il * m;
@@ -208,8 +216,11 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
         }
       }
     }
-    __syncthreads();
+    // the next owner reads its own updated row before the next cluster
+    // barrier; the other CTAs are ordered by that barrier
+    if ((j + 1) % C == q) __syncthreads();
   }
+  __syncthreads();
   for (int il = tid; il < rl; il += blockDim.x) {
     const int i = il * C + q;
     if (i < m) dd[i] = X::re(L[(long)il * m + i]);
@@ -292,23 +303,33 @@ __device__ inline int expb(double v) { return (int)(((unsigned long long)__doubl
 __device__ inline bool zerob(double v) { return ((unsigned long long)__double_as_longlong(v) << 1) == 0ull; }
 
 __device__ inline int sturm_count(int m, const double *__restrict__ d, const double *__restrict__ e2, double x) {
+  // per step: three FP64 operations and a few 32-bit integer operations on
+  // the high word (sign, zero test, exponent range); the rare rescaling and
+  // zero fix-up leave the main path
   double pm = 1.0, p = d[0] - x;
   if (zerob(p)) p = -0x1p-1000;
-  int cnt = sgnb(p);
+  int hp = __double2hiint(p);
+  int cnt = (int)((unsigned)hp >> 31);
   for (int k = 1; k < m; ++k) {
     double pn = fma(d[k] - x, p, -(e2[k - 1] * pm));
-    if (zerob(pn)) pn = sgnb(p) ? 0x1p-1000 : -0x1p-1000;
-    cnt += sgnb(pn) ^ sgnb(p);
+    int hn = __double2hiint(pn);
+    // biased exponent outside [1023 - 600, 1023 + 600], or zero / subnormal
+    if ((unsigned)(((hn >> 20) & 0x7FF) - (1023 - 600)) > 1200u) {
+      if (zerob(pn)) {
+        pn = hp < 0 ? 0x1p-1000 : -0x1p-1000;
+      } else if (((hn >> 20) & 0x7FF) > 1023 + 600) {
+        pn *= 0x1p-600;
+        p *= 0x1p-600;
+      } else if (expb(p) < 1023 - 600) {
+        pn *= 0x1p600;
+        p *= 0x1p600;
+      }
+      hn = __double2hiint(pn);
+    }
+    cnt += (int)((unsigned)(hn ^ hp) >> 31);
     pm = p;
     p = pn;
-    const int ex = expb(p);
-    if (ex > 1023 + 600) {
-      p *= 0x1p-600;
-      pm *= 0x1p-600;
-    } else if (ex < 1023 - 600 && expb(pm) < 1023 - 600) {
-      p *= 0x1p600;
-      pm *= 0x1p600;
-    }
+    hp = hn;
   }
   return cnt;
 }
@@ -396,52 +417,53 @@ __global__ void __launch_bounds__(32) stein_kernel(int m, const double *__restri
   for (int kk = k; kk < kend; ++kk) {
     const double lam = w[kk];
     // LU with partial pivoting of T - lam I (tridiagonal; U gets a second
-    // superdiagonal from the swaps); pivots below eps tnorm become eps tnorm
-    for (int i = 0; i < m; ++i) {
-      V(a, i) = d[i] - lam;
-      V(b, i) = (i < m - 1) ? e[i] : 0.0;
-      V(c2, i) = 0.0;
-    }
+    // superdiagonal from the swaps), the running diagonal and superdiagonal
+    // entries carried in registers; pivots below eps tnorm become eps tnorm
+    // and are kept as reciprocals
+    double ai = d[0] - lam, bi = m > 1 ? e[0] : 0.0;
     for (int i = 0; i < m - 1; ++i) {
       const double sub = e[i];
-      double ai = V(a, i);
+      const double dn = d[i + 1] - lam, en = (i + 1 < m - 1) ? e[i + 1] : 0.0;
+      double piv, f, an, bn;
       if (fabs(ai) >= fabs(sub)) {
-        if (ai == 0.0) ai = tiny;
-        const double f = sub / ai;
-        V(a, i) = ai;
-        V(l, i) = f;
+        piv = (ai == 0.0) ? tiny : ai;
+        f = sub / piv;
+        V(b, i) = bi;
+        V(c2, i) = 0.0;
         V(fl, i) = 0.0;
-        V(a, i + 1) -= f * V(b, i);
+        an = fma(-f, bi, dn);
+        bn = en;
       } else {
-        const double f = ai / sub;
-        V(a, i) = sub;
-        V(l, i) = f;
+        piv = sub;
+        f = ai / sub;
+        V(b, i) = dn;
+        V(c2, i) = en;
         V(fl, i) = 1.0;
-        const double t = V(b, i);
-        V(b, i) = V(a, i + 1);
-        V(a, i + 1) = t - f * V(a, i + 1);
-        if (i < m - 2) {
-          V(c2, i) = V(b, i + 1);
-          V(b, i + 1) = -f * V(b, i + 1);
-        }
+        an = fma(-f, dn, bi);
+        bn = -f * en;
       }
+      V(l, i) = f;
+      V(a, i) = 1.0 / ((fabs(piv) < tiny) ? (piv < 0.0 ? -tiny : tiny) : piv);
+      ai = an;
+      bi = bn;
     }
-    for (int i = 0; i < m; ++i) {  // reciprocal pivots
-      const double ai = V(a, i);
-      const double v = (fabs(ai) < tiny) ? (ai < 0.0 ? -tiny : tiny) : ai;
-      V(a, i) = 1.0 / v;
-    }
+    V(a, m - 1) = 1.0 / ((fabs(ai) < tiny) ? (ai < 0.0 ? -tiny : tiny) : ai);
     for (int i = 0; i < m; ++i) V(x, i) = unit_rand(kk, i);
     for (int it = 0; it < 3; ++it) {
       // x <- (T - lam I)^{-1} x
-      for (int i = 0; i < m - 1; ++i) {
-        if (V(fl, i) != 0.0) {
-          const double t = V(x, i);
-          V(x, i) = V(x, i + 1);
-          V(x, i + 1) = fma(-V(l, i), V(x, i + 1), t);
-        } else {
-          V(x, i + 1) = fma(-V(l, i), V(x, i), V(x, i + 1));
+      {
+        double xi = V(x, 0);
+        for (int i = 0; i < m - 1; ++i) {
+          const double xn = V(x, i + 1), li = V(l, i);
+          if (V(fl, i) != 0.0) {
+            V(x, i) = xn;
+            xi = fma(-li, xn, xi);
+          } else {
+            V(x, i) = xi;
+            xi = fma(-li, xi, xn);
+          }
         }
+        V(x, m - 1) = xi;
       }
       double xn1 = V(x, m - 1) * V(a, m - 1), xn2 = 0.0;
       V(x, m - 1) = xn1;
@@ -567,6 +589,7 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
   T *lpub = L + (size_t)rl * m;        // [m] column j of L, published by the owner of row j
   T *lfull = lpub + m;                 // [m] copy
   __shared__ int s_fail;
+  __shared__ double s_r, s_ir;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (long t = tid; t < (long)rl * m; t += blockDim.x) {
     const int k = (int)(t / rl), il = (int)(t % rl);
@@ -578,11 +601,17 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
     const int own = j % C;
     if (q == own) {
       const T *Lj = L + (long)(j / C) * m;
-      const double piv = X::re(Lj[j]);
-      const bool ok = piv > 0.0;
-      if (tid == 0) s_fail = ok ? 0 : j + 1;
+      if (tid == 0) {  // the pivot's root and reciprocal, once
+        const double piv = X::re(Lj[j]);
+        const bool okp = piv > 0.0;
+        s_fail = okp ? 0 : j + 1;
+        s_r = okp ? sqrt(piv) : 0.0;
+        s_ir = okp ? 1.0 / s_r : 0.0;
+      }
+      __syncthreads();
+      const bool ok = s_fail == 0;
       if (ok) {
-        const double r = sqrt(piv), ir = 1.0 / r;
+        const double r = s_r, ir = s_ir;
         for (int k = tid; k < m; k += blockDim.x) {
           T l = X::zero();
           if (k == j)
