@@ -336,8 +336,7 @@ def run_gbf(args):
         # config 5 is quoted on the mixed path with the FP64 run beside it;
         # config 4 on both
         serving = run_serving_suite(g, torch, W, args)
-        batched = {name: run_batched(g, torch, W, args.batch_problems, prec=pr)
-                   for name, pr in (("fp64", 0), ("mixed", 1))}
+        batched = run_batched_suite(g, torch, W, args.batch_problems)
         if not args.no_herm:
             herm = run_hermitian(g, torch, W)
 
@@ -524,31 +523,66 @@ def run_hermitian(g, torch, W):
     return out
 
 
-def run_batched(g, torch, W, count, nworkers=4, prec=0):
-    """Config-4 sample: `count` independent real symmetric generalized problems
-    (n log-uniform in [64, 1024], intervals holding 10-40, M0 = 1.5 count)
-    solved by one gbf_batch_solve call, FP64 path; eigenpairs/s over the call."""
-    probs = []
-    for p in W.batched_generalized(count=count, nmin=64, nmax=1024):
-        A = g.fortran(torch.from_numpy(p.A).cuda())
-        B = g.fortran(torch.from_numpy(p.B).cuda())
-        f = p.apply_fpm(g.gbf_init())
-        f[41] = prec
-        probs.append((p, g.DeviceProblem(A, B, p.emin, p.emax, p.m0, fpm=f)))
-    g.batch_solve([dp for _, dp in probs[:2]], nworkers=nworkers)  # warm-up
-    torch.cuda.synchronize()
+def run_batched_suite(g, torch, W, count, tune_sample=48):
+    """Config 4: `count` independent real symmetric generalized problems
+    (n log-uniform in [64, 1024], intervals holding 10-40, M0 = 1.5 count,
+    Ne = 8), FP64 and mixed paths.  The autotuner (paper_1203_4031_gb300.
+    autotune) first times gbf_batch_solve on the first `tune_sample`
+    problems for each path (worker count, then the LU width per size
+    bucket) and saves its table; the whole batch then runs once with the
+    tuned settings (eigenpairs/s over the call), and once with the untuned
+    default (4 workers, width 32) for comparison."""
+    from paper_1203_4031_gb300 import autotune
+
     t0 = time.perf_counter()
-    rc, outs = g.batch_solve([dp for _, dp in probs], nworkers=nworkers)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    ok = rc == 0
-    for (p, dp), r in zip(probs, outs):
-        w = p.spectrum
-        ok = ok and r.info == 0 and r.M == int(((w >= p.emin) & (w <= p.emax)).sum())
-    return {"problems": count, "eigenpairs_per_s": sum(r.M for r in outs) / dt, "ms": dt * 1e3,
-            "workers": nworkers, "all_counts_exact": bool(ok),
-            "workload": "batched generalized problems (config 4 distribution), bounded sample, "
-                        + ("mixed path" if prec else "FP64 path")}
+    gen = W.batched_generalized(count=count, nmin=64, nmax=1024)
+    mats = [(g.fortran(torch.from_numpy(p.A).cuda()), g.fortran(torch.from_numpy(p.B).cuda())) for p in gen]
+    gen_s = time.perf_counter() - t0
+    out = {"workload": f"batched generalized problems (config 4 distribution): {count} problems, "
+                       f"n log-uniform in [64, 1024]", "generation_s": gen_s}
+    entries = []
+    for name, prec in (("fp64", 0), ("mixed", 1)):
+        def make(ps):
+            dps = []
+            for p, (A, B) in ps:
+                f = p.apply_fpm(g.gbf_init())
+                f[41] = prec
+                dps.append(g.DeviceProblem(A, B, p.emin, p.emax, p.m0, fpm=f))
+            return dps
+        pairs = list(zip(gen, mats))
+        t0 = time.perf_counter()
+        entry = autotune.tune(make(pairs[:tune_sample]))
+        entries.append(entry)
+        tune_s = time.perf_counter() - t0
+        table = autotune.merge([entry])
+        res = {}
+        for label, tbl in (("tuned", table), ("default_4_workers", autotune.DEFAULT)):
+            dps = make(pairs)
+            nw = autotune.apply(dps, tbl) if label == "tuned" else 4
+            if label != "tuned":
+                for q in dps:
+                    q.p.fpm[42] = 0
+            g.batch_solve(dps[:nw], nworkers=nw)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, outs = g.batch_solve(dps, nworkers=nw)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            ok = rc == 0
+            for p, r in zip(gen, outs):
+                w = p.spectrum
+                ok = ok and r.info == 0 and r.M == int(((w >= p.emin) & (w <= p.emax)).sum())
+            res[label] = {"eigenpairs_per_s": sum(r.M for r in outs) / dt, "ms": dt * 1e3, "workers": nw,
+                          "all_counts_exact": bool(ok)}
+        res["tuning"] = {"workers": entry["workers"], "width": entry["width"], "tune_s": tune_s,
+                         "sample": tune_sample}
+        res["eigenpairs_per_s"] = res["tuned"]["eigenpairs_per_s"]
+        out[name] = res
+    try:
+        out["tuning_file"] = os.path.relpath(autotune.save(autotune.merge(entries)), ROOT)
+    except OSError:
+        out["tuning_file"] = None
+    return out
 
 
 def measured_peaks():

@@ -935,21 +935,15 @@ __global__ void __maxnreg__(96)
         const unsigned long long sgn = neg ? 0x8000000000000000ull : 0ull;
         if (fast && full) {
           // whole 32 x ZEC block in range: straight-line code, so the ZEC
-          // independent conversions interleave
-          // Odd columns go through the FP64 unit (conversion, then a fused
-          // multiply-add by +-2^E into C), even columns through the integer
-          // construction and one FP64 add: the two pipes share the work.
+          // independent conversions interleave.  Every entry goes through
+          // the integer construction and one FP64 add: an FP64 instruction
+          // costs as much issue time on this GPU as a few dozen integer
+          // ones, so the conversion stays off the FP64 unit.
           double v[ZEC];
 #pragma unroll
           for (int j = 0; j < ZEC; ++j) {
-            if (j & 1) {
-              const double p2 = __longlong_as_double(((long long)(es + et[j] + 1023) << 52) | (long long)sgn);
-              v[j] = BETA ? fma(__ll2double_rn((long long)x[j]), p2, (double)cur[j])
-                          : __ll2double_rn((long long)x[j]) * p2;
-            } else {
-              v[j] = i64_scaled((long long)x[j], es + et[j], sgn);
-              if constexpr (BETA) v[j] += (double)cur[j];
-            }
+            v[j] = i64_scaled((long long)x[j], es + et[j], sgn);
+            if constexpr (BETA) v[j] += (double)cur[j];
           }
 #pragma unroll
           for (int j = 0; j < ZEC; ++j) crow[2L * (col0 + j) * ldc] = (R)v[j];

@@ -21,8 +21,9 @@
 //                   (the sign changes of the characteristic-polynomial
 //                   recurrence, rescaled against overflow), one thread each
 //   stein           eigenvectors of T by inverse iteration (tridiagonal LU
-//                   with partial pivoting of T - lambda I), three steps from
-//                   a fixed pseudo-random start; eigenvalues closer than
+//                   with partial pivoting of T - lambda I), two steps from
+//                   a fixed pseudo-random start (three in a cluster);
+//                   eigenvalues closer than
 //                   1e-10 ||T|| form a cluster whose vectors one thread
 //                   computes in turn, each orthogonalised against the
 //                   previous ones
@@ -424,18 +425,21 @@ __global__ void __launch_bounds__(32) stein_kernel(int m, const double *__restri
     for (int i = 0; i < m - 1; ++i) {
       const double sub = e[i];
       const double dn = d[i + 1] - lam, en = (i + 1 < m - 1) ? e[i + 1] : 0.0;
-      double piv, f, an, bn;
-      if (fabs(ai) >= fabs(sub)) {
-        piv = (ai == 0.0) ? tiny : ai;
-        f = sub / piv;
+      // one division per step: the pivot (raised to eps tnorm in modulus
+      // when smaller) is inverted once and the multiplier formed from it
+      const bool noswap = fabs(ai) >= fabs(sub);
+      double piv = noswap ? ai : sub;
+      if (fabs(piv) < tiny) piv = (piv < 0.0 ? -tiny : tiny);
+      const double r = 1.0 / piv;
+      const double f = (noswap ? sub : ai) * r;
+      double an, bn;
+      if (noswap) {
         V(b, i) = bi;
         V(c2, i) = 0.0;
         V(fl, i) = 0.0;
         an = fma(-f, bi, dn);
         bn = en;
       } else {
-        piv = sub;
-        f = ai / sub;
         V(b, i) = dn;
         V(c2, i) = en;
         V(fl, i) = 1.0;
@@ -443,13 +447,16 @@ __global__ void __launch_bounds__(32) stein_kernel(int m, const double *__restri
         bn = -f * en;
       }
       V(l, i) = f;
-      V(a, i) = 1.0 / ((fabs(piv) < tiny) ? (piv < 0.0 ? -tiny : tiny) : piv);
+      V(a, i) = r;
       ai = an;
       bi = bn;
     }
     V(a, m - 1) = 1.0 / ((fabs(ai) < tiny) ? (ai < 0.0 ? -tiny : tiny) : ai);
     for (int i = 0; i < m; ++i) V(x, i) = unit_rand(kk, i);
-    for (int it = 0; it < 3; ++it) {
+    // two solves reach the backward error for an isolated eigenvalue; a
+    // cluster member, orthogonalised against the earlier ones, gets three
+    const int nit = (kk == k) ? 2 : 3;
+    for (int it = 0; it < nit; ++it) {
       // x <- (T - lam I)^{-1} x
       {
         double xi = V(x, 0);

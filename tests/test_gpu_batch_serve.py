@@ -96,3 +96,60 @@ def test_server_alone_vs_mix_and_budget(gbf):
     assert r.info == -1
     small.close()
     srv.close()
+
+
+def test_batch_full_range_and_worker_counts(gbf):
+    """Config 4's whole size range (n up to 1024): every count exact, and the
+    results bitwise the same for 1, 5 and 12 workers (the worker count only
+    changes what overlaps on the GPU)."""
+    import torch
+
+    ps = W.batched_generalized(count=12, nmin=512, nmax=1024, seed=99)
+    assert max(p.n for p in ps) > 800
+    runs = []
+    for nw in (1, 5, 12):
+        dps = []
+        for p in ps:
+            A = gbf.fortran(torch.from_numpy(p.A).cuda())
+            B = gbf.fortran(torch.from_numpy(p.B).cuda())
+            dps.append(gbf.DeviceProblem(A, B, p.emin, p.emax, p.m0, fpm=p.apply_fpm(gbf.gbf_init())))
+        rc, outs = gbf.batch_solve(dps, nworkers=nw)
+        torch.cuda.synchronize()
+        assert rc == 0
+        for p, dp, r in zip(ps, dps, outs):
+            check_result(p, dp, r)
+        runs.append([(dp.E.cpu().numpy().copy(), dp.X.cpu().numpy().copy()) for dp in dps])
+    for other in runs[1:]:
+        for (e0, x0), (e1, x1) in zip(runs[0], other):
+            assert np.array_equal(e0, e1) and np.array_equal(x0, x1)
+
+
+def test_autotuner_picks_and_applies(gbf, tmp_path):
+    """The autotuner times the batched solve, returns a worker count among
+    its candidates and a width per size bucket, and its table (saved and
+    loaded back) drives batch_solve to exact counts."""
+    import torch
+
+    from paper_1203_4031_gb300 import autotune
+
+    ps = W.batched_generalized(count=8, nmin=64, nmax=400, seed=5)
+
+    def make():
+        out = []
+        for p in ps:
+            A = gbf.fortran(torch.from_numpy(p.A).cuda())
+            B = gbf.fortran(torch.from_numpy(p.B).cuda())
+            out.append(gbf.DeviceProblem(A, B, p.emin, p.emax, p.m0, fpm=p.apply_fpm(gbf.gbf_init())))
+        return out
+
+    entry = autotune.tune(make(), workers=(2, 4), widths=(0, 16), reps=1)
+    assert entry["workers"] in (2, 4)
+    assert set(entry["width"].values()) <= {0, 16}
+    path = autotune.save(autotune.merge([entry], name="test"), str(tmp_path / "tune.json"))
+    table = autotune.load(path)
+    dps = make()
+    rc, outs = autotune.batch_solve(dps, table)
+    torch.cuda.synchronize()
+    assert rc == 0
+    for p, dp, r in zip(ps, dps, outs):
+        check_result(p, dp, r)
