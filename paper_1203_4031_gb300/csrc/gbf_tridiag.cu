@@ -14,12 +14,13 @@
 //   sytrd_cluster   Householder reduction C = Q T_c Q^H to a Hermitian
 //                   tridiagonal T_c (one cluster of up to 16 CTAs; the
 //                   matrix lives in distributed shared memory, rows dealt
-//                   cyclically to the CTAs; four cluster barriers per column)
+//                   cyclically to the CTAs; two cluster barriers per column)
 //   tridiag_prep    T_c = D T D^H with T real symmetric tridiagonal (D a
 //                   diagonal of unit phases), Gershgorin bounds
 //   stebz           every eigenvalue of T by bisection on its Sturm count
 //                   (the sign changes of the characteristic-polynomial
-//                   recurrence, rescaled against overflow), one thread each
+//                   recurrence, rescaled against overflow), one warp each
+//                   (32-point multisection)
 //   stein           eigenvectors of T by inverse iteration (tridiagonal LU
 //                   with partial pivoting of T - lambda I), two steps from
 //                   a fixed pseudo-random start (three in a cluster);
