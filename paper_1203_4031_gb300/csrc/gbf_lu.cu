@@ -195,17 +195,80 @@ __global__ void __launch_bounds__(PANEL_THREADS)
 
 // ------------------------------------------------------- cluster panel --
 // The panel of node e (rows [k, n), columns [k, k+w)) split by rows over the
-// C CTAs of a thread-block cluster, each slice held in shared memory
-// (column-major, R rows).  Per column: local argmax (warp shuffles), the C
-// candidates read over distributed shared memory and reduced identically by
-// every CTA (largest |re|+|im|, lowest row on ties), the pivot row and the
-// displaced row read remotely, a cluster barrier, the swap written locally,
-// then the local scale + rank-1 update.  Two cluster barriers per column.
+// C CTAs of a thread-block cluster, R >= w rows each, so that the diagonal
+// row c = k + j of every column j lies in CTA 0.  The slice sits in shared
+// memory (column-major, ld R) when it fits, else the CTA works on it in
+// place in the matrix (ld n; a few MB per node, L2-resident).
+// One cluster barrier per column:
+//   1. each CTA publishes its best pivot candidate for column j (key, row
+//      index and the row's w entries) and CTA 0 also the current row c, in
+//      the buffer of parity j % 2;
+//   2. cluster barrier;
+//   3. every CTA reads all C candidates and row c over distributed shared
+//      memory (one round of remote loads), warp 0 picks the pivot (largest
+//      |re| + |im|, lowest row on ties; the same choice in every CTA), writes
+//      the swap into the CTA's own rows and forms the pivot's reciprocal;
+//   4. the column below c is scaled, then the rank-1 update runs on all
+//      warps (each thread one row and every G-th column), and the thread
+//      that updates column j + 1 of a row forms that row's next candidate.
+// A buffer of parity j % 2 is rewritten at column j + 2, after every CTA has
+// passed barrier j + 1 and therefore finished its reads of it.
 template <class T>
+struct PanelPub {
+  T row[MAX_NB];   // entries of this CTA's candidate row
+  T diag[MAX_NB];  // CTA 0: the current row c
+  long long key;
+  int idx;
+  int pad;
+};
+
+// Argmax of (key, row) pairs over a warp: the larger key wins, the lower row
+// on ties.  Butterfly, so every lane ends with the result.
+__device__ __forceinline__ void argmax_all(long long &b, int &bi) {
+  for (int off = 16; off > 0; off >>= 1) {
+    const long long ov = __shfl_xor_sync(0xffffffffu, b, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+    if (ov > b || (ov == b && oi < bi)) {
+      b = ov;
+      bi = oi;
+    }
+  }
+}
+
+__device__ __forceinline__ zd shfl_t(zd v, int src) {
+  return zd{__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)};
+}
+__device__ __forceinline__ cf shfl_t(cf v, int src) {
+  return cf{__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)};
+}
+
+// Reciprocal of a nonzero pivot with one division: a is scaled by the power
+// of two f that brings its larger part into [1, 2) (exact), then
+// 1/a = conj(f a) f / |f a|^2 with |f a|^2 in [1, 8).  Zero, subnormal,
+// huge or non-finite pivots take Smith's division.
+__device__ inline zd pivot_recip(zd a) {
+  const double s = fmax(fabs(a.x), fabs(a.y));
+  const long long eb = (__double_as_longlong(s) >> 52) & 0x7FF;
+  if (eb == 0 || eb >= 2046) return zdiv(zd{1.0, 0.0}, a);
+  const double f = __longlong_as_double((2046LL - eb) << 52);
+  const double ax = a.x * f, ay = a.y * f;
+  const double r = f / fma(ax, ax, ay * ay);
+  return zd{ax * r, -ay * r};
+}
+__device__ inline cf pivot_recip(cf a) {
+  const float s = fmaxf(fabsf(a.x), fabsf(a.y));
+  const int eb = (__float_as_int(s) >> 23) & 0xFF;
+  if (eb == 0 || eb >= 254) return cinv<cf>(a);
+  const float f = __int_as_float((254 - eb) << 23);
+  const float ax = a.x * f, ay = a.y * f;
+  const float r = f / fmaf(ax, ax, ay * ay);
+  return cf{ax * r, -ay * r};
+}
+
+template <class T, bool SMEM>
 __global__ void __launch_bounds__(PANEL_THREADS)
-    lu_panel_cluster_kernel(int n, int k, int w, int R, T *S, int *ipiv, int *sing) {
+    lu_panel_cluster_kernel(int n, int k, int w, int R, T *S, int *ipiv, int *sing, T *linv, long lsb, int lld) {
   using X = tr<T>;
-  using Rt = typename X::R;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int q = (int)cl.block_rank();
@@ -213,185 +276,306 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   const long nn = (long)n * n;
   T *a = S + e * nn;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *sl = reinterpret_cast<T *>(smem_raw);  // [w][R]
-  T *urow = sl + (long)w * R;               // pivot row (old row p)
-  T *xrow = urow + MAX_NB;                  // old row c (kept by the owner of p)
-  long long *cval = reinterpret_cast<long long *>(xrow + MAX_NB);
-  int *cidx = reinterpret_cast<int *>(cval + 2);
-  __shared__ long long wv[32];
-  __shared__ int wi[32];
+  const int r0 = k + q * R;
+  const int rows = max(0, min(R, n - r0));
+  unsigned char *sp = smem_raw;
+  T *sl;
+  long ld;
+  if constexpr (SMEM) {
+    sl = reinterpret_cast<T *>(sp);
+    ld = R;
+    sp += (size_t)R * w * sizeof(T);
+  } else {
+    sl = a + r0 + (long)k * n;
+    ld = n;
+  }
+  PanelPub<T> *pub = reinterpret_cast<PanelPub<T> *>(sp);  // [2]
+  sp += 2 * sizeof(PanelPub<T>);
+  T *srow = reinterpret_cast<T *>(sp);  // [C][w] candidate rows of all CTAs
+  sp += (size_t)C * w * sizeof(T);
+  T *sdiag = reinterpret_cast<T *>(sp);  // [w] row c
+  sp += (size_t)MAX_NB * sizeof(T);
+  T *l11 = reinterpret_cast<T *>(sp);  // [32][32] copy of L11 for its inverse
+  sp += (size_t)32 * 32 * sizeof(T);
+  long long *skey = reinterpret_cast<long long *>(sp);  // [C]
+  int *sidx = reinterpret_cast<int *>(skey + 16);       // [C]
+  __shared__ long long wv[PANEL_THREADS / 32];
+  __shared__ int wi[PANEL_THREADS / 32];
   __shared__ T s_inv;
   __shared__ int s_p, s_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const int r0 = k + q * R;
-  const int rows = max(0, min(R, n - r0));
-  for (int t = tid; t < rows * w; t += blockDim.x) {
-    const int rl = t % rows, jj = t / rows;
-    sl[(long)jj * R + rl] = a[(r0 + rl) + (long)(k + jj) * n];
+  // thread (rt, g): rows rt, rt + Rt, ...; columns j+1+g, j+1+g+G, ...
+  const int Rt = min((int)blockDim.x, max(32, (rows + 31) & ~31));
+  const int G = (int)blockDim.x / Rt;
+  const int rt = tid % Rt, g = tid / Rt;
+  if constexpr (SMEM) {
+    for (int t = tid; t < rows * w; t += blockDim.x) {
+      const int rl = t % rows, jj = t / rows;
+      sl[(long)jj * R + rl] = a[(r0 + rl) + (long)(k + jj) * n];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int j = 0; j < w; ++j) {
-    const int c = k + j;
-    // 1. local candidate
-    long long best = -1;
-    int bidx = n;
-    for (int rl = tid; rl < rows; rl += blockDim.x) {
-      const int gr = r0 + rl;
-      if (gr < c) continue;
-      const long long v = pivkey(X::abs1(sl[(long)j * R + rl]));
+  // candidates of column 0 (rows >= k: all of them)
+  long long best = -1;
+  int bidx = n;
+  if (g == 0)
+    for (int rl = rt; rl < rows; rl += Rt) {
+      const long long v = pivkey(X::abs1(sl[rl]));
       if (v > best) {
         best = v;
-        bidx = gr;
+        bidx = r0 + rl;
       }
     }
-    for (int off = 16; off > 0; off >>= 1) {
-      const long long ov = __shfl_down_sync(0xffffffffu, best, off);
-      const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
-      if (ov > best || (ov == best && oi < bidx)) {
-        best = ov;
-        bidx = oi;
-      }
-    }
+  for (int j = 0; j < w; ++j) {
+    const int c = k + j, par = j & 1;
+    // 1. this CTA's candidate, published with its row (and row c by CTA 0)
+    argmax_all(best, bidx);
     if (lane == 0) {
       wv[warp] = best;
       wi[warp] = bidx;
     }
     __syncthreads();
-    if (tid == 0) {
-      long long b = -1;
-      int bi = n;
-      for (int w2 = 0; w2 < nwarps; ++w2)
-        if (wv[w2] > b || (wv[w2] == b && wi[w2] < bi)) {
-          b = wv[w2];
-          bi = wi[w2];
-        }
-      cval[0] = b;
-      cidx[0] = bi;
-    }
-    cl.sync();  // (A) candidates visible; previous column's updates complete
-    // 2. cluster argmax (every CTA reduces the same list in the same order)
     if (warp == 0) {
-      long long b = -1;
-      int bi = n;
-      if (lane < C) {
-        b = *cl.map_shared_rank(cval, lane);
-        bi = *cl.map_shared_rank(cidx, lane);
+      long long b = lane < nwarps ? wv[lane] : -1;
+      int bi = lane < nwarps ? wi[lane] : n;
+      argmax_all(b, bi);
+      if (lane == 0) {
+        pub[par].key = b;
+        pub[par].idx = bi;
       }
-      for (int off = 16; off > 0; off >>= 1) {
-        const long long ov = __shfl_down_sync(0xffffffffu, b, off);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-        if (ov > b || (ov == b && oi < bi)) {
-          b = ov;
-          bi = oi;
+      const int lr = (b > 0 && bi < n) ? bi - r0 : -1;
+      for (int jj = lane; jj < w; jj += 32) {
+        if (lr >= 0) pub[par].row[jj] = sl[(long)jj * ld + lr];
+        if (q == 0) pub[par].diag[jj] = sl[(long)jj * ld + j];
+      }
+    }
+    cl.sync();  // every candidate of column j published; column j-1 done everywhere
+    // 2. all candidates and row c, one round of remote loads
+    const int nload = C * w + C + w;
+    for (int t = tid; t < nload; t += blockDim.x) {
+      if (t < C * w) {
+        srow[t] = cl.map_shared_rank(pub + par, t / w)->row[t % w];
+      } else if (t < C * w + C) {
+        const PanelPub<T> *rp = cl.map_shared_rank(pub + par, t - C * w);
+        skey[t - C * w] = rp->key;
+        sidx[t - C * w] = rp->idx;
+      } else {
+        sdiag[t - C * w - C] = cl.map_shared_rank(pub + par, 0)->diag[t - C * w - C];
+      }
+    }
+    __syncthreads();
+    // 3. pivot, swap of this CTA's rows, reciprocal (warp 0)
+    if (warp == 0) {
+      long long b = lane < C ? skey[lane] : -1;
+      int bi = lane < C ? sidx[lane] : n;
+      argmax_all(b, bi);
+      const int ok = (b > 0) && (bi < n);
+      const int p = ok ? bi : c;
+      const int qp = (p - k) / R;
+      const T *urow = srow + (long)qp * w;
+      if (ok && p != c)
+        for (int jj = lane; jj < w; jj += 32) {
+          if (q == 0) sl[(long)jj * ld + j] = urow[jj];
+          if (q == qp) sl[(long)jj * ld + (p - r0)] = sdiag[jj];
+        }
+      if (lane == 0) {
+        s_p = p;
+        s_ok = ok;
+        if (ok) s_inv = pivot_recip(urow[j]);
+        if (q == 0) {
+          ipiv[(long)e * n + c] = p;
+          if (!ok && sing[e] == 0) sing[e] = c + 1;
         }
       }
-      if (lane == 0) {
-        const int ok = (b > 0) && (bi < n);
-        s_ok = ok;
-        s_p = ok ? bi : c;
-      }
     }
     __syncthreads();
-    const int p = s_p, ok = s_ok;
-    const int qc = (c - k) / R, lc = (c - k) % R;
-    const int qp = (p - k) / R, lp = (p - k) % R;
-    // 3. remote reads of the old rows p and c
-    if (ok && tid < w) {
-      urow[tid] = cl.map_shared_rank(sl, qp)[(long)tid * R + lp];
-      if (q == qp && p != c) xrow[tid] = cl.map_shared_rank(sl, qc)[(long)tid * R + lc];
-    }
-    cl.sync();  // (B) every read done before any write
-    // 4. swap (local writes)
-    if (ok && p != c && tid < w) {
-      if (q == qc) sl[(long)tid * R + lc] = urow[tid];
-      if (q == qp) sl[(long)tid * R + lp] = xrow[tid];
-    }
-    if (q == 0 && tid == 0) {
-      ipiv[(long)e * n + c] = ok ? p : c;
-      if (!ok && sing[e] == 0) sing[e] = c + 1;
-    }
-    // the pivot's reciprocal, formed once per CTA (a complex division is
-    // several FP64 divisions; every thread forming it cost more than the
-    // rank-1 update)
-    if (tid == 32 && ok) s_inv = cinv<T>(urow[j]);
-    __syncthreads();
-    // 5. scale and rank-1 update of the local rows below c
-    if (ok) {
+    const int ok = s_ok;
+    const T *urow = srow + (long)((s_p - k) / R) * w;
+    // 4a. scale the column below c
+    if (ok && g == 0) {
       const T inv = s_inv;
-      for (int rl = tid; rl < rows; rl += blockDim.x) {
-        if (r0 + rl <= c) continue;
-        const T l = X::mul(sl[(long)j * R + rl], inv);
-        sl[(long)j * R + rl] = l;
-        for (int jj = j + 1; jj < w; ++jj) sl[(long)jj * R + rl] = X::fma(l, X::neg(urow[jj]), sl[(long)jj * R + rl]);
-      }
+      for (int rl = rt; rl < rows; rl += Rt)
+        if (r0 + rl > c) sl[(long)j * ld + rl] = X::mul(sl[(long)j * ld + rl], inv);
     }
     __syncthreads();
+    // 4b. rank-1 update; column j+1's candidates from the updated entries
+    best = -1;
+    bidx = n;
+    if (g < G && j + 1 < w) {
+      for (int rl = rt; rl < rows; rl += Rt) {
+        const int gr = r0 + rl;
+        if (gr <= c) continue;
+        int jj = j + 1 + g;
+        if (ok) {
+          const T l = sl[(long)j * ld + rl];
+          if (g == 0) {
+            const T v = X::fma(l, X::neg(urow[jj]), sl[(long)jj * ld + rl]);
+            sl[(long)jj * ld + rl] = v;
+            const long long kv = pivkey(X::abs1(v));
+            if (kv > best) {
+              best = kv;
+              bidx = gr;
+            }
+            jj += G;
+          }
+          for (; jj < w; jj += G) sl[(long)jj * ld + rl] = X::fma(l, X::neg(urow[jj]), sl[(long)jj * ld + rl]);
+        } else if (g == 0) {
+          const long long kv = pivkey(X::abs1(sl[(long)jj * ld + rl]));
+          if (kv > best) {
+            best = kv;
+            bidx = gr;
+          }
+        }
+      }
+    }
   }
-  for (int t = tid; t < rows * w; t += blockDim.x) {
-    const int rl = t % rows, jj = t / rows;
-    a[(r0 + rl) + (long)(k + jj) * n] = sl[(long)jj * R + rl];
+  __syncthreads();
+  if (linv) {
+    // L11^{-1} (unit lower, w x w, ld lld), the columns dealt to the warps
+    // of all CTAs: column j by warp j / C of CTA j % C, lane i holding entry
+    // i, forward substitution with the column of L11 broadcast per step
+    cl.sync();  // rows k .. k+w-1 final in CTA 0
+    for (int t = tid; t < w * w; t += blockDim.x) {
+      const int i = t % w, l = t / w;
+      T v;
+      if constexpr (SMEM)
+        v = (q == 0) ? sl[(long)l * R + i] : cl.map_shared_rank(sl, 0)[(long)l * R + i];
+      else
+        v = a[(k + i) + (long)(k + l) * n];
+      l11[i + l * 32] = v;
+    }
+    __syncthreads();
+    T *li = linv + (long)e * lsb;
+    for (int j = q + C * warp; j < w; j += C * nwarps) {
+      T x = lane == j ? X::one() : X::zero();
+      for (int l = j; l < w - 1; ++l) {
+        const T xl = shfl_t(x, l);
+        if (lane > l && lane < w) x = X::fma(l11[l * 32 + lane], X::neg(xl), x);
+      }
+      if (lane < w) li[lane + (long)j * lld] = x;
+    }
   }
-  cl.sync();  // no CTA leaves while another may still read its slice
+  if constexpr (SMEM)
+    for (int t = tid; t < rows * w; t += blockDim.x) {
+      const int rl = t % rows, jj = t / rows;
+      a[(r0 + rl) + (long)(k + jj) * n] = sl[(long)jj * R + rl];
+    }
+  cl.sync();  // no CTA leaves while another may still read its buffers
 }
 
-// Launch the cluster panel: C CTAs (power of two <= 16) so that each slice
-// fits in shared memory.  Returns 1 when the caller should use the
-// single-CTA panel instead (no suitable cluster shape).
+// Dynamic shared memory of the cluster panel for C CTAs of R rows.
 template <class T>
-static int launch_cluster_panel(cudaStream_t st, int n, int ne, int k, int w, T *S, int *ipiv, int *sing) {
+static size_t panel_smem(int R, int w, int C, bool slice_in_smem) {
+  return (slice_in_smem ? (size_t)R * w * sizeof(T) : 0) + 2 * sizeof(PanelPub<T>) + (size_t)C * w * sizeof(T) +
+         MAX_NB * sizeof(T) + 32 * 32 * sizeof(T) + 16 * (sizeof(long long) + sizeof(int));
+}
+
+// Clusters of C CTAs with `smem` bytes of dynamic shared memory each that
+// the device runs at once (queried once per device, C and 16 KB bucket).
+template <class T>
+static int panel_clusters(int C, size_t smem) {
+  static std::atomic<int> cache[16][5][14];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int lc = 0;
+  while ((1 << lc) < C) ++lc;
+  const int sb = (int)((smem + 16383) / 16384);
+  if (dev >= 16 || lc > 4 || sb > 13) return 0;
+  int v = cache[dev][lc][sb].load(std::memory_order_relaxed);
+  if (v != 0) return v - 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, 1, 1);
+  cfg.blockDim = dim3(PANEL_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)sb * 16384;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, lu_panel_cluster_kernel<T, true>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    nc = 0;
+  }
+  cache[dev][lc][sb].store(nc + 1, std::memory_order_relaxed);
+  return nc;
+}
+
+// Launch the cluster panel.  C (a power of two <= 16, R = ceil((n-k)/C) >= w
+// rows per CTA) minimises waves x (R + 64): the FP64 rank-1 work of a CTA
+// grows with R, and the per-column barrier and remote-load latency costs
+// about as much as 64 rows; waves = ceil(ne / clusters the device runs at
+// once).  The slice goes to shared memory when it fits, else the CTAs work
+// in place.  With linv, the kernel also writes L11^{-1} of every node there
+// (ld lld, node stride lsb).  Returns 1 when the caller should use the
+// single-CTA panel
+// instead (no cluster shape can run).
+template <class T>
+static int launch_cluster_panel(cudaStream_t st, int n, int ne, int k, int w, T *S, int *ipiv, int *sing, T *linv,
+                                long lsb, int lld) {
   const int rowsp = n - k;
   const size_t cap = 200 * 1024;
   static std::atomic<unsigned long long> attr_done{0};
   once_per_device(attr_done, [&]() -> int {
-    cudaFuncSetAttribute(lu_panel_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    cudaFuncSetAttribute(lu_panel_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(lu_panel_cluster_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(lu_panel_cluster_kernel<T, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(lu_panel_cluster_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(lu_panel_cluster_kernel<T, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaGetLastError();
     return 0;
   });
-  int C0 = 1;
-  while (C0 < 16 && C0 * 256 < rowsp) C0 *= 2;
-  // largest C first (more SMs per panel), smaller clusters when the GPU
-  // cannot co-schedule it; every candidate must fit the shared memory cap
-  for (int C = C0; C >= 1; C /= 2) {
+  int bestC = 0;
+  double best_cost = 0.0;
+  for (int C = 1; C <= 16; C *= 2) {
     const int R = ceil_div(rowsp, C);
-    const size_t smem = (size_t)R * w * sizeof(T) + 2 * MAX_NB * sizeof(T) + 64;
-    if (smem > cap) break;  // smaller C only makes the slice larger
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(C, ne, 1);
-    cfg.blockDim = dim3(PANEL_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, lu_panel_cluster_kernel<T>, &cfg) != cudaSuccess ||
-        nclusters < 1) {
-      cudaGetLastError();
-      continue;
+    if (C > 1 && R < w) break;
+    const size_t sm = panel_smem<T>(R, w, C, true);
+    const int nc = panel_clusters<T>(C, sm <= cap ? sm : panel_smem<T>(R, w, C, false));
+    if (nc < 1) continue;
+    const double cost = (double)ceil_div(ne, nc) * (R + 64);
+    if (bestC == 0 || cost < best_cost) {
+      bestC = C;
+      best_cost = cost;
     }
-    if (cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<T>, n, k, w, R, S, ipiv, sing) != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
-    GBF_LAUNCHED();
-    return 0;
   }
-  return 1;
+  if (bestC == 0) return 1;
+  const int C = bestC, R = ceil_div(rowsp, C);
+  const bool in_smem = panel_smem<T>(R, w, C, true) <= cap;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, ne, 1);
+  cfg.blockDim = dim3(PANEL_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = panel_smem<T>(R, w, C, in_smem);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t rc =
+      in_smem ? cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<T, true>, n, k, w, R, S, ipiv, sing, linv, lsb, lld)
+              : cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<T, false>, n, k, w, R, S, ipiv, sing, linv, lsb, lld);
+  if (rc != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  GBF_LAUNCHED();
+  return 0;
 }
 
 // --------------------------------------------------------- laswp + trsm --
 // Columns outside the panel: apply the panel's row swaps; columns right of
 // the panel additionally get U12 = L11^{-1} A12 (unit lower forward solve).
+// One thread per column.
 constexpr int SWAP_COLS = 64;
 
+// Panels of more than 32 columns: the swaps one after another.
 template <class T>
 __global__ void __launch_bounds__(SWAP_COLS)
-    laswp_trsm_kernel(int n, int k, int w, T *S, const int *ipiv) {
+    laswp_trsm_wide_kernel(int n, int k, int w, T *S, const int *ipiv) {
   using X = tr<T>;
   const int e = blockIdx.y;
   const long nn = (long)n * n;
@@ -427,6 +611,102 @@ __global__ void __launch_bounds__(SWAP_COLS)
     for (int ii = jj + 1; ii < w; ++ii) x[ii] = X::fma(L[ii + jj * w], X::neg(xj), x[ii]);
   }
   for (int jj = 0; jj < w; ++jj) cj[k + jj] = x[jj];
+}
+
+// Panels of at most 32 columns.  Warp 0 first turns the swap sequence (row
+// k+jj with ipiv[k+jj], jj = 0..w-1) into the rows' final sources: panel row
+// k+jj receives original row srcp[jj], and each row below the panel that was
+// chosen as a pivot receives an original panel row.  (A row chosen at step
+// jj hands its contents to panel row k+jj, which no later step touches, so
+// rows below the panel only ever receive panel rows.)  Every thread then
+// reads all its sources before it writes anything: independent loads instead
+// of a chain of dependent swaps.  The solve (trsm != 0; otherwise U12 is
+// formed afterwards by a product with L11^{-1}) keeps the 32 entries in
+// registers.
+template <class T>
+__global__ void __launch_bounds__(SWAP_COLS)
+    laswp_trsm_kernel(int n, int k, int w, T *S, const int *ipiv, int trsm) {
+  using X = tr<T>;
+  const int e = blockIdx.y;
+  const long nn = (long)n * n;
+  T *a = S + e * nn;
+  const int *piv = ipiv + (long)e * n + k;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *L = reinterpret_cast<T *>(smem_raw);         // [w][w]
+  int *srcp = reinterpret_cast<int *>(L + w * w);  // [32] source of panel row k + jj
+  int *orow = srcp + 32;                           // [32] rows below the panel that receive ...
+  int *osrc = orow + 32;                           // [32] ... this original panel row
+  __shared__ int s_nout;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid < 32) {
+    const unsigned FULL = 0xffffffffu;
+    const int pv = lane < w ? piv[lane] : -1;
+    int cont = k + lane, bef = k + lane;  // lane jj: contents of row k+jj now / before step jj
+    for (int jj = 0; jj < w; ++jj) {
+      const int P = __shfl_sync(FULL, pv, jj);
+      const int cj = __shfl_sync(FULL, cont, jj);
+      if (lane == jj) bef = cj;
+      if (P == k + jj) continue;
+      if (P < k + w) {  // swap inside the panel
+        const int cp = __shfl_sync(FULL, cont, P - k);
+        if (lane == jj) cont = cp;
+        if (lane == P - k) cont = cj;
+      } else {  // row P holds what it received at its last earlier step, else itself
+        const unsigned m = __ballot_sync(FULL, lane < jj && pv == P);
+        const int v = __shfl_sync(FULL, bef, m ? 31 - __clz((int)m) : 0);
+        if (lane == jj) cont = m ? v : P;
+      }
+    }
+    if (lane < w) srcp[lane] = cont;
+    const bool below = lane < w && pv >= k + w;
+    const unsigned grp = __match_any_sync(FULL, below ? pv : -1 - lane);
+    const bool last = below && 31 - __clz((int)grp) == lane;  // the row's last step
+    const unsigned lm = __ballot_sync(FULL, last);
+    if (last) {
+      const int slot = __popc(lm & ((1u << lane) - 1u));
+      orow[slot] = pv;
+      osrc[slot] = bef;
+    }
+    if (lane == 0) s_nout = __popc(lm);
+  }
+  if (trsm)
+    for (int t = tid; t < w * w; t += blockDim.x) {
+      const int ii = t % w, jj = t / w;
+      L[ii + jj * w] = a[(k + ii) + (long)(k + jj) * n];
+    }
+  __syncthreads();
+  const int idx = blockIdx.x * SWAP_COLS + tid;
+  if (idx >= n - w) return;
+  const int col = idx < k ? idx : idx + w;
+  T *cj = a + (long)col * n;
+  const int nout = s_nout;
+  T x[32];
+#pragma unroll
+  for (int jj = 0; jj < 32; ++jj)
+    if (jj < w) x[jj] = cj[srcp[jj]];
+  for (int i0 = 0; i0 < nout; i0 += 8) {
+    T v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (i0 + i < nout) v[i] = cj[osrc[i0 + i]];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (i0 + i < nout) cj[orow[i0 + i]] = v[i];
+  }
+  if (trsm && col >= k + w) {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      if (jj < w) {
+        const T xj = X::neg(x[jj]);
+#pragma unroll
+        for (int ii = jj + 1; ii < 32; ++ii)
+          if (ii < w) x[ii] = X::fma(L[ii + jj * w], xj, x[ii]);
+      }
+    }
+  }
+#pragma unroll
+  for (int jj = 0; jj < 32; ++jj)
+    if (jj < w) cj[k + jj] = x[jj];
 }
 
 // -------------------------------------------------------- permutation --
@@ -563,13 +843,24 @@ int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T 
   const long nn = (long)n * n;
   T m1 = X::zero();
   m1 = X::sub(m1, X::one());
+  // U12 = L11^{-1} A12 as a product on the engine of the trailing updates,
+  // with L11^{-1} formed by the cluster panel straight into its block of
+  // Linv (the inverted diagonal blocks the solves use; rows k .. k+w-1 are
+  // final once their panel is done), when the blocks are the panel's width
+  const int nblk = ceil_div(n, bs);
+  const long sblk = (long)nblk * bs * bs;
+  const bool inv_trsm = (nb == bs && bs <= 32);
+  bool linv_ready = false;  // set by the panel of the step being processed
   auto panel = [&](cudaStream_t s, int k) {
     const int w = std::min(nb, n - k);
     CatScope cat_panel(CAT_LU_PANEL);
     const int slot = prof_begin(s);
-    if (launch_cluster_panel<T>(s, n, ne, k, w, S, ipiv, sing)) {
+    T *li = inv_trsm ? Linv + (long)(k / bs) * bs * bs : nullptr;
+    linv_ready = inv_trsm;
+    if (launch_cluster_panel<T>(s, n, ne, k, w, S, ipiv, sing, li, sblk, bs)) {
       lu_panel_kernel<T><<<ne, PANEL_THREADS, 0, s>>>(n, k, w, S, ipiv, sing);
       GBF_LAUNCHED();
+      linv_ready = false;
     }
     prof_end(s, slot, 0.0);
   };
@@ -592,17 +883,28 @@ int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T 
       CatScope cat_swap(CAT_LU_SWAP);
       const int slot2 = prof_begin(st);
       dim3 g(ceil_div(n - w, SWAP_COLS), ne);
-      const size_t sm = (size_t)w * w * sizeof(T) + (size_t)w * sizeof(int);
       static std::atomic<unsigned long long> attr_set{0};
       if (int rc = once_per_device(attr_set, [&]() -> int {
-            GBF_CUDA(cudaFuncSetAttribute(laswp_trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            GBF_CUDA(cudaFuncSetAttribute(laswp_trsm_wide_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)(MAX_NB * MAX_NB * sizeof(T) + MAX_NB * sizeof(int))));
             return 0;
           }))
         return rc;
-      laswp_trsm_kernel<T><<<g, SWAP_COLS, sm, st>>>(n, k, w, S, ipiv);
+      const bool by_inverse = linv_ready && w <= 32 && n - k - w > 0;
+      if (w <= 32)
+        laswp_trsm_kernel<T><<<g, SWAP_COLS, (size_t)w * w * sizeof(T) + 96 * sizeof(int), st>>>(
+            n, k, w, S, ipiv, by_inverse ? 0 : 1);
+      else
+        laswp_trsm_wide_kernel<T><<<g, SWAP_COLS, (size_t)w * w * sizeof(T) + (size_t)w * sizeof(int), st>>>(
+            n, k, w, S, ipiv);
       GBF_LAUNCHED();
       prof_end(st, slot2, 0.0);
+      if (by_inverse) {  // the product times itself, in the same category
+        T *A12 = S + k + (long)(k + w) * n;
+        if (int rc = gemm<T>(st, 'N', 'N', w, n - k - w, w, X::one(), Linv + (long)(k / bs) * bs * bs, bs, sblk, A12,
+                             n, nn, X::zero(), A12, n, nn, ne))
+          return rc;
+      }
     }
     const int kn = k + w;  // next panel
     if (kn >= n) break;
@@ -623,7 +925,6 @@ int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T 
   }
   perm_from_ipiv_kernel<<<ne, 256, 0, st>>>(n, ipiv, perm);
   GBF_LAUNCHED();
-  const int nblk = ceil_div(n, bs);
   dim3 g(nblk, ne);
   tri_inverse_kernel<T><<<g, bs, 0, st>>>(n, bs, nblk, S, Linv, Uinv);
   GBF_LAUNCHED();
@@ -655,6 +956,148 @@ size_t solve_kwork_bytes_cf(int n, int nrhs, int bs, int ne) {
   const int nblk = ceil_div(n, bs);
   const int half = std::min(n, (nblk - nblk / 2) * bs);
   return cgemm_tf32k_work(half, nrhs, half, std::min(ne, 8));
+}
+
+// Leaf of the recursive solves with FP32 factors: up to four 32-row blocks
+// [b0, b0 + nb) of one triangular sweep in one launch, with the same
+// operations as the blocked sweep (multiply by the inverted diagonal block,
+// then subtract its product from the blocks still to be solved), on the CUDA
+// cores in FP32.  One CTA per (16-column slab of Y, node): the slab's rows
+// and every factor block the leaf needs (at most 4 inverted diagonal blocks
+// and 6 off-diagonal blocks, as op(block) rows, stride 33) are staged in
+// shared memory once.  Thread (ry, cx) owns rows ry and ry + 16 of a block,
+// column cx of the slab.  Rows past n are zero (the inverted blocks are
+// identity-padded there).
+constexpr int LEAF_NC = 16, LEAF_THREADS = 256, LEAF_LD = 33;
+constexpr size_t LEAF_SMEM = (size_t)128 * LEAF_NC * sizeof(cf) + (size_t)10 * 32 * LEAF_LD * sizeof(cf);
+
+__global__ void __launch_bounds__(LEAF_THREADS)
+    trsv_leaf_kernel(int kind, int n, int nrhs, int b0, int nb, const cf *__restrict__ S, const cf *__restrict__ Dinv,
+                     long sblk, cf *Y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cf *ys = reinterpret_cast<cf *>(smem_raw);  // [128][LEAF_NC]
+  cf *fb = ys + 128 * LEAF_NC;               // blocks [slot][32][LEAF_LD]
+  const int e = blockIdx.y, c0 = blockIdx.x * LEAF_NC;
+  const long nn = (long)n * n;
+  const cf *Se = S + e * nn;
+  const cf *De = Dinv + e * sblk;
+  cf *Ye = Y + e * (long)n * nrhs;
+  const int r0 = b0 * 32, tid = threadIdx.x;
+  const bool fwd = (kind == 0 || kind == 2), herm = kind >= 2;
+  // slot of the block that updates block d from block s (s solved first):
+  // the (s, d) pairs in solve order, at most 6
+  auto pair_slot = [&](int s2, int d2) {
+    // position of s in solve order, then d among the later blocks
+    const int ps = fwd ? s2 : nb - 1 - s2, pd = fwd ? d2 - s2 - 1 : s2 - d2 - 1;
+    int base = 0;
+    for (int i = 0; i < ps; ++i) base += nb - 1 - i;
+    return 4 + base + pd;
+  };
+  // 1. stage Y and the factor blocks
+  for (int t = tid; t < 128 * LEAF_NC; t += LEAF_THREADS) {
+    const int r = t % 128, c = t / 128;
+    const int gr = r0 + r, gc = c0 + c;
+    ys[r * LEAF_NC + c] = (r < nb * 32 && gr < n && gc < nrhs) ? Ye[gr + (long)gc * n] : cf{0.f, 0.f};
+  }
+  for (int d = 0; d < nb; ++d) {
+    const cf *D = De + (long)(b0 + d) * 32 * 32;
+    cf *dst = fb + d * 32 * LEAF_LD;
+    for (int t = tid; t < 32 * 32; t += LEAF_THREADS) {
+      const int i = t % 32, j = t / 32;  // element (i, j) of the stored block
+      const cf v = D[i + j * 32];
+      if (herm)
+        dst[j * LEAF_LD + i] = cf{v.x, -v.y};
+      else
+        dst[i * LEAF_LD + j] = v;
+    }
+  }
+  for (int s2 = 0; s2 < nb; ++s2)
+    for (int d2 = 0; d2 < nb; ++d2) {
+      if (fwd ? d2 <= s2 : d2 >= s2) continue;
+      cf *dst = fb + pair_slot(s2, d2) * 32 * LEAF_LD;
+      // op(A)[r][l]: r a row of block d2, l a row of block s2
+      //   kind 0/1: A = S[rows of d2, cols of s2]          (op N)
+      //   kind 2/3: A = S[rows of s2, cols of d2]^H        (op C)
+      const int rd = r0 + d2 * 32, rs = r0 + s2 * 32;
+      for (int t = tid; t < 32 * 32; t += LEAF_THREADS) {
+        const int i = t % 32, j = t / 32;  // element (i, j) of the stored block, i fastest
+        if (!herm) {
+          const int gr = rd + i, gc = rs + j;
+          dst[i * LEAF_LD + j] = (gr < n && gc < n) ? Se[gr + (long)gc * n] : cf{0.f, 0.f};
+        } else {
+          const int gr = rs + i, gc = rd + j;
+          const cf v = (gr < n && gc < n) ? Se[gr + (long)gc * n] : cf{0.f, 0.f};
+          dst[j * LEAF_LD + i] = cf{v.x, -v.y};
+        }
+      }
+    }
+  __syncthreads();
+  // 2. the sweep
+  const int ry = tid / LEAF_NC, cx = tid % LEAF_NC;
+  for (int step = 0; step < nb; ++step) {
+    const int s2 = fwd ? step : nb - 1 - step;
+    // y_s <- op(Dinv_s) y_s
+    {
+      const cf *A = fb + s2 * 32 * LEAF_LD;
+      const cf *yb = ys + s2 * 32 * LEAF_NC;
+      float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f;
+#pragma unroll 8
+      for (int l = 0; l < 32; ++l) {
+        const cf y = yb[l * LEAF_NC + cx];
+        const cf p = A[ry * LEAF_LD + l], q = A[(ry + 16) * LEAF_LD + l];
+        a0r = fmaf(p.x, y.x, fmaf(-p.y, y.y, a0r));
+        a0i = fmaf(p.x, y.y, fmaf(p.y, y.x, a0i));
+        a1r = fmaf(q.x, y.x, fmaf(-q.y, y.y, a1r));
+        a1i = fmaf(q.x, y.y, fmaf(q.y, y.x, a1i));
+      }
+      __syncthreads();
+      ys[(s2 * 32 + ry) * LEAF_NC + cx] = cf{a0r, a0i};
+      ys[(s2 * 32 + ry + 16) * LEAF_NC + cx] = cf{a1r, a1i};
+      __syncthreads();
+    }
+    // y_d -= op(A_ds) y_s for the blocks d solved later
+    for (int d2 = 0; d2 < nb; ++d2) {
+      if (fwd ? d2 <= s2 : d2 >= s2) continue;
+      const cf *A = fb + pair_slot(s2, d2) * 32 * LEAF_LD;
+      const cf *yb = ys + s2 * 32 * LEAF_NC;
+      float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f;
+#pragma unroll 8
+      for (int l = 0; l < 32; ++l) {
+        const cf y = yb[l * LEAF_NC + cx];
+        const cf p = A[ry * LEAF_LD + l], q = A[(ry + 16) * LEAF_LD + l];
+        a0r = fmaf(p.x, y.x, fmaf(-p.y, y.y, a0r));
+        a0i = fmaf(p.x, y.y, fmaf(p.y, y.x, a0i));
+        a1r = fmaf(q.x, y.x, fmaf(-q.y, y.y, a1r));
+        a1i = fmaf(q.x, y.y, fmaf(q.y, y.x, a1i));
+      }
+      cf *o0 = ys + (d2 * 32 + ry) * LEAF_NC + cx, *o1 = ys + (d2 * 32 + ry + 16) * LEAF_NC + cx;
+      *o0 = cf{o0->x - a0r, o0->y - a0i};
+      *o1 = cf{o1->x - a1r, o1->y - a1i};
+    }
+    __syncthreads();
+  }
+  // 3. write back
+  for (int t = tid; t < 128 * LEAF_NC; t += LEAF_THREADS) {
+    const int r = t % 128, c = t / 128;
+    const int gr = r0 + r, gc = c0 + c;
+    if (r < nb * 32 && gr < n && gc < nrhs) Ye[gr + (long)gc * n] = ys[r * LEAF_NC + c];
+  }
+}
+
+static int trsv_leaf(cudaStream_t st, int kind, int n, int ne, int nrhs, const cf *S, const cf *Dinv, cf *Y, int b0,
+                     int nb) {
+  static std::atomic<unsigned long long> attr_done{0};
+  if (int rc = once_per_device(attr_done, [&]() -> int {
+        GBF_CUDA(cudaFuncSetAttribute(trsv_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM));
+        return 0;
+      }))
+    return rc;
+  const long sblk = (long)ceil_div(n, 32) * 32 * 32;
+  trsv_leaf_kernel<<<dim3(ceil_div(nrhs, LEAF_NC), ne), LEAF_THREADS, LEAF_SMEM, st>>>(kind, n, nrhs, b0, nb, S,
+                                                                                       Dinv, sblk, Y);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
 }
 
 // C[e] -= op(A[e]) Y[e] for all nodes e with the any-k 3xTF32 GEMM (FP32
@@ -701,6 +1144,9 @@ static int trsv_rec(cudaStream_t st, int kind, int n, int ne, int nrhs, const T 
   using X = tr<T>;
   const long nn = (long)n * n, ny = (long)n * nrhs, sblk = (long)ceil_div(n, bs) * bs * bs;
   const T one = X::one(), zero = X::zero(), m1 = X::sub(X::zero(), X::one());
+  if constexpr (std::is_same<T, cf>::value) {
+    if (b1 - b0 <= 4 && bs == 32 && g_tc && g_tc->kwork) return trsv_leaf(st, kind, n, ne, nrhs, S, Dinv, Y, b0, b1 - b0);
+  }
   if (b1 - b0 == 1) {
     const int r0 = b0 * bs, bsz = std::min(bs, n - r0);
     return gemm<T>(st, kind >= 2 ? 'C' : 'N', 'N', bsz, nrhs, bsz, one, Dinv + (long)b0 * bs * bs, bs, sblk,
