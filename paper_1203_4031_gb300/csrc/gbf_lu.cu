@@ -843,13 +843,15 @@ int getrf_batched(cudaStream_t st, int n, int ne, T *S, int *ipiv, int *perm, T 
   const long nn = (long)n * n;
   T m1 = X::zero();
   m1 = X::sub(m1, X::one());
-  // U12 = L11^{-1} A12 as a product on the engine of the trailing updates,
-  // with L11^{-1} formed by the cluster panel straight into its block of
-  // Linv (the inverted diagonal blocks the solves use; rows k .. k+w-1 are
-  // final once their panel is done), when the blocks are the panel's width
+  // FP64 factors: U12 = L11^{-1} A12 as a product on the engine of the
+  // trailing updates, with L11^{-1} formed by the cluster panel straight into
+  // its block of Linv (the inverted diagonal blocks the solves use; rows
+  // k .. k+w-1 are final once their panel is done), when the blocks are the
+  // panel's width.  (FP32 factors: the substitution in the swap kernel costs
+  // less than the extra launches.)
   const int nblk = ceil_div(n, bs);
   const long sblk = (long)nblk * bs * bs;
-  const bool inv_trsm = (nb == bs && bs <= 32);
+  const bool inv_trsm = std::is_same<T, zd>::value && nb == bs && bs <= 32;
   bool linv_ready = false;  // set by the panel of the step being processed
   auto panel = [&](cudaStream_t s, int k) {
     const int w = std::min(nb, n - k);

@@ -127,6 +127,30 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sm_u32(bar))
                : "memory");
 }
+// The same arrival on the barrier at this offset in every CTA of `mask`.
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
+                   "r"(sm_u32(bar)), "h"(mask)
+               : "memory");
+}
+// Tiled load written to the same shared-memory offset of every CTA of
+// `mask`, each CTA's barrier at `bar`'s offset receiving the bytes.
+__device__ __forceinline__ void tma_load_3d_mc(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                               int c2, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster [%0], "
+      "[%1, {%3, %4, %5}], [%2], %6;" ::"r"(sm_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(sm_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 
 // Epilogue mode 0: C = acc (FP32).  Mode 1: C64 += scale * acc (FP64).
 template <int MODE>
@@ -1995,7 +2019,14 @@ __device__ __forceinline__ void add_chunk(unsigned long long *hi, unsigned long 
 // 32 columns) runs over all nkc K chunks.  Counters per CTA: h = chunks
 // processed (B ring stage h % KNB, accumulator buffer h % 2), h*SK + t =
 // A slices processed (A ring stage (h*SK+t) % KNA).
-template <class T, bool BETA>
+// MC: CTA pairs (clusters of 2) take the two column tiles 2p, 2p+1 of an
+// item p; they stream the same A chunks, so each A slice is loaded once for
+// both, by the CTA of rank t % 2, multicast into both CTAs' rings; a ring
+// stage is free again when both CTAs' MMAs are done with it (each MMA
+// thread's commit arrives in both CTAs).  A tile past the last column runs
+// like the others and stores nothing.  Halves the A traffic into the SMs,
+// the limit of this kernel at 32 columns per tile.
+template <class T, bool BETA, bool MC>
 __global__ void __launch_bounds__(KTHREADS, 1)
     gemm_sliced_k_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int R,
                          int n, int batch, int nkc, int nch, int tpc, const int *__restrict__ sexp,
@@ -2015,11 +2046,24 @@ __global__ void __launch_bounds__(KTHREADS, 1)
   const int nrb = (R + BM - 1) / BM, nct = (n + KBN - 1) / KBN;
   const int items = nch * nrb * batch;
   constexpr uint32_t NCOLS = 2 * K_ACC;  // 512
+  const int crank = MC ? (int)cluster_rank() : 0;
+  const int cid = MC ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int ncl = MC ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  // this CTA's column tiles of item chunk cc
+  auto tiles = [&](int cc, int &t0, int &t1) {
+    if (MC) {
+      t0 = 2 * cc + crank;
+      t1 = t0 + 1;
+    } else {
+      t0 = cc * tpc;
+      t1 = min(nct, (cc + 1) * tpc);
+    }
+  };
 
   if (threadIdx.x == 0) {
     for (int j = 0; j < KNA; ++j) {
       mbar_init(&a_full[j], 1);
-      mbar_init(&a_empty[j], 1);
+      mbar_init(&a_empty[j], MC ? 2 : 1);
     }
     for (int j = 0; j < KNB; ++j) {
       mbar_init(&b_full[j], 1);
@@ -2040,6 +2084,7 @@ __global__ void __launch_bounds__(KTHREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (MC) cluster_sync_all();  // both CTAs' barriers initialised before any multicast
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
@@ -2048,10 +2093,11 @@ __global__ void __launch_bounds__(KTHREADS, 1)
     long h = 0;
     long last_a = -1, last_b = -1;
     bool ok = true;
-    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+    for (int item = cid; item < items && ok; item += ncl) {
       const int cc = item % nch, rb = (item / nch) % nrb, b = item / (nch * nrb);
-      const int ct1 = min(nct, (cc + 1) * tpc);
-      for (int ct = cc * tpc; ct < ct1 && ok; ++ct)
+      int ct0, ct1;
+      tiles(cc, ct0, ct1);
+      for (int ct = ct0; ct < ct1 && ok; ++ct)
         for (int c = 0; c < nkc && ok; ++c, ++h) {
           const int sb = (int)(h % KNB);
           if (h >= KNB && !mbar_wait(&b_empty[sb], (uint32_t)((h / KNB - 1) & 1), abort_flag, gerr, 41)) {
@@ -2070,7 +2116,10 @@ __global__ void __launch_bounds__(KTHREADS, 1)
               break;
             }
             mbar_expect_tx(&a_full[sa], KA_STAGE);
-            tma_load_3d(sA + sa * KA_STAGE, &ta, &a_full[sa], c * KC, rb * BM, t * batch + b);
+            if (!MC)
+              tma_load_3d(sA + sa * KA_STAGE, &ta, &a_full[sa], c * KC, rb * BM, t * batch + b);
+            else if ((t & 1) == crank)
+              tma_load_3d_mc(sA + sa * KA_STAGE, &ta, &a_full[sa], c * KC, rb * BM, t * batch + b, 0x3);
             last_a = ga;
           }
         }
@@ -2083,10 +2132,11 @@ __global__ void __launch_bounds__(KTHREADS, 1)
     // ------------------------------------------------------------ MMA --
     long h = 0;
     bool ok = true;
-    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+    for (int item = cid; item < items && ok; item += ncl) {
       const int cc = item % nch;
-      const int ct1 = min(nct, (cc + 1) * tpc);
-      for (int ct = cc * tpc; ct < ct1 && ok; ++ct)
+      int ct0, ct1;
+      tiles(cc, ct0, ct1);
+      for (int ct = ct0; ct < ct1 && ok; ++ct)
         for (int c = 0; c < nkc; ++c) {
           const int sb = (int)(h % KNB), buf = (int)(h & 1);
           if (!mbar_wait(&b_full[sb], (uint32_t)((h / KNB) & 1), abort_flag, gerr, 45) ||
@@ -2113,7 +2163,10 @@ __global__ void __launch_bounds__(KTHREADS, 1)
             for (int kk = 0; kk < KC / 16; ++kk)
               mma_bf16(dbase + (uint32_t)(t * KBN), ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
                        (t > 0 || kk > 0) ? 1u : 0u);
-            mma_commit(&a_empty[sa]);
+            if (MC)
+              mma_commit_mc(&a_empty[sa], 0x3);
+            else
+              mma_commit(&a_empty[sa]);
             issued = true;
           }
           if (!ok) {
@@ -2137,16 +2190,17 @@ __global__ void __launch_bounds__(KTHREADS, 1)
     const bool neg = alpha < 0.0;
     long h = 0;
     bool ok = true;
-    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+    for (int item = cid; item < items && ok; item += ncl) {
       const int cc = item % nch, rb = (item / nch) % nrb, b = item / (nch * nrb);
-      const int ct1 = min(nct, (cc + 1) * tpc);
+      int ct0, ct1;
+      tiles(cc, ct0, ct1);
       const int r = rb * BM + q * 32 + lane;
       const bool rv = r < R;
       const int es = rv ? __ldg(sexp + (long)b * R + r) - 7 * (SK + 1) : 0;
       double *crow = CX ? reinterpret_cast<double *>(C + (long)b * sc + (r >> 1)) + (r & 1)
                         : reinterpret_cast<double *>(C + (long)b * sc + r);
       const long cstride = CX ? 2L * ldc : ldc;  // doubles between columns
-      for (int ct = cc * tpc; ct < ct1 && ok; ++ct) {
+      for (int ct = ct0; ct < ct1 && ok; ++ct) {
         const int col0 = ct * KBN + c0;
         const int tcol = (col0 + (lane & 15) < n) ? __ldg(texp + (long)b * n + col0 + (lane & 15)) : 0;
         unsigned long long hi[16], lo[16];
@@ -2211,6 +2265,9 @@ __global__ void __launch_bounds__(KTHREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  // neither CTA of a pair leaves while the other may still multicast into
+  // it or arrive on its barriers
+  if (MC) cluster_sync_all();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS) : "memory");
@@ -2249,10 +2306,14 @@ static int gemm_sliced_k_launch(cudaStream_t st, const SlicedOp &a, const Sliced
   if (int rc = make_map_k(&tb, b.slices, b.rows, b.Kp, SK * batch, KBN)) return rc;
   static std::atomic<unsigned long long> attr_done{0};
   if (int rc = once_per_device(attr_done, [&]() -> int {
-      GBF_CUDA(cudaFuncSetAttribute(gemm_sliced_k_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    K_SMEM));
-      GBF_CUDA(cudaFuncSetAttribute(gemm_sliced_k_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    K_SMEM));
+        GBF_CUDA(cudaFuncSetAttribute(gemm_sliced_k_kernel<T, true, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, K_SMEM));
+        GBF_CUDA(cudaFuncSetAttribute(gemm_sliced_k_kernel<T, false, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, K_SMEM));
+        GBF_CUDA(cudaFuncSetAttribute(gemm_sliced_k_kernel<T, true, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, K_SMEM));
+        GBF_CUDA(cudaFuncSetAttribute(gemm_sliced_k_kernel<T, false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, K_SMEM));
         return 0;
       }))
     return rc;
@@ -2260,19 +2321,48 @@ static int gemm_sliced_k_launch(cudaStream_t st, const SlicedOp &a, const Sliced
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int base_items = ceil_div(a.rows, (long)BM) * batch, nct = ceil_div(b.rows, KBN);
-  // one work item per tile: every tile streams its own A chunks, so finer
-  // items cost no traffic and balance the last round; consecutive items are
-  // the column tiles of one row block (its A chunks shared in L2)
+  const int nkc = (int)(a.Kp / KC);
+  // pairs of column tiles on CTA pairs sharing the A stream (more than one
+  // column tile); else one work item per tile: every tile streams its own A
+  // chunks, so finer items cost no traffic and balance the last round;
+  // consecutive items are the column tiles of one row block (its A chunks
+  // shared in L2)
+  if (nct > 1) {
+    const int npair = ceil_div(nct, 2), items = base_items * npair;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * std::min(items, sms / 2), 1, 1);
+    cfg.blockDim = dim3(KTHREADS, 1, 1);
+    cfg.dynamicSmemBytes = K_SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e =
+        beta_one ? cudaLaunchKernelEx(&cfg, gemm_sliced_k_kernel<T, true, true>, ta, tb, (int)a.rows, (int)b.rows,
+                                      batch, nkc, npair, 1, a.exps, b.exps, alpha, C, ldc, sc, gerr)
+                 : cudaLaunchKernelEx(&cfg, gemm_sliced_k_kernel<T, false, true>, ta, tb, (int)a.rows, (int)b.rows,
+                                      batch, nkc, npair, 1, a.exps, b.exps, alpha, C, ldc, sc, gerr);
+    if (e == cudaSuccess) {
+      GBF_LAUNCHED();
+      return 0;
+    }
+    cudaGetLastError();
+  }
   const int tpc = 1, nch = nct;
   const int items = base_items * nch;
-  const int nkc = (int)(a.Kp / KC);
   dim3 grid(std::min(items, sms));
   if (beta_one)
-    gemm_sliced_k_kernel<T, true><<<grid, KTHREADS, K_SMEM, st>>>(ta, tb, (int)a.rows, (int)b.rows, batch, nkc, nch,
-                                                                   tpc, a.exps, b.exps, alpha, C, ldc, sc, gerr);
+    gemm_sliced_k_kernel<T, true, false><<<grid, KTHREADS, K_SMEM, st>>>(ta, tb, (int)a.rows, (int)b.rows, batch, nkc,
+                                                                          nch, tpc, a.exps, b.exps, alpha, C, ldc, sc,
+                                                                          gerr);
   else
-    gemm_sliced_k_kernel<T, false><<<grid, KTHREADS, K_SMEM, st>>>(ta, tb, (int)a.rows, (int)b.rows, batch, nkc,
-                                                                    nch, tpc, a.exps, b.exps, alpha, C, ldc, sc, gerr);
+    gemm_sliced_k_kernel<T, false, false><<<grid, KTHREADS, K_SMEM, st>>>(ta, tb, (int)a.rows, (int)b.rows, batch,
+                                                                           nkc, nch, tpc, a.exps, b.exps, alpha, C,
+                                                                           ldc, sc, gerr);
   GBF_LAUNCHED();
   GBF_CUDA(cudaGetLastError());
   return 0;
