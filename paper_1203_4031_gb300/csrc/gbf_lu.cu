@@ -213,6 +213,9 @@ __global__ void __launch_bounds__(PANEL_THREADS)
 //      that updates column j + 1 of a row forms that row's next candidate.
 // A buffer of parity j % 2 is rewritten at column j + 2, after every CTA has
 // passed barrier j + 1 and therefore finished its reads of it.
+// Leading dimension of a panel slice of R rows in shared memory.
+__host__ __device__ constexpr int panel_ld(int R) { return ((R + 15) & ~15) + 1; }
+
 template <class T>
 struct PanelPub {
   T row[MAX_NB];   // entries of this CTA's candidate row
@@ -282,9 +285,11 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   T *sl;
   long ld;
   if constexpr (SMEM) {
+    // leading dimension 1 mod 16: the row accesses (publishing a candidate,
+    // the swap) fall into distinct banks; column accesses stay contiguous
     sl = reinterpret_cast<T *>(sp);
-    ld = R;
-    sp += (size_t)R * w * sizeof(T);
+    ld = panel_ld(R);
+    sp += (size_t)ld * w * sizeof(T);
   } else {
     sl = a + r0 + (long)k * n;
     ld = n;
@@ -311,7 +316,7 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   if constexpr (SMEM) {
     for (int t = tid; t < rows * w; t += blockDim.x) {
       const int rl = t % rows, jj = t / rows;
-      sl[(long)jj * R + rl] = a[(r0 + rl) + (long)(k + jj) * n];
+      sl[(long)jj * ld + rl] = a[(r0 + rl) + (long)(k + jj) * n];
     }
     __syncthreads();
   }
@@ -439,7 +444,7 @@ __global__ void __launch_bounds__(PANEL_THREADS)
       const int i = t % w, l = t / w;
       T v;
       if constexpr (SMEM)
-        v = (q == 0) ? sl[(long)l * R + i] : cl.map_shared_rank(sl, 0)[(long)l * R + i];
+        v = (q == 0) ? sl[(long)l * ld + i] : cl.map_shared_rank(sl, 0)[(long)l * ld + i];
       else
         v = a[(k + i) + (long)(k + l) * n];
       l11[i + l * 32] = v;
@@ -458,7 +463,7 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   if constexpr (SMEM)
     for (int t = tid; t < rows * w; t += blockDim.x) {
       const int rl = t % rows, jj = t / rows;
-      a[(r0 + rl) + (long)(k + jj) * n] = sl[(long)jj * R + rl];
+      a[(r0 + rl) + (long)(k + jj) * n] = sl[(long)jj * ld + rl];
     }
   cl.sync();  // no CTA leaves while another may still read its buffers
 }
@@ -466,7 +471,7 @@ __global__ void __launch_bounds__(PANEL_THREADS)
 // Dynamic shared memory of the cluster panel for C CTAs of R rows.
 template <class T>
 static size_t panel_smem(int R, int w, int C, bool slice_in_smem) {
-  return (slice_in_smem ? (size_t)R * w * sizeof(T) : 0) + 2 * sizeof(PanelPub<T>) + (size_t)C * w * sizeof(T) +
+  return (slice_in_smem ? (size_t)panel_ld(R) * w * sizeof(T) : 0) + 2 * sizeof(PanelPub<T>) + (size_t)C * w * sizeof(T) +
          MAX_NB * sizeof(T) + 32 * 32 * sizeof(T) + 16 * (sizeof(long long) + sizeof(int));
 }
 
