@@ -959,15 +959,25 @@ __global__ void __maxnreg__(96)
         const unsigned long long sgn = neg ? 0x8000000000000000ull : 0ull;
         if (fast && full) {
           // whole 32 x ZEC block in range: straight-line code, so the ZEC
-          // independent conversions interleave.  Every entry goes through
-          // the integer construction and one FP64 add: an FP64 instruction
-          // costs as much issue time on this GPU as a few dozen integer
-          // ones, so the conversion stays off the FP64 unit.
+          // independent conversions interleave.  The integer pipe and the
+          // FP64 unit share the conversions: even columns are built with
+          // integer operations (leading-zero count, rounding, exponent
+          // field) and added to C with one FP64 add, odd columns are
+          // converted by the FP64 unit and joined to C by one fused
+          // multiply-add (both round twice: the product entry, then the
+          // sum); with all of them on the integer pipe it was the busiest.
           double v[ZEC];
 #pragma unroll
           for (int j = 0; j < ZEC; ++j) {
-            v[j] = i64_scaled((long long)x[j], es + et[j], sgn);
-            if constexpr (BETA) v[j] += (double)cur[j];
+            if (j & 1) {
+              const double p2 =
+                  __longlong_as_double((long long)(((unsigned long long)(es + et[j] + 1023) << 52) ^ sgn));
+              v[j] = BETA ? fma(__ll2double_rn((long long)x[j]), p2, (double)cur[j])
+                          : __ll2double_rn((long long)x[j]) * p2;
+            } else {
+              v[j] = i64_scaled((long long)x[j], es + et[j], sgn);
+              if constexpr (BETA) v[j] += (double)cur[j];
+            }
           }
 #pragma unroll
           for (int j = 0; j < ZEC; ++j) crow[2L * (col0 + j) * ldc] = (R)v[j];
@@ -1124,7 +1134,10 @@ constexpr int TF_B_BOX = TF_BN * TF_KC * 4;       // 8 KB: one (plane, chunk) of
 constexpr int TF_A_TILE = 4 * TF_A_BOX;           // hi/lo x 2 chunks
 constexpr int TF_B_TILE = 4 * TF_B_BOX;
 constexpr int TF_NB = 4;                          // B ring depth
+constexpr int TF_NB_TC = 2;                       // B ring depth with the C tiles staged in shared memory
+constexpr int TF_C_TILE = BM * TF_BN * 4;         // 32 KB: one C tile (128 embedded rows x 64 columns, FP32)
 constexpr int TF_SMEM = TF_A_TILE + TF_NB * TF_B_TILE + 1024 + 256;
+constexpr int TF_SMEM_TC = TF_A_TILE + TF_NB_TC * TF_B_TILE + 2 * TF_C_TILE + 1024 + 256;
 constexpr int TF_EC = 16;                         // columns per epilogue warp
 constexpr int TF_EW = 4 * (TF_BN / TF_EC);        // epilogue warps
 constexpr int TF_THREADS = 64 + 32 * TF_EW;
@@ -1235,19 +1248,24 @@ __global__ void tf32_split_kernel(char opa, char opb, int m, int n, int k, const
     tf32_split_b<T>((blockIdx.x - ablocks) * 8 + w, blockIdx.y, opb, k, n, B, ldb, sb, batch, Bp);
 }
 
-template <bool BETA>
+template <bool BETA, bool TC>
 __global__ void __launch_bounds__(TF_THREADS, 1)
-    ctf32_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int m, int n,
-                 int batch, int nch, int tpc, float alpha, cf *C, long ldc, long sc, int *gerr) {
+    ctf32_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                 const __grid_constant__ CUtensorMap tcm, int m, int n, int batch, int nch, int tpc, float alpha,
+                 cf *C, long ldc, long sc, int *gerr) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
+  constexpr int NBT = TC ? TF_NB_TC : TF_NB;
   unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char *sA = base;               // [plane][chunk][128][32] FP32
-  unsigned char *sB = base + TF_A_TILE;   // TF_NB x [plane][chunk][64][32]
-  uint64_t *bars = reinterpret_cast<uint64_t *>(base + TF_A_TILE + TF_NB * TF_B_TILE);
+  unsigned char *sB = base + TF_A_TILE;   // NBT x [plane][chunk][64][32]
+  float *sC = reinterpret_cast<float *>(base + TF_A_TILE + NBT * TF_B_TILE);  // TC: 2 x [64 cols][128 rows]
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + TF_A_TILE + NBT * TF_B_TILE + (TC ? 2 * TF_C_TILE : 0));
   uint64_t *a_full = bars, *a_empty = bars + 1;
-  uint64_t *b_full = bars + 2, *b_empty = b_full + TF_NB;
-  uint64_t *acc_full = b_empty + TF_NB, *acc_empty = acc_full + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+  uint64_t *b_full = bars + 2, *b_empty = b_full + NBT;
+  uint64_t *acc_full = b_empty + NBT, *acc_empty = acc_full + 2;
+  uint64_t *c_full = acc_empty + 2, *c_empty = c_full + 2;  // TC: C tile landed / stored out of the buffer
+  uint64_t *epi_done = c_empty + 2;                         // TC: all epilogue warps wrote the tile
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(epi_done + 2);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rows = 2 * m;
@@ -1257,13 +1275,16 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
   if (threadIdx.x == 0) {
     mbar_init(a_full, 1);
     mbar_init(a_empty, 1);
-    for (int j = 0; j < TF_NB; ++j) {
+    for (int j = 0; j < NBT; ++j) {
       mbar_init(&b_full[j], 1);
       mbar_init(&b_empty[j], 1);
     }
     for (int j = 0; j < 2; ++j) {
       mbar_init(&acc_full[j], 1);
       mbar_init(&acc_empty[j], TF_EW);  // one arrival per epilogue warp
+      mbar_init(&c_full[j], 1);
+      mbar_init(&c_empty[j], 1);
+      mbar_init(&epi_done[j], TF_EW);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1281,7 +1302,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ TMA --
-    int g = 0, it_local = 0, last_b = -1;
+    int g = 0, it_local = 0, last_b = -1, last_c = -1;
     bool ok = true;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it_local) {
       const int cc = item % nch, rb = (item / nch) % nrb, b = item / (nch * nrb);
@@ -1294,7 +1315,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
       for (int pc = 0; pc < 4; ++pc)  // (plane, chunk) = (pc / 2, pc % 2)
         tma_load_3d(sA + pc * TF_A_BOX, &ta, a_full, 0, rb * BM, ((pc >> 1) * batch + b) * 2 + (pc & 1));
       for (int ct = cc * tpc; ct < ct1; ++ct, ++g) {
-        const int st = g % TF_NB, use = g / TF_NB;
+        const int st = g % NBT, use = g / NBT;
         if (use > 0 && !mbar_wait(&b_empty[st], (use - 1) & 1, abort_flag, gerr, 42)) {
           ok = false;
           break;
@@ -1304,11 +1325,23 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
           tma_load_3d(sB + st * TF_B_TILE + pc * TF_B_BOX, &tb, &b_full[st], 0, ct * TF_BN,
                       ((pc >> 1) * batch + b) * 2 + (pc & 1));
         last_b = g;
+        if (TC && BETA) {  // C tile g into buffer g % 2 once the store of tile g - 2 has read it
+          const int cb = g & 1;
+          if (g >= 2 && !mbar_wait(&c_empty[cb], ((g >> 1) - 1) & 1, abort_flag, gerr, 50)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&c_full[cb], TF_C_TILE);
+          tma_load_3d(sC + cb * (TF_C_TILE / 4), &tcm, &c_full[cb], rb * BM, ct * TF_BN, b);
+          last_c = g;
+        }
       }
     }
     if (it_local > 0) mbar_drain(a_full, (it_local - 1) & 1, gerr, 43);
-    for (int gg = (last_b - TF_NB + 1 > 0 ? last_b - TF_NB + 1 : 0); gg <= last_b; ++gg)
-      mbar_drain(&b_full[gg % TF_NB], (gg / TF_NB) & 1, gerr, 44);
+    for (int gg = (last_b - NBT + 1 > 0 ? last_b - NBT + 1 : 0); gg <= last_b; ++gg)
+      mbar_drain(&b_full[gg % NBT], (gg / NBT) & 1, gerr, 44);
+    for (int gg = (last_c - 1 > 0 ? last_c - 1 : 0); gg <= last_c; ++gg)
+      mbar_drain(&c_full[gg & 1], (gg >> 1) & 1, gerr, 51);
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA --
     constexpr uint32_t idesc = idesc_tf32();
@@ -1318,9 +1351,9 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
       const int cc = item % nch;
       const int ct0 = cc * tpc, ct1 = min(nct, ct0 + tpc);
       for (int ct = ct0; ct < ct1; ++ct, ++g) {
-        const int st = g % TF_NB, buf = g & 1;
+        const int st = g % NBT, buf = g & 1;
         if ((ct == ct0 && !mbar_wait(a_full, it_local & 1, abort_flag, gerr, 45)) ||
-            !mbar_wait(&b_full[st], (g / TF_NB) & 1, abort_flag, gerr, 46) ||
+            !mbar_wait(&b_full[st], (g / NBT) & 1, abort_flag, gerr, 46) ||
             (g >= 2 && !mbar_wait(&acc_empty[buf], ((g >> 1) - 1) & 1, abort_flag, gerr, 47))) {
           ok = false;
           break;
@@ -1348,7 +1381,81 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
       if (ok) mma_commit(a_empty);
     }
     if (g > 0) mbar_drain(&acc_full[(g - 1) & 1], ((g - 1) >> 1) & 1, gerr, 48);
-  } else if (warp >= 2) {
+  } else if (TC && warp >= 2) {
+    // ------------------------------------------- epilogue, C staged --
+    // The C tile (128 embedded rows x 64 columns, [column][row] FP32) is in
+    // shared memory buffer g % 2; warp w updates rows 32 (w % 4) .. +31 of
+    // columns c0 .. c0 + 15 in place, then arrives on epi_done; thread 0 of
+    // warp 2 waits for all 16 warps, stores the tile with one bulk tensor
+    // copy and frees the buffer for the load of tile g + 2 once the copy has
+    // read it.
+    const int q = warp & 3, c0 = ((warp - 2) >> 2) * TF_EC;
+    const bool issuer = (warp == 2 && lane == 0);
+    int item = blockIdx.x, ct = 0, ct1 = 0;
+    if (item < items) {
+      ct = (item % nch) * tpc;
+      ct1 = min(nct, ct + tpc);
+    }
+    for (int g = 0; item < items; ++g) {
+      const int buf = g & 1, use = g >> 1;
+      int okw = 0;
+      if (lane == 0)
+        okw = (mbar_wait(&acc_full[buf], use & 1, abort_flag, gerr, 49) &&
+               (!BETA || mbar_wait(&c_full[buf], use & 1, abort_flag, gerr, 52)))
+                  ? 1
+                  : 0;
+      if (__shfl_sync(0xffffffffu, okw, 0) == 0) break;
+      __syncwarp();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t acc[TF_EC];
+      tmem_ld<TF_EC>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TF_BN + c0), acc);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(&acc_empty[buf])) : "memory");
+      const int rb = (item / nch) % nrb, b = item / (nch * nrb);
+      float *tile = sC + buf * (TF_C_TILE / 4) + q * 32 + lane;
+#pragma unroll
+      for (int j = 0; j < TF_EC; ++j) {
+        const float v = __uint_as_float(acc[j]);
+        float *cp = tile + (c0 + j) * BM;
+        *cp = BETA ? fmaf(alpha, v, *cp) : alpha * v;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(&epi_done[buf])) : "memory");
+      int stored = 1;
+      if (issuer) stored = mbar_wait(&epi_done[buf], use & 1, abort_flag, gerr, 53) ? 1 : 0;
+      if (issuer && stored) {
+        asm volatile(
+            "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                reinterpret_cast<uint64_t>(&tcm)),
+            "r"(sm_u32(sC + buf * (TF_C_TILE / 4))), "r"(rb * BM), "r"(ct * TF_BN), "r"(b)
+            : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(&c_empty[buf])) : "memory");
+      }
+      if (__shfl_sync(0xffffffffu, stored, 0) == 0) break;  // warp-uniform (lane 0 decides)
+      int nitem = item, nct0 = ct + 1;
+      if (nct0 >= ct1) {
+        nitem = item + gridDim.x;
+        if (nitem < items) nct0 = (nitem % nch) * tpc;
+      }
+      if (nitem != item) {
+        item = nitem;
+        if (item < items) {
+          ct = nct0;
+          ct1 = min(nct, ct + tpc);
+        }
+      } else {
+        ct = nct0;
+      }
+    }
+    if (issuer) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // every store written
+  } else if (!TC && warp >= 2) {
     // ------------------------------------------------------- epilogue --
     // Warp w: TMEM lanes 32 (w % 4) .. +31 (embedded rows), columns
     // c0 .. c0 + 15 of each tile, c0 = 16 ((w - 2) / 4).  Embedded row rr is
@@ -1447,6 +1554,22 @@ static int make_map_tf32(CUtensorMap *map, const void *ptr, long rows, int plane
   return 0;
 }
 
+// 3-D map over C (complex FP32, column-major, ldc, batch stride sc) seen as
+// FP32 [batch][n columns][2m embedded rows], box (128 rows, 64 columns, 1),
+// no swizzle.
+static int make_map_ctile(CUtensorMap *map, const cf *C, long rows, int n, int batch, long ldc, long sc) {
+  auto fn = encode_fn();
+  if (!fn) return -4;
+  cuuint64_t dims[3] = {(cuuint64_t)rows, (cuuint64_t)n, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)ldc * 8, (cuuint64_t)(batch > 1 ? sc : (long)ldc * n) * 8};
+  cuuint32_t box[3] = {(cuuint32_t)BM, (cuuint32_t)TF_BN, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<cf *>(C), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -4;
+}
+
 static size_t ctf32_work(int m, int n, int batch) {
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
   return al((size_t)2 * batch * 2 * (2L * m) * TF_KC * 4) + al((size_t)2 * batch * 2 * (long)n * TF_KC * 4);
@@ -1482,11 +1605,22 @@ static int ctf32_run(cudaStream_t st, char opa, char opb, int m, int n, int k, d
   if (int rc = make_map_tf32(&tb, Bp, n, 4 * batch, TF_BN)) return rc;
   static std::atomic<unsigned long long> attr_done{0};
   if (int rc = once_per_device(attr_done, [&]() -> int {
-      GBF_CUDA(cudaFuncSetAttribute(ctf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TF_SMEM));
-      GBF_CUDA(cudaFuncSetAttribute(ctf32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TF_SMEM));
+        GBF_CUDA(cudaFuncSetAttribute(ctf32_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TF_SMEM));
+        GBF_CUDA(cudaFuncSetAttribute(ctf32_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TF_SMEM));
+        GBF_CUDA(cudaFuncSetAttribute(ctf32_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TF_SMEM_TC));
         return 0;
       }))
     return rc;
+  // C staged through shared memory by bulk tensor copies when beta = 1 and
+  // its layout meets the copies' 16-byte rules (start, column and batch
+  // strides); otherwise the epilogue reads and writes C directly
+  CUtensorMap tcm;
+  const bool staged = beta_one && ((uintptr_t)C % 16 == 0) && (ldc % 2 == 0) && (batch == 1 || sc % 2 == 0) &&
+                      make_map_ctile(&tcm, C, rows, n, batch, ldc, sc) == 0;
+  if (!staged) tcm = ta;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1496,12 +1630,15 @@ static int ctf32_run(cudaStream_t st, char opa, char opb, int m, int n, int k, d
   const int items = base_items * nch;
   dim3 grid(std::min(items, sms));
   const int slot = prof_begin(st);
-  if (beta_one)
-    ctf32_kernel<true><<<grid, TF_THREADS, TF_SMEM, st>>>(ta, tb, m, n, batch, nch, tpc, (float)alpha, C, ldc, sc,
-                                                          gerr);
+  if (staged)
+    ctf32_kernel<true, true><<<grid, TF_THREADS, TF_SMEM_TC, st>>>(ta, tb, tcm, m, n, batch, nch, tpc, (float)alpha,
+                                                                   C, ldc, sc, gerr);
+  else if (beta_one)
+    ctf32_kernel<true, false><<<grid, TF_THREADS, TF_SMEM, st>>>(ta, tb, tcm, m, n, batch, nch, tpc, (float)alpha, C,
+                                                                 ldc, sc, gerr);
   else
-    ctf32_kernel<false><<<grid, TF_THREADS, TF_SMEM, st>>>(ta, tb, m, n, batch, nch, tpc, (float)alpha, C, ldc, sc,
-                                                           gerr);
+    ctf32_kernel<false, false><<<grid, TF_THREADS, TF_SMEM, st>>>(ta, tb, tcm, m, n, batch, nch, tpc, (float)alpha,
+                                                                  C, ldc, sc, gerr);
   prof_end(st, slot, 8.0 * m * (double)n * k * batch);
   GBF_LAUNCHED();
   GBF_CUDA(cudaGetLastError());
