@@ -226,16 +226,17 @@ struct PanelPub {
 };
 
 // Argmax of (key, row) pairs over a warp: the larger key wins, the lower row
-// on ties.  Butterfly, so every lane ends with the result.
+// on ties; every lane ends with the result.  Keys are >= -1 and rows >= 0.
+// Three hardware warp reductions (the key's high word, its low word among
+// the lanes holding that high word, the lowest row holding the key): the
+// five-round 64-bit shuffle butterfly took about ten times longer here.
 __device__ __forceinline__ void argmax_all(long long &b, int &bi) {
-  for (int off = 16; off > 0; off >>= 1) {
-    const long long ov = __shfl_xor_sync(0xffffffffu, b, off);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-    if (ov > b || (ov == b && oi < bi)) {
-      b = ov;
-      bi = oi;
-    }
-  }
+  const unsigned long long u = (unsigned long long)(b + 1);
+  const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(u >> 32));
+  const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(u >> 32) == hi ? (unsigned)u : 0u);
+  const long long mx = (long long)(((unsigned long long)hi << 32) | lo) - 1;
+  bi = (int)__reduce_min_sync(0xffffffffu, b == mx ? (unsigned)bi : 0xffffffffu);
+  b = mx;
 }
 
 __device__ __forceinline__ zd shfl_t(zd v, int src) {
