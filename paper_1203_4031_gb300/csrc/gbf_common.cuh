@@ -82,6 +82,35 @@ template <> struct tr<cf> {
 
 // Complex double arithmetic used by host and device helpers.
 __host__ __device__ inline zd zmul(zd a, zd b) { return tr<zd>::mul(a, b); }
+// 1/d and 1/sqrt(x) for the serial scalar steps of the reduced-space
+// kernels (a pivot's reciprocal, a reflector's norm), where one thread's
+// chain of dependent FP64 instructions is the critical path: the hardware's
+// approximate value (about 20 correct bits) refined by two steps of
+// Newton's iteration, r <- r + r (1 - d r) for the reciprocal and
+// y <- y (3/2 - (x/2) y^2) for the reciprocal square root: a few ulp, in
+// fewer dependent instructions than a division or a square root.  Outside
+// [2^-1000, 2^1000] in magnitude (and for zero, non-finite or, for the
+// square root, non-positive input) the exact operations are used.
+__device__ __forceinline__ bool fast_range(double v) {
+  const int eb = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+  return eb > 23 && eb < 2023;
+}
+__device__ __forceinline__ double fast_rcp(double d) {
+  if (!fast_range(d)) return 1.0 / d;
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  r = fma(r, fma(-d, r, 1.0), r);
+  return fma(r, fma(-d, r, 1.0), r);
+}
+__device__ __forceinline__ double fast_rsqrt(double x) {
+  if (!(x > 0.0) || !fast_range(x)) return 1.0 / sqrt(x);
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double h = 0.5 * x;
+  y = y * fma(-h * y, y, 1.5);
+  return y * fma(-h * y, y, 1.5);
+}
+
 __host__ __device__ inline zd zdiv(zd a, zd b) {
   // Smith's algorithm (scaled division)
   if (fabs(b.x) >= fabs(b.y)) {

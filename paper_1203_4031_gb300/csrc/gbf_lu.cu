@@ -246,17 +246,18 @@ __device__ __forceinline__ cf shfl_t(cf v, int src) {
   return cf{__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)};
 }
 
-// Reciprocal of a nonzero pivot with one division: a is scaled by the power
-// of two f that brings its larger part into [1, 2) (exact), then
-// 1/a = conj(f a) f / |f a|^2 with |f a|^2 in [1, 8).  Zero, subnormal,
-// huge or non-finite pivots take Smith's division.
+// Reciprocal of a nonzero pivot: a is scaled by the power of two f that
+// brings its larger part into [1, 2) (exact), then 1/a = conj(f a) f / d
+// with d = |f a|^2 in [1, 8), 1/d by fast_rcp (a few ulp, a much shorter
+// chain on this GPU's FP64 unit than a division).  Zero, subnormal, huge or
+// non-finite pivots take Smith's division.
 __device__ inline zd pivot_recip(zd a) {
   const double s = fmax(fabs(a.x), fabs(a.y));
   const long long eb = (__double_as_longlong(s) >> 52) & 0x7FF;
   if (eb == 0 || eb >= 2046) return zdiv(zd{1.0, 0.0}, a);
   const double f = __longlong_as_double((2046LL - eb) << 52);
   const double ax = a.x * f, ay = a.y * f;
-  const double r = f / fma(ax, ax, ay * ay);
+  const double r = fast_rcp(fma(ax, ax, ay * ay)) * f;
   return zd{ax * r, -ay * r};
 }
 __device__ inline cf pivot_recip(cf a) {
@@ -977,14 +978,15 @@ size_t solve_kwork_bytes_cf(int n, int nrhs, int bs, int ne) {
 // column cx of the slab.  Rows past n are zero (the inverted blocks are
 // identity-padded there).
 constexpr int LEAF_NC = 16, LEAF_THREADS = 256, LEAF_LD = 33;
-constexpr size_t LEAF_SMEM = (size_t)128 * LEAF_NC * sizeof(cf) + (size_t)10 * 32 * LEAF_LD * sizeof(cf);
+constexpr int LEAF_YLD = LEAF_NC + 1;  // slab row stride: the row-wise staging stores hit distinct banks
+constexpr size_t LEAF_SMEM = (size_t)128 * LEAF_YLD * sizeof(cf) + (size_t)10 * 32 * LEAF_LD * sizeof(cf);
 
 __global__ void __launch_bounds__(LEAF_THREADS)
     trsv_leaf_kernel(int kind, int n, int nrhs, int b0, int nb, const cf *__restrict__ S, const cf *__restrict__ Dinv,
                      long sblk, cf *Y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cf *ys = reinterpret_cast<cf *>(smem_raw);  // [128][LEAF_NC]
-  cf *fb = ys + 128 * LEAF_NC;               // blocks [slot][32][LEAF_LD]
+  cf *ys = reinterpret_cast<cf *>(smem_raw);  // [128][LEAF_YLD]
+  cf *fb = ys + 128 * LEAF_YLD;              // blocks [slot][32][LEAF_LD]
   const int e = blockIdx.y, c0 = blockIdx.x * LEAF_NC;
   const long nn = (long)n * n;
   const cf *Se = S + e * nn;
@@ -1002,14 +1004,16 @@ __global__ void __launch_bounds__(LEAF_THREADS)
     return 4 + base + pd;
   };
   // 1. stage Y and the factor blocks
+#pragma unroll
   for (int t = tid; t < 128 * LEAF_NC; t += LEAF_THREADS) {
     const int r = t % 128, c = t / 128;
     const int gr = r0 + r, gc = c0 + c;
-    ys[r * LEAF_NC + c] = (r < nb * 32 && gr < n && gc < nrhs) ? Ye[gr + (long)gc * n] : cf{0.f, 0.f};
+    ys[r * LEAF_YLD + c] = (r < nb * 32 && gr < n && gc < nrhs) ? Ye[gr + (long)gc * n] : cf{0.f, 0.f};
   }
   for (int d = 0; d < nb; ++d) {
     const cf *D = De + (long)(b0 + d) * 32 * 32;
     cf *dst = fb + d * 32 * LEAF_LD;
+#pragma unroll
     for (int t = tid; t < 32 * 32; t += LEAF_THREADS) {
       const int i = t % 32, j = t / 32;  // element (i, j) of the stored block
       const cf v = D[i + j * 32];
@@ -1027,6 +1031,7 @@ __global__ void __launch_bounds__(LEAF_THREADS)
       //   kind 0/1: A = S[rows of d2, cols of s2]          (op N)
       //   kind 2/3: A = S[rows of s2, cols of d2]^H        (op C)
       const int rd = r0 + d2 * 32, rs = r0 + s2 * 32;
+#pragma unroll
       for (int t = tid; t < 32 * 32; t += LEAF_THREADS) {
         const int i = t % 32, j = t / 32;  // element (i, j) of the stored block, i fastest
         if (!herm) {
@@ -1047,11 +1052,11 @@ __global__ void __launch_bounds__(LEAF_THREADS)
     // y_s <- op(Dinv_s) y_s
     {
       const cf *A = fb + s2 * 32 * LEAF_LD;
-      const cf *yb = ys + s2 * 32 * LEAF_NC;
+      const cf *yb = ys + s2 * 32 * LEAF_YLD;
       float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f;
 #pragma unroll 8
       for (int l = 0; l < 32; ++l) {
-        const cf y = yb[l * LEAF_NC + cx];
+        const cf y = yb[l * LEAF_YLD + cx];
         const cf p = A[ry * LEAF_LD + l], q = A[(ry + 16) * LEAF_LD + l];
         a0r = fmaf(p.x, y.x, fmaf(-p.y, y.y, a0r));
         a0i = fmaf(p.x, y.y, fmaf(p.y, y.x, a0i));
@@ -1059,36 +1064,37 @@ __global__ void __launch_bounds__(LEAF_THREADS)
         a1i = fmaf(q.x, y.y, fmaf(q.y, y.x, a1i));
       }
       __syncthreads();
-      ys[(s2 * 32 + ry) * LEAF_NC + cx] = cf{a0r, a0i};
-      ys[(s2 * 32 + ry + 16) * LEAF_NC + cx] = cf{a1r, a1i};
+      ys[(s2 * 32 + ry) * LEAF_YLD + cx] = cf{a0r, a0i};
+      ys[(s2 * 32 + ry + 16) * LEAF_YLD + cx] = cf{a1r, a1i};
       __syncthreads();
     }
     // y_d -= op(A_ds) y_s for the blocks d solved later
     for (int d2 = 0; d2 < nb; ++d2) {
       if (fwd ? d2 <= s2 : d2 >= s2) continue;
       const cf *A = fb + pair_slot(s2, d2) * 32 * LEAF_LD;
-      const cf *yb = ys + s2 * 32 * LEAF_NC;
+      const cf *yb = ys + s2 * 32 * LEAF_YLD;
       float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f;
 #pragma unroll 8
       for (int l = 0; l < 32; ++l) {
-        const cf y = yb[l * LEAF_NC + cx];
+        const cf y = yb[l * LEAF_YLD + cx];
         const cf p = A[ry * LEAF_LD + l], q = A[(ry + 16) * LEAF_LD + l];
         a0r = fmaf(p.x, y.x, fmaf(-p.y, y.y, a0r));
         a0i = fmaf(p.x, y.y, fmaf(p.y, y.x, a0i));
         a1r = fmaf(q.x, y.x, fmaf(-q.y, y.y, a1r));
         a1i = fmaf(q.x, y.y, fmaf(q.y, y.x, a1i));
       }
-      cf *o0 = ys + (d2 * 32 + ry) * LEAF_NC + cx, *o1 = ys + (d2 * 32 + ry + 16) * LEAF_NC + cx;
+      cf *o0 = ys + (d2 * 32 + ry) * LEAF_YLD + cx, *o1 = ys + (d2 * 32 + ry + 16) * LEAF_YLD + cx;
       *o0 = cf{o0->x - a0r, o0->y - a0i};
       *o1 = cf{o1->x - a1r, o1->y - a1i};
     }
     __syncthreads();
   }
   // 3. write back
+#pragma unroll
   for (int t = tid; t < 128 * LEAF_NC; t += LEAF_THREADS) {
     const int r = t % 128, c = t / 128;
     const int gr = r0 + r, gc = c0 + c;
-    if (r < nb * 32 && gr < n && gc < nrhs) Ye[gr + (long)gc * n] = ys[r * LEAF_NC + c];
+    if (r < nb * 32 && gr < n && gc < nrhs) Ye[gr + (long)gc * n] = ys[r * LEAF_YLD + c];
   }
 }
 

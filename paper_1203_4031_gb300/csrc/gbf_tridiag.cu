@@ -143,12 +143,15 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
           double tj = 0.0;
           T beta = x0, sc = X::zero();
           if (rest > 0.0) {
-            const double a0 = sqrt(absq(x0));
-            const double nx = sqrt(a0 * a0 + rest);
-            const T ph = a0 > 0.0 ? scl(x0, 1.0 / a0) : X::one();
+            // |x0| and ||x|| from reciprocal square roots (independent),
+            // then one reciprocal: the shortest chain on the FP64 unit
+            const double q0 = absq(x0), s2 = q0 + rest;
+            const double ia0 = q0 > 0.0 ? fast_rsqrt(q0) : 0.0, inx = fast_rsqrt(s2);
+            const double a0 = q0 * ia0, nx = s2 * inx;
+            const T ph = a0 > 0.0 ? scl(x0, ia0) : X::one();
             beta = scl(ph, -nx);
-            sc = scl(X::conj(ph), 1.0 / (a0 + nx));
-            tj = 1.0 + a0 / nx;
+            sc = scl(X::conj(ph), fast_rcp(a0 + nx));
+            tj = 1.0 + a0 * inx;
           }
           s_tau = tj;
           s_sc = sc;
@@ -431,7 +434,7 @@ __global__ void __launch_bounds__(32) stein_kernel(int m, const double *__restri
       const bool noswap = fabs(ai) >= fabs(sub);
       double piv = noswap ? ai : sub;
       if (fabs(piv) < tiny) piv = (piv < 0.0 ? -tiny : tiny);
-      const double r = 1.0 / piv;
+      const double r = fast_rcp(piv);
       const double f = (noswap ? sub : ai) * r;
       double an, bn;
       if (noswap) {
@@ -452,7 +455,7 @@ __global__ void __launch_bounds__(32) stein_kernel(int m, const double *__restri
       ai = an;
       bi = bn;
     }
-    V(a, m - 1) = 1.0 / ((fabs(ai) < tiny) ? (ai < 0.0 ? -tiny : tiny) : ai);
+    V(a, m - 1) = fast_rcp((fabs(ai) < tiny) ? (ai < 0.0 ? -tiny : tiny) : ai);
     for (int i = 0; i < m; ++i) V(x, i) = unit_rand(kk, i);
     // two solves reach the backward error for an isolated eigenvalue; a
     // cluster member, orthogonalised against the earlier ones, gets three
@@ -503,7 +506,7 @@ __global__ void __launch_bounds__(32) stein_kernel(int m, const double *__restri
         V(x, i) = xi;
         nn = fma(xi, xi, nn);
       }
-      const double r = 1.0 / sqrt(nn);
+      const double r = fast_rsqrt(nn);
       for (int i = 0; i < m; ++i) V(x, i) *= r;
     }
     for (int i = 0; i < m; ++i) Z[(size_t)kk * m + i] = V(x, i);
@@ -613,8 +616,9 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
         const double piv = X::re(Lj[j]);
         const bool okp = piv > 0.0;
         s_fail = okp ? 0 : j + 1;
-        s_r = okp ? sqrt(piv) : 0.0;
-        s_ir = okp ? 1.0 / s_r : 0.0;
+        const double ir = okp ? fast_rsqrt(piv) : 0.0;  // one reciprocal square root
+        s_r = piv * ir;
+        s_ir = ir;
       }
       __syncthreads();
       const bool ok = s_fail == 0;
