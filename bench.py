@@ -281,7 +281,7 @@ def run_gbf(args):
                  "M": mx["M"], "loops": mx["loop"], "max_rel_residual": mx["worst"],
                  "gpu_launches": mx["launches"], "dtype": "c32 factor/solve + f64 correction",
                  "kernels_ms": {k: round(v[1], 3) for k, v in mx["prof"].items()},
-                 "roofline": roofline(mx["prof"], mx["tc"], "mixed")}
+                 "roofline": roofline(mx["prof"], mx["tc"], "mixed", p.n, int(p.fpm.get(2, 8)))}
 
     # end to end through the public API from pinned host buffers: H2D of A
     # and B and D2H of E, X, res inside the timed region
@@ -599,7 +599,18 @@ def measured_peaks():
 SLICED_TRAFFIC_BYTES = None
 
 
-def roofline(prof, tc, path):
+def lu_update_bytes(n, ne, nb=32, entry_bytes=8):
+    """Algorithmic bytes of one factorisation's trailing updates: every
+    update reads and writes its C block once ((n - k - w)^2 entries per
+    node, each entry_bytes wide: complex FP32 = 8)."""
+    tot = 0
+    for k in range(0, n, nb):
+        r = n - k - min(nb, n - k)
+        tot += r * r
+    return 2.0 * entry_bytes * ne * tot
+
+
+def roofline(prof, tc, path, n=None, ne=None):
     """Dominant kernel by device time.  The FP64 factor / solve / projection
     products run as sliced tensor-core GEMMs (zgemm_sliced_kernel for k <= 32,
     7 digits; gemm_sliced_k_kernel for any k, 8 digits): their work is the
@@ -608,6 +619,18 @@ def roofline(prof, tc, path):
     FP64 flops they deliver are reported beside as "useful".  The other
     kernels run on the FP64 ALUs (nominal 1.25 TFLOP/s)."""
     tn, tms, tfl, ttf = tc
+    if path == "mixed" and n and prof.get("lu_update_gemm", (0, 0.0, 0.0))[1] > 0:
+        # the FP32 factorisation's trailing updates (3xTF32 on the tensor
+        # cores, C staged through shared memory): bound by C's traffic
+        ln, lms, _ = prof["lu_update_gemm"]
+        byt = lu_update_bytes(n, ne)
+        pk = measured_peaks().get("hbm_gbs", 6800.0) * 1e9
+        ach = byt / (lms / 1e3)
+        return {"kernel": "ctf32_kernel (FP32 LU trailing updates, C read and written once per step)",
+                "bound": "hbm", "achieved": ach / 1e9, "peak": pk / 1e9, "unit": "GB/s", "frac": ach / pk,
+                "traffic": None, "algorithmic_bytes_per_step": byt, "launches": ln,
+                "avg_launch_ms": lms / max(ln, 1), "ms_per_step": lms,
+                "peak_source": "measured HBM copy (MEASURED_PEAKS.json), of measured"}
     other = {k: v for k, v in prof.items() if k not in ("lu_update_gemm", "solve_gemm")}
     oname, (onl, oms, ofl) = max(other.items(), key=lambda kv: kv[1][1])
     if tms > 0 and tms >= oms:

@@ -279,6 +279,7 @@ template <class TQ, class TL> struct WS {
   void *kw;               // any-k sliced updates of the recursive solves
   size_t kw_bytes;
   TL *dinv_l, *dinv_u;    // 128 x 128 diagonal-block inverses (recursive solves' leaves)
+  float *fpre_n, *fpre_c; // TF32 planes of the FP32 factors (op N, op C), split once
 
   // ne: quadrature nodes; nf: nodes factored and solved here (all of them,
   // or this shard's share); slots: node solution blocks (ne, or nranks x the
@@ -350,6 +351,12 @@ template <class TQ, class TL> struct WS {
     const bool big = kw_bytes && sizeof(TL) == sizeof(zd) && bs == 32 && n % 128 == 0;
     dinv_l = big ? b.take<TL>((size_t)nfa * n * 128) : nullptr;
     dinv_u = big ? b.take<TL>((size_t)nfa * n * 128) : nullptr;
+    // FP32 factors of large problems: TF32 planes split once per
+    // factorisation for the solves' large-K updates (op N; op C for the
+    // adjoint solves of Hermitian problems)
+    const bool pre = kw_bytes && sizeof(TL) == sizeof(cf) && n >= 1024;
+    fpre_n = pre ? b.take<float>(tf32_planes_bytes(n, nfa) / 4) : nullptr;
+    fpre_c = pre && herm ? b.take<float>(tf32_planes_bytes(n, nfa) / 4) : nullptr;
     pja = pjb = pjq = pjh = pjx = pjw = rrw = nullptr;
     rrw_bytes = 0;
     if (proj) {
@@ -485,6 +492,9 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
   tcx.kbytes = ws.kw_bytes;
   tcx.dinv_l = ws.dinv_l;
   tcx.dinv_u = ws.dinv_u;
+  tcx.fpre_n = ws.fpre_n;
+  tcx.fpre_c = ws.fpre_c;
+  tcx.fpre_ne = ws.fpre_n ? std::max(nf, 1) : 0;
   TcScope tc_scope(tcS ? &tcx : nullptr);
   AuxScope aux_scope(ensure_aux(h));
   if (ensure_hbuf(h, (size_t)std::max(m0, ne) + 64)) return out.info = -1;
@@ -519,6 +529,10 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
     CK(form_shift<TL>(st, n, nf, ws.z + nlo, kind_of<TQ>::v, 'F', Af, lda, hasB ? (const void *)Bf : nullptr, ldb,
                       ws.S, ws.sing + nfa));
     CK(getrf_batched<TL>(st, n, nf, ws.S, ws.ipiv, ws.perm, ws.Linv, ws.Uinv, bs, ws.sing, nullptr));
+    if constexpr (std::is_same<TL, cf>::value) {
+      if (ws.fpre_n) CK(tf32_presplit(st, 'N', n, nf, ws.S, ws.fpre_n));
+      if (ws.fpre_c) CK(tf32_presplit(st, 'C', n, nf, ws.S, ws.fpre_c));
+    }
   }
   {
     int *hs = (int *)h->hbuf;

@@ -215,6 +215,9 @@ struct TcCtx {
   size_t kbytes = 0;
   void *dinv_l = nullptr;  // inverses of the 128 x 128 diagonal blocks of L and U (FP64
   void *dinv_u = nullptr;  // factors, n a multiple of 128): the recursive solves' leaves
+  const float *fpre_n = nullptr;  // FP32 factors split once into TF32 planes, op 'N' and op 'C'
+  const float *fpre_c = nullptr;  // (tf32_presplit; nullptr: every update splits its operand)
+  int fpre_ne = 0;                // nodes in the planes
 };
 // Workspace bytes of the recursive solves' any-k sliced updates for n x n
 // factors, nrhs right-hand sides, block size bs (node groups of up to 8).
@@ -269,6 +272,16 @@ size_t zgemm_sliced_work(int m, int n, int batch, int S);
 // large-K solve updates): C = alpha op(A) op(B) + beta C, alpha = +-1, beta
 // in {0, 1}; work: cgemm_tf32k_work bytes (the split TF32 planes).
 size_t cgemm_tf32k_work(int m, int n, int k, int batch);
+// TF32 hi/lo planes of op(S) (op 'N' or 'C') for ne complex FP32 n x n
+// matrices (node stride n^2), in the any-k 3xTF32 GEMM's A layout, and the
+// product C -= op(S)[r0 .. r0+m, 32 c0 .. 32 c0 + k] Y read from them (nodes
+// b0 .. b0 + batch - 1 of bt; only Y is split per call).
+size_t tf32_planes_bytes(int n, int ne);
+int tf32_presplit(cudaStream_t st, char op, int n, int ne, const cf *S, float *planes);
+size_t cgemm_tf32k_pre_work(int n, int k, int batch);
+int cgemm_tf32k_pre(cudaStream_t st, int m, int n, int k, double alpha, const float *pre, int nfull, int bt, int b0,
+                    int r0, int c0, const cf *B, long ldb, long sb, int beta_one, cf *C, long ldc, long sc, int batch,
+                    void *work, size_t work_bytes, int *gerr);
 int cgemm_tf32k(cudaStream_t st, char opa, char opb, int m, int n, int k, double alpha, const cf *A, long lda, long sa,
                 const cf *B, long ldb, long sb, int beta_one, cf *C, long ldc, long sc, int batch, void *work,
                 size_t work_bytes, int *gerr);

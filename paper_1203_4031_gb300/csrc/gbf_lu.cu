@@ -511,11 +511,10 @@ static int panel_clusters(int C, size_t smem) {
 }
 
 // Launch the cluster panel.  C (a power of two <= 16, R = ceil((n-k)/C) >= w
-// rows per CTA) minimises waves x (R + 64): the FP64 rank-1 work of a CTA
-// grows with R, and the per-column barrier and remote-load latency costs
-// about as much as 64 rows; waves = ceil(ne / clusters the device runs at
-// once).  The slice goes to shared memory when it fits, else the CTAs work
-// in place.  With linv, the kernel also writes L11^{-1} of every node there
+// rows per CTA) and the slice's place minimise waves x (R + 64): the FP64
+// rank-1 work of a CTA grows with R, and the per-column barrier and
+// remote-load latency costs about as much as 64 rows; waves = ceil(ne /
+// clusters the device runs at once).  With linv, the kernel also writes L11^{-1} of every node there
 // (ld lld, node stride lsb).  Returns 1 when the caller should use the
 // single-CTA panel
 // instead (no cluster shape can run).
@@ -533,23 +532,32 @@ static int launch_cluster_panel(cudaStream_t st, int n, int ne, int k, int w, T 
     cudaGetLastError();
     return 0;
   });
+  // candidates: every C with the slice in shared memory (when it fits) and
+  // in place; in place costs a quarter more per row (its row accesses go to
+  // L2) but needs little shared memory, so more clusters run at once
   int bestC = 0;
+  bool best_smem = true;
   double best_cost = 0.0;
   for (int C = 1; C <= 16; C *= 2) {
     const int R = ceil_div(rowsp, C);
     if (C > 1 && R < w) break;
-    const size_t sm = panel_smem<T>(R, w, C, true);
-    const int nc = panel_clusters<T>(C, sm <= cap ? sm : panel_smem<T>(R, w, C, false));
-    if (nc < 1) continue;
-    const double cost = (double)ceil_div(ne, nc) * (R + 64);
-    if (bestC == 0 || cost < best_cost) {
-      bestC = C;
-      best_cost = cost;
+    for (int mode = 0; mode < 2; ++mode) {
+      const bool sm_mode = (mode == 0);
+      const size_t sm = panel_smem<T>(R, w, C, sm_mode);
+      if (sm_mode && sm > cap) continue;
+      const int nc = panel_clusters<T>(C, sm);
+      if (nc < 1) continue;
+      const double cost = (double)ceil_div(ne, nc) * (R * (sm_mode ? 1.0 : 1.25) + 64);
+      if (bestC == 0 || cost < best_cost) {
+        bestC = C;
+        best_smem = sm_mode;
+        best_cost = cost;
+      }
     }
   }
   if (bestC == 0) return 1;
   const int C = bestC, R = ceil_div(rowsp, C);
-  const bool in_smem = panel_smem<T>(R, w, C, true) <= cap;
+  const bool in_smem = best_smem;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C, ne, 1);
   cfg.blockDim = dim3(PANEL_THREADS, 1, 1);
@@ -1116,8 +1124,23 @@ static int trsv_leaf(cudaStream_t st, int kind, int n, int ne, int nrhs, const c
 
 // C[e] -= op(A[e]) Y[e] for all nodes e with the any-k 3xTF32 GEMM (FP32
 // factors), nodes grouped so that each group's TF32 planes fit the workspace.
+// op(A) is the block of op(S) at complex row ar and column ac; when the
+// factors were split into TF32 planes once (g_tc->fpre_*), they are read
+// from there and only Y is split.
 static int tf32_update(cudaStream_t st, char opa, int m, int k, int nrhs, const cf *A, long lda, long sa,
-                       const cf *Y, long ldy, long sy, cf *C, long ldc, long sc, int ne) {
+                       const cf *Y, long ldy, long sy, cf *C, long ldc, long sc, int ne, int n, int ar, int ac) {
+  const float *pre = (opa == 'N') ? g_tc->fpre_n : g_tc->fpre_c;
+  if (pre && g_tc->fpre_ne >= ne && ac % 32 == 0) {
+    const size_t per = cgemm_tf32k_pre_work(nrhs, k, 1);
+    const int g = (int)std::max<size_t>(1, std::min<size_t>(ne, g_tc->kbytes / std::max<size_t>(per, 1)));
+    for (int e0 = 0; e0 < ne; e0 += g) {
+      const int gb = std::min(g, ne - e0);
+      const int rc = cgemm_tf32k_pre(st, m, nrhs, k, -1.0, pre, n, g_tc->fpre_ne, e0, ar, ac / 32, Y + (long)e0 * sy,
+                                     ldy, sy, 1, C + (long)e0 * sc, ldc, sc, gb, g_tc->kwork, g_tc->kbytes, g_tc->gerr);
+      if (rc) return rc;
+    }
+    return 0;
+  }
   const size_t per = cgemm_tf32k_work(m, nrhs, k, 1);
   const int g = (int)std::max<size_t>(1, std::min<size_t>(ne, g_tc->kbytes / std::max<size_t>(per, 1)));
   for (int e0 = 0; e0 < ne; e0 += g) {
@@ -1191,6 +1214,7 @@ static int trsv_rec(cudaStream_t st, int kind, int n, int ne, int nrhs, const T 
     case 2: A = S + r0 + (long)rm * n; op = 'C'; m = r1 - rm; k = rm - r0; rdst = rm; rsrc = r0; break;
     default: A = S + rm + (long)r0 * n; op = 'C'; m = rm - r0; k = r1 - rm; rdst = r0; rsrc = rm; break;
   }
+  // op(A) is the block of op(S) at complex row rdst, column rsrc
   bool done = false;
   if constexpr (std::is_same<T, zd>::value) {
     if (k > 32 && g_tc && g_tc->kwork) {  // FP64 factors on the tensor-core engine
@@ -1200,7 +1224,7 @@ static int trsv_rec(cudaStream_t st, int kind, int n, int ne, int nrhs, const T 
   }
   if constexpr (std::is_same<T, cf>::value) {
     if (k > 32 && g_tc && g_tc->kwork) {  // FP32 factors: 3xTF32 on the tensor cores
-      rc = tf32_update(st, op, m, k, nrhs, A, n, nn, Y + rsrc, n, ny, Y + rdst, n, ny, ne);
+      rc = tf32_update(st, op, m, k, nrhs, A, n, nn, Y + rsrc, n, ny, Y + rdst, n, ny, ne, n, rdst, rsrc);
       done = true;
     }
   }

@@ -1667,6 +1667,14 @@ static int ctf32_run(cudaStream_t st, char opa, char opb, int m, int n, int k, d
 // warps: 4 lane quarters x 4 groups of 32 columns.  Bounded waits as in the
 // other kernels.
 // ===================================================================
+// Where the A planes of a call sit in a stored plane array: rows row0 ..
+// (embedded), K chunks c0 .. of the real parts and nkh + c0 .. of the
+// imaginary parts, nodes b0 .. of bt; the planes of one call split on the
+// spot are the special case row0 = c0 = b0 = 0, nkh = nk, bt = batch.
+struct APlanes {
+  int row0, c0, nkh, bt, b0;
+};
+
 constexpr int TK_BN = 128;
 constexpr int TK_BOX = BM * TF_KC * 4;               // 16 KB: one plane of one chunk (A, or B with 128 rows)
 constexpr int TK_STAGE = 4 * TK_BOX;                 // A hi, A lo, B hi, B lo
@@ -1746,7 +1754,7 @@ __global__ void __launch_bounds__(256) tf32k_split_kernel(int asA, char op, int 
 template <bool BETA>
 __global__ void __launch_bounds__(TK_THREADS, 1)
     ctf32k_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int m, int n,
-                  int batch, int nk, float alpha, cf *C, long ldc, long sc, int *gerr) {
+                  int batch, int nk, float alpha, cf *C, long ldc, long sc, int *gerr, APlanes ap) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *bars = reinterpret_cast<uint64_t *>(base + TK_NS * TK_STAGE);
@@ -1796,8 +1804,9 @@ __global__ void __launch_bounds__(TK_THREADS, 1)
         }
         unsigned char *st = base + s * TK_STAGE;
         mbar_expect_tx(&full[s], TK_STAGE);
+        const int ach = ch < nk ? ap.c0 + ch : ap.nkh + ap.c0 + (ch - nk);  // chunk in the stored A planes
         for (int pl = 0; pl < 2; ++pl) {
-          tma_load_3d(st + pl * TK_BOX, &ta, &full[s], 0, rb * BM, (pl * batch + b) * nch + ch);
+          tma_load_3d(st + pl * TK_BOX, &ta, &full[s], 0, ap.row0 + rb * BM, (pl * ap.bt + ap.b0 + b) * 2 * ap.nkh + ach);
           tma_load_3d(st + (2 + pl) * TK_BOX, &tb, &full[s], 0, ct * TK_BN, (pl * batch + b) * nch + ch);
         }
       }
@@ -1907,6 +1916,15 @@ static size_t ctf32k_work(int m, int n, int k, int batch) {
   return al((size_t)2 * batch * 2 * nk * (2L * m) * TF_KC * 4) + al((size_t)2 * batch * 2 * nk * (long)n * TF_KC * 4);
 }
 
+static int ctf32k_attrs() {
+  static std::atomic<unsigned long long> attr_done{0};
+  return once_per_device(attr_done, [&]() -> int {
+    GBF_CUDA(cudaFuncSetAttribute(ctf32k_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_SMEM));
+    GBF_CUDA(cudaFuncSetAttribute(ctf32k_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_SMEM));
+    return 0;
+  });
+}
+
 static int ctf32k_run(cudaStream_t st, char opa, char opb, int m, int n, int k, double alpha, const cf *A, long lda,
                       long sa, const cf *B, long ldb, long sb, int beta_one, cf *C, long ldc, long sc, int batch,
                       void *work, size_t work_bytes, int *gerr) {
@@ -1935,23 +1953,68 @@ static int ctf32k_run(cudaStream_t st, char opa, char opb, int m, int n, int k, 
   CUtensorMap ta, tb;
   if (int rc = make_map_tf32(&ta, Ap, rows, 2 * batch * 2 * nk, BM)) return rc;
   if (int rc = make_map_tf32(&tb, Bp, n, 2 * batch * 2 * nk, TK_BN)) return rc;
-  static std::atomic<unsigned long long> attr_done{0};
-  if (int rc = once_per_device(attr_done, [&]() -> int {
-        GBF_CUDA(cudaFuncSetAttribute(ctf32k_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_SMEM));
-        GBF_CUDA(cudaFuncSetAttribute(ctf32k_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_SMEM));
-        return 0;
-      }))
-    return rc;
+  if (int rc = ctf32k_attrs()) return rc;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int items = ceil_div(rows, BM) * ceil_div(n, TK_BN) * batch;
   dim3 grid(std::min(items, sms));
   const int slot = prof_begin(st);
+  const APlanes ap{0, 0, nk, batch, 0};
   if (beta_one)
-    ctf32k_kernel<true><<<grid, TK_THREADS, TK_SMEM, st>>>(ta, tb, m, n, batch, nk, (float)alpha, C, ldc, sc, gerr);
+    ctf32k_kernel<true><<<grid, TK_THREADS, TK_SMEM, st>>>(ta, tb, m, n, batch, nk, (float)alpha, C, ldc, sc, gerr,
+                                                           ap);
   else
-    ctf32k_kernel<false><<<grid, TK_THREADS, TK_SMEM, st>>>(ta, tb, m, n, batch, nk, (float)alpha, C, ldc, sc, gerr);
+    ctf32k_kernel<false><<<grid, TK_THREADS, TK_SMEM, st>>>(ta, tb, m, n, batch, nk, (float)alpha, C, ldc, sc, gerr,
+                                                            ap);
+  prof_end(st, slot, 8.0 * m * (double)n * k * batch);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+
+// The same product with op(A) read from stored TF32 planes (split once and
+// reused, as the factors are by every solve of a FEAST iteration): `pre`
+// holds [plane][bt nodes][2 nkh chunks][prows][32]; this call's op(A) rows
+// start at complex row r0 and its K positions at 32 c0, for nodes b0 ..
+// b0 + batch - 1.  Only B is split here.  Positions of a chunk past k meet
+// B's zero padding, rows past m are computed and not stored.
+static size_t ctf32k_work_pre(int n, int k, int batch) {
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  return al((size_t)2 * batch * 2 * ceil_div(k, TF_KC) * (long)n * TF_KC * 4);
+}
+
+static int ctf32k_run_pre(cudaStream_t st, int m, int n, int k, double alpha, const float *pre, long prows, int nkh,
+                          int bt, int b0, int r0, int c0, char opb, const cf *B, long ldb, long sb, int beta_one,
+                          cf *C, long ldc, long sc, int batch, void *work, size_t work_bytes, int *gerr) {
+  if (k < 1 || (alpha != 1.0 && alpha != -1.0) || ctf32k_work_pre(n, k, batch) > work_bytes ||
+      c0 + ceil_div(k, TF_KC) > nkh || b0 + batch > bt) {
+    set_error("3xTF32 GEMM on stored planes: bad arguments or workspace too small");
+    return -4;
+  }
+  const int nk = ceil_div(k, TF_KC);
+  float *Bp = (float *)work;
+  const int sslot = prof_begin(st);
+  tf32k_split_kernel<cf><<<dim3(ceil_div(n, 32), nk, batch), 256, 0, st>>>(0, opb, n, k, nk, B, ldb, sb, batch, Bp);
+  prof_end(st, sslot, 0.0);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  CUtensorMap ta, tb;
+  if (int rc = make_map_tf32(&ta, pre, prows, 2 * bt * 2 * nkh, BM)) return rc;
+  if (int rc = make_map_tf32(&tb, Bp, n, 2 * batch * 2 * nk, TK_BN)) return rc;
+  if (int rc = ctf32k_attrs()) return rc;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int items = ceil_div(2 * m, BM) * ceil_div(n, TK_BN) * batch;
+  dim3 grid(std::min(items, sms));
+  const int slot = prof_begin(st);
+  const APlanes ap{2 * r0, c0, nkh, bt, b0};
+  if (beta_one)
+    ctf32k_kernel<true><<<grid, TK_THREADS, TK_SMEM, st>>>(ta, tb, m, n, batch, nk, (float)alpha, C, ldc, sc, gerr,
+                                                           ap);
+  else
+    ctf32k_kernel<false><<<grid, TK_THREADS, TK_SMEM, st>>>(ta, tb, m, n, batch, nk, (float)alpha, C, ldc, sc, gerr,
+                                                            ap);
   prof_end(st, slot, 8.0 * m * (double)n * k * batch);
   GBF_LAUNCHED();
   GBF_CUDA(cudaGetLastError());
@@ -2659,6 +2722,29 @@ int cgemm_tf32k(cudaStream_t st, char opa, char opb, int m, int n, int k, double
   if (m <= 0 || n <= 0 || batch <= 0) return 0;
   return tc::ctf32k_run(st, opa, opb, m, n, k, alpha, A, lda, sa, B, ldb, sb, beta_one, C, ldc, sc, batch, work,
                         work_bytes, gerr);
+}
+
+size_t tf32_planes_bytes(int n, int ne) {
+  return (size_t)2 * ne * 2 * ceil_div(n, tc::TF_KC) * (2L * n) * tc::TF_KC * 4;
+}
+
+int tf32_presplit(cudaStream_t st, char op, int n, int ne, const cf *S, float *planes) {
+  const int nkh = ceil_div(n, tc::TF_KC);
+  tc::tf32k_split_kernel<cf><<<dim3(ceil_div(n, 32), nkh, ne), 256, 0, st>>>(1, op, n, n, nkh, S, n, (long)n * n, ne,
+                                                                             planes);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+
+size_t cgemm_tf32k_pre_work(int n, int k, int batch) { return tc::ctf32k_work_pre(n, k, batch); }
+
+int cgemm_tf32k_pre(cudaStream_t st, int m, int n, int k, double alpha, const float *pre, int nfull, int bt, int b0,
+                    int r0, int c0, const cf *B, long ldb, long sb, int beta_one, cf *C, long ldc, long sc, int batch,
+                    void *work, size_t work_bytes, int *gerr) {
+  if (m <= 0 || n <= 0 || batch <= 0) return 0;
+  return tc::ctf32k_run_pre(st, m, n, k, alpha, pre, 2L * nfull, ceil_div(nfull, tc::TF_KC), bt, b0, r0, c0, 'N', B,
+                            ldb, sb, beta_one, C, ldc, sc, batch, work, work_bytes, gerr);
 }
 template int zgemm_sliced<zd>(cudaStream_t, int, char, char, int, int, int, double, const zd *, long, long,
                               const zd *, long, long, int, zd *, long, long, int, void *, size_t, int *);

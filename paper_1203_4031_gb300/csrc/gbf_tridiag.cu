@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
   T *vfull = vpub + m;                 // [m] copy of v
   T *wfull = vfull + m;                // [m] w
   __shared__ T s_pvw[NW];              // each warp's part of v^H p
+  __shared__ T s_pcta;                 // this CTA's part of v^H p
   __shared__ double s_tau;             // published by the owner of row j
   __shared__ T s_sc;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -188,15 +189,19 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
         pv = X::fma(X::conj(vfull[i]), s, pv);
       }
       if (lane == 0) s_pvw[warp] = pv;
-    }
-    cl.sync();  // B2: every CTA's p and parts of v^H p visible
-    if (tj != 0.0) {
-      // (c) v^H p: warp 0 reads the C x NW parts (lane-parallel, then a
-      // fixed-pattern shuffle sum, the same in every CTA); w = p - K v
+      // this CTA's part of v^H p: its warps' parts in warp order
+      __syncthreads();
       if (warp == 0) {
-        T r = X::zero();
-        for (int t = lane; t < C * NW; t += 32) r = X::add(r, *cl.map_shared_rank(&s_pvw[t % NW], t / NW));
-        const T tot = warp_sum(r);
+        const T r = warp_sum(lane < NW ? s_pvw[lane] : X::zero());
+        if (lane == 0) s_pcta = r;
+      }
+    }
+    cl.sync();  // B2: every CTA's p and part of v^H p visible
+    if (tj != 0.0) {
+      // (c) v^H p: warp 0 reads the C parts (one remote load per lane, then
+      // a fixed-pattern shuffle sum, the same in every CTA); w = p - K v
+      if (warp == 0) {
+        const T tot = warp_sum(lane < C ? *cl.map_shared_rank(&s_pcta, lane) : X::zero());
         if (lane == 0) s_sc = tot;
       }
       __syncthreads();
