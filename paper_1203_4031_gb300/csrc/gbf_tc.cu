@@ -1137,7 +1137,8 @@ constexpr int TF_NB = 4;                          // B ring depth
 constexpr int TF_NB_TC = 2;                       // B ring depth with the C tiles staged in shared memory
 constexpr int TF_C_TILE = BM * TF_BN * 4;         // 32 KB: one C tile (128 embedded rows x 64 columns, FP32)
 constexpr int TF_SMEM = TF_A_TILE + TF_NB * TF_B_TILE + 1024 + 256;
-constexpr int TF_SMEM_TC = TF_A_TILE + TF_NB_TC * TF_B_TILE + 2 * TF_C_TILE + 1024 + 256;
+constexpr int TF_NC = 3;                          // C tile buffers (staged C)
+constexpr int TF_SMEM_TC = TF_A_TILE + TF_NB_TC * TF_B_TILE + TF_NC * TF_C_TILE + 1024 + 256;
 constexpr int TF_EC = 16;                         // columns per epilogue warp
 constexpr int TF_EW = 4 * (TF_BN / TF_EC);        // epilogue warps
 constexpr int TF_THREADS = 64 + 32 * TF_EW;
@@ -1258,14 +1259,14 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
   unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char *sA = base;               // [plane][chunk][128][32] FP32
   unsigned char *sB = base + TF_A_TILE;   // NBT x [plane][chunk][64][32]
-  float *sC = reinterpret_cast<float *>(base + TF_A_TILE + NBT * TF_B_TILE);  // TC: 2 x [64 cols][128 rows]
-  uint64_t *bars = reinterpret_cast<uint64_t *>(base + TF_A_TILE + NBT * TF_B_TILE + (TC ? 2 * TF_C_TILE : 0));
+  float *sC = reinterpret_cast<float *>(base + TF_A_TILE + NBT * TF_B_TILE);  // TC: TF_NC x [64 cols][128 rows]
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + TF_A_TILE + NBT * TF_B_TILE + (TC ? TF_NC * TF_C_TILE : 0));
   uint64_t *a_full = bars, *a_empty = bars + 1;
   uint64_t *b_full = bars + 2, *b_empty = b_full + NBT;
   uint64_t *acc_full = b_empty + NBT, *acc_empty = acc_full + 2;
-  uint64_t *c_full = acc_empty + 2, *c_empty = c_full + 2;  // TC: C tile landed / stored out of the buffer
-  uint64_t *epi_done = c_empty + 2;                         // TC: all epilogue warps wrote the tile
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(epi_done + 2);
+  uint64_t *c_full = acc_empty + 2, *c_empty = c_full + TF_NC;  // TC: C tile landed / stored out of the buffer
+  uint64_t *epi_done = c_empty + TF_NC;                         // TC: all epilogue warps wrote the tile
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(epi_done + TF_NC);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rows = 2 * m;
@@ -1282,6 +1283,8 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
     for (int j = 0; j < 2; ++j) {
       mbar_init(&acc_full[j], 1);
       mbar_init(&acc_empty[j], TF_EW);  // one arrival per epilogue warp
+    }
+    for (int j = 0; j < TF_NC; ++j) {
       mbar_init(&c_full[j], 1);
       mbar_init(&c_empty[j], 1);
       mbar_init(&epi_done[j], TF_EW);
@@ -1325,9 +1328,9 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
           tma_load_3d(sB + st * TF_B_TILE + pc * TF_B_BOX, &tb, &b_full[st], 0, ct * TF_BN,
                       ((pc >> 1) * batch + b) * 2 + (pc & 1));
         last_b = g;
-        if (TC && BETA) {  // C tile g into buffer g % 2 once the store of tile g - 2 has read it
-          const int cb = g & 1;
-          if (g >= 2 && !mbar_wait(&c_empty[cb], ((g >> 1) - 1) & 1, abort_flag, gerr, 50)) {
+        if (TC && BETA) {  // C tile g into buffer g % TF_NC once the store of tile g - TF_NC has read it
+          const int cb = g % TF_NC;
+          if (g >= TF_NC && !mbar_wait(&c_empty[cb], ((g / TF_NC) - 1) & 1, abort_flag, gerr, 50)) {
             ok = false;
             break;
           }
@@ -1340,8 +1343,8 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
     if (it_local > 0) mbar_drain(a_full, (it_local - 1) & 1, gerr, 43);
     for (int gg = (last_b - NBT + 1 > 0 ? last_b - NBT + 1 : 0); gg <= last_b; ++gg)
       mbar_drain(&b_full[gg % NBT], (gg / NBT) & 1, gerr, 44);
-    for (int gg = (last_c - 1 > 0 ? last_c - 1 : 0); gg <= last_c; ++gg)
-      mbar_drain(&c_full[gg & 1], (gg >> 1) & 1, gerr, 51);
+    for (int gg = (last_c - TF_NC + 1 > 0 ? last_c - TF_NC + 1 : 0); gg <= last_c; ++gg)
+      mbar_drain(&c_full[gg % TF_NC], (gg / TF_NC) & 1, gerr, 51);
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA --
     constexpr uint32_t idesc = idesc_tf32();
@@ -1384,11 +1387,11 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
   } else if (TC && warp >= 2) {
     // ------------------------------------------- epilogue, C staged --
     // The C tile (128 embedded rows x 64 columns, [column][row] FP32) is in
-    // shared memory buffer g % 2; warp w updates rows 32 (w % 4) .. +31 of
-    // columns c0 .. c0 + 15 in place, then arrives on epi_done; thread 0 of
-    // warp 2 waits for all 16 warps, stores the tile with one bulk tensor
-    // copy and frees the buffer for the load of tile g + 2 once the copy has
-    // read it.
+    // shared memory buffer g % TF_NC; warp w updates rows 32 (w % 4) .. +31
+    // of columns c0 .. c0 + 15 in place, then arrives on epi_done; thread 0
+    // of warp 2 waits for all 16 warps, stores the tile with one bulk tensor
+    // copy and frees the buffer for the load of tile g + TF_NC once the copy
+    // has read it.
     const int q = warp & 3, c0 = ((warp - 2) >> 2) * TF_EC;
     const bool issuer = (warp == 2 && lane == 0);
     int item = blockIdx.x, ct = 0, ct1 = 0;
@@ -1397,11 +1400,11 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
       ct1 = min(nct, ct + tpc);
     }
     for (int g = 0; item < items; ++g) {
-      const int buf = g & 1, use = g >> 1;
+      const int buf = g & 1, use = g >> 1, cb = g % TF_NC, cuse = g / TF_NC;
       int okw = 0;
       if (lane == 0)
         okw = (mbar_wait(&acc_full[buf], use & 1, abort_flag, gerr, 49) &&
-               (!BETA || mbar_wait(&c_full[buf], use & 1, abort_flag, gerr, 52)))
+               (!BETA || mbar_wait(&c_full[cb], cuse & 1, abort_flag, gerr, 52)))
                   ? 1
                   : 0;
       if (__shfl_sync(0xffffffffu, okw, 0) == 0) break;
@@ -1415,7 +1418,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
       if (lane == 0)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(&acc_empty[buf])) : "memory");
       const int rb = (item / nch) % nrb, b = item / (nch * nrb);
-      float *tile = sC + buf * (TF_C_TILE / 4) + q * 32 + lane;
+      float *tile = sC + cb * (TF_C_TILE / 4) + q * 32 + lane;
 #pragma unroll
       for (int j = 0; j < TF_EC; ++j) {
         const float v = __uint_as_float(acc[j]);
@@ -1425,18 +1428,18 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0)
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(&epi_done[buf])) : "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(&epi_done[cb])) : "memory");
       int stored = 1;
-      if (issuer) stored = mbar_wait(&epi_done[buf], use & 1, abort_flag, gerr, 53) ? 1 : 0;
+      if (issuer) stored = mbar_wait(&epi_done[cb], cuse & 1, abort_flag, gerr, 53) ? 1 : 0;
       if (issuer && stored) {
         asm volatile(
             "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
                 reinterpret_cast<uint64_t>(&tcm)),
-            "r"(sm_u32(sC + buf * (TF_C_TILE / 4))), "r"(rb * BM), "r"(ct * TF_BN), "r"(b)
+            "r"(sm_u32(sC + cb * (TF_C_TILE / 4))), "r"(rb * BM), "r"(ct * TF_BN), "r"(b)
             : "memory");
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(&c_empty[buf])) : "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(&c_empty[cb])) : "memory");
       }
       if (__shfl_sync(0xffffffffu, stored, 0) == 0) break;  // warp-uniform (lane 0 decides)
       int nitem = item, nct0 = ct + 1;
