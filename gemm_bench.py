@@ -5,12 +5,16 @@ kernel in isolation:
   python gemm_bench.py --kind k32 --m 4096 --n 300 --k 32 --batch 8
   python gemm_bench.py --kind anyk --cplx 1 --m 2048 --n 300 --k 2048
   python gemm_bench.py --kind tf32 --m 4096 --n 4096 --k 32 --batch 2
+  python gemm_bench.py --kind lu --m 4096 --batch 8 --prec 1
 
 k32: gbf_zgemm_sliced (k <= 32, 7 digits, complex FP64), C -= A B.
 tf32: gbf_zgemm_sliced with S = 1 (k <= 32, complex FP32, 3xTF32 products),
 C -= A B: the engine of the FP32 factorisation's trailing updates.
 anyk: gbf_gemm_sliced (any k, 8 digits, real or complex FP64), C -= op(A) B with
 op(A) = A^T read from an (m x k)-transposed store, as the projections use it.
+lu: gbf_factor_dev, the blocked LU of `batch` shifted systems z_e I - A of one
+m x m complex Hermitian A (panels, swaps, trailing updates), FP64 factors
+(--prec 0) or FP32 (--prec 1).
 Prints the time per call (CUDA events, after warm-up) and the useful FP64
 rate; inputs are seeded normal values resident on the device."""
 import argparse
@@ -25,7 +29,8 @@ from paper_1203_4031_gb300 import _ptr, _stream_ptr, last_error, lib  # noqa: E4
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kind", choices=["k32", "anyk", "tf32"], default="k32")
+    ap.add_argument("--kind", choices=["k32", "anyk", "tf32", "lu"], default="k32")
+    ap.add_argument("--prec", type=int, default=0)
     ap.add_argument("--cplx", type=int, default=1)
     ap.add_argument("--m", type=int, default=4096)
     ap.add_argument("--n", type=int, default=300)
@@ -36,6 +41,8 @@ def main(argv=None):
     a = ap.parse_args(argv)
     L = lib()
     g = torch.Generator(device="cuda").manual_seed(1)
+    if a.kind == "lu":
+        return factor_bench(a, g)
     cplx = 1 if a.kind in ("k32", "tf32") else a.cplx
     dt = torch.complex128 if cplx else torch.float64
     m, n, k, bt = a.m, a.n, a.k, a.batch
@@ -89,6 +96,35 @@ def main(argv=None):
     cbytes = 2 * C.numel() * C.element_size()   # C read and written once
     print(f"{a.kind} cplx={cplx} m={m} n={n} k={k} batch={bt}: {ms * 1e3:.1f} us per call "
           f"(slicing included), {flops / ms / 1e9:.2f} useful {what} TFLOP/s, C traffic {cbytes / ms / 1e6:.0f} GB/s")
+
+
+def factor_bench(a, g):
+    import numpy as np
+
+    import paper_1203_4031_gb300 as gb
+
+    n, ne = a.m, a.batch
+    X = torch.complex(torch.randn(n, n, device="cuda", dtype=torch.float64, generator=g),
+                      torch.randn(n, n, device="cuda", dtype=torch.float64, generator=g))
+    A = gb.fortran(0.5 * (X + X.conj().T))
+    zne = np.exp(1j * np.pi * (np.arange(ne) + 0.5) / ne)   # nodes on the unit half-circle
+    h = gb.Handle()
+    for _ in range(a.warmup):
+        if gb.gbf_factor_dev(h, A, None, zne, prec=a.prec) != 0:
+            raise RuntimeError(last_error())
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(a.reps):
+        gb.gbf_factor_dev(h, A, None, zne, prec=a.prec)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(a.reps, 1)
+    flops = 8.0 / 3.0 * n ** 3 * ne
+    print(f"lu prec={a.prec} n={n} nodes={ne}: {ms:.2f} ms per factorisation of all nodes, "
+          f"{flops / ms / 1e9:.2f} useful TFLOP/s")
+    h.close()
 
 
 if __name__ == "__main__":
