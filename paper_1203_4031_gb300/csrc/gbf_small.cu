@@ -102,33 +102,33 @@ __global__ void recip_diag_kernel(int m, const T *L, double *rd) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < m) rd[i] = 1.0 / tr<T>::re(L[i + (long)i * m]);
 }
+// Column j of L^{-1} by one warp, in the column-oriented (axpy) form of the
+// forward substitution: the running sums acc_i = sum_{k<i} L_ik x_k sit in
+// shared memory; at step k the warp forms x_k = (delta_kj - acc_k) / L_kk
+// and adds L_ik x_k into acc_i for every i > k, the lanes on consecutive
+// rows (coalesced column of L).  One dependent step per row and no
+// reduction across lanes.
 template <class T>
-__global__ void trinv_lower_kernel(int m, const T *L, const double *rd, T *Linv) {
+__global__ void __launch_bounds__(256) trinv_lower_kernel(int m, const T *L, const double *rd, T *Linv) {
   using X = tr<T>;
-  const int lane = threadIdx.x & 31;
-  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (j >= m) return;
-  T *x = Linv + (long)j * m;
-  for (int i = lane; i < m; i += 32) x[i] = X::zero();
+  extern __shared__ __align__(16) unsigned char tsm_raw[];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int j = blockIdx.x * (blockDim.x >> 5) + wl;
+  if (j >= m) return;  // warp-uniform; no block-wide barrier below
+  T *acc = reinterpret_cast<T *>(tsm_raw) + (long)wl * m;
+  for (int i = j + lane; i < m; i += 32) acc[i] = X::zero();
   __syncwarp();
-  for (int i = j; i < m; ++i) {
-    // x_i = (delta_ij - sum_{k=j}^{i-1} L_ik x_k) / L_ii
-    T s = X::zero();
-    for (int k = j + lane; k < i; k += 32) s = X::fma(L[i + (long)k * m], x[k], s);
-    for (int off = 16; off > 0; off >>= 1) {
-      if constexpr (tr<T>::cplx) {
-        s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
-        s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
-      } else {
-        s += __shfl_xor_sync(0xffffffffu, s, off);
-      }
-    }
-    if (lane == 0) {
-      T rhs = (i == j) ? X::sub(X::one(), s) : X::neg(s);
-      x[i] = X::mul(rhs, cvt<T, double>(rd[i]));
-    }
+  for (int k = j; k < m; ++k) {
+    const T a = acc[k];
+    const T xk = X::mul((k == j) ? X::sub(X::one(), a) : X::neg(a), cvt<T, double>(rd[k]));
+    __syncwarp();
+    const T *Lk = L + (long)k * m;
+    for (int i = k + 1 + lane; i < m; i += 32) acc[i] = X::fma(Lk[i], xk, acc[i]);
+    if (lane == 0) acc[k] = xk;
     __syncwarp();
   }
+  T *x = Linv + (long)j * m;
+  for (int i = lane; i < m; i += 32) x[i] = (i < j) ? X::zero() : acc[i];
 }
 
 template <class T>
@@ -150,7 +150,20 @@ template <class T>
 int trinv_lower(cudaStream_t st, int m, const T *L, T *Linv, double *rd) {
   recip_diag_kernel<T><<<ceil_div(m, 256), 256, 0, st>>>(m, L, rd);
   GBF_LAUNCHED();
-  trinv_lower_kernel<T><<<ceil_div((long)m * 32, 256), 256, 0, st>>>(m, L, rd, Linv);
+  // warps per block: as many columns' running sums as fit 48 KB of shared
+  // memory (one column up to 200 KB)
+  if ((size_t)m * sizeof(T) > 200 * 1024) {
+    set_error("triangular inverse: m too large (%d)", m);
+    return -4;
+  }
+  static std::atomic<unsigned long long> attr_done{0};
+  if (int rc = once_per_device(attr_done, [&]() -> int {
+        GBF_CUDA(cudaFuncSetAttribute(trinv_lower_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        return 0;
+      }))
+    return rc;
+  const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (48 * 1024) / ((size_t)m * sizeof(T))));
+  trinv_lower_kernel<T><<<ceil_div(m, wpb), 32 * wpb, (size_t)wpb * m * sizeof(T), st>>>(m, L, rd, Linv);
   GBF_LAUNCHED();
   GBF_CUDA(cudaGetLastError());
   return 0;

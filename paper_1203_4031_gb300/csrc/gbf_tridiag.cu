@@ -58,10 +58,42 @@ __device__ inline double shfl_x(double v, int o) { return __shfl_xor_sync(0xffff
 __device__ inline zd shfl_x(zd v, int o) {
   return zd{__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)};
 }
-template <class T> __device__ inline T warp_sum(T v) {
-  for (int o = 16; o > 0; o >>= 1) v = tr<T>::add(v, shfl_x(v, o));
-  return v;
+// Sum over the warp of one double per lane, exactly in fixed point and
+// rounded once: each value is shifted to the warp's largest exponent (57
+// significant bits kept; the bits dropped lie below 2^-57 of the largest
+// term), the 32 integers are summed by hardware warp reductions on three
+// 20-bit chunks (no carry can leave a chunk), and the sum is converted once.
+// Independent of the lanes' order, hence the same in every CTA.  In these
+// kernels a shuffle-and-add butterfly took several times longer than its
+// latency in isolation while the other CTAs' remote loads were being served.
+// Zero, infinite or NaN extremes take the butterfly.
+__device__ inline double warp_sum_fx(double v) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  const unsigned emax = __reduce_max_sync(0xffffffffu, (unsigned)ex);
+  if (emax == 0 || emax == 0x7FF) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+  }
+  const unsigned long long mant = (bits & 0x000FFFFFFFFFFFFFull) | (ex ? 0x0010000000000000ull : 0ull);
+  const int sh = (int)emax - (ex ? ex : 1);  // >= 0
+  const long long q = sh > 57 ? 0LL : (long long)((mant << 4) >> sh);  // < 2^57
+  const unsigned long long u = (unsigned long long)((bits >> 63) ? -q : q) + (1ull << 57);  // in [0, 2^58)
+  const unsigned c0 = __reduce_add_sync(0xffffffffu, (unsigned)(u & 0xFFFFFu));
+  const unsigned c1 = __reduce_add_sync(0xffffffffu, (unsigned)((u >> 20) & 0xFFFFFu));
+  const unsigned c2 = __reduce_add_sync(0xffffffffu, (unsigned)(u >> 40));
+  const long long sum = (long long)((unsigned long long)c0 + ((unsigned long long)c1 << 20) +
+                                    ((unsigned long long)c2 << 40) - (32ull << 57));
+  // value = sum 2^(emax - 1075 - 4); emax - 1079 >= -1078 may be below the
+  // normal range: scale in two exact steps
+  const int e2 = (int)emax - 1079;
+  const double h = __longlong_as_double((long long)(e2 / 2 + 1023) << 52);
+  const double r = __longlong_as_double((long long)(e2 - e2 / 2 + 1023) << 52);
+  return (__ll2double_rn(sum) * h) * r;
 }
+__device__ inline double warp_sum_v(double v) { return warp_sum_fx(v); }
+__device__ inline zd warp_sum_v(zd v) { return zd{warp_sum_fx(v.x), warp_sum_fx(v.y)}; }
+template <class T> __device__ inline T warp_sum(T v) { return warp_sum_v(v); }
 
 // Deterministic CTA sum of one value per thread (fixed shuffle pattern, then
 // the warps' partials in warp order, added by one thread: FP64 instructions
