@@ -267,3 +267,124 @@ def serving_matrices(req: dict, device="cuda"):
     A = 0.5 * (A + A.T)
     B = 0.5 * (B + B.T)
     return A.t().contiguous().t(), B.t().contiguous().t(), a, b
+
+
+# ------------------------------------------------------- non-Hermitian --
+def _reflect_left(M: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """(I - 2 v v^H / v^H v) M."""
+    beta = 2.0 / np.real(np.vdot(v, v))
+    return M - beta * np.outer(v, v.conj() @ M)
+
+
+def _reflect_right(M: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """M (I - 2 v v^H / v^H v)."""
+    beta = 2.0 / np.real(np.vdot(v, v))
+    return M - beta * np.outer(M @ v, v.conj())
+
+
+@dataclass
+class GeneralProblem:
+    """A non-Hermitian pencil (A, B) with a known spectrum and a circular
+    contour (centre emid, radius r) holding exactly `count` eigenvalues."""
+    name: str
+    complex_: bool                  # False: A, B real non-symmetric
+    A: np.ndarray
+    B: np.ndarray | None
+    emid: complex
+    r: float
+    m0: int
+    spectrum: np.ndarray
+    count: int
+    fpm: dict = field(default_factory=dict)
+    note: str = ""
+
+    @property
+    def n(self) -> int:
+        return self.A.shape[0]
+
+    def apply_fpm(self, fpm):
+        for i, v in self.fpm.items():
+            fpm[i - 1] = v
+        return fpm
+
+
+def general_spectrum(n: int, seed: int, complex_: bool) -> np.ndarray:
+    """Eigenvalues of dense_nonsymmetric: complex: uniform in the box
+    [-1, 1] x [-1/2, 1/2]; real: half of them real, uniform in [-1, 1], the
+    rest conjugate pairs a +- ib, a ~ U[-1, 1], b ~ U(0, 1/2]."""
+    if complex_:
+        return uniform(derive_seed(seed, 11), n) + 0.5j * uniform(derive_seed(seed, 12), n)
+    npair = n // 4
+    nreal = n - 2 * npair
+    re = uniform(derive_seed(seed, 11), nreal)
+    a = uniform(derive_seed(seed, 12), npair)
+    b = 0.5 * (1.0 - uniform01(derive_seed(seed, 13), npair))
+    lam = np.concatenate([re.astype(np.complex128), a + 1j * b, a - 1j * b])
+    return lam
+
+
+def dense_nonsymmetric(n: int = 4096, count: int = 40, m0: int = 64, ne: int = 16, complex_: bool = False,
+                       generalized: bool = False, emid: complex | None = None, seed: int = 20260106,
+                       nref: int = 4) -> GeneralProblem:
+    """Non-normal dense pencil with a known spectrum and well-conditioned
+    eigenvectors.  M = S D S^{-1} with S = H_1 diag(s) H_2 (H_i products of
+    `nref` seeded reflectors, s ~ U[1, 2], so cond(S) <= 2) and D the
+    spectrum (real problems: 1x1 blocks and 2x2 blocks [[a, b], [-b, a]]).
+    Standard: A = M.  Generalized: B = G_1 diag(mu) G_2 (mu log-uniform in
+    [1, 10], its own reflectors, non-symmetric) and A = B M, so that the
+    pencil's eigenvalues are D's.  The circle is centred at emid (real for
+    real problems, so that the node set is conjugate-symmetric) with the
+    radius halfway between the count-th and next distance to emid."""
+    lam = general_spectrum(n, seed, complex_)
+    dt = np.complex128 if complex_ else np.float64
+    D = np.zeros((n, n), dtype=dt)
+    if complex_:
+        D[np.arange(n), np.arange(n)] = lam
+    else:
+        npair = n // 4
+        nreal = n - 2 * npair
+        D[np.arange(nreal), np.arange(nreal)] = lam[:nreal].real
+        for k in range(npair):
+            i = nreal + 2 * k
+            a, b = lam[nreal + k].real, lam[nreal + k].imag
+            D[i, i] = D[i + 1, i + 1] = a
+            D[i, i + 1] = b
+            D[i + 1, i] = -b
+    s = 1.0 + uniform01(derive_seed(seed, 21), n)
+    h1 = reflector_vectors(derive_seed(seed, 22), n, nref, complex_=complex_)
+    h2 = reflector_vectors(derive_seed(seed, 23), n, nref, complex_=complex_)
+    # M = H1 diag(s) H2 D H2^H diag(1/s) H1^H (H_i Hermitian unitary products)
+    M = D
+    for v in h2:
+        M = _reflect_right(_reflect_left(M, v), v)
+    M = (s[:, None] * M) / s[None, :]
+    for v in h1:
+        M = _reflect_right(_reflect_left(M, v), v)
+    B = None
+    if generalized:
+        mu = 10.0 ** uniform(derive_seed(seed, 31), n, 0.0, 1.0)
+        g1 = reflector_vectors(derive_seed(seed, 32), n, nref, complex_=complex_)
+        g2 = reflector_vectors(derive_seed(seed, 33), n, nref, complex_=complex_)
+        # B = G1 diag(mu) G2, A = B M = G1 diag(mu) (G2 M)
+        Am = M.copy()
+        G2 = np.eye(n, dtype=dt)
+        for v in reversed(g2):
+            G2 = _reflect_left(G2, v)
+            Am = _reflect_left(Am, v)
+        Bm = mu[:, None] * G2
+        Am = mu[:, None] * Am
+        for v in reversed(g1):
+            Bm = _reflect_left(Bm, v)
+            Am = _reflect_left(Am, v)
+        A, B = Am, Bm
+    else:
+        A = M
+    if emid is None:
+        emid = 0.1 + (0.05j if complex_ else 0.0)
+    dist = np.sort(np.abs(lam - emid))
+    r = float(0.5 * (dist[count - 1] + dist[count]))
+    kind = "complex" if complex_ else "real"
+    return GeneralProblem(f"{kind}-nonsymmetric{'-generalized' if generalized else ''}-n{n}", bool(complex_),
+                          np.asfortranarray(A), None if B is None else np.asfortranarray(B), complex(emid), r, m0,
+                          lam, count, fpm={8: ne, 3: 10, 6: 1},
+                          note="S D S^-1, cond(S) <= 2; generalized: A = B M, B = G1 diag(mu) G2")
