@@ -225,6 +225,64 @@ int gbf_zhegv_dev_shard(gbf_handle h, void *stream, char uplo, int n, const doub
                         const gbf_shard *sh);
 
 /* ---------------------------------------------------------------------
+ * Non-Hermitian FEAST (guide section "From v2.1 to v3.0": dual subspaces Q,
+ * Q^ for the right and left eigenvectors; RCI cases 10/11/21/30/31/40/41 of
+ * Table "tab_ijob"; outputs of Table "tab_common" for the general types).
+ * Dense A (and B) of any structure, all eigenvalues inside an ellipse of
+ * centre Emid = (emid_re, emid_im), horizontal semi-axis r,
+ * vertical/horizontal ratio fpm(18)/100, rotated by fpm(19) degrees.
+ * ------------------------------------------------------------------- */
+/* Full-contour nodes and weights (the guide's gcontour tool): fpm(8) = ne
+ * points, fpm(17) = 0 Gauss, 1 trapezoidal in the angle t of z(t) = Emid +
+ * r e^{i phi} (cos t + i rho sin t); f(lambda) = sum_e w_e / (z_e - lambda)
+ * approximates 1 inside and 0 outside.  Gauss: t_e = pi (1 + x_e) (x the
+ * ascending Legendre points, omega their weights); trapezoidal: t_e =
+ * 2 pi (e + 1/2) / ne, omega_e = 2 / ne; w_e = (omega_e / 2) r e^{i phi}
+ * (rho cos t_e + i sin t_e).  Zne, Wne: ne complex (host).  Returns 0, 200
+ * (r <= 0), 108, 117, 118 or 119 (bad fpm(8), fpm(17), fpm(18), fpm(19)). */
+int gbf_gcontour(double emid_re, double emid_im, double r, int ne, int fpm17, int fpm18, int fpm19, double *Zne,
+                 double *Wne);
+/* f(eig_i) = sum_e Wne_e / (Zne_e - eig_i) for m complex eig (host; f complex). */
+int gbf_grationalx(const double *Zne, const double *Wne, int ne, const double *eig, int m, double *f);
+
+/* Solve A x = lambda B x (dB NULL: the standard problem, the guide's
+ * [dz]feast_geev; otherwise [dz]feast_gegv), A, B general dense: real
+ * (gbf_dgegv_dev, dA/dB doubles) or complex (gbf_zgegv_dev).  Device
+ * pointers; the work runs on `stream` and the call returns after it.
+ *  - fpm: fpm(8) nodes (default 16), fpm(17) rule (default 1, trapezoidal),
+ *    fpm(18), fpm(19) the ellipse; fpm(3), fpm(4), fpm(5), fpm(6), fpm(14) =
+ *    0/1 and fpm(43), fpm(44) as above.  The factors are complex FP64 (fpm(42)
+ *    is ignored).  For real A, B, a real Emid, fpm(19) = 0 and an even
+ *    fpm(8), the nodes pair up as z and conj(z) and only fpm(8)/2 systems are
+ *    factored (the guide's remark on real non-symmetric problems).
+ *  - *M0 (1..min(n, 1024)): subspace size.  dE: M0 complex eigenvalues,
+ *    the M inside first, each group ordered by ascending (Re, Im).  dX:
+ *    complex n x 2 M0 (ld n): right eigenvectors in columns 0..M0-1 (unit
+ *    2-norm), left ones in columns M0..2 M0-1, scaled so that the returned
+ *    pairs are bi-orthonormal (X^^H B X = I).  dres: 2 M0 residuals,
+ *    right ||A x - lambda B x||_1 / ||alpha B x||_1, then left
+ *    ||A^H x^ - conj(lambda) B^H x^||_1 / ||alpha B^H x^||_1, alpha =
+ *    |Emid| + r.  fpm(14) = 1: dX holds Q and Q^ after one contour, info 4.
+ *  - Convergence: fpm(6) = 1 on the largest right or left residual of the
+ *    pairs inside, fpm(6) = 0 on |trace_k - trace_{k-1}| / alpha (complex
+ *    trace of the pairs inside).
+ *  - info: 0, 1 (none inside), 2 (loops > fpm(4)), 3 (M0 too small), 4,
+ *    6 (converged, but the returned pairs' bi-orthonormality defect
+ *    max |X^^H B X - I| exceeds 1e-8), 200/201/202/1xx (bad arguments),
+ *    -1 (device memory), -2 (zero pivot or non-finite input/results), -3
+ *    (the reduced pencil is singular), -4 (CUDA error, bounded wait timed
+ *    out, or the reduced QR did not converge). */
+int gbf_dgegv_dev(gbf_handle h, void *stream, int n, const double *dA, int lda, const double *dB, int ldb, int *fpm,
+                  double *epsout, int *loop, double emid_re, double emid_im, double r, int *M0, double *dE,
+                  double *dX, int *M, double *dres, int *info, const double *Zne, const double *Wne);
+int gbf_zgegv_dev(gbf_handle h, void *stream, int n, const double *dA, int lda, const double *dB, int ldb, int *fpm,
+                  double *epsout, int *loop, double emid_re, double emid_im, double r, int *M0, double *dE,
+                  double *dX, int *M, double *dres, int *info, const double *Zne, const double *Wne);
+/* max |X^^H B X - I| over the pairs inside of the last converged
+ * non-Hermitian solve on this handle (the quantity info 6 tests). */
+double gbf_biorth_defect(gbf_handle h);
+
+/* ---------------------------------------------------------------------
  * Step-level entry points (device pointers) exposing single rows of the
  * hot path for verification and for callers that drive the iteration
  * themselves (the RCI pattern of Fig. "fig_rci").

@@ -53,6 +53,14 @@ def load(build: bool = True):
     L.gbf_dsygv_dev_shard.argtypes = dev + [vp]
     L.gbf_zhegv_dev_shard.argtypes = dev + [vp]
     L.gbf_shard_nodes.argtypes = [C.c_int, C.c_int, C.c_int, ip, ip]
+    gen = [vp, vp, C.c_int, vp, C.c_int, vp, C.c_int, ip, dp, ip, C.c_double, C.c_double, C.c_double, ip, vp, vp,
+           ip, vp, ip, vp, vp]
+    L.gbf_dgegv_dev.argtypes = gen
+    L.gbf_zgegv_dev.argtypes = gen
+    L.gbf_gcontour.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
+    L.gbf_grationalx.argtypes = [vp, vp, C.c_int, vp, C.c_int, vp]
+    L.gbf_biorth_defect.argtypes = [vp]
+    L.gbf_biorth_defect.restype = C.c_double
     L.gbf_factor_dev.argtypes = [vp, vp, C.c_int, C.c_int, C.c_char, C.c_int, vp, C.c_int, vp, C.c_int, C.c_int, vp]
     L.gbf_solve_dev.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp]
     L.gbf_heev_dev.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp, vp]
@@ -293,6 +301,69 @@ def feast_dev(A, B, emin, emax, m0, fpm=None, E=None, X=None, res=None, uplo="F"
        _ip(fpm), C.byref(eps), C.byref(loop), float(emin), float(emax), C.byref(M0), _ptr(E), _ptr(X),
        C.byref(M), _ptr(res), C.byref(info), zp, wp)
     return dict(E=E, X=X, res=res, M=M.value, loop=loop.value, epsout=eps.value, m0=M0.value, info=info.value)
+
+
+def gbf_gcontour(emid, r, ne, fpm17=1, fpm18=100, fpm19=0):
+    """Full-contour nodes and weights of the non-Hermitian drivers."""
+    z = np.zeros(ne, dtype=np.complex128)
+    w = np.zeros(ne, dtype=np.complex128)
+    emid = complex(emid)
+    rc = lib().gbf_gcontour(emid.real, emid.imag, float(r), int(ne), int(fpm17), int(fpm18), int(fpm19), _ptr(z),
+                            _ptr(w))
+    if rc:
+        raise ValueError(f"gbf_gcontour failed ({rc})")
+    return z, w
+
+
+def gbf_grationalx(zne, wne, eig):
+    """f(eig) = sum_e w_e / (z_e - eig) for complex eig (host)."""
+    zne = np.ascontiguousarray(zne, dtype=np.complex128)
+    wne = np.ascontiguousarray(wne, dtype=np.complex128)
+    eig = np.ascontiguousarray(eig, dtype=np.complex128)
+    f = np.zeros(eig.shape[0], dtype=np.complex128)
+    lib().gbf_grationalx(_ptr(zne), _ptr(wne), len(zne), _ptr(eig), eig.shape[0], _ptr(f))
+    return f
+
+
+def feast_gen_dev(A, B, emid, r, m0, fpm=None, X=None, handle=None, stream=None, Zne=None, Wne=None):
+    """Non-Hermitian drivers gbf_dgegv_dev (real A, B) / gbf_zgegv_dev
+    (complex) on torch CUDA tensors (column-major; B None for the standard
+    problem).  Returns E (m0 complex), X (n x 2 m0 complex: right, then left
+    vectors; read as the initial guesses when fpm(5)=1), res (2 m0), M, loop,
+    epsout, info and the bi-orthonormality defect of a converged solve."""
+    import torch
+
+    if fpm is None:
+        fpm = gbf_init()
+    fpm = np.ascontiguousarray(fpm, dtype=np.int32).copy()
+    cplx = A.is_complex()
+    n = A.shape[0]
+    lda = _check_colmajor(A, n)
+    ldb = _check_colmajor(B, n) if B is not None else n
+    dev = A.device
+    E = torch.zeros(m0, dtype=torch.complex128, device=dev)
+    res = torch.zeros(2 * m0, dtype=torch.float64, device=dev)
+    if X is None:
+        X = torch.zeros((2 * m0, n), dtype=torch.complex128, device=dev).t()
+    elif X.stride(0) != 1 or X.stride(1) != n or X.dtype != torch.complex128:
+        raise ValueError("X must be complex128, column-major n x 2 m0 with ld n")
+    eps, loop, M, info = _scalars()
+    M0 = C.c_int(int(m0))
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    sp = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    zp = wp = None
+    if Zne is not None:
+        zne = np.ascontiguousarray(Zne, dtype=np.complex128)
+        wne = np.ascontiguousarray(Wne, dtype=np.complex128)
+        zp, wp = _ptr(zne), _ptr(wne)
+    emid = complex(emid)
+    fn = lib().gbf_zgegv_dev if cplx else lib().gbf_dgegv_dev
+    h = handle.h if handle is not None else None
+    fn(h, sp, n, _ptr(A), lda, _ptr(B), ldb, _ip(fpm), C.byref(eps), C.byref(loop), emid.real, emid.imag,
+       float(r), C.byref(M0), _ptr(E), _ptr(X), C.byref(M), _ptr(res), C.byref(info), zp, wp)
+    bi = lib().gbf_biorth_defect(h) if h is not None else None
+    return dict(E=E, X=X, res=res, M=M.value, loop=loop.value, epsout=eps.value, info=info.value, biorth=bi)
 
 
 def gbf_factor_dev(handle, A, B, zne, prec=0, uplo="F", stream=None):

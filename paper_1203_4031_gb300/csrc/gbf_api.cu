@@ -60,6 +60,7 @@ struct gbf_context {
   // factors kept by gbf_factor_dev
   int f_n = 0, f_ne = 0, f_prec = -1, f_bs = 32;
   size_t f_bytes = 0;
+  double gen_biorth = 0.0;  // bi-orthonormality defect of the last converged non-Hermitian solve
 };
 
 // ------------------------------------------------------------ quadrature --
@@ -865,6 +866,436 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
   }
 }
 
+// ------------------------------------------------- non-Hermitian driver --
+// Full-contour nodes and weights (guide: the gcontour tool).  On z(t) =
+// Emid + r e^{i phi} (cos t + i rho sin t), t in [0, 2 pi), the residue
+// theorem's (1 / 2 pi i) dz = (r e^{i phi} / 2 pi) (rho cos t + i sin t) dt;
+// a rule in t with points t_e, weights pi omega_e (omega summing to 2) gives
+// w_e = (omega_e / 2) r e^{i phi} (rho cos t_e + i sin t_e).  Gauss:
+// t_e = pi (1 + x_e), x ascending; trapezoidal: t_e = 2 pi (e + 1/2) / ne.
+// Node ne-1-e is the mirror image of node e (t -> 2 pi - t).
+static int make_gcontour(zd emid, double r, int ne, int qtype, int ratio, int angle, zd *z, zd *w) {
+  if (!(r > 0.0)) return 200;
+  if (ne < 1 || ne > 1024) return 108;
+  if (qtype != 0 && qtype != 1) return 117;
+  if (ratio <= 0) return 118;
+  if (angle < -180 || angle > 180) return 119;
+  std::vector<double> x(ne), om(ne);
+  if (qtype == 0) {
+    gl_nodes(ne, x.data(), om.data());
+  } else {
+    for (int e = 0; e < ne; ++e) {
+      x[e] = 2.0 * (e + 0.5) / ne - 1.0;
+      om[e] = 2.0 / ne;
+    }
+  }
+  const double rho = ratio / 100.0, ph = angle * (PI_ / 180.0);
+  const double cr = r * cos(ph), sr = r * sin(ph);
+  for (int e = 0; e < ne; ++e) {
+    const double t = PI_ * (1.0 + x[e]), c = cos(t), s = rho * sin(t);
+    const double tc = rho * cos(t), ts = sin(t);
+    z[e] = zd{emid.x + cr * c - sr * s, emid.y + sr * c + cr * s};
+    w[e] = zd{0.5 * om[e] * (cr * tc - sr * ts), 0.5 * om[e] * (sr * tc + cr * ts)};
+  }
+  return 0;
+}
+
+struct GenReq {
+  int n;
+  bool real;  // A, B real (double) instead of complex
+  const void *A;
+  long lda;
+  const void *B;
+  long ldb;
+  const int *fpm;
+  zd emid;
+  double r;
+  int m0;
+  const double *Zne, *Wne;
+  double *E;    // 2 m0 doubles: complex eigenvalues
+  double *X;    // complex n x 2 m0: right vectors, then left ones
+  double *res;  // 2 m0: right residuals, then left ones
+};
+
+// Non-Hermitian FEAST on the dense pencil (A, B) (guide section "From v2.1
+// to v3.0": dual subspaces; Table tab_ijob, cases 10/11/21/30/31/40/41),
+// FP64 factors on the tensor-core engine.  Each iteration:
+//   Q  = sum_e w_e       S_e^{-1} B Y,    Q^ = sum_e conj(w_e) S_e^{-H} B^H Y^
+//   Aq = Q^^H A Q, Bq = Q^^H B Q; Aq W = Bq W Lambda, V = (Bq W)^{-H}
+//   X = Q W (unit columns), X^ = Q^ V (scaled so that X^^H B X = I),
+//   residuals of Table tab_common, next Y = X, Y^ = X^ with unit columns.
+// For real A, B, a real centre, no rotation and an even node count, node
+// ne-1-e is the mirror image of node e and S_{ne-1-e} = conj(S_e): only the
+// upper half is factored, each solve taking [b, conj(b)], and the mirror
+// node's term is conj(c_e S_e^{-1} conj(b)).
+static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &out) {
+  const int n = q.n, m0 = q.m0;
+  const int *fpm = q.fpm;
+  const bool hasB = q.B != nullptr;
+  const int ne = fpm[7];
+  const int bs = fpm[42] ? fpm[42] : 32;
+  const double eps = pow(10.0, -fpm[2]);
+  const double alpha = hypot(q.emid.x, q.emid.y) + q.r;
+  out = Res{};
+  out.m0 = m0;
+  std::vector<zd> zh(ne), wh(ne);
+  if (q.Zne && q.Wne) {
+    for (int e = 0; e < ne; ++e) {
+      zh[e] = zd{q.Zne[2 * e], q.Zne[2 * e + 1]};
+      wh[e] = zd{q.Wne[2 * e], q.Wne[2 * e + 1]};
+    }
+  } else {
+    const int rc = make_gcontour(q.emid, q.r, ne, fpm[16], fpm[17], fpm[18], zh.data(), wh.data());
+    if (rc) return out.info = rc;
+  }
+  const bool half = q.real && !(q.Zne && q.Wne) && q.emid.y == 0.0 && fpm[18] == 0 && ne % 2 == 0;
+  const int nf = half ? ne / 2 : ne;  // factored nodes (the first nf of the rule)
+  const int mw = half ? 2 * m0 : m0;  // right-hand sides per factored node
+  const int nblk = ceil_div(n, bs), nbm = ceil_div(m0, bs);
+  const size_t nn = (size_t)n * n, nm = (size_t)n * m0, mm = (size_t)m0 * m0;
+  const int tcS = (fpm[43] == 0 && bs <= 32) ? 7 : 0;
+
+  struct {
+    zd *Af, *Bf, *S, *Linv, *Uinv, *Ysol, *Ytmp, *Yadj, *R2;
+    zd *Q, *Qh, *AQ, *BQ, *AhQh, *BhQh, *Xr, *AXr, *BXr, *Xl, *AXl, *BXl, *Yr, *Yl, *RBr, *RBl, *Tmp;
+    zd *Aq, *Bq, *G, *Z, *Yv, *W, *V, *Mm, *P, *Sr, *Lr, *Ur, *Id, *Vt, *lam, *Eo, *z, *w;
+    int *ipiv, *perm, *sing, *ipr, *pmr, *sgr, *pos, *src, *flag, *tc_err;
+    double *rr, *rl, *nr, *nl, *Rr, *Rl, *stats;
+    void *tcw, *kw, *dinv_l, *dinv_u, *pja, *pjah, *pjb, *pjbh, *pjq, *pjh, *pjx, *pjw, *rrw;
+    size_t tcw_bytes, kw_bytes, rrw_bytes;
+  } ws;
+  auto layout = [&](Bump &b) {
+    ws.Af = q.real ? b.take<zd>(nn) : nullptr;
+    ws.Bf = (q.real && hasB) ? b.take<zd>(nn) : nullptr;
+    ws.S = b.take<zd>((size_t)nf * nn);
+    ws.Linv = b.take<zd>((size_t)nf * nblk * bs * bs);
+    ws.Uinv = b.take<zd>((size_t)nf * nblk * bs * bs);
+    ws.Ysol = b.take<zd>((size_t)nf * n * mw);
+    ws.Ytmp = b.take<zd>((size_t)nf * n * mw);
+    ws.Yadj = b.take<zd>((size_t)nf * n * mw);
+    ws.R2 = b.take<zd>((size_t)n * mw);
+    zd **nmb[] = {&ws.Q, &ws.Qh, &ws.AQ, &ws.AhQh, &ws.Xr, &ws.AXr, &ws.Xl, &ws.AXl, &ws.Yr, &ws.Yl, &ws.RBr,
+                  &ws.RBl, &ws.Tmp};
+    for (zd **p : nmb) *p = b.take<zd>(nm);
+    ws.BQ = hasB ? b.take<zd>(nm) : nullptr;
+    ws.BhQh = hasB ? b.take<zd>(nm) : nullptr;
+    ws.BXr = hasB ? b.take<zd>(nm) : nullptr;
+    ws.BXl = hasB ? b.take<zd>(nm) : nullptr;
+    zd **mmb[] = {&ws.Aq, &ws.Bq, &ws.G, &ws.Z, &ws.Yv, &ws.W, &ws.V, &ws.Mm, &ws.P, &ws.Sr, &ws.Id, &ws.Vt};
+    for (zd **p : mmb) *p = b.take<zd>(mm);
+    ws.Lr = b.take<zd>((size_t)nbm * bs * bs);
+    ws.Ur = b.take<zd>((size_t)nbm * bs * bs);
+    ws.lam = b.take<zd>(m0);
+    ws.Eo = b.take<zd>(m0);
+    ws.z = b.take<zd>(ne);
+    ws.w = b.take<zd>(ne);
+    ws.ipiv = b.take<int>((size_t)nf * n);
+    ws.perm = b.take<int>((size_t)nf * n);
+    ws.sing = b.take<int>(nf + 1);
+    ws.ipr = b.take<int>(m0);
+    ws.pmr = b.take<int>(m0);
+    ws.sgr = b.take<int>(2);
+    ws.pos = b.take<int>(m0);
+    ws.src = b.take<int>(m0);
+    ws.flag = b.take<int>(4);
+    ws.tc_err = b.take<int>(4);
+    double **db[] = {&ws.rr, &ws.rl, &ws.nr, &ws.nl, &ws.Rr, &ws.Rl};
+    for (double **p : db) *p = b.take<double>(m0);
+    ws.stats = b.take<double>(8);
+    ws.tcw_bytes = tcS ? std::max(zgemm_sliced_work(n, n, nf, tcS), zgemm_sliced_work(n, mw, nf, tcS)) : 0;
+    ws.tcw = tcS ? (void *)b.take<char>(ws.tcw_bytes) : nullptr;
+    ws.kw_bytes = tcS ? solve_kwork_bytes(n, mw, bs, nf) : 0;
+    ws.kw = ws.kw_bytes ? (void *)b.take<char>(ws.kw_bytes) : nullptr;
+    const bool big = ws.kw_bytes && bs == 32 && n % 128 == 0;
+    ws.dinv_l = big ? (void *)b.take<zd>((size_t)nf * n * 128) : nullptr;
+    ws.dinv_u = big ? (void *)b.take<zd>((size_t)nf * n * 128) : nullptr;
+    const long Kp = sliced_kp(n, true), R = 2L * n, Km = sliced_kp(m0, true), Rm = 2L * m0;
+    ws.pja = b.take<char>(sliced_op_bytes(R, Kp, 1));
+    ws.pjah = b.take<char>(sliced_op_bytes(R, Kp, 1));
+    ws.pjb = hasB ? (void *)b.take<char>(sliced_op_bytes(R, Kp, 1)) : nullptr;
+    ws.pjbh = hasB ? (void *)b.take<char>(sliced_op_bytes(R, Kp, 1)) : nullptr;
+    ws.pjq = b.take<char>(sliced_op_bytes(m0, Kp, 1));
+    ws.pjh = b.take<char>(sliced_op_bytes(Rm, Kp, 1));
+    ws.pjx = b.take<char>(sliced_op_bytes(R, Km, 1));
+    ws.pjw = b.take<char>(sliced_op_bytes(m0, Km, 1));
+    ws.rrw_bytes = gemm_sliced_k_work(true, m0, m0, m0, 1);
+    ws.rrw = b.take<char>(ws.rrw_bytes);
+  };
+  {
+    Bump sizing(nullptr);
+    layout(sizing);
+    if (ensure_arena(h, sizing.off + 4096)) return out.info = -1;
+    Bump real(h->arena);
+    layout(real);
+  }
+  TcCtx tcx;
+  tcx.work = ws.tcw;
+  tcx.bytes = ws.tcw_bytes;
+  tcx.gerr = ws.tc_err;
+  tcx.S = tcS;
+  tcx.kwork = ws.kw;
+  tcx.kbytes = ws.kw_bytes;
+  tcx.dinv_l = ws.dinv_l;
+  tcx.dinv_u = ws.dinv_u;
+  TcScope tc_scope(tcS ? &tcx : nullptr);
+  AuxScope aux_scope(ensure_aux(h));
+  if (ensure_hbuf(h, (size_t)std::max(m0, ne) + 64)) return out.info = -1;
+  h->f_prec = -1;
+
+  GBF_CUDA(cudaMemcpyAsync(ws.z, zh.data(), sizeof(zd) * ne, cudaMemcpyHostToDevice, st));
+  GBF_CUDA(cudaMemcpyAsync(ws.w, wh.data(), sizeof(zd) * ne, cudaMemcpyHostToDevice, st));
+  GBF_CUDA(cudaMemsetAsync(ws.sing, 0, sizeof(int) * (nf + 1), st));
+  GBF_CUDA(cudaMemsetAsync(ws.tc_err, 0, sizeof(int) * 4, st));
+  GBF_CUDA(cudaMemsetAsync(ws.flag, 0, sizeof(int) * 4, st));
+
+  const zd *Af = (const zd *)q.A, *Bf = (const zd *)q.B;
+  long lda = q.lda, ldb = q.ldb;
+  CatScope cat_other(CAT_OTHER);
+  if (q.real) {
+    CK(gen_widen(st, n, (const double *)q.A, q.lda, ws.Af));
+    Af = ws.Af;
+    lda = n;
+    if (hasB) {
+      CK(gen_widen(st, n, (const double *)q.B, q.ldb, ws.Bf));
+      Bf = ws.Bf;
+      ldb = n;
+    }
+  }
+  // factor the nodes (kept for the whole iteration)
+  CK(form_shift<zd>(st, n, nf, ws.z, 1, 'G', Af, lda, hasB ? (const void *)Bf : nullptr, ldb, ws.S, ws.sing + nf));
+  CK(getrf_batched<zd>(st, n, nf, ws.S, ws.ipiv, ws.perm, ws.Linv, ws.Uinv, bs, ws.sing, nullptr));
+  {
+    int *hs = (int *)h->hbuf;
+    GBF_CUDA(cudaMemcpyAsync(hs, ws.sing, sizeof(int) * (nf + 1), cudaMemcpyDeviceToHost, st));
+    GBF_CUDA(cudaMemcpyAsync(hs + nf + 1, ws.tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GBF_CUDA(cudaStreamSynchronize(st));
+    if (hs[nf + 1]) {
+      set_error("tensor-core GEMM: bounded wait timed out (code %d)", hs[nf + 1]);
+      return out.info = -4;
+    }
+    if (hs[nf]) {
+      set_error("A or B holds a non-finite entry (NaN or Inf)");
+      return out.info = -2;
+    }
+    for (int e = 0; e < nf; ++e)
+      if (hs[e]) {
+        set_error("zero pivot in column %d of the shifted system of node %d", hs[e], e);
+        return out.info = -2;
+      }
+  }
+  // rows of A, A^H, B, B^H sliced once (RCI cases 30, 31, 40, 41)
+  SlicedOp opA{}, opAh{}, opB{}, opBh{};
+  {
+    CatScope cat_pj(CAT_PROJECT);
+    CK(slice_rows<zd>(st, 'N', n, n, Af, lda, 0, 1, ws.pja, &opA));
+    CK(slice_rows<zd>(st, 'C', n, n, Af, lda, 0, 1, ws.pjah, &opAh));
+    if (hasB) {
+      CK(slice_rows<zd>(st, 'N', n, n, Bf, ldb, 0, 1, ws.pjb, &opB));
+      CK(slice_rows<zd>(st, 'C', n, n, Bf, ldb, 0, 1, ws.pjbh, &opBh));
+    }
+  }
+  auto sliced_product = [&](const SlicedOp &opM, const zd *Y, int mm_, zd *o) -> int {
+    SlicedOp opY;
+    if (int rc = slice_cols<zd>(st, 'N', n, mm_, Y, n, 0, 1, ws.pjq, &opY)) return rc;
+    return gemm_sliced_ops<zd>(st, opM, opY, 1, 1.0, 0, o, n, 0, ws.tc_err);
+  };
+  // rows(P) x cols(Mx): an n x m (or m x m) product with a sliced m x m right factor
+  auto rr_gemm = [&](char opa, char opb, int mm_, int nn_, int kk, const zd *A_, int lda_, const zd *B_, int ldb_,
+                     zd *C_, int ldc_) -> int {
+    return gemm_sliced_k<zd>(st, opa, opb, mm_, nn_, kk, 1.0, A_, lda_, 0, B_, ldb_, 0, 0, C_, ldc_, 0, 1, ws.rrw,
+                             ws.rrw_bytes, ws.tc_err);
+  };
+
+  // initial subspaces: right/left guesses from X (fpm(5)=1) or the seeded one
+  const int m = m0;
+  if (fpm[4] == 1) {
+    GBF_CUDA(cudaMemcpyAsync(ws.Yr, q.X, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
+    GBF_CUDA(cudaMemcpyAsync(ws.Yl, (const zd *)q.X + nm, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
+  } else {
+    CK(random_subspace<zd>(st, (long)nm, SUBSPACE_SEED, ws.Yr));
+    GBF_CUDA(cudaMemcpyAsync(ws.Yl, ws.Yr, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
+  }
+  if (hasB) {
+    CatScope cat_pj(CAT_PROJECT);
+    CK(sliced_product(opB, ws.Yr, m, ws.RBr));
+    CK(sliced_product(opBh, ws.Yl, m, ws.RBl));
+  } else {
+    GBF_CUDA(cudaMemcpyAsync(ws.RBr, ws.Yr, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
+    GBF_CUDA(cudaMemcpyAsync(ws.RBl, ws.Yl, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
+  }
+
+  zd trace_prev{0.0, 0.0};
+  for (int k = 0;; ++k) {
+    // ---- spectral projections (cases 11 and 21) ----
+    const zd *rr_src = ws.RBr, *rl_src = ws.RBl;
+    if (half) {
+      CK(gen_conj_pair(st, n, m, ws.RBr, ws.R2));
+      rr_src = ws.R2;
+    }
+    CK(gather_rhs<zd>(st, n, nf, mw, ws.perm, 1, rr_src, n, nullptr, ws.Ysol));
+    CK(getrs_inplace<zd>(st, 0, n, nf, mw, ws.S, ws.Linv, ws.Uinv, bs, ws.Ysol, nullptr));
+    CK(gen_accumulate(st, n, m, nf, ws.w, ws.Ysol, mw, half ? 1 : 0, 0, ws.Q));
+    if (half) {
+      CK(gen_conj_pair(st, n, m, ws.RBl, ws.R2));
+      rl_src = ws.R2;
+    }
+    CK(gather_rhs<zd>(st, n, nf, mw, nullptr, 1, rl_src, n, nullptr, ws.Ytmp));
+    CK(getrs_inplace<zd>(st, 1, n, nf, mw, ws.S, ws.Linv, ws.Uinv, bs, ws.Ytmp, nullptr));
+    CK(scatter_perm<zd>(st, n, nf, mw, ws.perm, ws.Ytmp, ws.Yadj));
+    CK(gen_accumulate(st, n, m, nf, ws.w, ws.Yadj, mw, half ? 1 : 0, 1, ws.Qh));
+    if (fpm[13] == 1) {  // the subspaces after one contour
+      GBF_CUDA(cudaMemcpyAsync(q.X, ws.Q, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
+      GBF_CUDA(cudaMemcpyAsync((zd *)q.X + nm, ws.Qh, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
+      GBF_CUDA(cudaMemsetAsync(q.E, 0, sizeof(zd) * m0, st));
+      GBF_CUDA(cudaMemsetAsync(q.res, 0, sizeof(double) * 2 * m0, st));
+      GBF_CUDA(cudaStreamSynchronize(st));
+      out.loop = k;
+      return out.info = 4;
+    }
+    // ---- Rayleigh-Ritz on the dual subspaces (cases 30, 31, 40, 41) ----
+    {
+      CatScope cat_proj(CAT_PROJECT);
+      SlicedOp opQ, opM;
+      CK(slice_cols<zd>(st, 'N', n, m, ws.Q, n, 0, 1, ws.pjq, &opQ));
+      CK(gemm_sliced_ops<zd>(st, opA, opQ, 1, 1.0, 0, ws.AQ, n, 0, ws.tc_err));
+      if (hasB) CK(gemm_sliced_ops<zd>(st, opB, opQ, 1, 1.0, 0, ws.BQ, n, 0, ws.tc_err));
+      CK(slice_cols<zd>(st, 'N', n, m, ws.Qh, n, 0, 1, ws.pjq, &opQ));
+      CK(gemm_sliced_ops<zd>(st, opAh, opQ, 1, 1.0, 0, ws.AhQh, n, 0, ws.tc_err));
+      if (hasB) CK(gemm_sliced_ops<zd>(st, opBh, opQ, 1, 1.0, 0, ws.BhQh, n, 0, ws.tc_err));
+      SlicedOp opQhH;
+      CK(slice_rows<zd>(st, 'C', m, n, ws.Qh, n, 0, 1, ws.pjh, &opQhH));
+      CK(slice_cols<zd>(st, 'N', n, m, ws.AQ, n, 0, 1, ws.pjq, &opM));
+      CK(gemm_sliced_ops<zd>(st, opQhH, opM, 1, 1.0, 0, ws.Aq, m, 0, ws.tc_err));
+      CK(slice_cols<zd>(st, 'N', n, m, hasB ? ws.BQ : ws.Q, n, 0, 1, ws.pjq, &opM));
+      CK(gemm_sliced_ops<zd>(st, opQhH, opM, 1, 1.0, 0, ws.Bq, m, 0, ws.tc_err));
+    }
+    // ---- reduced pencil: G = Bq^{-1} Aq = Z T Z^H, W = Z Y, V = (Bq W)^{-H} ----
+    {
+      CatScope cat_red(CAT_REDUCED);
+      TcScope no_tc(nullptr);  // the m-sized LU keeps clear of the n-sized factor workspace
+      GBF_CUDA(cudaMemsetAsync(ws.sgr, 0, sizeof(int) * 2, st));
+      GBF_CUDA(cudaMemcpyAsync(ws.Sr, ws.Bq, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, st));
+      CK(getrf_batched<zd>(st, m, 1, ws.Sr, ws.ipr, ws.pmr, ws.Lr, ws.Ur, bs, ws.sgr, nullptr));
+      CK(gather_rhs<zd>(st, m, 1, m, ws.pmr, 1, ws.Aq, m, nullptr, ws.G));
+      CK(getrs_inplace<zd>(st, 0, m, 1, m, ws.Sr, ws.Lr, ws.Ur, bs, ws.G, nullptr));
+      CK(gen_hessenberg(st, m, ws.G, ws.Z));
+      CK(gen_hqr(st, m, ws.G, ws.Z, ws.lam, ws.flag + 2));
+      CK(gen_trevc(st, m, ws.G, ws.Yv));
+      CK(rr_gemm('N', 'N', m, m, m, ws.Z, m, ws.Yv, m, ws.W, m));
+      CK(gen_col_norms(st, m, m, ws.W, ws.nr));
+      CK(gen_col_scale(st, m, m, ws.W, ws.W, ws.nr, 1));
+      CK(rr_gemm('N', 'N', m, m, m, ws.Bq, m, ws.W, m, ws.Mm, m));
+      GBF_CUDA(cudaMemcpyAsync(ws.Sr, ws.Mm, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, st));
+      CK(getrf_batched<zd>(st, m, 1, ws.Sr, ws.ipr, ws.pmr, ws.Lr, ws.Ur, bs, ws.sgr + 1, nullptr));
+      CK(gen_identity(st, m, ws.Id));
+      CK(gather_rhs<zd>(st, m, 1, m, nullptr, 1, ws.Id, m, nullptr, ws.Vt));
+      CK(getrs_inplace<zd>(st, 1, m, 1, m, ws.Sr, ws.Lr, ws.Ur, bs, ws.Vt, nullptr));
+      CK(scatter_perm<zd>(st, m, 1, m, ws.pmr, ws.Vt, ws.V));
+    }
+    // ---- Ritz vectors, residuals, order ----
+    {
+      CatScope cat_proj(CAT_PROJECT);
+      SlicedOp opW, opM;
+      CK(slice_cols<zd>(st, 'N', m, m, ws.W, m, 0, 1, ws.pjw, &opW));
+      const zd *srcR[3] = {ws.Q, ws.AQ, ws.BQ};
+      zd *dstR[3] = {ws.Xr, ws.AXr, ws.BXr};
+      for (int t = 0; t < (hasB ? 3 : 2); ++t) {
+        CK(slice_rows<zd>(st, 'N', n, m, srcR[t], n, 0, 1, ws.pjx, &opM));
+        CK(gemm_sliced_ops<zd>(st, opM, opW, 1, 1.0, 0, dstR[t], n, 0, ws.tc_err));
+      }
+      CK(slice_cols<zd>(st, 'N', m, m, ws.V, m, 0, 1, ws.pjw, &opW));
+      const zd *srcL[3] = {ws.Qh, ws.AhQh, ws.BhQh};
+      zd *dstL[3] = {ws.Xl, ws.AXl, ws.BXl};
+      for (int t = 0; t < (hasB ? 3 : 2); ++t) {
+        CK(slice_rows<zd>(st, 'N', n, m, srcL[t], n, 0, 1, ws.pjx, &opM));
+        CK(gemm_sliced_ops<zd>(st, opM, opW, 1, 1.0, 0, dstL[t], n, 0, ws.tc_err));
+      }
+    }
+    // right vectors to unit 2-norm, left ones scaled inversely
+    CK(gen_col_norms(st, n, m, ws.Xr, ws.nr));
+    for (zd *p : {ws.Xr, ws.AXr, ws.BXr})
+      if (p) CK(gen_col_scale(st, n, m, p, p, ws.nr, 1));
+    for (zd *p : {ws.Xl, ws.AXl, ws.BXl})
+      if (p) CK(gen_col_scale(st, n, m, p, p, ws.nr, 0));
+    CK(gen_residual(st, n, m, ws.AXr, hasB ? ws.BXr : ws.Xr, ws.lam, 0, alpha, ws.rr));
+    CK(gen_residual(st, n, m, ws.AXl, hasB ? ws.BXl : ws.Xl, ws.lam, 1, alpha, ws.rl));
+    CK(gen_order(st, m, ws.lam, ws.rr, ws.rl, q.emid, q.r, fpm[17] / 100.0, (double)fpm[18], ws.pos, ws.src, ws.Eo,
+                 ws.Rr, ws.Rl, ws.stats));
+    // next right subspace and its B product; next left one with unit columns
+    CK(permute_cols<zd>(st, n, m, ws.pos, ws.Xr, ws.Yr));
+    CK(permute_cols<zd>(st, n, m, ws.pos, ws.Xl, ws.Yl));
+    if (hasB) CK(permute_cols<zd>(st, n, m, ws.pos, ws.BXr, ws.RBr));
+    else GBF_CUDA(cudaMemcpyAsync(ws.RBr, ws.Yr, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
+    CK(gen_col_norms(st, n, m, ws.Yl, ws.nl));
+    if (hasB) {
+      CK(permute_cols<zd>(st, n, m, ws.pos, ws.BXl, ws.Tmp));
+      CK(gen_col_scale(st, n, m, ws.Tmp, ws.RBl, ws.nl, 1));
+    } else {
+      CK(gen_col_scale(st, n, m, ws.Yl, ws.RBl, ws.nl, 1));
+    }
+    double *hs = h->hbuf;
+    GBF_CUDA(cudaMemcpyAsync(hs, ws.stats, sizeof(double) * 5, cudaMemcpyDeviceToHost, st));
+    GBF_CUDA(cudaMemcpyAsync(h->hflag, ws.flag, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+    GBF_CUDA(cudaMemcpyAsync(h->hflag + 4, ws.tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GBF_CUDA(cudaMemcpyAsync(h->hflag + 5, ws.sgr, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+    GBF_CUDA(cudaStreamSynchronize(st));
+    if (h->hflag[4]) {
+      set_error("tensor-core GEMM: bounded wait timed out (code %d)", h->hflag[4]);
+      return out.info = -4;
+    }
+    if (h->hflag[5] || h->hflag[6]) {
+      set_error("reduced pencil: %s is singular (the subspaces are not independent)",
+                h->hflag[5] ? "Q^^H B Q" : "Bq W");
+      return out.info = -3;
+    }
+    if (h->hflag[2]) {
+      set_error("reduced non-Hermitian eigenproblem: the shifted QR did not converge");
+      return out.info = -4;
+    }
+    const int nin = (int)hs[0];
+    const zd trace{hs[1], hs[2]};
+    const double maxres = hs[3];
+    const bool finite = hs[4] != 0.0;
+    const double eout = (k == 0) ? 1.0 : hypot(trace.x - trace_prev.x, trace.y - trace_prev.y) / alpha;
+    out.M = nin;
+    out.loop = k;
+    out.epsout = eout;
+    if (fpm[0] == 1)
+      fprintf(stderr, "%d\t%d\t%.15e %+.15ei\t%.15e\t%.15e\t(M0 %d, non-Hermitian)\n", k, nin, trace.x, trace.y,
+              eout, maxres, m);
+    int info = -99;
+    if (!finite) {
+      set_error("non-finite Ritz values or residuals");
+      info = -2;
+    } else if (nin == 0) {
+      info = 1;
+    } else if (nin >= m0 && m0 < n) {
+      info = 3;
+    } else if ((fpm[5] == 0) ? (eout < eps) : (maxres < eps)) {
+      info = 0;
+      // bi-orthonormality of the returned pairs: X^_M^H B X_M = I
+      CK(rr_gemm('C', 'N', m, m, m, ws.V, m, ws.Mm, m, ws.P, m));
+      CK(gen_biorth(st, m, nin, ws.P, ws.nr, ws.src, ws.stats + 5));
+      GBF_CUDA(cudaMemcpyAsync(hs + 5, ws.stats + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
+      GBF_CUDA(cudaStreamSynchronize(st));
+      h->gen_biorth = hs[5];
+      if (!(hs[5] <= 1e-8)) info = 6;
+    } else if (k >= fpm[3]) {
+      info = 2;
+    }
+    if (info != -99) {
+      GBF_CUDA(cudaMemcpyAsync(q.E, ws.Eo, sizeof(zd) * m, cudaMemcpyDeviceToDevice, st));
+      GBF_CUDA(cudaMemcpyAsync(q.res, ws.Rr, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+      GBF_CUDA(cudaMemcpyAsync(q.res + m0, ws.Rl, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+      GBF_CUDA(cudaMemcpyAsync(q.X, ws.Yr, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
+      GBF_CUDA(cudaMemcpyAsync((zd *)q.X + nm, ws.Yl, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
+      GBF_CUDA(cudaStreamSynchronize(st));
+      return out.info = info;
+    }
+    trace_prev = trace;
+  }
+}
+
 // ----------------------------------------------------------- validation --
 static int validate(char uplo, int n, long lda, bool hasB, long ldb, const int *fpm, double emin, double emax,
                     int m0) {
@@ -912,6 +1343,46 @@ static int run_dev(gbf_handle h, void *stream, char uplo, int n, const double *d
     if (loop) *loop = out.loop;
     if (M) *M = out.M;
     if (M0 && code >= 0) *M0 = out.m0;
+  }
+  if (info) *info = code;
+  return code;
+}
+
+// Checks of the non-Hermitian drivers' arguments (Table tab_info codes).
+static int validate_gen(int n, long lda, bool hasB, long ldb, const int *fpm, double r, int m0) {
+  if (n < 1) return 202;
+  if (lda < n) return -104;
+  if (hasB && ldb < n) return -106;
+  if (!fpm) return -107;
+  if (m0 < 1 || m0 > n || m0 > 1024) return 201;
+  if (!(r > 0.0)) return 200;
+  if (fpm[2] < 0 || fpm[2] > 16) return 103;
+  if (fpm[3] < 0) return 104;
+  if (fpm[4] != 0 && fpm[4] != 1) return 105;
+  if (fpm[5] != 0 && fpm[5] != 1) return 106;
+  if (fpm[7] < 1 || fpm[7] > 1024) return 108;
+  if (fpm[13] != 0 && fpm[13] != 1) return 114;
+  if (fpm[16] != 0 && fpm[16] != 1) return 117;
+  if (fpm[17] <= 0) return 118;
+  if (fpm[18] < -180 || fpm[18] > 180) return 119;
+  if (fpm[42] != 0 && (fpm[42] < 8 || fpm[42] > 64 || fpm[42] % 8)) return 143;
+  if (fpm[43] != 0 && fpm[43] != 1) return 144;
+  return 0;
+}
+
+static int run_gen_dev(gbf_handle h, void *stream, bool real, int n, const double *dA, int lda, const double *dB,
+                       int ldb, int *fpm, double *epsout, int *loop, double emid_re, double emid_im, double r,
+                       int *M0, double *dE, double *dX, int *M, double *dres, int *info, const double *Zne,
+                       const double *Wne) {
+  int code = validate_gen(n, lda, dB != nullptr, ldb, fpm, r, M0 ? *M0 : 0);
+  Res out;
+  if (code == 0 && (!dA || !dE || !dX || !dres)) code = -103;
+  if (code == 0) {
+    GenReq q{n, real, dA, lda, dB, ldb, fpm, zd{emid_re, emid_im}, r, *M0, Zne, Wne, dE, dX, dres};
+    code = feast_run_gen(h, (cudaStream_t)stream, q, out);
+    if (epsout) *epsout = out.epsout;
+    if (loop) *loop = out.loop;
+    if (M) *M = out.M;
   }
   if (info) *info = code;
   return code;
@@ -1031,7 +1502,7 @@ int gbf_create(gbf_handle *hp) {
   gbf_context *h = new (std::nothrow) gbf_context();
   if (!h) return -1;
   GBF_CUDA(cudaGetDevice(&h->device));
-  GBF_CUDA(cudaMallocHost((void **)&h->hflag, sizeof(int) * 4));
+  GBF_CUDA(cudaMallocHost((void **)&h->hflag, sizeof(int) * 16));
   GBF_CUDA(cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking));
   *hp = h;
   return 0;
@@ -1146,6 +1617,56 @@ int gbf_zhegv_dev(gbf_handle h, void *stream, char uplo, int n, const double *dA
   if (!h) return -4;
   return run_dev<zd>(h, stream, uplo, n, dA, lda, dB, ldb, fpm, epsout, loop, emin, emax, M0, dE, dX, M, dres,
                      info, Zne, Wne);
+}
+
+// ---------------------------------------------------- non-Hermitian entries
+int gbf_gcontour(double emid_re, double emid_im, double r, int ne, int fpm17, int fpm18, int fpm19, double *Zne,
+                 double *Wne) {
+  if (!Zne || !Wne) return -103;
+  std::vector<zd> z(std::max(ne, 1)), w(std::max(ne, 1));
+  const int rc = make_gcontour(zd{emid_re, emid_im}, r, ne, fpm17, fpm18, fpm19, z.data(), w.data());
+  if (rc) return rc;
+  for (int e = 0; e < ne; ++e) {
+    Zne[2 * e] = z[e].x;
+    Zne[2 * e + 1] = z[e].y;
+    Wne[2 * e] = w[e].x;
+    Wne[2 * e + 1] = w[e].y;
+  }
+  return 0;
+}
+
+int gbf_grationalx(const double *Zne, const double *Wne, int ne, const double *eig, int m, double *f) {
+  if (!Zne || !Wne || !eig || !f || ne < 1 || m < 0) return -103;
+  for (int i = 0; i < m; ++i) {
+    double sx = 0.0, sy = 0.0;
+    for (int e = 0; e < ne; ++e) {
+      const zd q = zdiv(zd{Wne[2 * e], Wne[2 * e + 1]}, zd{Zne[2 * e] - eig[2 * i], Zne[2 * e + 1] - eig[2 * i + 1]});
+      sx += q.x;
+      sy += q.y;
+    }
+    f[2 * i] = sx;
+    f[2 * i + 1] = sy;
+  }
+  return 0;
+}
+
+double gbf_biorth_defect(gbf_handle h) { return h ? h->gen_biorth : -1.0; }
+
+int gbf_dgegv_dev(gbf_handle h, void *stream, int n, const double *dA, int lda, const double *dB, int ldb, int *fpm,
+                  double *epsout, int *loop, double emid_re, double emid_im, double r, int *M0, double *dE,
+                  double *dX, int *M, double *dres, int *info, const double *Zne, const double *Wne) {
+  if (!h) h = default_ctx();
+  if (!h) return -4;
+  return run_gen_dev(h, stream, true, n, dA, lda, dB, ldb, fpm, epsout, loop, emid_re, emid_im, r, M0, dE, dX, M,
+                     dres, info, Zne, Wne);
+}
+int gbf_zgegv_dev(gbf_handle h, void *stream, int n, const double *dA, int lda, const double *dB, int ldb, int *fpm,
+                  double *epsout, int *loop, double emid_re, double emid_im, double r, int *M0, double *dE,
+                  double *dX, int *M, double *dres, int *info, const double *Zne, const double *Wne) {
+  if (!h) h = default_ctx();
+  if (!h) return -4;
+  return run_gen_dev(h, stream, false, n, dA, lda, dB, ldb, fpm, epsout, loop, emid_re, emid_im, r, M0, dE, dX, M,
+                     dres, info, Zne, Wne);
 }
 
 int gbf_shard_nodes(int ne, int rank, int nranks, int *first, int *count) {

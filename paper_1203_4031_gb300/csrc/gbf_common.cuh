@@ -302,7 +302,9 @@ int gemm(cudaStream_t st, char opa, char opb, int m, int n, int k, T alpha, cons
 
 // ------------------------------------------------------ LU / solve (lu.cu) --
 // Form S_e = z_e B - A for all nodes (B == nullptr: B = I) in type T.
-// kindA: 0 real input (double), 1 complex input (zd). uplo: 'F','L','U'.
+// kindA: 0 real input (double), 1 complex input (zd). uplo: 'F','L','U'
+// (Hermitian: the referenced triangle, a real diagonal) or 'G' (a general
+// matrix, every entry as stored).
 // bad (may be null): set to 1 when a referenced entry of A or B is not finite.
 template <class T>
 int form_shift(cudaStream_t st, int n, int ne, const zd *z, int kindA, char uplo, const void *A,
@@ -392,5 +394,28 @@ template <class TQ> int random_subspace(cudaStream_t st, long count, uint64_t se
 template <class TQ> int rademacher_probes(cudaStream_t st, long count, uint64_t seed, TQ *Y);
 template <class TQ> int probe_running_mean(cudaStream_t st, int n, int m, const TQ *Y, const TQ *Q, double *res);
 template <class T> int ns_prep(cudaStream_t st, int m, const T *P, T *Tn, double *norm);
+
+// ----------------------------------------- non-Hermitian FEAST (gen.cu) --
+// Elementwise glue of the dual-subspace iteration (n x m column-major, ld n).
+int gen_widen(cudaStream_t st, int n, const double *A, long lda, zd *Af);
+int gen_conj_pair(cudaStream_t st, int n, int m, const zd *src, zd *dst);
+// Q = sum over the nf factored nodes of c_e Y_e (+ the mirror node's term
+// conj(c_e Y_e[:, m..2m)) when `half`), c_e = w_e, or conj(w_e) when `left`.
+int gen_accumulate(cudaStream_t st, int n, int m, int nf, const zd *w, const zd *Y, int mw, int half, int left,
+                   zd *Q);
+int gen_col_norms(cudaStream_t st, int n, int m, const zd *X, double *nrm);
+int gen_col_scale(cudaStream_t st, int n, int m, const zd *src, zd *dst, const double *s, int divide);
+int gen_residual(cudaStream_t st, int n, int m, const zd *MX, const zd *NX, const zd *lam, int conjl, double alpha,
+                 double *res);
+int gen_order(cudaStream_t st, int m, const zd *lam, const double *rr, const double *rl, zd emid, double r,
+              double rho, double angle_deg, int *pos, int *src, zd *Eo, double *Rr, double *Rl, double *stats);
+int gen_biorth(cudaStream_t st, int m, int nin, const zd *P, const double *nr, const int *src, double *out);
+int gen_identity(cudaStream_t st, int m, zd *I);
+// Reduced non-Hermitian eigensolver steps (m x m, ld m): Hessenberg form
+// with Z accumulated; complex Schur form by shifted QR (err = 1: no
+// convergence); eigenvectors of the triangular factor.
+int gen_hessenberg(cudaStream_t st, int m, zd *G, zd *Z);
+int gen_hqr(cudaStream_t st, int m, zd *H, zd *Z, zd *lam, int *err);
+int gen_trevc(cudaStream_t st, int m, const zd *T, zd *Y);
 
 }  // namespace gbf

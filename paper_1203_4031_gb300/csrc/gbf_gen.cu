@@ -1,0 +1,553 @@
+// Non-Hermitian FEAST (guide section "From v2.1 to v3.0": dual subspaces Q
+// and Q^ for the right and left eigenvectors, a full contour around complex
+// eigenvalues; RCI cases 11/21 and 30/31/40/41 of Table tab_ijob): the node
+// sums of the two subspaces, the reduced non-Hermitian eigensolver of the
+// Rayleigh-Ritz step, and the residuals, ordering and bi-orthonormality
+// check of Tables tab_common and tab_info.
+//
+// Reduced eigensolver.  After G = Bq^{-1} Aq (LU of Bq on the batched LU
+// engine), G = Z T Z^H by
+//   hessenberg   Householder reduction to upper Hessenberg form, reflectors
+//                accumulated into Z (one CTA),
+//   hqr          complex single-shift QR sweeps with the Wilkinson shift of
+//                the trailing 2 x 2 block (an exceptional shift every tenth
+//                sweep), small subdiagonals deflated, rotations applied to
+//                the whole of T (Schur form) and accumulated into Z (one CTA;
+//                all threads run the same control flow on the same values),
+//   trevc        eigenvectors of the triangular T by back substitution, one
+//                warp per eigenvector, column-oriented (a running sum per
+//                row in registers, no reduction per row),
+// then W = Z Y on the sliced tensor-core GEMM.  These M0-sized kernels are
+// latency- and FP64-bound on one SM; their cost grows as M0^3.
+#include "gbf_common.cuh"
+
+#include <cfloat>
+
+namespace gbf {
+namespace {
+using X = tr<zd>;
+
+__device__ __forceinline__ double cabs1(zd a) { return fabs(a.x) + fabs(a.y); }
+__device__ __forceinline__ zd zsc(zd a, double s) { return zd{a.x * s, a.y * s}; }
+__device__ __forceinline__ double absq(zd a) { return a.x * a.x + a.y * a.y; }
+
+// principal square root of a complex number
+__device__ zd zsqrt(zd z) {
+  const double r = hypot(z.x, z.y);
+  if (r == 0.0) return zd{0.0, 0.0};
+  if (z.x >= 0.0) {
+    const double t = sqrt(0.5 * (r + z.x));
+    return zd{t, z.y / (2.0 * t)};
+  }
+  const double t = sqrt(0.5 * (r - z.x));
+  return zd{fabs(z.y) / (2.0 * t), copysign(t, z.y)};
+}
+
+// Plane rotation R = [[c, s], [-conj(s), c]] (c real) with R [x; y] = [r; 0].
+__device__ void make_rot(zd x, zd y, double &c, zd &s) {
+  const double ax = hypot(x.x, x.y), ay = hypot(y.x, y.y);
+  if (ay == 0.0) {
+    c = 1.0;
+    s = zd{0.0, 0.0};
+    return;
+  }
+  if (ax == 0.0) {
+    c = 0.0;
+    s = zd{y.x / ay, -y.y / ay};
+    return;
+  }
+  const double nrm = hypot(ax, ay);
+  c = ax / nrm;
+  s = zsc(X::mul(zd{x.x / ax, x.y / ax}, X::conj(y)), 1.0 / nrm);
+}
+
+// Deterministic block sum / max (fixed tree over blockDim.x = 256).
+constexpr int RT = 256;
+__device__ double block_sum(double v, double *red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = RT / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+__device__ double block_max(double v, double *red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = RT / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------ elementwise --
+__global__ void widen_ld_kernel(int n, const double *A, long lda, zd *Af) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i < n) Af[i + (long)j * n] = zd{A[i + (long)j * lda], 0.0};
+}
+
+// dst = [src, conj(src)] (n x 2m): the right-hand sides of a node and of its
+// mirror image, whose system is the conjugate of this one for real A, B
+__global__ void conj_pair_kernel(int n, int m, const zd *src, zd *dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= n) return;
+  const zd v = src[i + (long)j * n];
+  dst[i + (long)j * n] = v;
+  dst[i + (long)(m + j) * n] = X::conj(v);
+}
+
+// Q[i, j] = sum_e c_e Y_e[i, j] (+ conj(c_e Y_e[i, m + j]) for the mirror
+// node when `half`), c_e = w_e (right) or conj(w_e) (left); nodes in order.
+__global__ void accum_gen_kernel(int n, int m, int nf, const zd *w, const zd *Y, int mw, int half, int left,
+                                 zd *Q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= n) return;
+  const long ny = (long)n * mw;
+  zd acc{0.0, 0.0};
+  for (int e = 0; e < nf; ++e) {
+    const zd ce = left ? X::conj(w[e]) : w[e];
+    const zd *Ye = Y + e * ny;
+    acc = X::fma(ce, Ye[i + (long)j * n], acc);
+    if (half) acc = X::add(acc, X::conj(X::mul(ce, Ye[i + (long)(m + j) * n])));
+  }
+  Q[i + (long)j * n] = acc;
+}
+
+__global__ void __launch_bounds__(RT) col_norms_kernel(int n, const zd *Xm, double *nrm) {
+  __shared__ double red[RT];
+  const int j = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += RT) s += absq(Xm[i + (long)j * n]);
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) nrm[j] = sqrt(s);
+}
+
+// dst[:, j] = src[:, j] * s_j (or / s_j); dst may alias src
+__global__ void col_scale_kernel(int n, const zd *src, zd *dst, const double *s, int divide) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= n) return;
+  const double f = divide ? 1.0 / s[j] : s[j];
+  dst[i + (long)j * n] = zsc(src[i + (long)j * n], f);
+}
+
+// res_j = ||MX_j - l_j NX_j||_1 / ||alpha NX_j||_1, l_j = lam_j or conj(lam_j)
+__global__ void __launch_bounds__(RT) gen_residual_kernel(int n, const zd *MX, const zd *NX, const zd *lam,
+                                                           int conjl, double alpha, double *res) {
+  __shared__ double red[RT];
+  const int j = blockIdx.x;
+  const zd l = conjl ? X::conj(lam[j]) : lam[j];
+  double num = 0.0, den = 0.0;
+  for (int i = threadIdx.x; i < n; i += RT) {
+    const zd b = NX[i + (long)j * n];
+    const zd d = X::sub(MX[i + (long)j * n], X::mul(l, b));
+    num += hypot(d.x, d.y);
+    den += hypot(b.x, b.y);
+  }
+  num = block_sum(num, red);
+  den = block_sum(den, red);
+  if (threadIdx.x == 0) res[j] = num / (alpha * den);
+}
+
+// Order: pairs inside the contour first, each group by ascending (Re, Im)
+// (then index); pos[j] = output slot of pair j, src[slot] = j; outputs in
+// that order; stats = {nin, Re trace, Im trace, max over inside of
+// max(right, left residual), all finite}.
+__global__ void order_gen_kernel(int m, const zd *lam, const double *rr, const double *rl, double er, double ei,
+                                 double r, double rho, double cph, double sph, int *pos, int *src, zd *Eo,
+                                 double *Rr, double *Rl, double *stats) {
+  __shared__ int s_in[1024];
+  const int j = threadIdx.x;
+  if (j < m) {
+    const double dx = lam[j].x - er, dy = lam[j].y - ei;
+    const double ux = (dx * cph + dy * sph) / r, uy = (dy * cph - dx * sph) / r;
+    s_in[j] = (ux * ux + (uy / rho) * (uy / rho) <= 1.0) ? 1 : 0;
+  }
+  __syncthreads();
+  if (j < m) {
+    const int ij = s_in[j];
+    const zd lj = lam[j];
+    int rank = 0;
+    for (int k = 0; k < m; ++k) {
+      if (k == j) continue;
+      const int ik = s_in[k];
+      const zd lk = lam[k];
+      bool before;
+      if (ik != ij) before = ik > ij;
+      else if (lk.x != lj.x) before = lk.x < lj.x;
+      else if (lk.y != lj.y) before = lk.y < lj.y;
+      else before = k < j;
+      rank += before ? 1 : 0;
+    }
+    pos[j] = rank;
+    src[rank] = j;
+    Eo[rank] = lj;
+    Rr[rank] = rr[j];
+    Rl[rank] = rl[j];
+  }
+  __syncthreads();
+  if (j == 0) {
+    int nin = 0;
+    for (int k = 0; k < m; ++k) nin += s_in[k];
+    double tx = 0.0, ty = 0.0, mx = 0.0;
+    for (int k = 0; k < nin; ++k) {
+      tx += Eo[k].x;
+      ty += Eo[k].y;
+      mx = fmax(mx, fmax(Rr[k], Rl[k]));
+    }
+    bool fin = true;
+    for (int k = 0; k < m; ++k)
+      fin = fin && isfinite(lam[k].x) && isfinite(lam[k].y) && isfinite(rr[k]) && isfinite(rl[k]);
+    stats[0] = nin;
+    stats[1] = tx;
+    stats[2] = ty;
+    stats[3] = mx;
+    stats[4] = fin ? 1.0 : 0.0;
+  }
+}
+
+// max over slots a, b < nin of |(nr_pa / nr_pb) P[pa, pb] - delta_ab| (pa =
+// src[a]): the bi-orthonormality defect of the returned pairs, X^_a^H B X_b -
+// delta_ab, from P = V^H Bq W and the rescaling x = Q W / nr, x^ = Q^ V nr
+__global__ void __launch_bounds__(RT) biorth_kernel(int m, int nin, const zd *P, const double *nr, const int *src,
+                                                     double *out) {
+  __shared__ double red[RT];
+  double mx = 0.0;
+  for (long t = threadIdx.x; t < (long)nin * nin; t += RT) {
+    const int a = (int)(t % nin), b = (int)(t / nin);
+    const int pa = src[a], pb = src[b];
+    zd v = zsc(P[pa + (long)pb * m], nr[pa] / nr[pb]);
+    if (a == b) v.x -= 1.0;
+    mx = fmax(mx, hypot(v.x, v.y));
+  }
+  mx = block_max(mx, red);
+  if (threadIdx.x == 0) out[0] = mx;
+}
+
+__global__ void identity_kernel(int m, zd *I) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i < m) I[i + (long)j * m] = zd{i == j ? 1.0 : 0.0, 0.0};
+}
+
+// ------------------------------------------------------------ Hessenberg --
+// G <- H_j G H_j for j = 0..m-3, H_j = I - tau v v^H (Hermitian, unitary)
+// annihilating G[j+2.., j]; v_{j+1} = 1, v_i = x_i conj(ph) / (|x_{j+1}| +
+// ||x||) with ph the phase of x_{j+1}, tau = 1 + |x_{j+1}| / ||x||, so that
+// H_j x = -ph ||x|| e_{j+1}.  Z <- Z H_j from Z = I.
+__global__ void __launch_bounds__(RT) hessenberg_kernel(int m, zd *G, zd *Z) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  zd *sv = reinterpret_cast<zd *>(smem);  // [m]
+  __shared__ double red[RT];
+  __shared__ double s_tau;
+  __shared__ zd s_sc, s_beta;
+  const int tid = threadIdx.x;
+  for (long t = tid; t < (long)m * m; t += RT) Z[t] = zd{(t % m) == (t / m) ? 1.0 : 0.0, 0.0};
+  __syncthreads();
+  for (int j = 0; j + 2 < m; ++j) {
+    double part = 0.0;
+    for (int i = j + 2 + tid; i < m; i += RT) part += absq(G[i + (long)j * m]);
+    const double rest = block_sum(part, red);
+    if (tid == 0) {
+      const zd x0 = G[j + 1 + (long)j * m];
+      double tau = 0.0;
+      zd sc{0.0, 0.0}, beta = x0;
+      if (rest > 0.0) {
+        const double a0 = hypot(x0.x, x0.y), nx = sqrt(a0 * a0 + rest);
+        const zd ph = a0 > 0.0 ? zd{x0.x / a0, x0.y / a0} : zd{1.0, 0.0};
+        beta = zsc(ph, -nx);
+        sc = zsc(X::conj(ph), 1.0 / (a0 + nx));
+        tau = 1.0 + a0 / nx;
+      }
+      s_tau = tau;
+      s_sc = sc;
+      s_beta = beta;
+    }
+    __syncthreads();
+    const double tau = s_tau;
+    if (tau == 0.0) continue;  // uniform: column already in Hessenberg form
+    const zd sc = s_sc;
+    for (int i = j + 1 + tid; i < m; i += RT) sv[i] = (i == j + 1) ? zd{1.0, 0.0} : X::mul(G[i + (long)j * m], sc);
+    __syncthreads();
+    // left: columns c > j (thread per column)
+    for (int c = j + 1 + tid; c < m; c += RT) {
+      zd *Gc = G + (long)c * m;
+      zd s{0.0, 0.0};
+      for (int r = j + 1; r < m; ++r) s = X::fma(X::conj(sv[r]), Gc[r], s);
+      s = zsc(s, tau);
+      for (int r = j + 1; r < m; ++r) Gc[r] = X::sub(Gc[r], X::mul(sv[r], s));
+    }
+    for (int r = j + 1 + tid; r < m; r += RT) G[r + (long)j * m] = (r == j + 1) ? s_beta : zd{0.0, 0.0};
+    __syncthreads();
+    // right: every row of G and Z (thread per row, coalesced across threads)
+    for (int i = tid; i < m; i += RT) {
+      zd t{0.0, 0.0}, u{0.0, 0.0};
+      for (int c = j + 1; c < m; ++c) {
+        t = X::fma(G[i + (long)c * m], sv[c], t);
+        u = X::fma(Z[i + (long)c * m], sv[c], u);
+      }
+      t = zsc(t, tau);
+      u = zsc(u, tau);
+      for (int c = j + 1; c < m; ++c) {
+        const zd vc = X::conj(sv[c]);
+        G[i + (long)c * m] = X::sub(G[i + (long)c * m], X::mul(t, vc));
+        Z[i + (long)c * m] = X::sub(Z[i + (long)c * m], X::mul(u, vc));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// -------------------------------------------------------------------- QR --
+// Complex Schur form of the upper Hessenberg H (in place) with Z <- Z R^H for
+// every rotation R; lam = diag(T).  err = 1 when more than 30 m sweeps were
+// needed (not converged).
+__global__ void __launch_bounds__(RT) hqr_kernel(int m, zd *H, zd *Z, zd *lam, int *err) {
+  __shared__ double red[RT];
+  __shared__ zd s_x, s_y;
+  const int tid = threadIdx.x;
+  auto h = [&](int i, int j) -> zd & { return H[i + (long)j * m]; };
+  double part = 0.0;
+  for (long t = tid; t < (long)m * m; t += RT) part = fmax(part, cabs1(H[t]));
+  const double hnorm = block_max(part, red);
+  const double small = DBL_MIN * ((double)m / DBL_EPSILON);
+  const int maxsweeps = 30 * (m > 10 ? m : 10);
+  int hi = m - 1, its = 0, sweeps = 0;
+  while (hi > 0) {
+    __syncthreads();
+    int lo = hi;
+    for (; lo > 0; --lo) {
+      const double s = cabs1(h(lo, lo - 1));
+      if (s <= small) break;
+      double tst = cabs1(h(lo - 1, lo - 1)) + cabs1(h(lo, lo));
+      if (tst == 0.0) tst = hnorm;
+      if (s <= DBL_EPSILON * tst) break;
+    }
+    __syncthreads();  // every thread has scanned before the subdiagonal is zeroed
+    if (lo > 0 && tid == 0) h(lo, lo - 1) = zd{0.0, 0.0};
+    if (lo == hi) {  // h(hi, hi) is an eigenvalue of the deflated block
+      --hi;
+      its = 0;
+      continue;
+    }
+    if (++sweeps > maxsweeps) {
+      if (tid == 0) *err = 1;
+      break;
+    }
+    ++its;
+    zd mu;
+    if (its % 10 == 0) {  // exceptional shift
+      mu = X::add(h(hi, hi), zd{0.75 * cabs1(h(hi, hi - 1)), 0.0});
+    } else {  // eigenvalue of the trailing 2 x 2 block closer to h(hi, hi)
+      const zd a = h(hi - 1, hi - 1), b = h(hi - 1, hi), cc = h(hi, hi - 1), d = h(hi, hi);
+      const zd t = zsc(X::sub(a, d), 0.5), bc = X::mul(b, cc);
+      zd disc = zsqrt(X::fma(t, t, bc));
+      if (t.x * disc.x + t.y * disc.y < 0.0) disc = X::neg(disc);
+      const zd den = X::add(t, disc);
+      mu = (den.x == 0.0 && den.y == 0.0) ? d : X::sub(d, zdiv(bc, den));
+    }
+    __syncthreads();
+    if (tid == 0) {
+      s_x = X::sub(h(lo, lo), mu);
+      s_y = h(lo + 1, lo);
+    }
+    __syncthreads();
+    for (int k = lo; k < hi; ++k) {
+      double c;
+      zd s;
+      make_rot(s_x, s_y, c, s);
+      const zd cs = X::conj(s), ms = X::neg(s), mcs = X::neg(cs);
+      // left: rows k, k+1 from column k-1 (k > lo: the bulge column) on
+      const int j0 = (k == lo) ? lo : k - 1;
+      for (int j = j0 + tid; j < m; j += RT) {
+        const zd a = h(k, j), b = h(k + 1, j);
+        h(k, j) = X::fma(s, b, zsc(a, c));
+        h(k + 1, j) = (j == k - 1) ? zd{0.0, 0.0} : X::fma(mcs, a, zsc(b, c));
+      }
+      __syncthreads();
+      // right: columns k, k+1 of rows 0..min(k+2, hi) and of Z
+      const int i1 = (k + 2 < hi) ? k + 2 : hi;
+      for (int i = tid; i <= i1; i += RT) {
+        const zd a = h(i, k), b = h(i, k + 1);
+        const zd na = X::fma(cs, b, zsc(a, c));
+        h(i, k) = na;
+        h(i, k + 1) = X::fma(ms, a, zsc(b, c));
+        if (i == k + 1) s_x = na;  // the next rotation's pair
+        if (i == k + 2) s_y = na;
+      }
+      for (int i = tid; i < m; i += RT) {
+        const zd a = Z[i + (long)k * m], b = Z[i + (long)(k + 1) * m];
+        Z[i + (long)k * m] = X::fma(cs, b, zsc(a, c));
+        Z[i + (long)(k + 1) * m] = X::fma(ms, a, zsc(b, c));
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < m; i += RT) lam[i] = h(i, i);
+}
+
+// ------------------------------------------------------------ eigenvectors --
+// Column k of Y: the eigenvector of the upper triangular T for T[k, k]:
+// y_k = 1, y_i = -(sum_{l=i+1..k} T[i, l] y_l) / (T[i, i] - T[k, k]) for
+// i < k (the denominator raised to smin when smaller), y_i = 0 for i > k.
+// One warp per k; lane l keeps the running sums of rows l, l+32, ...
+template <int MAXR>
+__global__ void trevc_kernel(int m, const zd *T, zd *Y) {
+  const int k = (int)((blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= m) return;
+  const zd tkk = T[k + (long)k * m];
+  const double smin = fmax(DBL_EPSILON * cabs1(tkk), DBL_MIN * ((double)m / DBL_EPSILON));
+  zd acc[MAXR];
+#pragma unroll
+  for (int r = 0; r < MAXR; ++r) {
+    const int i = lane + 32 * r;
+    acc[r] = (i < k) ? T[i + (long)k * m] : zd{0.0, 0.0};
+  }
+  zd *Yk = Y + (long)k * m;
+  for (int i = k + lane; i < m; i += 32) Yk[i] = zd{(i == k) ? 1.0 : 0.0, 0.0};
+#pragma unroll
+  for (int r = MAXR - 1; r >= 0; --r) {
+    if (32 * r >= k) continue;
+    for (int l = 31; l >= 0; --l) {
+      const int i = 32 * r + l;
+      if (i >= k) continue;
+      zd y{0.0, 0.0};
+      if (lane == l) {
+        zd den = X::sub(T[i + (long)i * m], tkk);
+        if (cabs1(den) < smin) den = zd{smin, 0.0};
+        y = X::neg(zdiv(acc[r], den));
+        Yk[i] = y;
+      }
+      y.x = __shfl_sync(0xffffffffu, y.x, l);
+      y.y = __shfl_sync(0xffffffffu, y.y, l);
+      const zd *Ti = T + (long)i * m;
+#pragma unroll
+      for (int q = 0; q < MAXR; ++q) {
+        if (q > r) break;
+        const int row = lane + 32 * q;
+        if (row < i) acc[q] = X::fma(Ti[row], y, acc[q]);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers --
+static dim3 grid2(int n, int m) { return dim3((unsigned)ceil_div(n, 256), (unsigned)m); }
+
+int gen_widen(cudaStream_t st, int n, const double *A, long lda, zd *Af) {
+  widen_ld_kernel<<<grid2(n, n), 256, 0, st>>>(n, A, lda, Af);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+int gen_conj_pair(cudaStream_t st, int n, int m, const zd *src, zd *dst) {
+  if (m < 1) return 0;
+  conj_pair_kernel<<<grid2(n, m), 256, 0, st>>>(n, m, src, dst);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+int gen_accumulate(cudaStream_t st, int n, int m, int nf, const zd *w, const zd *Y, int mw, int half, int left,
+                   zd *Q) {
+  if (m < 1) return 0;
+  accum_gen_kernel<<<grid2(n, m), 256, 0, st>>>(n, m, nf, w, Y, mw, half, left, Q);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+int gen_col_norms(cudaStream_t st, int n, int m, const zd *Xm, double *nrm) {
+  if (m < 1) return 0;
+  col_norms_kernel<<<m, RT, 0, st>>>(n, Xm, nrm);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+int gen_col_scale(cudaStream_t st, int n, int m, const zd *src, zd *dst, const double *s, int divide) {
+  if (m < 1) return 0;
+  col_scale_kernel<<<grid2(n, m), 256, 0, st>>>(n, src, dst, s, divide);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+int gen_residual(cudaStream_t st, int n, int m, const zd *MX, const zd *NX, const zd *lam, int conjl, double alpha,
+                 double *res) {
+  if (m < 1) return 0;
+  gen_residual_kernel<<<m, RT, 0, st>>>(n, MX, NX, lam, conjl, alpha, res);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+int gen_order(cudaStream_t st, int m, const zd *lam, const double *rr, const double *rl, zd emid, double r,
+              double rho, double angle_deg, int *pos, int *src, zd *Eo, double *Rr, double *Rl, double *stats) {
+  if (m < 1 || m > 1024) {
+    set_error("non-Hermitian ordering: subspace size %d outside 1..1024", m);
+    return -4;
+  }
+  const double ph = angle_deg * (3.14159265358979323846 / 180.0);
+  order_gen_kernel<<<1, (m + 31) / 32 * 32, 0, st>>>(m, lam, rr, rl, emid.x, emid.y, r, rho, cos(ph), sin(ph), pos,
+                                                      src, Eo, Rr, Rl, stats);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+int gen_biorth(cudaStream_t st, int m, int nin, const zd *P, const double *nr, const int *src, double *out) {
+  biorth_kernel<<<1, RT, 0, st>>>(m, nin, P, nr, src, out);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+int gen_identity(cudaStream_t st, int m, zd *I) {
+  identity_kernel<<<grid2(m, m), 256, 0, st>>>(m, I);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+int gen_hessenberg(cudaStream_t st, int m, zd *G, zd *Z) {
+  const size_t sm = sizeof(zd) * (size_t)m;
+  static std::atomic<unsigned long long> attr{0};
+  if (int rc = once_per_device(attr, [] {
+        GBF_CUDA(cudaFuncSetAttribute(hessenberg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        return 0;
+      }))
+    return rc;
+  if (sm > 200 * 1024) {
+    set_error("Hessenberg reduction: subspace size %d too large", m);
+    return -4;
+  }
+  hessenberg_kernel<<<1, RT, sm, st>>>(m, G, Z);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+int gen_hqr(cudaStream_t st, int m, zd *H, zd *Z, zd *lam, int *err) {
+  hqr_kernel<<<1, RT, 0, st>>>(m, H, Z, lam, err);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+int gen_trevc(cudaStream_t st, int m, const zd *T, zd *Y) {
+  const int blocks = ceil_div(m, 8);
+  if (m <= 64)
+    trevc_kernel<2><<<blocks, 256, 0, st>>>(m, T, Y);
+  else if (m <= 256)
+    trevc_kernel<8><<<blocks, 256, 0, st>>>(m, T, Y);
+  else if (m <= 1024)
+    trevc_kernel<32><<<blocks, 256, 0, st>>>(m, T, Y);
+  else {
+    set_error("triangular eigenvectors: subspace size %d above 1024", m);
+    return -4;
+  }
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace gbf

@@ -57,7 +57,7 @@ __global__ void form_shift_kernel(int n, int ne, const zd *__restrict__ z, int k
       a.y = -a.y;
       b.y = -b.y;
     }
-    if (i == j) {
+    if (i == j && uplo != 'G') {  // 'G': a general (non-Hermitian) pencil, taken as stored
       a.y = 0.0;
       b.y = 0.0;
     }

@@ -111,3 +111,32 @@ def test_tensor_core_workspace_sizes():
             s = abs(S)
             assert L.gbf_zgemm_sliced_work(m, n, b, S) == (al(s * b * 2 * m * 64 * 2) + al(s * b * n * 64 * 2)
                                                             + al(b * 2 * m * 8) + al(b * n * 8))
+
+
+# ------------------------------------------------ non-Hermitian contour --
+@pytest.mark.parametrize("ne", [1, 2, 7, 16, 40])
+@pytest.mark.parametrize("qtype,ratio,angle", [(0, 100, 0), (1, 100, 0), (0, 50, 30), (1, 170, -135)])
+def test_gcontour_matches_oracle(ne, qtype, ratio, angle):
+    from oracle import feast_gen as G
+
+    for emid, r in [(0.0, 1.0), (0.3 - 0.2j, 1.7), (-4.0 + 2.0j, 0.01)]:
+        z, w = g.gbf_gcontour(emid, r, ne, qtype, ratio, angle)
+        zo, wo = G.gcontour(emid, r, ne, qtype, ratio, angle)
+        scale = abs(emid) + r
+        assert np.max(np.abs(z - zo)) <= 1e-15 * scale * 16
+        assert np.max(np.abs(w - wo)) <= 1e-15 * r * 16
+        lam = emid + r * np.array([0.1 + 0.2j, 0.9, -1.3j, 2.0 + 1.0j])
+        f = g.gbf_grationalx(z, w, lam)
+        assert np.allclose(f, G.grationalx(zo, wo, lam), rtol=1e-10 * (abs(emid) + r) / r, atol=1e-14)
+
+
+def test_gcontour_info_codes():
+    L = g.load()
+    z = np.zeros(32)
+    w = np.zeros(32)
+    zp, wp = C.c_void_p(z.ctypes.data), C.c_void_p(w.ctypes.data)
+    assert L.gbf_gcontour(0.0, 0.0, 0.0, 8, 1, 100, 0, zp, wp) == 200
+    assert L.gbf_gcontour(0.0, 0.0, 1.0, 0, 1, 100, 0, zp, wp) == 108
+    assert L.gbf_gcontour(0.0, 0.0, 1.0, 8, 2, 100, 0, zp, wp) == 117
+    assert L.gbf_gcontour(0.0, 0.0, 1.0, 8, 1, 0, 0, zp, wp) == 118
+    assert L.gbf_gcontour(0.0, 0.0, 1.0, 8, 1, 100, 181, zp, wp) == 119
