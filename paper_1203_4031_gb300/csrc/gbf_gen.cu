@@ -43,24 +43,6 @@ __device__ zd zsqrt(zd z) {
   return zd{fabs(z.y) / (2.0 * t), copysign(t, z.y)};
 }
 
-// Plane rotation R = [[c, s], [-conj(s), c]] (c real) with R [x; y] = [r; 0].
-__device__ void make_rot(zd x, zd y, double &c, zd &s) {
-  const double ax = hypot(x.x, x.y), ay = hypot(y.x, y.y);
-  if (ay == 0.0) {
-    c = 1.0;
-    s = zd{0.0, 0.0};
-    return;
-  }
-  if (ax == 0.0) {
-    c = 0.0;
-    s = zd{y.x / ay, -y.y / ay};
-    return;
-  }
-  const double nrm = hypot(ax, ay);
-  c = ax / nrm;
-  s = zsc(X::mul(zd{x.x / ax, x.y / ax}, X::conj(y)), 1.0 / nrm);
-}
-
 // Deterministic block sum / max (fixed tree over blockDim.x = 256).
 constexpr int RT = 256;
 __device__ double block_sum(double v, double *red) {
@@ -238,15 +220,22 @@ __global__ void identity_kernel(int m, zd *I) {
 // G <- H_j G H_j for j = 0..m-3, H_j = I - tau v v^H (Hermitian, unitary)
 // annihilating G[j+2.., j]; v_{j+1} = 1, v_i = x_i conj(ph) / (|x_{j+1}| +
 // ||x||) with ph the phase of x_{j+1}, tau = 1 + |x_{j+1}| / ||x||, so that
-// H_j x = -ph ||x|| e_{j+1}.  Z <- Z H_j from Z = I.
-__global__ void __launch_bounds__(RT) hessenberg_kernel(int m, zd *G, zd *Z) {
+// H_j x = -ph ||x|| e_{j+1}.  Z <- Z H_j from Z = I.  G and Z are worked on
+// in shared memory when they fit (`in_smem`), else in place in global memory.
+__global__ void __launch_bounds__(RT) hessenberg_kernel(int m, zd *Gg, zd *Zg, int in_smem) {
   extern __shared__ __align__(16) unsigned char smem[];
   zd *sv = reinterpret_cast<zd *>(smem);  // [m]
+  zd *G = in_smem ? sv + m : Gg;
+  zd *Z = in_smem ? sv + m + (size_t)m * m : Zg;
   __shared__ double red[RT];
   __shared__ double s_tau;
   __shared__ zd s_sc, s_beta;
   const int tid = threadIdx.x;
-  for (long t = tid; t < (long)m * m; t += RT) Z[t] = zd{(t % m) == (t / m) ? 1.0 : 0.0, 0.0};
+  const long mm = (long)m * m;
+  for (long t = tid; t < mm; t += RT) {
+    if (in_smem) G[t] = Gg[t];
+    Z[t] = zd{(t % m) == (t / m) ? 1.0 : 0.0, 0.0};
+  }
   __syncthreads();
   for (int j = 0; j + 2 < m; ++j) {
     double part = 0.0;
@@ -273,61 +262,131 @@ __global__ void __launch_bounds__(RT) hessenberg_kernel(int m, zd *G, zd *Z) {
     const zd sc = s_sc;
     for (int i = j + 1 + tid; i < m; i += RT) sv[i] = (i == j + 1) ? zd{1.0, 0.0} : X::mul(G[i + (long)j * m], sc);
     __syncthreads();
-    // left: columns c > j (thread per column)
-    for (int c = j + 1 + tid; c < m; c += RT) {
+    // left: columns c > j; four lanes per column, each over every fourth
+    // row, partial sums combined by two shuffles (a fixed order)
+    for (int c0 = j + 1; c0 < m; c0 += RT / 4) {
+      const int c = c0 + (tid >> 2), q = tid & 3;
+      const bool act = c < m;
       zd *Gc = G + (long)c * m;
-      zd s{0.0, 0.0};
-      for (int r = j + 1; r < m; ++r) s = X::fma(X::conj(sv[r]), Gc[r], s);
-      s = zsc(s, tau);
-      for (int r = j + 1; r < m; ++r) Gc[r] = X::sub(Gc[r], X::mul(sv[r], s));
+      zd sp{0.0, 0.0};
+      if (act)
+        for (int r = j + 1 + q; r < m; r += 4) sp = X::fma(X::conj(sv[r]), Gc[r], sp);
+      sp.x += __shfl_xor_sync(0xffffffffu, sp.x, 1);
+      sp.y += __shfl_xor_sync(0xffffffffu, sp.y, 1);
+      sp.x += __shfl_xor_sync(0xffffffffu, sp.x, 2);
+      sp.y += __shfl_xor_sync(0xffffffffu, sp.y, 2);
+      sp = zsc(sp, tau);
+      if (act)
+        for (int r = j + 1 + q; r < m; r += 4) Gc[r] = X::sub(Gc[r], X::mul(sv[r], sp));
     }
     for (int r = j + 1 + tid; r < m; r += RT) G[r + (long)j * m] = (r == j + 1) ? s_beta : zd{0.0, 0.0};
     __syncthreads();
-    // right: every row of G and Z (thread per row, coalesced across threads)
-    for (int i = tid; i < m; i += RT) {
+    // right: every row of G and Z, four lanes per row over every fourth column
+    for (int i0 = 0; i0 < m; i0 += RT / 4) {
+      const int i = i0 + (tid >> 2), q = tid & 3;
+      const bool act = i < m;
       zd t{0.0, 0.0}, u{0.0, 0.0};
-      for (int c = j + 1; c < m; ++c) {
-        t = X::fma(G[i + (long)c * m], sv[c], t);
-        u = X::fma(Z[i + (long)c * m], sv[c], u);
-      }
+      if (act)
+        for (int c = j + 1 + q; c < m; c += 4) {
+          t = X::fma(G[i + (long)c * m], sv[c], t);
+          u = X::fma(Z[i + (long)c * m], sv[c], u);
+        }
+      t.x += __shfl_xor_sync(0xffffffffu, t.x, 1);
+      t.y += __shfl_xor_sync(0xffffffffu, t.y, 1);
+      u.x += __shfl_xor_sync(0xffffffffu, u.x, 1);
+      u.y += __shfl_xor_sync(0xffffffffu, u.y, 1);
+      t.x += __shfl_xor_sync(0xffffffffu, t.x, 2);
+      t.y += __shfl_xor_sync(0xffffffffu, t.y, 2);
+      u.x += __shfl_xor_sync(0xffffffffu, u.x, 2);
+      u.y += __shfl_xor_sync(0xffffffffu, u.y, 2);
       t = zsc(t, tau);
       u = zsc(u, tau);
-      for (int c = j + 1; c < m; ++c) {
-        const zd vc = X::conj(sv[c]);
-        G[i + (long)c * m] = X::sub(G[i + (long)c * m], X::mul(t, vc));
-        Z[i + (long)c * m] = X::sub(Z[i + (long)c * m], X::mul(u, vc));
-      }
+      if (act)
+        for (int c = j + 1 + q; c < m; c += 4) {
+          const zd vc = X::conj(sv[c]);
+          G[i + (long)c * m] = X::sub(G[i + (long)c * m], X::mul(t, vc));
+          Z[i + (long)c * m] = X::sub(Z[i + (long)c * m], X::mul(u, vc));
+        }
     }
     __syncthreads();
   }
+  if (in_smem)
+    for (long t = tid; t < mm; t += RT) {
+      Gg[t] = G[t];
+      Zg[t] = Z[t];
+    }
 }
 
 // -------------------------------------------------------------------- QR --
+// Plane rotation R = (1/nu) [[conj(x), conj(y)], [-y, x]], nu = ||(x, y)||,
+// as c = conj(x)/nu, s = conj(y)/nu: R [x; y] = [nu; 0], R unitary.  One
+// reciprocal square root (the FP64 chain of one thread is the critical path
+// of every rotation); inputs rescaled first when |x|^2 + |y|^2 would leave
+// the normal range.
+__device__ void make_rot(zd x, zd y, zd &c, zd &s) {
+  double n2 = fma(x.x, x.x, fma(x.y, x.y, fma(y.x, y.x, y.y * y.y)));
+  if (!(n2 > 1e-290 && n2 < 1e290)) {
+    const double sc = fmax(fmax(fabs(x.x), fabs(x.y)), fmax(fabs(y.x), fabs(y.y)));
+    if (!(sc > 0.0) || !isfinite(sc)) {
+      c = zd{1.0, 0.0};
+      s = zd{0.0, 0.0};
+      return;
+    }
+    const double is = 1.0 / sc;
+    x = zsc(x, is);
+    y = zsc(y, is);
+    n2 = fma(x.x, x.x, fma(x.y, x.y, fma(y.x, y.x, y.y * y.y)));
+  }
+  const double r = fast_rsqrt(n2);
+  c = zd{x.x * r, -x.y * r};
+  s = zd{y.x * r, -y.y * r};
+}
+
 // Complex Schur form of the upper Hessenberg H (in place) with Z <- Z R^H for
 // every rotation R; lam = diag(T).  err = 1 when more than 30 m sweeps were
-// needed (not converged).
-__global__ void __launch_bounds__(RT) hqr_kernel(int m, zd *H, zd *Z, zd *lam, int *err) {
-  __shared__ double red[RT];
-  __shared__ zd s_x, s_y;
+// needed (not converged).  H (and Z) are worked on in shared memory when they
+// fit.  FP64 instructions issue slowly per warp on this GPU, so the serial
+// scalar steps (deflation test, shift, rotation) run in one thread, and each
+// rotation's update gives every thread one complex output: the two threads
+// of a row (or column) pair read both inputs, meet at a warp barrier, then
+// write.
+__global__ void __launch_bounds__(RT) hqr_kernel(int m, zd *Hg, zd *Zg, zd *lam, int *err, int h_smem, int z_smem) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ zd s_x, s_y, s_c, s_s;
+  // lo of step t in slot t % 3; slot (t + 2) % 3 is cleared after step t's
+  // barrier, which every thread passes only after reading slot (t - 1) % 3,
+  // and step t + 2 scans only after step t + 1's barrier
+  __shared__ int s_lo[3];
   const int tid = threadIdx.x;
+  const long mm = (long)m * m;
+  zd *H = h_smem ? reinterpret_cast<zd *>(smem) : Hg;
+  zd *Z = z_smem ? reinterpret_cast<zd *>(smem) + (h_smem ? mm : 0) : Zg;
+  for (long t = tid; t < mm; t += RT) {
+    if (h_smem) H[t] = Hg[t];
+    if (z_smem) Z[t] = Zg[t];
+  }
   auto h = [&](int i, int j) -> zd & { return H[i + (long)j * m]; };
+  __shared__ double red[RT];
   double part = 0.0;
-  for (long t = tid; t < (long)m * m; t += RT) part = fmax(part, cabs1(H[t]));
-  const double hnorm = block_max(part, red);
+  for (long t = tid; t < mm; t += RT) part = fmax(part, cabs1(H[t]));
+  const double hnorm = block_max(part, red);  // (ends with a barrier)
   const double small = DBL_MIN * ((double)m / DBL_EPSILON);
   const int maxsweeps = 30 * (m > 10 ? m : 10);
-  int hi = m - 1, its = 0, sweeps = 0;
+  int hi = m - 1, its = 0, sweeps = 0, par = 0;
+  if (tid == 0) s_lo[0] = s_lo[1] = s_lo[2] = 0;
+  __syncthreads();
   while (hi > 0) {
-    __syncthreads();
-    int lo = hi;
-    for (; lo > 0; --lo) {
-      const double s = cabs1(h(lo, lo - 1));
-      if (s <= small) break;
-      double tst = cabs1(h(lo - 1, lo - 1)) + cabs1(h(lo, lo));
+    // lo: the largest l <= hi with a negligible h(l, l-1), else 0
+    for (int l = 1 + tid; l <= hi; l += RT) {
+      const double sl = cabs1(h(l, l - 1));
+      double tst = cabs1(h(l - 1, l - 1)) + cabs1(h(l, l));
       if (tst == 0.0) tst = hnorm;
-      if (s <= DBL_EPSILON * tst) break;
+      if (sl <= small || sl <= DBL_EPSILON * tst) atomicMax(&s_lo[par], l);
     }
-    __syncthreads();  // every thread has scanned before the subdiagonal is zeroed
+    __syncthreads();
+    const int lo = s_lo[par];
+    if (tid == 0) s_lo[(par + 2) % 3] = 0;
+    par = (par + 1) % 3;
     if (lo > 0 && tid == 0) h(lo, lo - 1) = zd{0.0, 0.0};
     if (lo == hi) {  // h(hi, hi) is an eigenvalue of the deflated block
       --hi;
@@ -339,56 +398,83 @@ __global__ void __launch_bounds__(RT) hqr_kernel(int m, zd *H, zd *Z, zd *lam, i
       break;
     }
     ++its;
-    zd mu;
-    if (its % 10 == 0) {  // exceptional shift
-      mu = X::add(h(hi, hi), zd{0.75 * cabs1(h(hi, hi - 1)), 0.0});
-    } else {  // eigenvalue of the trailing 2 x 2 block closer to h(hi, hi)
-      const zd a = h(hi - 1, hi - 1), b = h(hi - 1, hi), cc = h(hi, hi - 1), d = h(hi, hi);
-      const zd t = zsc(X::sub(a, d), 0.5), bc = X::mul(b, cc);
-      zd disc = zsqrt(X::fma(t, t, bc));
-      if (t.x * disc.x + t.y * disc.y < 0.0) disc = X::neg(disc);
-      const zd den = X::add(t, disc);
-      mu = (den.x == 0.0 && den.y == 0.0) ? d : X::sub(d, zdiv(bc, den));
-    }
-    __syncthreads();
     if (tid == 0) {
+      zd mu;
+      if (its % 10 == 0) {  // exceptional shift
+        mu = X::add(h(hi, hi), zd{0.75 * cabs1(h(hi, hi - 1)), 0.0});
+      } else {  // eigenvalue of the trailing 2 x 2 block closer to h(hi, hi)
+        const zd a = h(hi - 1, hi - 1), b = h(hi - 1, hi), cc = h(hi, hi - 1), d = h(hi, hi);
+        const zd t = zsc(X::sub(a, d), 0.5), bc = X::mul(b, cc);
+        zd disc = zsqrt(X::fma(t, t, bc));
+        if (t.x * disc.x + t.y * disc.y < 0.0) disc = X::neg(disc);
+        const zd den = X::add(t, disc);
+        mu = (den.x == 0.0 && den.y == 0.0) ? d : X::sub(d, zdiv(bc, den));
+      }
       s_x = X::sub(h(lo, lo), mu);
       s_y = h(lo + 1, lo);
     }
-    __syncthreads();
     for (int k = lo; k < hi; ++k) {
-      double c;
-      zd s;
-      make_rot(s_x, s_y, c, s);
-      const zd cs = X::conj(s), ms = X::neg(s), mcs = X::neg(cs);
-      // left: rows k, k+1 from column k-1 (k > lo: the bulge column) on
-      const int j0 = (k == lo) ? lo : k - 1;
-      for (int j = j0 + tid; j < m; j += RT) {
-        const zd a = h(k, j), b = h(k + 1, j);
-        h(k, j) = X::fma(s, b, zsc(a, c));
-        h(k + 1, j) = (j == k - 1) ? zd{0.0, 0.0} : X::fma(mcs, a, zsc(b, c));
+      if (tid == 0) {
+        zd c, sn;
+        make_rot(s_x, s_y, c, sn);
+        s_c = c;
+        s_s = sn;
       }
       __syncthreads();
-      // right: columns k, k+1 of rows 0..min(k+2, hi) and of Z
-      const int i1 = (k + 2 < hi) ? k + 2 : hi;
-      for (int i = tid; i <= i1; i += RT) {
-        const zd a = h(i, k), b = h(i, k + 1);
-        const zd na = X::fma(cs, b, zsc(a, c));
-        h(i, k) = na;
-        h(i, k + 1) = X::fma(ms, a, zsc(b, c));
-        if (i == k + 1) s_x = na;  // the next rotation's pair
-        if (i == k + 2) s_y = na;
+      const zd c = s_c, sn = s_s, cc = X::conj(c), cs = X::conj(sn), ms = X::neg(sn), mcs = X::neg(cs);
+      // left: rows k, k+1 from column k-1 (k > lo: the bulge column) on;
+      // lanes 2q, 2q+1 take column j0 + q, rows k and k+1
+      const int j0 = (k == lo) ? lo : k - 1;
+      for (int base = 0; base < 2 * (m - j0); base += RT) {
+        const int t = base + tid, j = j0 + (t >> 1);
+        const bool act = j < m;
+        zd a{0.0, 0.0}, b{0.0, 0.0};
+        if (act) {
+          a = h(k, j);
+          b = h(k + 1, j);
+        }
+        __syncwarp();
+        if (act) {
+          if ((t & 1) == 0) h(k, j) = X::fma(sn, b, X::mul(c, a));
+          else h(k + 1, j) = (j == k - 1) ? zd{0.0, 0.0} : X::fma(mcs, a, X::mul(cc, b));
+        }
       }
-      for (int i = tid; i < m; i += RT) {
-        const zd a = Z[i + (long)k * m], b = Z[i + (long)(k + 1) * m];
-        Z[i + (long)k * m] = X::fma(cs, b, zsc(a, c));
-        Z[i + (long)(k + 1) * m] = X::fma(ms, a, zsc(b, c));
+      __syncthreads();
+      // right: columns k, k+1 of rows 0..i1 of H and of every row of Z;
+      // lanes 2q, 2q+1 take one row, columns k and k+1
+      const int i1 = (k + 2 < hi) ? k + 2 : hi;
+      const int nh = 2 * (i1 + 1), items = nh + 2 * m;
+      for (int base = 0; base < items; base += RT) {
+        const int t = base + tid;
+        const bool act = t < items, onH = t < nh;
+        const int i = onH ? (t >> 1) : ((t - nh) >> 1);
+        zd *P = onH ? H : Z;
+        zd a{0.0, 0.0}, b{0.0, 0.0};
+        if (act) {
+          a = P[i + (long)k * m];
+          b = P[i + (long)(k + 1) * m];
+        }
+        __syncwarp();
+        if (act) {
+          if ((t & 1) == 0) {
+            const zd na = X::fma(cs, b, X::mul(cc, a));
+            P[i + (long)k * m] = na;
+            if (onH && i == k + 1) s_x = na;  // the next rotation's pair
+            if (onH && i == k + 2) s_y = na;
+          } else {
+            P[i + (long)(k + 1) * m] = X::fma(ms, a, X::mul(c, b));
+          }
+        }
       }
       __syncthreads();
     }
   }
   __syncthreads();
   for (int i = tid; i < m; i += RT) lam[i] = h(i, i);
+  for (long t = tid; t < mm; t += RT) {
+    if (h_smem) Hg[t] = H[t];
+    if (z_smem) Zg[t] = Z[t];
+  }
 }
 
 // ------------------------------------------------------------ eigenvectors --
@@ -510,43 +596,62 @@ int gen_identity(cudaStream_t st, int m, zd *I) {
   GBF_CUDA(cudaGetLastError());
   return 0;
 }
+static constexpr size_t GEN_SMEM = 200 * 1024;
 int gen_hessenberg(cudaStream_t st, int m, zd *G, zd *Z) {
-  const size_t sm = sizeof(zd) * (size_t)m;
   static std::atomic<unsigned long long> attr{0};
   if (int rc = once_per_device(attr, [] {
-        GBF_CUDA(cudaFuncSetAttribute(hessenberg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        GBF_CUDA(cudaFuncSetAttribute(hessenberg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEN_SMEM));
         return 0;
       }))
     return rc;
-  if (sm > 200 * 1024) {
+  const size_t full = sizeof(zd) * ((size_t)m + 2 * (size_t)m * m);
+  const int in_smem = full <= GEN_SMEM ? 1 : 0;
+  const size_t sm = in_smem ? full : sizeof(zd) * (size_t)m;
+  if (sm > GEN_SMEM) {
     set_error("Hessenberg reduction: subspace size %d too large", m);
     return -4;
   }
-  hessenberg_kernel<<<1, RT, sm, st>>>(m, G, Z);
+  const int slot = prof_begin(st);
+  hessenberg_kernel<<<1, RT, sm, st>>>(m, G, Z, in_smem);
   GBF_LAUNCHED();
   GBF_CUDA(cudaGetLastError());
+  prof_end(st, slot, 0.0);
   return 0;
 }
 int gen_hqr(cudaStream_t st, int m, zd *H, zd *Z, zd *lam, int *err) {
-  hqr_kernel<<<1, RT, 0, st>>>(m, H, Z, lam, err);
+  static std::atomic<unsigned long long> attr{0};
+  if (int rc = once_per_device(attr, [] {
+        GBF_CUDA(cudaFuncSetAttribute(hqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEN_SMEM));
+        return 0;
+      }))
+    return rc;
+  const size_t one = sizeof(zd) * (size_t)m * m;
+  const int h_smem = one <= GEN_SMEM ? 1 : 0;
+  const int z_smem = (h_smem && 2 * one <= GEN_SMEM) ? 1 : 0;
+  const size_t sm = one * (h_smem + z_smem);
+  const int slot = prof_begin(st);
+  hqr_kernel<<<1, RT, sm, st>>>(m, H, Z, lam, err, h_smem, z_smem);
   GBF_LAUNCHED();
   GBF_CUDA(cudaGetLastError());
+  prof_end(st, slot, 0.0);
   return 0;
 }
 int gen_trevc(cudaStream_t st, int m, const zd *T, zd *Y) {
   const int blocks = ceil_div(m, 8);
+  if (m > 1024) {
+    set_error("triangular eigenvectors: subspace size %d above 1024", m);
+    return -4;
+  }
+  const int slot = prof_begin(st);
   if (m <= 64)
     trevc_kernel<2><<<blocks, 256, 0, st>>>(m, T, Y);
   else if (m <= 256)
     trevc_kernel<8><<<blocks, 256, 0, st>>>(m, T, Y);
-  else if (m <= 1024)
+  else
     trevc_kernel<32><<<blocks, 256, 0, st>>>(m, T, Y);
-  else {
-    set_error("triangular eigenvectors: subspace size %d above 1024", m);
-    return -4;
-  }
   GBF_LAUNCHED();
   GBF_CUDA(cudaGetLastError());
+  prof_end(st, slot, 0.0);
   return 0;
 }
 
