@@ -665,6 +665,12 @@ def measured_peaks():
 # the sliced GEMM kernel on the solve shape 4096 x 300 x 32, 8 nodes (the
 # capture in profiles/), or None when the kernel changed since it was taken
 SLICED_TRAFFIC_BYTES = None
+# ctf32_kernel on the early trailing-update shape 4096 x 4096 x 32, 2 nodes
+# (profiles/ctf32_kernel_lu-update-shape_4096x4096x32x2.md): DRAM read +
+# write and the algorithmic bytes of that launch (C read + written, TF32
+# planes of A and B)
+CTF32_CAPTURE = {"dram_bytes": 284.2e6 + 208.1e6, "algorithmic_bytes": 549.5e6,
+                 "shape": "4096 x 4096 x 32, 2 nodes"}
 
 
 def lu_update_bytes(n, ne, nb=32, entry_bytes=8):
@@ -694,9 +700,15 @@ def roofline(prof, tc, path, n=None, ne=None):
         byt = lu_update_bytes(n, ne)
         pk = measured_peaks().get("hbm_gbs", 6800.0) * 1e9
         ach = byt / (lms / 1e3)
+        cap = CTF32_CAPTURE
+        ratio = cap["dram_bytes"] / cap["algorithmic_bytes"]
         return {"kernel": "ctf32_kernel (FP32 LU trailing updates, C read and written once per step)",
                 "bound": "hbm", "achieved": ach / 1e9, "peak": pk / 1e9, "unit": "GB/s", "frac": ach / pk,
-                "traffic": None, "algorithmic_bytes_per_step": byt, "launches": ln,
+                "traffic": byt * ratio,
+                "traffic_source": (f"per step: algorithmic bytes x the DRAM/algorithmic ratio {ratio:.3f} of one "
+                                   f"ncu capture ({cap['shape']}: {cap['dram_bytes'] / 1e6:.1f} MB DRAM for "
+                                   f"{cap['algorithmic_bytes'] / 1e6:.1f} MB algorithmic)"),
+                "algorithmic_bytes_per_step": byt, "launches": ln,
                 "avg_launch_ms": lms / max(ln, 1), "ms_per_step": lms,
                 "peak_source": "measured HBM copy (MEASURED_PEAKS.json), of measured"}
     other = {k: v for k, v in prof.items() if k not in ("lu_update_gemm", "solve_gemm")}

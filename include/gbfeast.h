@@ -383,8 +383,7 @@ int gbf_cgemm_tf32(void *stream, char opa, char opb, int m, int n, int k, double
  *    gbf_zgemm_sliced_noalloc_max() bytes is rejected with -7 and a message
  *    in gbf_last_error(); nothing is launched;
  *  - the first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture;
+ *    (cudaGetSymbolAddress) with that device current;
  *  - every call shares the one array and it keeps the last call's contents
  *    (the call clears what must start at zero): calls whose work overlaps on
  *    the GPU (other streams, other threads) race and must not be issued;
