@@ -562,11 +562,15 @@ def run_nonhermitian(g, torch, W, n=4096, count=40, m0=64):
         L.gbf_profile(1)
         g.feast_gen_dev(A, B, P.emid, P.r, P.m0, f, handle=h)
         torch.cuda.synchronize()
-        prof = {}
+        prof, prof_full = {}, {}
         for c in range(L.gbf_profile_categories()):
             nl, t, fl = C.c_longlong(), C.c_double(), C.c_double()
             L.gbf_profile_read(c, C.byref(nl), C.byref(t), C.byref(fl))
             prof[L.gbf_profile_name(c).decode()] = round(t.value, 3)
+            prof_full[L.gbf_profile_name(c).decode()] = (nl.value, t.value, fl.value)
+        nl, t, fl, tf = C.c_longlong(), C.c_double(), C.c_double(), C.c_double()
+        L.gbf_profile_tc(C.byref(nl), C.byref(t), C.byref(fl), C.byref(tf))
+        tc = (nl.value, t.value, fl.value, tf.value)
         L.gbf_profile(0)
         M = r["M"]
         E = r["E"][:M].cpu().numpy()
@@ -584,7 +588,8 @@ def run_nonhermitian(g, torch, W, n=4096, count=40, m0=64):
                      "pairs_passing": ok, "max_abs_eig_err": err,
                      "max_res_right": float(np.max(res[:M])) if M else None,
                      "max_res_left": float(np.max(res[P.m0:P.m0 + M])) if M else None,
-                     "biorth_defect": r["biorth"], "gpu_launches": launches, "kernels_ms": prof}
+                     "biorth_defect": r["biorth"], "gpu_launches": launches, "kernels_ms": prof,
+                     "roofline": roofline(prof_full, tc, "fp64")}
         h.close()
         del A, B
         torch.cuda.empty_cache()

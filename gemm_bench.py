@@ -6,6 +6,7 @@ kernel in isolation:
   python gemm_bench.py --kind anyk --cplx 1 --m 2048 --n 300 --k 2048
   python gemm_bench.py --kind tf32 --m 4096 --n 4096 --k 32 --batch 2
   python gemm_bench.py --kind lu --m 4096 --batch 8 --prec 1
+  python gemm_bench.py --kind gen --m 4096 --cplx 0 --reps 1
 
 k32: gbf_zgemm_sliced (k <= 32, 7 digits, complex FP64), C -= A B.
 tf32: gbf_zgemm_sliced with S = 1 (k <= 32, complex FP32, 3xTF32 products),
@@ -15,6 +16,9 @@ op(A) = A^T read from an (m x k)-transposed store, as the projections use it.
 lu: gbf_factor_dev, the blocked LU of `batch` shifted systems z_e I - A of one
 m x m complex Hermitian A (panels, swaps, trailing updates), FP64 factors
 (--prec 0) or FP32 (--prec 1).
+gen: one non-Hermitian FEAST solve (gbf_dgegv_dev / gbf_zgegv_dev) of the
+seeded n = m pencil with a known spectrum (real generalized with --cplx 0,
+complex standard with --cplx 1), 40 eigenvalues inside, M0 = 64, 16 nodes.
 Prints the time per call (CUDA events, after warm-up) and the useful FP64
 rate; inputs are seeded normal values resident on the device."""
 import argparse
@@ -29,7 +33,7 @@ from paper_1203_4031_gb300 import _ptr, _stream_ptr, last_error, lib  # noqa: E4
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kind", choices=["k32", "anyk", "tf32", "lu"], default="k32")
+    ap.add_argument("--kind", choices=["k32", "anyk", "tf32", "lu", "gen"], default="k32")
     ap.add_argument("--prec", type=int, default=0)
     ap.add_argument("--cplx", type=int, default=1)
     ap.add_argument("--m", type=int, default=4096)
@@ -43,6 +47,8 @@ def main(argv=None):
     g = torch.Generator(device="cuda").manual_seed(1)
     if a.kind == "lu":
         return factor_bench(a, g)
+    if a.kind == "gen":
+        return gen_bench(a)
     cplx = 1 if a.kind in ("k32", "tf32") else a.cplx
     dt = torch.complex128 if cplx else torch.float64
     m, n, k, bt = a.m, a.n, a.k, a.batch
@@ -124,6 +130,32 @@ def factor_bench(a, g):
     flops = 8.0 / 3.0 * n ** 3 * ne
     print(f"lu prec={a.prec} n={n} nodes={ne}: {ms:.2f} ms per factorisation of all nodes, "
           f"{flops / ms / 1e9:.2f} useful TFLOP/s")
+    h.close()
+
+
+def gen_bench(a):
+    import numpy as np
+
+    import paper_1203_4031_gb300 as gb
+    from paper_1203_4031_gb300 import workloads as W
+
+    P = W.dense_nonsymmetric(a.m, count=40, m0=64, complex_=bool(a.cplx), generalized=not a.cplx)
+    A = gb.fortran(torch.from_numpy(np.ascontiguousarray(P.A)).cuda())
+    B = gb.fortran(torch.from_numpy(np.ascontiguousarray(P.B)).cuda()) if P.B is not None else None
+    f = P.apply_fpm(gb.gbf_init())
+    h = gb.Handle()
+    for _ in range(a.warmup):
+        gb.feast_gen_dev(A, B, P.emid, P.r, P.m0, f, handle=h)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(a.reps):
+        r = gb.feast_gen_dev(A, B, P.emid, P.r, P.m0, f, handle=h)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(a.reps, 1)
+    print(f"gen {P.name}: {ms:.1f} ms per solve, info {r['info']}, M {r['M']}, loops {r['loop']}")
     h.close()
 
 

@@ -281,6 +281,9 @@ template <class TQ, class TL> struct WS {
   size_t kw_bytes;
   TL *dinv_l, *dinv_u;    // 128 x 128 diagonal-block inverses (recursive solves' leaves)
   float *fpre_n, *fpre_c; // TF32 planes of the FP32 factors (op N, op C), split once
+  char *acache_base;      // FP64 factors: digit slices of the solves' factor blocks
+  size_t acache_bytes;
+  SliceCache acache;
 
   // ne: quadrature nodes; nf: nodes factored and solved here (all of them,
   // or this shard's share); slots: node solution blocks (ne, or nranks x the
@@ -358,6 +361,12 @@ template <class TQ, class TL> struct WS {
     const bool pre = kw_bytes && sizeof(TL) == sizeof(cf) && n >= 1024;
     fpre_n = pre ? b.take<float>(tf32_planes_bytes(n, nfa) / 4) : nullptr;
     fpre_c = pre && herm ? b.take<float>(tf32_planes_bytes(n, nfa) / 4) : nullptr;
+    // FP64 factors: the factor blocks' slices, kept across the FEAST
+    // iterations (sweeps L, U, and for adjoint solves U^H, L^H), at most 24 GB
+    acache_bytes = (kw_bytes && sizeof(TL) == sizeof(zd))
+                       ? std::min(solve_slice_cache_bytes(n, m0, bs, nfa, herm ? 4 : 2, big), (size_t)24 << 30)
+                       : 0;
+    acache_base = acache_bytes ? b.take<char>(acache_bytes) : nullptr;
     pja = pjb = pjq = pjh = pjx = pjw = rrw = nullptr;
     rrw_bytes = 0;
     if (proj) {
@@ -496,6 +505,10 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
   tcx.fpre_n = ws.fpre_n;
   tcx.fpre_c = ws.fpre_c;
   tcx.fpre_ne = ws.fpre_n ? std::max(nf, 1) : 0;
+  ws.acache.base = ws.acache_base;
+  ws.acache.cap = ws.acache_bytes;
+  ws.acache.reset();
+  tcx.acache = ws.acache_bytes ? &ws.acache : nullptr;
   TcScope tc_scope(tcS ? &tcx : nullptr);
   AuxScope aux_scope(ensure_aux(h));
   if (ensure_hbuf(h, (size_t)std::max(m0, ne) + 64)) return out.info = -1;
@@ -530,6 +543,7 @@ static int feast_run(gbf_context *h, cudaStream_t st, const Req &q, Res &out) {
     CK(form_shift<TL>(st, n, nf, ws.z + nlo, kind_of<TQ>::v, 'F', Af, lda, hasB ? (const void *)Bf : nullptr, ldb,
                       ws.S, ws.sing + nfa));
     CK(getrf_batched<TL>(st, n, nf, ws.S, ws.ipiv, ws.perm, ws.Linv, ws.Uinv, bs, ws.sing, nullptr));
+    ws.acache.reset();  // slices of these factors are taken by the first solves
     if constexpr (std::is_same<TL, cf>::value) {
       if (ws.fpre_n) CK(tf32_presplit(st, 'N', n, nf, ws.S, ws.fpre_n));
       if (ws.fpre_c) CK(tf32_presplit(st, 'C', n, nf, ws.S, ws.fpre_c));
@@ -963,7 +977,10 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
     double *rr, *rl, *nr, *nl, *Rr, *Rl, *stats;
     void *tcw, *kw, *dinv_l, *dinv_u, *pja, *pjah, *pjb, *pjbh, *pjq, *pjh, *pjx, *pjw, *rrw;
     size_t tcw_bytes, kw_bytes, rrw_bytes;
+    char *acache_base;
+    size_t acache_bytes;
   } ws;
+  SliceCache acache;
   auto layout = [&](Bump &b) {
     ws.Af = q.real ? b.take<zd>(nn) : nullptr;
     ws.Bf = (q.real && hasB) ? b.take<zd>(nn) : nullptr;
@@ -1009,6 +1026,9 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
     const bool big = ws.kw_bytes && bs == 32 && n % 128 == 0;
     ws.dinv_l = big ? (void *)b.take<zd>((size_t)nf * n * 128) : nullptr;
     ws.dinv_u = big ? (void *)b.take<zd>((size_t)nf * n * 128) : nullptr;
+    ws.acache_bytes =
+        ws.kw_bytes ? std::min(solve_slice_cache_bytes(n, mw, bs, nf, 4, big), (size_t)24 << 30) : 0;
+    ws.acache_base = ws.acache_bytes ? b.take<char>(ws.acache_bytes) : nullptr;
     const long Kp = sliced_kp(n, true), R = 2L * n, Km = sliced_kp(m0, true), Rm = 2L * m0;
     ws.pja = b.take<char>(sliced_op_bytes(R, Kp, 1));
     ws.pjah = b.take<char>(sliced_op_bytes(R, Kp, 1));
@@ -1037,6 +1057,14 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
   tcx.kbytes = ws.kw_bytes;
   tcx.dinv_l = ws.dinv_l;
   tcx.dinv_u = ws.dinv_u;
+  acache.base = ws.acache_base;
+  acache.cap = ws.acache_bytes;
+  tcx.acache = ws.acache_bytes ? &acache : nullptr;
+  // the M0-sized LU and solves of the reduced pencil: the same engine
+  // without the n-sized leaf inverses and slice cache
+  TcCtx tcr = tcx;
+  tcr.dinv_l = tcr.dinv_u = nullptr;
+  tcr.acache = nullptr;
   TcScope tc_scope(tcS ? &tcx : nullptr);
   AuxScope aux_scope(ensure_aux(h));
   if (ensure_hbuf(h, (size_t)std::max(m0, ne) + 64)) return out.info = -1;
@@ -1064,6 +1092,7 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
   // factor the nodes (kept for the whole iteration)
   CK(form_shift<zd>(st, n, nf, ws.z, 1, 'G', Af, lda, hasB ? (const void *)Bf : nullptr, ldb, ws.S, ws.sing + nf));
   CK(getrf_batched<zd>(st, n, nf, ws.S, ws.ipiv, ws.perm, ws.Linv, ws.Uinv, bs, ws.sing, nullptr));
+  acache.reset();
   {
     int *hs = (int *)h->hbuf;
     GBF_CUDA(cudaMemcpyAsync(hs, ws.sing, sizeof(int) * (nf + 1), cudaMemcpyDeviceToHost, st));
@@ -1172,7 +1201,7 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
     // ---- reduced pencil: G = Bq^{-1} Aq = Z T Z^H, W = Z Y, V = (Bq W)^{-H} ----
     {
       CatScope cat_red(CAT_REDUCED);
-      TcScope no_tc(nullptr);  // the m-sized LU keeps clear of the n-sized factor workspace
+      TcScope red_tc(tcS ? &tcr : nullptr);
       GBF_CUDA(cudaMemsetAsync(ws.sgr, 0, sizeof(int) * 2, st));
       GBF_CUDA(cudaMemcpyAsync(ws.Sr, ws.Bq, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, st));
       CK(getrf_batched<zd>(st, m, 1, ws.Sr, ws.ipr, ws.pmr, ws.Lr, ws.Ur, bs, ws.sgr, nullptr));

@@ -8,6 +8,7 @@
 
 #include <atomic>
 #include <mutex>
+#include <unordered_map>
 
 namespace gbf {
 
@@ -206,6 +207,7 @@ void prof_set_flops(int slot, double flops);  // flops known only after the laun
 // enough) run on the tensor cores using the scope's workspace and error
 // word: S = 7 sliced digits (FP64-class) for zd, S = 1 3xTF32 products
 // (FP32-class) for cf.
+struct SliceCache;
 struct TcCtx {
   void *work = nullptr;
   size_t bytes = 0;
@@ -218,12 +220,17 @@ struct TcCtx {
   const float *fpre_n = nullptr;  // FP32 factors split once into TF32 planes, op 'N' and op 'C'
   const float *fpre_c = nullptr;  // (tf32_presplit; nullptr: every update splits its operand)
   int fpre_ne = 0;                // nodes in the planes
+  SliceCache *acache = nullptr;   // FP64 factors: digit slices of the solves' factor blocks, kept
+                                  // from the first solve of a factorisation for the later ones
 };
 // Workspace bytes of the recursive solves' any-k sliced updates for n x n
 // factors, nrhs right-hand sides, block size bs (node groups of up to 8).
 size_t solve_kwork_bytes(int n, int nrhs, int bs, int ne);
 // The same for FP32 factors (3xTF32 any-k updates of the recursive solves).
 size_t solve_kwork_bytes_cf(int n, int nrhs, int bs, int ne);
+// Bytes of the factor-block slices of nkinds recursive FP64 sweeps (the
+// SliceCache of TcCtx; leaves128: the 128-row leaf inverses are used).
+size_t solve_slice_cache_bytes(int n, int nrhs, int bs, int ne, int nkinds, bool leaves128);
 extern thread_local TcCtx *g_tc;
 // Side stream (high priority) and two events of the calling context, for
 // the factorisation's look-ahead: panel k+1 runs there while the rest of
@@ -250,6 +257,20 @@ struct SlicedOp {
   const int *exps;
   long rows;
   long Kp;
+};
+// Slices of operands that stay fixed across calls (the factor blocks of the
+// recursive solves: the same blocks in every FEAST iteration), in a region
+// of the caller's workspace, looked up by (address, op, shape, batch).
+// Cleared when the factors change.  A block that no longer fits is sliced
+// per call as before.
+struct SliceCache {
+  char *base = nullptr;
+  size_t cap = 0, used = 0;
+  std::unordered_map<uint64_t, SlicedOp> ops;
+  void reset() {
+    used = 0;
+    ops.clear();
+  }
 };
 long sliced_kp(int k, bool cplx);
 size_t sliced_op_bytes(long rows, long Kp, int batch);

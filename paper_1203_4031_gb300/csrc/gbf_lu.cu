@@ -969,6 +969,38 @@ size_t solve_kwork_bytes(int n, int nrhs, int bs, int ne) {
   return b;
 }
 
+// Bytes of the factor-block slices the recursive FP64 solves would keep in a
+// SliceCache for `nkinds` sweeps (kinds 0, 1 and, for adjoint solves, 2, 3):
+// the same walk over the block ranges as trsv_rec, with the same node groups.
+size_t solve_slice_cache_bytes(int n, int nrhs, int bs, int ne, int nkinds, bool leaves128) {
+  const size_t kb = solve_kwork_bytes(n, nrhs, bs, ne);
+  const int nblk = ceil_div(n, bs);
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  size_t total = 0;
+  // kinds 0/2 and 1/3 have the same update shapes (m, k swapped by side)
+  auto walk = [&](auto &&self, int kind, int b0, int b1) -> void {
+    if (b1 - b0 == 1) return;
+    if (leaves128 && b1 - b0 == 4 && bs == 32 && b0 % 4 == 0 && n % 128 == 0) {
+      total += al(sliced_op_bytes(256, sliced_kp(128, true), ne));
+      return;
+    }
+    const int mid = b0 + (b1 - b0) / 2;
+    const int r0 = b0 * bs, rm = mid * bs, r1 = std::min(n, b1 * bs);
+    self(self, kind, b0, mid);
+    const bool lowerside = (kind == 0 || kind == 2);
+    const int m = lowerside ? r1 - rm : rm - r0, k = lowerside ? rm - r0 : r1 - rm;
+    if (k > 32) {
+      const size_t per = gemm_sliced_k_work(true, m, nrhs, k, 1);
+      const int g = (int)std::max<size_t>(1, std::min<size_t>(ne, kb / std::max<size_t>(per, 1)));
+      for (int e0 = 0; e0 < ne; e0 += g)
+        total += al(sliced_op_bytes(2L * m, sliced_kp(k, true), std::min(g, ne - e0)));
+    }
+    self(self, kind, mid, b1);
+  };
+  for (int kind = 0; kind < nkinds; ++kind) walk(walk, kind, 0, nblk);
+  return total;
+}
+
 size_t solve_kwork_bytes_cf(int n, int nrhs, int bs, int ne) {
   const int nblk = ceil_div(n, bs);
   const int half = std::min(n, (nblk - nblk / 2) * bs);
@@ -1152,6 +1184,45 @@ static int tf32_update(cudaStream_t st, char opa, int m, int k, int nrhs, const 
   return 0;
 }
 
+// C = alpha op(A) Y (+ C when beta_one) for a group of gb nodes with the any-k
+// sliced GEMM; A's slices come from the factorisation's slice cache when
+// there is one (sliced on first use, kept until the factors change), else
+// A is sliced into the workspace with Y.  Same slices either way, so the
+// same results.
+static int sliced_gemm_cached(cudaStream_t st, char opa, int m, int nrhs, int k, double alpha, const zd *A, long lda,
+                              long sa, const zd *Y, long ldy, long sy, int beta_one, zd *C, long ldc, long sc,
+                              int gb) {
+  SliceCache *cache = g_tc->acache;
+  if (cache) {
+    uint64_t key = (uint64_t)(uintptr_t)A;
+    key = key * 0x9E3779B97F4A7C15ULL ^ ((uint64_t)(unsigned char)opa << 56 | (uint64_t)gb << 40 |
+                                         (uint64_t)(unsigned)m << 20 | (uint64_t)(unsigned)k);
+    key = key * 0xBF58476D1CE4E5B9ULL ^ (uint64_t)lda ^ ((uint64_t)sa << 17);
+    SlicedOp a;
+    bool have = false;
+    const auto it = cache->ops.find(key);
+    if (it != cache->ops.end()) {
+      a = it->second;
+      have = true;
+    } else {
+      const size_t bytes = (sliced_op_bytes(2L * m, sliced_kp(k, true), gb) + 255) & ~(size_t)255;
+      if (cache->used + bytes <= cache->cap) {
+        if (int rc = slice_rows<zd>(st, opa, m, k, A, lda, sa, gb, cache->base + cache->used, &a)) return rc;
+        cache->used += bytes;
+        cache->ops.emplace(key, a);
+        have = true;
+      }
+    }
+    if (have) {
+      SlicedOp b;
+      if (int rc = slice_cols<zd>(st, 'N', k, nrhs, Y, ldy, sy, gb, g_tc->kwork, &b)) return rc;
+      return gemm_sliced_ops<zd>(st, a, b, gb, alpha, beta_one, C, ldc, sc, g_tc->gerr);
+    }
+  }
+  return gemm_sliced_k<zd>(st, opa, 'N', m, nrhs, k, alpha, A, lda, sa, Y, ldy, sy, beta_one, C, ldc, sc, gb,
+                           g_tc->kwork, g_tc->kbytes, g_tc->gerr);
+}
+
 // C[e] -= op(A[e]) Y[e] for all nodes e with the any-k sliced GEMM, nodes
 // grouped so that each group's slices fit the workspace.
 template <class T>
@@ -1161,8 +1232,13 @@ static int sliced_update(cudaStream_t st, char opa, int m, int k, int nrhs, cons
   const int g = (int)std::max<size_t>(1, std::min<size_t>(ne, g_tc->kbytes / std::max<size_t>(per, 1)));
   for (int e0 = 0; e0 < ne; e0 += g) {
     const int gb = std::min(g, ne - e0);
-    const int rc = gemm_sliced_k<T>(st, opa, 'N', m, nrhs, k, -1.0, A + (long)e0 * sa, lda, sa, Y + (long)e0 * sy,
-                                    ldy, sy, 1, C + (long)e0 * sc, ldc, sc, gb, g_tc->kwork, g_tc->kbytes, g_tc->gerr);
+    int rc;
+    if constexpr (std::is_same<T, zd>::value)
+      rc = sliced_gemm_cached(st, opa, m, nrhs, k, -1.0, A + (long)e0 * sa, lda, sa, Y + (long)e0 * sy, ldy, sy, 1,
+                              C + (long)e0 * sc, ldc, sc, gb);
+    else
+      rc = gemm_sliced_k<T>(st, opa, 'N', m, nrhs, k, -1.0, A + (long)e0 * sa, lda, sa, Y + (long)e0 * sy, ldy, sy,
+                            1, C + (long)e0 * sc, ldc, sc, gb, g_tc->kwork, g_tc->kbytes, g_tc->gerr);
     if (rc) return rc;
   }
   return 0;
@@ -1194,9 +1270,8 @@ static int trsv_rec(cudaStream_t st, int kind, int n, int ne, int nrhs, const T 
       // a 128-row leaf: one product with the inverted 128 x 128 diagonal block
       const T *D = (const T *)((kind == 0 || kind == 3) ? g_tc->dinv_l : g_tc->dinv_u);
       const long nb128 = n / 128;
-      return gemm_sliced_k<T>(st, kind >= 2 ? 'C' : 'N', 'N', 128, nrhs, 128, 1.0, D + (long)(b0 / 4) * 128 * 128,
-                              128, nb128 * 128 * 128, Y + (long)b0 * bs, n, ny, 0, Y + (long)b0 * bs, n, ny, ne,
-                              g_tc->kwork, g_tc->kbytes, g_tc->gerr);
+      return sliced_gemm_cached(st, kind >= 2 ? 'C' : 'N', 128, nrhs, 128, 1.0, D + (long)(b0 / 4) * 128 * 128, 128,
+                                nb128 * 128 * 128, Y + (long)b0 * bs, n, ny, 0, Y + (long)b0 * bs, n, ny, ne);
     }
   }
   const int mid = b0 + (b1 - b0) / 2;

@@ -14,7 +14,7 @@
 //   sytrd_cluster   Householder reduction C = Q T_c Q^H to a Hermitian
 //                   tridiagonal T_c (one cluster of up to 16 CTAs; the
 //                   matrix lives in distributed shared memory, rows dealt
-//                   cyclically to the CTAs; two cluster barriers per column)
+//                   cyclically to the CTAs; one cluster barrier per column)
 //   tridiag_prep    T_c = D T D^H with T real symmetric tridiagonal (D a
 //                   diagonal of unit phases), Gershgorin bounds
 //   stebz           every eigenvalue of T by bisection on its Sturm count
@@ -120,19 +120,25 @@ template <class T> __device__ T cta_sum(T v, T *red) {
 // whole (m entries) in that CTA's shared memory.
 
 // ------------------------------------------------- tridiagonalisation --
-// Step j, with the rows of the trailing block dealt to the CTAs as above:
-//  (a) the owner of row j forms the reflector from that row (the matrix is
-//      Hermitian, so column j below the diagonal is the conjugate of row j
-//      right of it, and the owner holds all of it): v into its shared
-//      memory and into column j of Vr, tau and the new subdiagonal entry;
+// Step j, with the rows of the trailing block dealt to the CTAs as above and
+// one cluster barrier per step:
+//  (a) every CTA holds row j as updated by steps 0..j-1 (xrow) and forms
+//      the reflector from it (the matrix is Hermitian, so column j below
+//      the diagonal is the conjugate of row j right of it): the same inputs
+//      and the same instructions give the same v and tau in every CTA, so
+//      nothing is published; the owner of row j writes tau, the new
+//      subdiagonal entry, column j of Vr and the diagonal entry;
+//  (b) p_i = tau sum_k A[i][k] v_k for the own rows i > j (one warp per
+//      row) and this CTA's part of v^H p, double-buffered by the step's
+//      parity;
 //  -- cluster barrier --
-//  (b) every CTA copies v from the owner, forms p_i = tau sum_k A[i][k] v_k
-//      for its rows (one warp per row) and its part of v^H p;
-//  -- cluster barrier --
-//  (c) every CTA copies p and the parts of v^H p from all CTAs (summed in
-//      CTA order, so every CTA gets the same K = tau/2 Re(v^H p)), forms w =
-//      p - K v and updates its rows: A[i][k] -= v_i conj(w_k) + w_i conj(v_k).
-// Two cluster barriers per column; FP64 work as fused multiply-adds.
+//  (c) every CTA reads p and the parts of v^H p from all CTAs (summed in
+//      CTA order, so K = tau/2 Re(v^H p) is the same everywhere), and row
+//      j+1 from its owner, who never updates it in place: w = p - K v; the
+//      own rows i > j+1 get A[i][k] -= v_i conj(w_k) + w_i conj(v_k), and
+//      row j+1 gets the same update in xrow, in every CTA.
+// Reading row j+1 with p merges the reflector's round of remote loads into
+// the one that follows the barrier; FP64 work as fused multiply-adds.
 template <class T>
 __global__ void __launch_bounds__(TRD_THREADS, 1)
     sytrd_cluster_kernel(int m, const T *__restrict__ A, long lda, T *__restrict__ Vr, double *__restrict__ tau,
@@ -144,14 +150,14 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
   const int rl = (m + C - 1) / C;
   extern __shared__ __align__(16) unsigned char smem[];
   T *L = reinterpret_cast<T *>(smem);  // [rl][m]
-  T *pown = L + (size_t)rl * m;        // [rl] p of this CTA's rows
-  T *vpub = pown + rl;                 // [m] v, published by the owner of row j
-  T *vfull = vpub + m;                 // [m] copy of v
-  T *wfull = vfull + m;                // [m] w
+  T *pown = L + (size_t)rl * m;        // [2][rl] p of this CTA's rows, by step parity
+  T *vfull = pown + 2 * (size_t)rl;    // [m] v of the current step
+  T *wfull = vfull + m;                // [m] w of the current step
+  T *xrow = wfull + m;                 // [m] row j as updated by the steps before j
   __shared__ T s_pvw[NW];              // each warp's part of v^H p
-  __shared__ T s_pcta;                 // this CTA's part of v^H p
-  __shared__ double s_tau;             // published by the owner of row j
-  __shared__ T s_sc;
+  __shared__ T s_pcta[2];              // this CTA's part of v^H p, by step parity
+  __shared__ double s_tau;
+  __shared__ T s_sc, s_tot;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (long t = tid; t < (long)rl * m; t += blockDim.x) {
@@ -159,114 +165,121 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
     const int i = il * C + q;
     L[(long)il * m + k] = (i < m) ? A[i + (long)k * lda] : X::zero();
   }
+  cl.sync();  // every CTA's rows in place before the first remote read
+  {
+    const T *r0 = cl.map_shared_rank(L, 0);  // row 0: local row 0 of CTA 0
+    for (int k = tid; k < m; k += blockDim.x) xrow[k] = r0[k];
+  }
   __syncthreads();
 
   for (int j = 0; j < m - 1; ++j) {
-    const int own = j % C;
-    if (q == own) {
-      // (a) x = conj(row j)[j+1 ..]: ||x_{2..}||^2 by warp 0 (fixed order),
-      // the reflector by its lane 0, v by the whole CTA
-      const T *Lj = L + (long)(j / C) * m;
-      if (warp == 0) {
-        double part = 0.0;
-        for (int k = j + 2 + lane; k < m; k += 32) part += absq(Lj[k]);
-        const double rest = warp_sum(part);
-        if (lane == 0) {
-          const T x0 = X::conj(Lj[j + 1]);
-          double tj = 0.0;
-          T beta = x0, sc = X::zero();
-          if (rest > 0.0) {
-            // |x0| and ||x|| from reciprocal square roots (independent),
-            // then one reciprocal: the shortest chain on the FP64 unit
-            const double q0 = absq(x0), s2 = q0 + rest;
-            const double ia0 = q0 > 0.0 ? fast_rsqrt(q0) : 0.0, inx = fast_rsqrt(s2);
-            const double a0 = q0 * ia0, nx = s2 * inx;
-            const T ph = a0 > 0.0 ? scl(x0, ia0) : X::one();
-            beta = scl(ph, -nx);
-            sc = scl(X::conj(ph), fast_rcp(a0 + nx));
-            tj = 1.0 + a0 * inx;
-          }
-          s_tau = tj;
-          s_sc = sc;
+    const int par = j & 1;
+    const bool own = (j % C) == q;
+    // (a) x = conj(xrow)[j+1 ..]: ||x_{2..}||^2 by warp 0 (fixed order),
+    // the reflector by its lane 0, v by the whole CTA
+    if (warp == 0) {
+      double part = 0.0;
+      for (int k = j + 2 + lane; k < m; k += 32) part += absq(xrow[k]);
+      const double rest = warp_sum(part);
+      if (lane == 0) {
+        const T x0 = X::conj(xrow[j + 1]);
+        double tj = 0.0;
+        T beta = x0, sc = X::zero();
+        if (rest > 0.0) {
+          // |x0| and ||x|| from reciprocal square roots (independent),
+          // then one reciprocal: the shortest chain on the FP64 unit
+          const double q0 = absq(x0), s2 = q0 + rest;
+          const double ia0 = q0 > 0.0 ? fast_rsqrt(q0) : 0.0, inx = fast_rsqrt(s2);
+          const double a0 = q0 * ia0, nx = s2 * inx;
+          const T ph = a0 > 0.0 ? scl(x0, ia0) : X::one();
+          beta = scl(ph, -nx);
+          sc = scl(X::conj(ph), fast_rcp(a0 + nx));
+          tj = 1.0 + a0 * inx;
+        }
+        s_tau = tj;
+        s_sc = sc;
+        if (own) {
           tau[j] = tj;
           betac[j] = beta;
+          dd[j] = X::re(xrow[j]);
         }
       }
-      __syncthreads();
+    }
+    __syncthreads();
+    const double tj = s_tau;
+    {
       const T sc = s_sc;
       for (int k = j + 1 + tid; k < m; k += blockDim.x) {
-        const T v = (k == j + 1) ? X::one() : X::mul(X::conj(Lj[k]), sc);
-        vpub[k] = v;
-        Vr[k + (long)j * m] = v;
+        const T v = (k == j + 1) ? X::one() : X::mul(X::conj(xrow[k]), sc);
+        vfull[k] = v;
+        if (own) Vr[k + (long)j * m] = v;
       }
     }
-    cl.sync();  // B1: the reflector is published
-    const double tj = *cl.map_shared_rank(&s_tau, own);
-    if (tj != 0.0) {  // uniform: every CTA reads the owner's tau
-      const T *vsrc = cl.map_shared_rank(vpub, own);
-      for (int k = j + 1 + tid; k < m; k += blockDim.x) vfull[k] = vsrc[k];
-      __syncthreads();
-      // (b) p_i for the own rows i > j, one warp per row; each warp's part
-      // of v^H p to s_pvw (no CTA-wide reduction here: the cross-CTA sum
-      // below reads every warp's part)
-      T pv = X::zero();
-      for (int il = warp; il < rl; il += NW) {
-        const int i = il * C + q;
-        if (i < j + 1 || i >= m) continue;
-        const T *Li = L + (long)il * m;
-        T s = X::zero();
-        for (int k = j + 1 + lane; k < m; k += 32) s = X::fma(Li[k], vfull[k], s);
-        s = scl(warp_sum(s), tj);
-        if (lane == 0) pown[il] = s;
-        pv = X::fma(X::conj(vfull[i]), s, pv);
-      }
-      if (lane == 0) s_pvw[warp] = pv;
-      // this CTA's part of v^H p: its warps' parts in warp order
-      __syncthreads();
-      if (warp == 0) {
-        const T r = warp_sum(lane < NW ? s_pvw[lane] : X::zero());
-        if (lane == 0) s_pcta = r;
+    __syncthreads();
+    // (b) p_i for the own rows i > j, one warp per row; each warp's part of
+    // v^H p to s_pvw, this CTA's part (the warps' parts in warp order) to
+    // s_pcta
+    T pv = X::zero();
+    for (int il = warp; il < rl; il += NW) {
+      const int i = il * C + q;
+      if (i < j + 1 || i >= m) continue;
+      const T *Li = L + (long)il * m;
+      T s = X::zero();
+      for (int k = j + 1 + lane; k < m; k += 32) s = X::fma(Li[k], vfull[k], s);
+      s = scl(warp_sum(s), tj);
+      if (lane == 0) pown[(size_t)par * rl + il] = s;
+      pv = X::fma(X::conj(vfull[i]), s, pv);
+    }
+    if (lane == 0) s_pvw[warp] = pv;
+    __syncthreads();
+    if (warp == 0) {
+      const T r = warp_sum(lane < NW ? s_pvw[lane] : X::zero());
+      if (lane == 0) s_pcta[par] = r;
+    }
+    cl.sync();  // every CTA's p and part of v^H p visible
+    // (c) v^H p: warp 0 reads the C parts (one remote load per lane, then
+    // the same sum in every CTA); row j+1 as its owner holds it
+    if (warp == 0) {
+      const T tot = warp_sum(lane < C ? *cl.map_shared_rank(&s_pcta[par], lane) : X::zero());
+      if (lane == 0) s_tot = tot;
+    }
+    {
+      const T *rn = cl.map_shared_rank(L, (j + 1) % C) + (size_t)((j + 1) / C) * m;
+      for (int k = j + 1 + tid; k < m; k += blockDim.x) xrow[k] = rn[k];
+    }
+    __syncthreads();
+    const double kk = 0.5 * tj * X::re(s_tot);
+    for (int k = j + 1 + tid; k < m; k += blockDim.x) {
+      const T pk = *cl.map_shared_rank(&pown[(size_t)par * rl + k / C], k % C);
+      wfull[k] = X::sub(pk, scl(vfull[k], kk));
+    }
+    __syncthreads();
+    // A[i][k] -= v_i conj(w_k) + w_i conj(v_k): own rows i > j+1 (one warp
+    // per row, lanes over the columns k > j), and row j+1 in xrow
+    for (int il = warp; il < rl; il += NW) {
+      const int i = il * C + q;
+      if (i < j + 2 || i >= m) continue;
+      T *Li = L + (long)il * m;
+      const T vi = X::neg(vfull[i]), wi = X::neg(wfull[i]);
+      for (int k = j + 1 + lane; k < m; k += 32) {
+        T a = Li[k];
+        a = X::fma(vi, X::conj(wfull[k]), a);
+        a = X::fma(wi, X::conj(vfull[k]), a);
+        Li[k] = a;
       }
     }
-    cl.sync();  // B2: every CTA's p and part of v^H p visible
-    if (tj != 0.0) {
-      // (c) v^H p: warp 0 reads the C parts (one remote load per lane, then
-      // a fixed-pattern shuffle sum, the same in every CTA); w = p - K v
-      if (warp == 0) {
-        const T tot = warp_sum(lane < C ? *cl.map_shared_rank(&s_pcta, lane) : X::zero());
-        if (lane == 0) s_sc = tot;
-      }
-      __syncthreads();
-      const double kk = 0.5 * tj * X::re(s_sc);
+    {
+      const T vi = X::neg(vfull[j + 1]), wi = X::neg(wfull[j + 1]);
       for (int k = j + 1 + tid; k < m; k += blockDim.x) {
-        const T pk = *cl.map_shared_rank(&pown[k / C], k % C);
-        wfull[k] = X::sub(pk, scl(vfull[k], kk));
-      }
-      __syncthreads();
-      // A[i][k] -= v_i conj(w_k) + w_i conj(v_k), own rows i > j, one warp
-      // per row, lanes over the columns k > j
-      for (int il = warp; il < rl; il += NW) {
-        const int i = il * C + q;
-        if (i < j + 1 || i >= m) continue;
-        T *Li = L + (long)il * m;
-        const T vi = X::neg(vfull[i]), wi = X::neg(wfull[i]);
-        for (int k = j + 1 + lane; k < m; k += 32) {
-          T a = Li[k];
-          a = X::fma(vi, X::conj(wfull[k]), a);
-          a = X::fma(wi, X::conj(vfull[k]), a);
-          Li[k] = a;
-        }
+        T a = xrow[k];
+        a = X::fma(vi, X::conj(wfull[k]), a);
+        a = X::fma(wi, X::conj(vfull[k]), a);
+        xrow[k] = a;
       }
     }
-    // the next owner reads its own updated row before the next cluster
-    // barrier; the other CTAs are ordered by that barrier
-    if ((j + 1) % C == q) __syncthreads();
+    __syncthreads();
   }
-  __syncthreads();
-  for (int il = tid; il < rl; il += blockDim.x) {
-    const int i = il * C + q;
-    if (i < m) dd[i] = X::re(L[(long)il * m + i]);
-  }
+  if (tid == 0 && ((m - 1) % C) == q) dd[m - 1] = X::re(xrow[m - 1]);
   cl.sync();  // no CTA leaves while another may read its shared memory
 }
 
@@ -755,7 +768,7 @@ int heev_tridiag(cudaStream_t st, int m, const T *A, double *w, T *V, void *work
   if (m < 2 || m > OR_THREADS * OR_PER) return 1;
   if (heev_tridiag_work(m, tr<T>::cplx) > work_bytes) return 1;
   size_t sm_t = 0;
-  const int C = cluster_shape<T>(m, 1, 3, &sm_t);
+  const int C = cluster_shape<T>(m, 2, 3, &sm_t);
   if (C == 0) return 1;
   const size_t mm = (size_t)m * m;
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
