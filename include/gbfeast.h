@@ -389,6 +389,15 @@ int gbf_cgemm_tf32(void *stream, char opa, char opb, int m, int n, int k, double
  *    the GPU (other streams, other threads) race and must not be issued;
  *  - the call reads the error word back and synchronises `stream` before
  *    it returns, so it returns after its stream has finished the work. */
+/* Bounded-wait check (no counterpart in the guide): one thread waits on a
+ * shared-memory barrier that nothing completes, with the same bounded loop
+ * as the tensor-core engine's pipeline waits, for `limit` (>= 1) polls.
+ * Returns -5 with a message in gbf_last_error() when the wait runs out (as
+ * every entry above reports an in-kernel time-out), -101 for limit < 1, -4
+ * on a CUDA error.  The device stays usable afterwards: the kernel returns
+ * with nothing in flight.  For tests of the failure path. */
+int gbf_wait_probe(void *stream, long limit);
+
 size_t gbf_zgemm_sliced_noalloc_max(void);
 int gbf_zgemm_sliced_noalloc(void *stream, int prec, int S, char opa, char opb, int m, int n, int k, double alpha,
                              const void *dA, long lda, long sa, const void *dB, long ldb, long sb, int beta, void *dC,

@@ -59,6 +59,7 @@ def load(build: bool = True):
     L.gbf_zgegv_dev.argtypes = gen
     L.gbf_gcontour.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
     L.gbf_grationalx.argtypes = [vp, vp, C.c_int, vp, C.c_int, vp]
+    L.gbf_wait_probe.argtypes = [vp, C.c_long]
     L.gbf_biorth_defect.argtypes = [vp]
     L.gbf_biorth_defect.restype = C.c_double
     L.gbf_factor_dev.argtypes = [vp, vp, C.c_int, C.c_int, C.c_char, C.c_int, vp, C.c_int, vp, C.c_int, C.c_int, vp]

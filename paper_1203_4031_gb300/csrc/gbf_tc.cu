@@ -69,15 +69,35 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait; false when the CTA aborted (time-out here or elsewhere).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *gerr,
-                                          int code) {
-  for (long it = 0; it < WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait_n(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *gerr,
+                                            int code, long limit) {
+  for (long it = 0; it < limit; ++it) {
     if (mbar_try(bar, parity)) return true;
     if (*abort_flag) return false;
   }
   *abort_flag = 1;
   atomicCAS(gerr, 0, code);
   return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *gerr,
+                                          int code) {
+  return mbar_wait_n(bar, parity, abort_flag, gerr, code, WAIT_LIMIT);
+}
+
+// The time-out path of the pipeline waits, exercised without a fault: one
+// thread waits, with the same bounded loop, on a barrier that nothing
+// completes, for `limit` polls; the error word gets `code` and the kernel
+// returns (no asynchronous work is in flight).
+__global__ void wait_probe_kernel(long limit, int *gerr, int code) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait_n(&bar, 0, &abort_flag, gerr, code, limit);
 }
 
 // Bounded wait that ignores the abort flag: used to let this thread's own
@@ -2782,6 +2802,28 @@ extern "C" int gbf_zgemm_sliced(void *stream, int prec, int S, char opa, char op
   GBF_CUDA(cudaStreamSynchronize(st));
   if (herr) {
     gbf::set_error("sliced GEMM: bounded wait timed out (code %d)", herr);
+    return -5;
+  }
+  return 0;
+}
+
+// Bounded-wait check: launches tc::wait_probe_kernel with `limit` polls and
+// reports its time-out as the GEMM entries do.
+extern "C" int gbf_wait_probe(void *stream, long limit) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (limit < 1) return -101;
+  int *dErr = nullptr;
+  GBF_CUDA(cudaMallocAsync((void **)&dErr, sizeof(int), st));
+  GBF_CUDA(cudaMemsetAsync(dErr, 0, sizeof(int), st));
+  gbf::tc::wait_probe_kernel<<<1, 32, 0, st>>>(limit, dErr, 1);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  int herr = 0;
+  GBF_CUDA(cudaMemcpyAsync(&herr, dErr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GBF_CUDA(cudaFreeAsync(dErr, st));
+  GBF_CUDA(cudaStreamSynchronize(st));
+  if (herr) {
+    gbf::set_error("wait probe: bounded wait timed out (code %d)", herr);
     return -5;
   }
   return 0;

@@ -143,3 +143,27 @@ def test_cgemm_tf32_any_k(gbf, m, n, k, batch, opa, opb, alpha, beta):
         scale = As[i].abs().max().item() * Bs[i].abs().max().item()
         tol = 4 * (2 * k) * 2.0 ** -22 * scale + 2.0 ** -23 * ref[i].abs().max().item()
         assert (got - ref[i]).abs().max().item() <= tol, ((got - ref[i]).abs().max().item(), tol)
+
+
+def test_bounded_wait_times_out_and_gpu_stays_usable(gbf):
+    """The time-out path of the engine's bounded waits: a wait on a barrier
+    that nothing completes runs out after the given polls and reports -5;
+    the next sliced GEMM on the same stream is correct."""
+    import torch
+
+    L = gbf.lib()
+    st = torch.cuda.current_stream()
+    sp = gbf._stream_ptr(st)
+    assert L.gbf_wait_probe(sp, 1000) == -5
+    assert "timed out" in gbf.last_error()
+    assert L.gbf_wait_probe(sp, 0) == -101
+    g = torch.Generator(device="cuda").manual_seed(5)
+    A = torch.randn((64, 32), device="cuda", dtype=torch.complex128, generator=g)
+    B = torch.randn((32, 48), device="cuda", dtype=torch.complex128, generator=g)
+    Cd = colmajor_batch(torch, [torch.zeros((64, 48), device="cuda", dtype=torch.complex128)])
+    ref = A @ B
+    rc = gbf.zgemm_sliced("N", "N", colmajor_batch(torch, [A]), colmajor_batch(torch, [B]), Cd, alpha=1.0, beta=0,
+                          S=7)
+    torch.cuda.synchronize()
+    assert rc == 0, gbf.last_error()
+    assert (Cd[0].t() - ref).abs().max().item() <= 4e-14 * 32 * (1 + ref.abs().max().item())
