@@ -534,10 +534,11 @@ def run_nonhermitian(g, torch, W, n=4096, count=40, m0=64):
     a real non-symmetric generalized pencil (conjugate node pairs: 8
     factorisations) and a complex non-symmetric standard matrix (16), n =
     4096, a circle holding `count` eigenvalues of the known spectrum, M0 =
-    m0.  One warm-up and one timed solve each (CUDA events around the call,
-    per-category kernel times from one more profiled solve); pairs counted
-    when both residuals pass 1e-10 and the eigenvalue matches the known one
-    to 1e-10."""
+    m0; FP64 factors and FP32 factors with the FP64 residual correction
+    (`_mixed`).  One warm-up and one timed solve each (CUDA events around the
+    call, per-category kernel times and the sliced GEMMs' roofline from one
+    more profiled solve); pairs counted when both residuals pass 1e-10 and
+    the eigenvalue matches the known one to 1e-10."""
     import ctypes as C
 
     out = {}
@@ -546,51 +547,55 @@ def run_nonhermitian(g, torch, W, n=4096, count=40, m0=64):
         P = W.dense_nonsymmetric(n, count=count, m0=m0, complex_=cplx, generalized=gen)
         A = g.fortran(torch.from_numpy(np.ascontiguousarray(P.A)).cuda())
         B = g.fortran(torch.from_numpy(np.ascontiguousarray(P.B)).cuda()) if P.B is not None else None
-        f = P.apply_fpm(g.gbf_init())
-        h = g.Handle()
-        stream = torch.cuda.current_stream()
-        r = g.feast_gen_dev(A, B, P.emid, P.r, P.m0, f, handle=h)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        l0 = g.launch_count()
-        e0.record(stream)
-        r = g.feast_gen_dev(A, B, P.emid, P.r, P.m0, f, handle=h)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        launches = g.launch_count() - l0
-        L.gbf_profile(1)
-        g.feast_gen_dev(A, B, P.emid, P.r, P.m0, f, handle=h)
-        torch.cuda.synchronize()
-        prof, prof_full = {}, {}
-        for c in range(L.gbf_profile_categories()):
-            nl, t, fl = C.c_longlong(), C.c_double(), C.c_double()
-            L.gbf_profile_read(c, C.byref(nl), C.byref(t), C.byref(fl))
-            prof[L.gbf_profile_name(c).decode()] = round(t.value, 3)
-            prof_full[L.gbf_profile_name(c).decode()] = (nl.value, t.value, fl.value)
-        nl, t, fl, tf = C.c_longlong(), C.c_double(), C.c_double(), C.c_double()
-        L.gbf_profile_tc(C.byref(nl), C.byref(t), C.byref(fl), C.byref(tf))
-        tc = (nl.value, t.value, fl.value, tf.value)
-        L.gbf_profile(0)
-        M = r["M"]
-        E = r["E"][:M].cpu().numpy()
-        res = r["res"].cpu().numpy()
         known = P.spectrum[np.abs(P.spectrum - P.emid) <= P.r]
-        ok = 0
-        err = float("nan")
-        if r["info"] == 0 and M == len(known):
-            d = np.array([np.min(np.abs(known - e)) for e in E])
-            err = float(np.max(d))
-            ok = int(np.sum((d < 1e-10) & (res[:M] < 1e-10) & (res[P.m0:P.m0 + M] < 1e-10)))
-        out[name] = {"workload": f"{P.name}: {P.note}; circle |z - {P.emid}| <= {P.r:.6g} holding {count}, "
-                                 f"M0 = {P.m0}, fpm(8) = 16",
-                     "eigenpairs_per_s": ok / (ms / 1e3), "ms": ms, "M": M, "loops": r["loop"], "info": r["info"],
-                     "pairs_passing": ok, "max_abs_eig_err": err,
-                     "max_res_right": float(np.max(res[:M])) if M else None,
-                     "max_res_left": float(np.max(res[P.m0:P.m0 + M])) if M else None,
-                     "biorth_defect": r["biorth"], "gpu_launches": launches, "kernels_ms": prof,
-                     "roofline": roofline(prof_full, tc, "fp64")}
-        h.close()
+        for prec in (0, 1):
+            f = P.apply_fpm(g.gbf_init())
+            f[41] = prec
+            h = g.Handle()
+            stream = torch.cuda.current_stream()
+            r = g.feast_gen_dev(A, B, P.emid, P.r, P.m0, f, handle=h)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            l0 = g.launch_count()
+            e0.record(stream)
+            r = g.feast_gen_dev(A, B, P.emid, P.r, P.m0, f, handle=h)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            launches = g.launch_count() - l0
+            L.gbf_profile(1)
+            g.feast_gen_dev(A, B, P.emid, P.r, P.m0, f, handle=h)
+            torch.cuda.synchronize()
+            prof, prof_full = {}, {}
+            for c in range(L.gbf_profile_categories()):
+                nl, t, fl = C.c_longlong(), C.c_double(), C.c_double()
+                L.gbf_profile_read(c, C.byref(nl), C.byref(t), C.byref(fl))
+                prof[L.gbf_profile_name(c).decode()] = round(t.value, 3)
+                prof_full[L.gbf_profile_name(c).decode()] = (nl.value, t.value, fl.value)
+            nl, t, fl, tf = C.c_longlong(), C.c_double(), C.c_double(), C.c_double()
+            L.gbf_profile_tc(C.byref(nl), C.byref(t), C.byref(fl), C.byref(tf))
+            tc = (nl.value, t.value, fl.value, tf.value)
+            L.gbf_profile(0)
+            M = r["M"]
+            E = r["E"][:M].cpu().numpy()
+            res = r["res"].cpu().numpy()
+            ok = 0
+            err = float("nan")
+            if r["info"] == 0 and M == len(known):
+                d = np.array([np.min(np.abs(known - e)) for e in E])
+                err = float(np.max(d))
+                ok = int(np.sum((d < 1e-10) & (res[:M] < 1e-10) & (res[P.m0:P.m0 + M] < 1e-10)))
+            key = name + ("_mixed" if prec else "")
+            out[key] = {"workload": f"{P.name}: {P.note}; circle |z - {P.emid}| <= {P.r:.6g} holding {count}, "
+                                    f"M0 = {P.m0}, fpm(8) = 16",
+                        "factors": "c32 + f64 residual correction" if prec else "f64",
+                        "eigenpairs_per_s": ok / (ms / 1e3), "ms": ms, "M": M, "loops": r["loop"],
+                        "info": r["info"], "pairs_passing": ok, "max_abs_eig_err": err,
+                        "max_res_right": float(np.max(res[:M])) if M else None,
+                        "max_res_left": float(np.max(res[P.m0:P.m0 + M])) if M else None,
+                        "biorth_defect": r["biorth"], "gpu_launches": launches, "kernels_ms": prof,
+                        "roofline": roofline(prof_full, tc, "fp64") if prec == 0 else None}
+            h.close()
         del A, B
         torch.cuda.empty_cache()
     return out

@@ -251,8 +251,11 @@ int gbf_grationalx(const double *Zne, const double *Wne, int ne, const double *e
  * pointers; the work runs on `stream` and the call returns after it.
  *  - fpm: fpm(8) nodes (default 16), fpm(17) rule (default 1, trapezoidal),
  *    fpm(18), fpm(19) the ellipse; fpm(3), fpm(4), fpm(5), fpm(6), fpm(14) =
- *    0/1 and fpm(43), fpm(44) as above.  The factors are complex FP64 (fpm(42)
- *    is ignored).  For real A, B, a real Emid, fpm(19) = 0 and an even
+ *    0/1 and fpm(43), fpm(44) as above.  fpm(42) = 0: complex FP64 factors;
+ *    1: complex FP32 factors, and from the second loop on the solves take
+ *    only the FP64 eigen-residuals R = A X - B X Lambda (right) and A^H X^ -
+ *    B^H X^ conj(Lambda) (left), as for the Hermitian drivers, so the
+ *    results reach FP64 accuracy.  For real A, B, a real Emid, fpm(19) = 0 and an even
  *    fpm(8), the nodes pair up as z and conj(z) and only fpm(8)/2 systems are
  *    factored (the guide's remark on real non-symmetric problems).
  *  - *M0 (1..min(n, 1024)): subspace size.  dE: M0 complex eigenvalues,

@@ -942,7 +942,9 @@ struct GenReq {
 // ne-1-e is the mirror image of node e and S_{ne-1-e} = conj(S_e): only the
 // upper half is factored, each solve taking [b, conj(b)], and the mirror
 // node's term is conj(c_e S_e^{-1} conj(b)).
+template <class TL>
 static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &out) {
+  constexpr bool mixed = std::is_same<TL, cf>::value;  // FP32 factors, FP64 residual correction
   const int n = q.n, m0 = q.m0;
   const int *fpm = q.fpm;
   const bool hasB = q.B != nullptr;
@@ -967,10 +969,14 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
   const int mw = half ? 2 * m0 : m0;  // right-hand sides per factored node
   const int nblk = ceil_div(n, bs), nbm = ceil_div(m0, bs);
   const size_t nn = (size_t)n * n, nm = (size_t)n * m0, mm = (size_t)m0 * m0;
-  const int tcS = (fpm[43] == 0 && bs <= 32) ? 7 : 0;
+  const int tcS = (fpm[43] == 0 && bs <= 32) ? (mixed ? 1 : 7) : 0;
 
   struct {
-    zd *Af, *Bf, *S, *Linv, *Uinv, *Ysol, *Ytmp, *Yadj, *R2;
+    zd *Af, *Bf, *R2, *AYr, *AYl, *YlN, *Rres, *SCr, *SCl, *fv;
+    TL *S, *Linv, *Uinv, *Ysol, *Ytmp, *Yadj;
+    float *fpre_n, *fpre_c;
+    void *tcw_r, *kw_r;
+    size_t tcw_r_bytes, kw_r_bytes;
     zd *Q, *Qh, *AQ, *BQ, *AhQh, *BhQh, *Xr, *AXr, *BXr, *Xl, *AXl, *BXl, *Yr, *Yl, *RBr, *RBl, *Tmp;
     zd *Aq, *Bq, *G, *Z, *Yv, *W, *V, *Mm, *P, *Sr, *Lr, *Ur, *Id, *Vt, *lam, *Eo, *z, *w;
     int *ipiv, *perm, *sing, *ipr, *pmr, *sgr, *pos, *src, *flag, *tc_err;
@@ -984,13 +990,20 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
   auto layout = [&](Bump &b) {
     ws.Af = q.real ? b.take<zd>(nn) : nullptr;
     ws.Bf = (q.real && hasB) ? b.take<zd>(nn) : nullptr;
-    ws.S = b.take<zd>((size_t)nf * nn);
-    ws.Linv = b.take<zd>((size_t)nf * nblk * bs * bs);
-    ws.Uinv = b.take<zd>((size_t)nf * nblk * bs * bs);
-    ws.Ysol = b.take<zd>((size_t)nf * n * mw);
-    ws.Ytmp = b.take<zd>((size_t)nf * n * mw);
-    ws.Yadj = b.take<zd>((size_t)nf * n * mw);
+    ws.S = b.take<TL>((size_t)nf * nn);
+    ws.Linv = b.take<TL>((size_t)nf * nblk * bs * bs);
+    ws.Uinv = b.take<TL>((size_t)nf * nblk * bs * bs);
+    ws.Ysol = b.take<TL>((size_t)nf * n * mw);
+    ws.Ytmp = b.take<TL>((size_t)nf * n * mw);
+    ws.Yadj = b.take<TL>((size_t)nf * n * mw);
     ws.R2 = b.take<zd>((size_t)n * mw);
+    ws.AYr = mixed ? b.take<zd>(nm) : nullptr;
+    ws.AYl = mixed ? b.take<zd>(nm) : nullptr;
+    ws.YlN = mixed ? b.take<zd>(nm) : nullptr;
+    ws.Rres = mixed ? b.take<zd>(nm) : nullptr;
+    ws.SCr = mixed ? b.take<zd>((size_t)nf * mw) : nullptr;
+    ws.SCl = mixed ? b.take<zd>((size_t)nf * mw) : nullptr;
+    ws.fv = mixed ? b.take<zd>(m0) : nullptr;
     zd **nmb[] = {&ws.Q, &ws.Qh, &ws.AQ, &ws.AhQh, &ws.Xr, &ws.AXr, &ws.Xl, &ws.AXl, &ws.Yr, &ws.Yl, &ws.RBr,
                   &ws.RBl, &ws.Tmp};
     for (zd **p : nmb) *p = b.take<zd>(nm);
@@ -1021,13 +1034,23 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
     ws.stats = b.take<double>(8);
     ws.tcw_bytes = tcS ? std::max(zgemm_sliced_work(n, n, nf, tcS), zgemm_sliced_work(n, mw, nf, tcS)) : 0;
     ws.tcw = tcS ? (void *)b.take<char>(ws.tcw_bytes) : nullptr;
-    ws.kw_bytes = tcS ? solve_kwork_bytes(n, mw, bs, nf) : 0;
+    ws.kw_bytes = tcS ? (mixed ? solve_kwork_bytes_cf(n, mw, bs, nf) : solve_kwork_bytes(n, mw, bs, nf)) : 0;
     ws.kw = ws.kw_bytes ? (void *)b.take<char>(ws.kw_bytes) : nullptr;
-    const bool big = ws.kw_bytes && bs == 32 && n % 128 == 0;
+    const bool pre = mixed && ws.kw_bytes && n >= 1024;  // FP32 factors split once into TF32 planes
+    ws.fpre_n = pre ? b.take<float>(tf32_planes_bytes(n, nf) / 4) : nullptr;
+    ws.fpre_c = pre ? b.take<float>(tf32_planes_bytes(n, nf) / 4) : nullptr;
+    // the M0-sized LU and solves of the reduced pencil (FP64, their own
+    // tensor-core workspace)
+    ws.tcw_r_bytes = tcS ? zgemm_sliced_work(m0, m0, 1, 7) : 0;
+    ws.tcw_r = tcS ? (void *)b.take<char>(ws.tcw_r_bytes) : nullptr;
+    ws.kw_r_bytes = tcS ? solve_kwork_bytes(m0, m0, bs, 1) : 0;
+    ws.kw_r = tcS ? (void *)b.take<char>(ws.kw_r_bytes) : nullptr;
+    const bool big = !mixed && ws.kw_bytes && bs == 32 && n % 128 == 0;
     ws.dinv_l = big ? (void *)b.take<zd>((size_t)nf * n * 128) : nullptr;
     ws.dinv_u = big ? (void *)b.take<zd>((size_t)nf * n * 128) : nullptr;
-    ws.acache_bytes =
-        ws.kw_bytes ? std::min(solve_slice_cache_bytes(n, mw, bs, nf, 4, big), (size_t)24 << 30) : 0;
+    ws.acache_bytes = (!mixed && ws.kw_bytes)
+                          ? std::min(solve_slice_cache_bytes(n, mw, bs, nf, 4, big), (size_t)24 << 30)
+                          : 0;
     ws.acache_base = ws.acache_bytes ? b.take<char>(ws.acache_bytes) : nullptr;
     const long Kp = sliced_kp(n, true), R = 2L * n, Km = sliced_kp(m0, true), Rm = 2L * m0;
     ws.pja = b.take<char>(sliced_op_bytes(R, Kp, 1));
@@ -1057,14 +1080,21 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
   tcx.kbytes = ws.kw_bytes;
   tcx.dinv_l = ws.dinv_l;
   tcx.dinv_u = ws.dinv_u;
+  tcx.fpre_n = ws.fpre_n;
+  tcx.fpre_c = ws.fpre_c;
+  tcx.fpre_ne = ws.fpre_n ? nf : 0;
   acache.base = ws.acache_base;
   acache.cap = ws.acache_bytes;
   tcx.acache = ws.acache_bytes ? &acache : nullptr;
-  // the M0-sized LU and solves of the reduced pencil: the same engine
-  // without the n-sized leaf inverses and slice cache
-  TcCtx tcr = tcx;
-  tcr.dinv_l = tcr.dinv_u = nullptr;
-  tcr.acache = nullptr;
+  // the M0-sized LU and solves of the reduced pencil: FP64 on the sliced
+  // engine with their own workspace
+  TcCtx tcr;
+  tcr.work = ws.tcw_r;
+  tcr.bytes = ws.tcw_r_bytes;
+  tcr.gerr = ws.tc_err;
+  tcr.S = 7;
+  tcr.kwork = ws.kw_r;
+  tcr.kbytes = ws.kw_r_bytes;
   TcScope tc_scope(tcS ? &tcx : nullptr);
   AuxScope aux_scope(ensure_aux(h));
   if (ensure_hbuf(h, (size_t)std::max(m0, ne) + 64)) return out.info = -1;
@@ -1090,9 +1120,13 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
     }
   }
   // factor the nodes (kept for the whole iteration)
-  CK(form_shift<zd>(st, n, nf, ws.z, 1, 'G', Af, lda, hasB ? (const void *)Bf : nullptr, ldb, ws.S, ws.sing + nf));
-  CK(getrf_batched<zd>(st, n, nf, ws.S, ws.ipiv, ws.perm, ws.Linv, ws.Uinv, bs, ws.sing, nullptr));
+  CK(form_shift<TL>(st, n, nf, ws.z, 1, 'G', Af, lda, hasB ? (const void *)Bf : nullptr, ldb, ws.S, ws.sing + nf));
+  CK(getrf_batched<TL>(st, n, nf, ws.S, ws.ipiv, ws.perm, ws.Linv, ws.Uinv, bs, ws.sing, nullptr));
   acache.reset();
+  if constexpr (mixed) {
+    if (ws.fpre_n) CK(tf32_presplit(st, 'N', n, nf, ws.S, ws.fpre_n));
+    if (ws.fpre_c) CK(tf32_presplit(st, 'C', n, nf, ws.S, ws.fpre_c));
+  }
   {
     int *hs = (int *)h->hbuf;
     GBF_CUDA(cudaMemcpyAsync(hs, ws.sing, sizeof(int) * (nf + 1), cudaMemcpyDeviceToHost, st));
@@ -1156,22 +1190,38 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
   zd trace_prev{0.0, 0.0};
   for (int k = 0;; ++k) {
     // ---- spectral projections (cases 11 and 21) ----
+    // FP32 factors after the first loop: the residual-correction form
+    // S_e^{-1} B X = X D_e + S_e^{-1} R D_e, R = A X - B X Lambda, D_e =
+    // (z_e - Lambda)^{-1}, so Q = X f(Lambda) + sum_e w_e S_e^{-1} R D_e; on
+    // the left S_e^{-H} B^H X^ = X^ conj(D_e) + S_e^{-H} R^ conj(D_e), R^ =
+    // A^H X^ - B^H X^ conj(Lambda): the FP32 solves see only the residuals
+    const bool rc_form = mixed && k > 0;
     const zd *rr_src = ws.RBr, *rl_src = ws.RBl;
+    if (rc_form) {
+      CK(gen_scales(st, m, nf, ne, ws.z, ws.w, ws.Eo, half ? 1 : 0, ws.SCr, ws.SCl, ws.fv));
+      CK(gen_eig_residual(st, n, m, ws.AYr, hasB ? ws.RBr : ws.Yr, ws.Eo, 0, nullptr, ws.Rres));
+      rr_src = ws.Rres;
+    }
     if (half) {
-      CK(gen_conj_pair(st, n, m, ws.RBr, ws.R2));
+      CK(gen_conj_pair(st, n, m, rr_src, ws.R2));
       rr_src = ws.R2;
     }
-    CK(gather_rhs<zd>(st, n, nf, mw, ws.perm, 1, rr_src, n, nullptr, ws.Ysol));
-    CK(getrs_inplace<zd>(st, 0, n, nf, mw, ws.S, ws.Linv, ws.Uinv, bs, ws.Ysol, nullptr));
-    CK(gen_accumulate(st, n, m, nf, ws.w, ws.Ysol, mw, half ? 1 : 0, 0, ws.Q));
+    CK(gather_rhs<TL>(st, n, nf, mw, ws.perm, 1, rr_src, n, rc_form ? ws.SCr : nullptr, ws.Ysol));
+    CK(getrs_inplace<TL>(st, 0, n, nf, mw, ws.S, ws.Linv, ws.Uinv, bs, ws.Ysol, nullptr));
+    CK(gen_accumulate<TL>(st, n, m, nf, ws.w, ws.Ysol, mw, half ? 1 : 0, 0, rc_form ? ws.Yr : nullptr, ws.fv, ws.Q));
+    if (rc_form) {
+      CK(gen_eig_residual(st, n, m, ws.AYl, ws.RBl, ws.Eo, 1, nullptr, ws.Rres));
+      rl_src = ws.Rres;
+    }
     if (half) {
-      CK(gen_conj_pair(st, n, m, ws.RBl, ws.R2));
+      CK(gen_conj_pair(st, n, m, rl_src, ws.R2));
       rl_src = ws.R2;
     }
-    CK(gather_rhs<zd>(st, n, nf, mw, nullptr, 1, rl_src, n, nullptr, ws.Ytmp));
-    CK(getrs_inplace<zd>(st, 1, n, nf, mw, ws.S, ws.Linv, ws.Uinv, bs, ws.Ytmp, nullptr));
-    CK(scatter_perm<zd>(st, n, nf, mw, ws.perm, ws.Ytmp, ws.Yadj));
-    CK(gen_accumulate(st, n, m, nf, ws.w, ws.Yadj, mw, half ? 1 : 0, 1, ws.Qh));
+    CK(gather_rhs<TL>(st, n, nf, mw, nullptr, 1, rl_src, n, rc_form ? ws.SCl : nullptr, ws.Ytmp));
+    CK(getrs_inplace<TL>(st, 1, n, nf, mw, ws.S, ws.Linv, ws.Uinv, bs, ws.Ytmp, nullptr));
+    CK(scatter_perm<TL>(st, n, nf, mw, ws.perm, ws.Ytmp, ws.Yadj));
+    CK(gen_accumulate<TL>(st, n, m, nf, ws.w, ws.Yadj, mw, half ? 1 : 0, 1, rc_form ? ws.YlN : nullptr, ws.fv,
+                          ws.Qh));
     if (fpm[13] == 1) {  // the subspaces after one contour
       GBF_CUDA(cudaMemcpyAsync(q.X, ws.Q, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
       GBF_CUDA(cudaMemcpyAsync((zd *)q.X + nm, ws.Qh, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
@@ -1261,6 +1311,12 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
       CK(gen_col_scale(st, n, m, ws.Tmp, ws.RBl, ws.nl, 1));
     } else {
       CK(gen_col_scale(st, n, m, ws.Yl, ws.RBl, ws.nl, 1));
+    }
+    if constexpr (mixed) {  // A X and A^H X^ of the next subspaces, for the residuals
+      CK(permute_cols<zd>(st, n, m, ws.pos, ws.AXr, ws.AYr));
+      CK(permute_cols<zd>(st, n, m, ws.pos, ws.AXl, ws.Tmp));
+      CK(gen_col_scale(st, n, m, ws.Tmp, ws.AYl, ws.nl, 1));
+      CK(gen_col_scale(st, n, m, ws.Yl, ws.YlN, ws.nl, 1));
     }
     double *hs = h->hbuf;
     GBF_CUDA(cudaMemcpyAsync(hs, ws.stats, sizeof(double) * 5, cudaMemcpyDeviceToHost, st));
@@ -1394,6 +1450,7 @@ static int validate_gen(int n, long lda, bool hasB, long ldb, const int *fpm, do
   if (fpm[16] != 0 && fpm[16] != 1) return 117;
   if (fpm[17] <= 0) return 118;
   if (fpm[18] < -180 || fpm[18] > 180) return 119;
+  if (fpm[41] != 0 && fpm[41] != 1) return 142;
   if (fpm[42] != 0 && (fpm[42] < 8 || fpm[42] > 64 || fpm[42] % 8)) return 143;
   if (fpm[43] != 0 && fpm[43] != 1) return 144;
   return 0;
@@ -1408,7 +1465,8 @@ static int run_gen_dev(gbf_handle h, void *stream, bool real, int n, const doubl
   if (code == 0 && (!dA || !dE || !dX || !dres)) code = -103;
   if (code == 0) {
     GenReq q{n, real, dA, lda, dB, ldb, fpm, zd{emid_re, emid_im}, r, *M0, Zne, Wne, dE, dX, dres};
-    code = feast_run_gen(h, (cudaStream_t)stream, q, out);
+    code = fpm[41] == 1 ? feast_run_gen<cf>(h, (cudaStream_t)stream, q, out)
+                        : feast_run_gen<zd>(h, (cudaStream_t)stream, q, out);
     if (epsout) *epsout = out.epsout;
     if (loop) *loop = out.loop;
     if (M) *M = out.M;

@@ -420,10 +420,19 @@ template <class T> int ns_prep(cudaStream_t st, int m, const T *P, T *Tn, double
 // Elementwise glue of the dual-subspace iteration (n x m column-major, ld n).
 int gen_widen(cudaStream_t st, int n, const double *A, long lda, zd *Af);
 int gen_conj_pair(cudaStream_t st, int n, int m, const zd *src, zd *dst);
-// Q = sum over the nf factored nodes of c_e Y_e (+ the mirror node's term
-// conj(c_e Y_e[:, m..2m)) when `half`), c_e = w_e, or conj(w_e) when `left`.
-int gen_accumulate(cudaStream_t st, int n, int m, int nf, const zd *w, const zd *Y, int mw, int half, int left,
-                   zd *Q);
+// Q = X0 diag(g) + the sum over the nf factored nodes of c_e Y_e (+ the
+// mirror node's term conj(c_e Y_e[:, m..2m)) when `half`), c_e = w_e and
+// g = f, or conj(w_e) and conj(f) when `left` (X0 null: no first term).
+template <class TY>
+int gen_accumulate(cudaStream_t st, int n, int m, int nf, const zd *w, const TY *Y, int mw, int half, int left,
+                   const zd *X0, const zd *f, zd *Q);
+// Residual-correction form: per-node column scales of the right and left
+// right-hand sides and the filter values f(lam) of the Ritz values.
+int gen_scales(cudaStream_t st, int m, int nf, int ne, const zd *z, const zd *w, const zd *lam, int half, zd *SCr,
+               zd *SCl, zd *f);
+// R = MX - NX diag(lam or conj(lam)), columns divided by sc (sc null: 1).
+int gen_eig_residual(cudaStream_t st, int n, int m, const zd *MX, const zd *NX, const zd *lam, int conjl,
+                     const double *sc, zd *R);
 int gen_col_norms(cudaStream_t st, int n, int m, const zd *X, double *nrm);
 int gen_col_scale(cudaStream_t st, int n, int m, const zd *src, zd *dst, const double *s, int divide);
 int gen_residual(cudaStream_t st, int n, int m, const zd *MX, const zd *NX, const zd *lam, int conjl, double alpha,

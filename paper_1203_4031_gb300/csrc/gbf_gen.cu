@@ -84,21 +84,63 @@ __global__ void conj_pair_kernel(int n, int m, const zd *src, zd *dst) {
   dst[i + (long)(m + j) * n] = X::conj(v);
 }
 
-// Q[i, j] = sum_e c_e Y_e[i, j] (+ conj(c_e Y_e[i, m + j]) for the mirror
-// node when `half`), c_e = w_e (right) or conj(w_e) (left); nodes in order.
-__global__ void accum_gen_kernel(int n, int m, int nf, const zd *w, const zd *Y, int mw, int half, int left,
-                                 zd *Q) {
+// Q[i, j] = X0[i, j] g_j + sum_e c_e Y_e[i, j] (+ conj(c_e Y_e[i, m + j])
+// for the mirror node when `half`), c_e = w_e (right) or conj(w_e) (left),
+// g = f or conj(f) (the residual-correction form; X0 may be null); nodes in
+// order.
+template <class TY>
+__global__ void accum_gen_kernel(int n, int m, int nf, const zd *w, const TY *Y, int mw, int half, int left,
+                                 const zd *X0, const zd *f, zd *Q) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
   if (i >= n) return;
   const long ny = (long)n * mw;
   zd acc{0.0, 0.0};
+  if (X0) acc = X::mul(X0[i + (long)j * n], left ? X::conj(f[j]) : f[j]);
   for (int e = 0; e < nf; ++e) {
     const zd ce = left ? X::conj(w[e]) : w[e];
-    const zd *Ye = Y + e * ny;
-    acc = X::fma(ce, Ye[i + (long)j * n], acc);
-    if (half) acc = X::add(acc, X::conj(X::mul(ce, Ye[i + (long)(m + j) * n])));
+    const TY *Ye = Y + e * ny;
+    acc = X::fma(ce, cvt<zd, TY>(Ye[i + (long)j * n]), acc);
+    if (half) acc = X::add(acc, X::conj(X::mul(ce, cvt<zd, TY>(Ye[i + (long)(m + j) * n]))));
   }
   Q[i + (long)j * n] = acc;
+}
+
+// Per-node column scales of the residual-correction right-hand sides: right
+// (left = 0) D_e[j] = 1/(z_e - lam_j), left conj(D_e[j]); with `half`, the
+// mirror node's column m + j holds conj(D_{e'}[j]) (right) or D_e'-conj form
+// (left), z_{e'} = conj(z_e): 1/(z_e - conj(lam_j)) and 1/(conj(z_e) -
+// lam_j).  Also f_j = sum over all ne nodes of w_e / (z_e - lam_j).
+__global__ void gen_scales_kernel(int m, int nf, int ne, const zd *z, const zd *w, const zd *lam, int half,
+                                  zd *SCr, zd *SCl, zd *f) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const zd l = lam[j], lc = X::conj(l);
+  const int mw = half ? 2 * m : m;
+  for (int e = 0; e < nf; ++e) {
+    const zd de = zdiv(zd{1.0, 0.0}, X::sub(z[e], l));
+    SCr[(long)e * mw + j] = de;
+    SCl[(long)e * mw + j] = X::conj(de);
+    if (half) {
+      SCr[(long)e * mw + m + j] = zdiv(zd{1.0, 0.0}, X::sub(z[e], lc));
+      SCl[(long)e * mw + m + j] = zdiv(zd{1.0, 0.0}, X::sub(X::conj(z[e]), l));
+    }
+  }
+  zd s{0.0, 0.0};
+  for (int e = 0; e < ne; ++e) s = X::add(s, zdiv(w[e], X::sub(z[e], l)));
+  f[j] = s;
+}
+
+// R[:, j] = MX[:, j] - lt_j NX[:, j] * s_j, lt = lam or conj(lam), s_j = 1 or
+// 1/sc_j (sc null: 1): the eigen-residual of the Ritz pairs, the
+// right-hand side of the residual-correction form
+__global__ void gen_eig_residual_kernel(int n, const zd *MX, const zd *NX, const zd *lam, int conjl, const double *sc,
+                                        zd *R) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= n) return;
+  const zd l = conjl ? X::conj(lam[j]) : lam[j];
+  const double s = sc ? 1.0 / sc[j] : 1.0;
+  const long o = i + (long)j * n;
+  R[o] = zsc(X::sub(MX[o], X::mul(l, NX[o])), s);
 }
 
 __global__ void __launch_bounds__(RT) col_norms_kernel(int n, const zd *Xm, double *nrm) {
@@ -541,10 +583,30 @@ int gen_conj_pair(cudaStream_t st, int n, int m, const zd *src, zd *dst) {
   GBF_CUDA(cudaGetLastError());
   return 0;
 }
-int gen_accumulate(cudaStream_t st, int n, int m, int nf, const zd *w, const zd *Y, int mw, int half, int left,
-                   zd *Q) {
+template <class TY>
+int gen_accumulate(cudaStream_t st, int n, int m, int nf, const zd *w, const TY *Y, int mw, int half, int left,
+                   const zd *X0, const zd *f, zd *Q) {
   if (m < 1) return 0;
-  accum_gen_kernel<<<grid2(n, m), 256, 0, st>>>(n, m, nf, w, Y, mw, half, left, Q);
+  accum_gen_kernel<TY><<<grid2(n, m), 256, 0, st>>>(n, m, nf, w, Y, mw, half, left, X0, f, Q);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+template int gen_accumulate<zd>(cudaStream_t, int, int, int, const zd *, const zd *, int, int, int, const zd *,
+                                const zd *, zd *);
+template int gen_accumulate<cf>(cudaStream_t, int, int, int, const zd *, const cf *, int, int, int, const zd *,
+                                const zd *, zd *);
+int gen_scales(cudaStream_t st, int m, int nf, int ne, const zd *z, const zd *w, const zd *lam, int half, zd *SCr,
+               zd *SCl, zd *f) {
+  gen_scales_kernel<<<ceil_div(m, 128), 128, 0, st>>>(m, nf, ne, z, w, lam, half, SCr, SCl, f);
+  GBF_LAUNCHED();
+  GBF_CUDA(cudaGetLastError());
+  return 0;
+}
+int gen_eig_residual(cudaStream_t st, int n, int m, const zd *MX, const zd *NX, const zd *lam, int conjl,
+                     const double *sc, zd *R) {
+  if (m < 1) return 0;
+  gen_eig_residual_kernel<<<grid2(n, m), 256, 0, st>>>(n, MX, NX, lam, conjl, sc, R);
   GBF_LAUNCHED();
   GBF_CUDA(cudaGetLastError());
   return 0;

@@ -65,16 +65,20 @@ def _check_outputs(P, o, fpm, exact=None):
 @pytest.mark.parametrize("n", [40, 130, 200])
 @pytest.mark.parametrize("cplx", [False, True])
 @pytest.mark.parametrize("gen", [False, True])
-def test_parity_with_oracle(gbf, n, cplx, gen):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_parity_with_oracle(gbf, n, cplx, gen, prec):
+    """FP64 factors (prec 0) and FP32 factors with the FP64 residual
+    correction (prec 1, fpm(42)=1) against the FP64 oracle."""
     P = W.dense_nonsymmetric(n, count=max(3, n // 20), m0=max(6, n // 12), complex_=cplx, generalized=gen)
     fpm = P.apply_fpm(gbf.gbf_init())
+    fpm[41] = prec
     h = gbf.Handle()
     o = _run(gbf, P, fpm, h)
     ref = G.feast_gen(P.A, P.B, P.emid, P.r, P.m0, P.apply_fpm(G.feastinit_gen()))
     assert ref["info"] == 0
     exact = ref["E"][:ref["M"]]
     _check_outputs(P, o, fpm, exact)
-    assert abs(o["loop"] - ref["loop"]) <= 1
+    assert abs(o["loop"] - ref["loop"]) <= (1 if prec == 0 else 2)
     known = P.spectrum[G.inside(P.spectrum, P.emid, P.r)]
     for lam in known:
         assert np.min(np.abs(o["E"].cpu().numpy()[:o["M"]] - lam)) < TOL_E
@@ -171,6 +175,9 @@ def test_info_codes(gbf):
     o = gbf.feast_gen_dev(A, None, P.emid, P.r, 101, fpm, handle=h)
     assert o["info"] == 201
     bad = fpm.copy()
+    bad[41] = 2
+    assert gbf.feast_gen_dev(A, None, P.emid, P.r, 12, bad, handle=h)["info"] == 142
+    bad = fpm.copy()
     bad[16] = 3
     assert gbf.feast_gen_dev(A, None, P.emid, P.r, 12, bad, handle=h)["info"] == 117
     An = A.clone()
@@ -203,12 +210,14 @@ def test_tiny_and_full_subspace(gbf, n, m0):
         assert np.min(np.abs(E - l)) < 1e-10 * max(1.0, abs(l))
 
 
-def test_known_spectrum_n2048(gbf):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_known_spectrum_n2048(gbf, prec):
     """A larger real non-symmetric pencil (several LU tiles, a ragged
     subspace): eigenvalues against the construction's spectrum, residuals
-    and bi-orthonormality through the outputs."""
+    and bi-orthonormality through the outputs, FP64 and FP32 factors."""
     P = W.dense_nonsymmetric(2048, count=24, m0=40, generalized=True, seed=21)
     fpm = P.apply_fpm(gbf.gbf_init())
+    fpm[41] = prec
     o = _run(gbf, P, fpm, gbf.Handle())
     known = P.spectrum[G.inside(P.spectrum, P.emid, P.r)]
     _check_outputs(P, o, fpm, known)
