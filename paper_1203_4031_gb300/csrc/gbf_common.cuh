@@ -263,10 +263,29 @@ struct SlicedOp {
 // of the caller's workspace, looked up by (address, op, shape, batch).
 // Cleared when the factors change.  A block that no longer fits is sliced
 // per call as before.
+struct SliceKey {
+  const void *A;
+  long lda, sa;
+  int m, k, batch;
+  char op;
+  bool operator==(const SliceKey &o) const {
+    return A == o.A && lda == o.lda && sa == o.sa && m == o.m && k == o.k && batch == o.batch && op == o.op;
+  }
+};
+struct SliceKeyHash {
+  size_t operator()(const SliceKey &s) const {
+    uint64_t h = (uint64_t)(uintptr_t)s.A;
+    h = h * 0x9E3779B97F4A7C15ULL ^ (uint64_t)s.lda;
+    h = h * 0x9E3779B97F4A7C15ULL ^ (uint64_t)s.sa;
+    h = h * 0x9E3779B97F4A7C15ULL ^ ((uint64_t)(unsigned)s.m << 32 | (uint64_t)(unsigned)s.k);
+    h = h * 0x9E3779B97F4A7C15ULL ^ ((uint64_t)(unsigned)s.batch << 8 | (uint64_t)(unsigned char)s.op);
+    return (size_t)(h ^ (h >> 29));
+  }
+};
 struct SliceCache {
   char *base = nullptr;
   size_t cap = 0, used = 0;
-  std::unordered_map<uint64_t, SlicedOp> ops;
+  std::unordered_map<SliceKey, SlicedOp, SliceKeyHash> ops;  // exact keys: no collisions
   void reset() {
     used = 0;
     ops.clear();

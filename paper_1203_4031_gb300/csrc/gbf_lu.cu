@@ -1194,10 +1194,7 @@ static int sliced_gemm_cached(cudaStream_t st, char opa, int m, int nrhs, int k,
                               int gb) {
   SliceCache *cache = g_tc->acache;
   if (cache) {
-    uint64_t key = (uint64_t)(uintptr_t)A;
-    key = key * 0x9E3779B97F4A7C15ULL ^ ((uint64_t)(unsigned char)opa << 56 | (uint64_t)gb << 40 |
-                                         (uint64_t)(unsigned)m << 20 | (uint64_t)(unsigned)k);
-    key = key * 0xBF58476D1CE4E5B9ULL ^ (uint64_t)lda ^ ((uint64_t)sa << 17);
+    const SliceKey key{A, lda, sa, m, k, gb, opa};
     SlicedOp a;
     bool have = false;
     const auto it = cache->ops.find(key);
