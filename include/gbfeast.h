@@ -284,6 +284,18 @@ int gbf_zgegv_dev(gbf_handle h, void *stream, int n, const double *dA, int lda, 
 /* max |X^^H B X - I| over the pairs inside of the last converged
  * non-Hermitian solve on this handle (the quantity info 6 tests). */
 double gbf_biorth_defect(gbf_handle h);
+/* The same drivers on HOST arrays (the guide's predefined [dz]feast_geev /
+ * [dz]feast_gegv, B NULL for the standard problem; with non-NULL Zne, Wne
+ * the expert form with the caller's fpm(8) nodes and weights): A, B copied
+ * to the device, solved with the library's default context for the current
+ * device, E (M0 complex), X (complex n x 2 M0; read when fpm(5)=1) and res
+ * (2 M0) copied back.  Same codes as the device-pointer drivers. */
+int gbf_dgegv(int n, const double *A, int lda, const double *B, int ldb, int *fpm, double *epsout, int *loop,
+              double emid_re, double emid_im, double r, int *M0, double *E, double *X, int *M, double *res, int *info,
+              const double *Zne, const double *Wne);
+int gbf_zgegv(int n, const double *A, int lda, const double *B, int ldb, int *fpm, double *epsout, int *loop,
+              double emid_re, double emid_im, double r, int *M0, double *E, double *X, int *M, double *res, int *info,
+              const double *Zne, const double *Wne);
 
 /* ---------------------------------------------------------------------
  * Step-level entry points (device pointers) exposing single rows of the

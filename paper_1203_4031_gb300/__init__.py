@@ -57,6 +57,10 @@ def load(build: bool = True):
            ip, vp, ip, vp, vp]
     L.gbf_dgegv_dev.argtypes = gen
     L.gbf_zgegv_dev.argtypes = gen
+    gen_host = [C.c_int, vp, C.c_int, vp, C.c_int, ip, dp, ip, C.c_double, C.c_double, C.c_double, ip, vp, vp, ip,
+                vp, ip, vp, vp]
+    L.gbf_dgegv.argtypes = gen_host
+    L.gbf_zgegv.argtypes = gen_host
     L.gbf_gcontour.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
     L.gbf_grationalx.argtypes = [vp, vp, C.c_int, vp, C.c_int, vp]
     L.gbf_wait_probe.argtypes = [vp, C.c_long]
@@ -365,6 +369,37 @@ def feast_gen_dev(A, B, emid, r, m0, fpm=None, X=None, handle=None, stream=None,
        float(r), C.byref(M0), _ptr(E), _ptr(X), C.byref(M), _ptr(res), C.byref(info), zp, wp)
     bi = lib().gbf_biorth_defect(h) if h is not None else None
     return dict(E=E, X=X, res=res, M=M.value, loop=loop.value, epsout=eps.value, info=info.value, biorth=bi)
+
+
+def feast_gen_host(A, B, emid, r, m0, fpm=None, X0=None, Zne=None, Wne=None):
+    """Host-array non-Hermitian drivers gbf_dgegv / gbf_zgegv (numpy A, B;
+    B None for the standard problem; Zne, Wne for the expert form).  Returns
+    E (m0 complex), X (n x 2 m0 complex), res (2 m0), M, loop, epsout, info."""
+    if fpm is None:
+        fpm = gbf_init()
+    fpm = np.ascontiguousarray(fpm, dtype=np.int32).copy()
+    cplx = np.iscomplexobj(A) or (B is not None and np.iscomplexobj(B))
+    dt = np.complex128 if cplx else np.float64
+    A = _fortran(A, dt)
+    n = A.shape[0]
+    Bf = None if B is None else _fortran(B, dt)
+    X = np.zeros((n, 2 * m0), dtype=np.complex128, order="F")
+    if X0 is not None:
+        X[:, :] = X0
+    E = np.zeros(m0, dtype=np.complex128)
+    res = np.zeros(2 * m0)
+    eps, loop, M, info = _scalars()
+    M0 = C.c_int(int(m0))
+    zp = wp = None
+    if Zne is not None:
+        zne = np.ascontiguousarray(Zne, dtype=np.complex128)
+        wne = np.ascontiguousarray(Wne, dtype=np.complex128)
+        zp, wp = _ptr(zne), _ptr(wne)
+    emid = complex(emid)
+    fn = lib().gbf_zgegv if cplx else lib().gbf_dgegv
+    fn(n, _ptr(A), n, _ptr(Bf), n, _ip(fpm), C.byref(eps), C.byref(loop), emid.real, emid.imag, float(r),
+       C.byref(M0), _ptr(E), _ptr(X), C.byref(M), _ptr(res), C.byref(info), zp, wp)
+    return dict(E=E, X=X, res=res, M=M.value, loop=loop.value, epsout=eps.value, info=info.value)
 
 
 def gbf_factor_dev(handle, A, B, zne, prec=0, uplo="F", stream=None):

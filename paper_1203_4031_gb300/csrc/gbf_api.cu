@@ -1475,6 +1475,64 @@ static int run_gen_dev(gbf_handle h, void *stream, bool real, int n, const doubl
   return code;
 }
 
+// Host-pointer form of the non-Hermitian drivers: the inputs copied to the
+// device, the device driver on the default context's stream, the outputs
+// (E: 2 M0 doubles, X: complex n x 2 M0, res: 2 M0) copied back.
+static int run_gen_host(bool real, int n, const double *A, int lda, const double *B, int ldb, int *fpm,
+                        double *epsout, int *loop, double emid_re, double emid_im, double r, int *M0, double *E,
+                        double *X, int *M, double *res, int *info, const double *Zne, const double *Wne) {
+  int code = validate_gen(n, lda, B != nullptr, ldb, fpm, r, M0 ? *M0 : 0);
+  if (code != 0 || !A || !E || !X || !res) {
+    if (code == 0) code = -103;
+    if (info) *info = code;
+    return code;
+  }
+  gbf_context *h = default_ctx();
+  if (!h) {
+    if (info) *info = -4;
+    return -4;
+  }
+  const int m0 = *M0;
+  const size_t szq = real ? sizeof(double) : sizeof(zd);
+  const size_t bytes_a = szq * (size_t)lda * n, bytes_b = B ? szq * (size_t)ldb * n : 0;
+  const size_t bytes_x = sizeof(zd) * (size_t)n * 2 * m0, bytes_e = sizeof(zd) * m0, bytes_r = sizeof(double) * 2 * m0;
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  char *buf = nullptr;
+  const size_t total = al(bytes_a) + al(bytes_b) + al(bytes_x) + al(bytes_e) + al(bytes_r);
+  if (cudaMalloc((void **)&buf, total) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of %zu bytes failed", total);
+    if (info) *info = -1;
+    return -1;
+  }
+  double *dA = (double *)buf;
+  double *dB = B ? (double *)(buf + al(bytes_a)) : nullptr;
+  double *dX = (double *)(buf + al(bytes_a) + al(bytes_b));
+  double *dE = (double *)((char *)dX + al(bytes_x));
+  double *dR = (double *)((char *)dE + al(bytes_e));
+  cudaStream_t st = h->own;
+  int rc = 0;
+  if (cudaMemcpyAsync(dA, A, bytes_a, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      (B && cudaMemcpyAsync(dB, B, bytes_b, cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+      (fpm[4] == 1 && cudaMemcpyAsync(dX, X, bytes_x, cudaMemcpyHostToDevice, st) != cudaSuccess))
+    rc = -4;
+  if (rc == 0)
+    rc = run_gen_dev(h, st, real, n, dA, lda, dB, ldb, fpm, epsout, loop, emid_re, emid_im, r, M0, dE, dX, M, dR,
+                     info, Zne, Wne);
+  if (rc >= 0 && rc != 200 && rc != 201 && rc != 202 && !(rc > 100 && rc < 200)) {
+    if (cudaMemcpyAsync(E, dE, bytes_e, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(res, dR, bytes_r, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(X, dX, bytes_x, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = -4;
+  }
+  if (rc == -4) set_error("CUDA error in host-pointer driver: %s", cudaGetErrorString(cudaGetLastError()));
+  cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (info) *info = rc;
+  return rc;
+}
+
 template <class TQ>
 static int run_host(char uplo, int n, const double *A, int lda, const double *B, int ldb, int *fpm,
                     double *epsout, int *loop, double emin, double emax, int *M0, double *E, double *X, int *M,
@@ -1738,6 +1796,19 @@ int gbf_grationalx(const double *Zne, const double *Wne, int ne, const double *e
 }
 
 double gbf_biorth_defect(gbf_handle h) { return h ? h->gen_biorth : -1.0; }
+
+int gbf_dgegv(int n, const double *A, int lda, const double *B, int ldb, int *fpm, double *epsout, int *loop,
+              double emid_re, double emid_im, double r, int *M0, double *E, double *X, int *M, double *res, int *info,
+              const double *Zne, const double *Wne) {
+  return run_gen_host(true, n, A, lda, B, ldb, fpm, epsout, loop, emid_re, emid_im, r, M0, E, X, M, res, info, Zne,
+                      Wne);
+}
+int gbf_zgegv(int n, const double *A, int lda, const double *B, int ldb, int *fpm, double *epsout, int *loop,
+              double emid_re, double emid_im, double r, int *M0, double *E, double *X, int *M, double *res, int *info,
+              const double *Zne, const double *Wne) {
+  return run_gen_host(false, n, A, lda, B, ldb, fpm, epsout, loop, emid_re, emid_im, r, M0, E, X, M, res, info, Zne,
+                      Wne);
+}
 
 int gbf_dgegv_dev(gbf_handle h, void *stream, int n, const double *dA, int lda, const double *dB, int ldb, int *fpm,
                   double *epsout, int *loop, double emid_re, double emid_im, double r, int *M0, double *dE,

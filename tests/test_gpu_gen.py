@@ -221,3 +221,33 @@ def test_known_spectrum_n2048(gbf, prec):
     o = _run(gbf, P, fpm, gbf.Handle())
     known = P.spectrum[G.inside(P.spectrum, P.emid, P.r)]
     _check_outputs(P, o, fpm, known)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_host_entry_and_expert_nodes(gbf, cplx):
+    """The host-array drivers equal the device ones bit for bit; the expert
+    form with the rule's own nodes and weights equals the default; custom
+    nodes (Gauss, 24 points, passed by the caller) reach the same pairs."""
+    P = W.dense_nonsymmetric(140, count=8, m0=13, complex_=cplx, generalized=True, seed=4)
+    fpm = P.apply_fpm(gbf.gbf_init())
+    h = gbf.Handle()
+    od = _run(gbf, P, fpm, h)
+    oh = gbf.feast_gen_host(P.A, P.B, P.emid, P.r, P.m0, fpm)
+    assert oh["info"] == od["info"] == 0 and oh["M"] == od["M"] and oh["loop"] == od["loop"]
+    assert np.array_equal(oh["E"], od["E"].cpu().numpy())
+    assert np.array_equal(oh["res"], od["res"].cpu().numpy())
+    assert np.array_equal(oh["X"], od["X"].cpu().numpy())
+    z, w = gbf.gbf_gcontour(P.emid, P.r, 16, 1, 100, 0)
+    ox = gbf.feast_gen_host(P.A, P.B, P.emid, P.r, P.m0, fpm, Zne=z, Wne=w)
+    assert ox["info"] == 0 and ox["M"] == od["M"]
+    Ed = od["E"].cpu().numpy()[:od["M"]]
+    for lam in ox["E"][:ox["M"]]:
+        assert np.min(np.abs(Ed - lam)) < 1e-12
+    z, w = G.gcontour(P.emid, P.r, 24, 0)
+    f2 = fpm.copy()
+    f2[7] = 24
+    og = gbf.feast_gen_host(P.A, P.B, P.emid, P.r, P.m0, f2, Zne=z, Wne=w)
+    assert og["info"] == 0 and og["M"] == od["M"]
+    for lam in og["E"][:og["M"]]:
+        assert np.min(np.abs(Ed - lam)) < 1e-10
+    h.close()
