@@ -129,16 +129,17 @@ template <class T> __device__ T cta_sum(T v, T *red) {
 //      nothing is published; the owner of row j writes tau, the new
 //      subdiagonal entry, column j of Vr and the diagonal entry;
 //  (b) p_i = tau sum_k A[i][k] v_k for the own rows i > j (one warp per
-//      row) and this CTA's part of v^H p, double-buffered by the step's
-//      parity;
+//      row) and this CTA's part of v^H p, written into every CTA's buffers
+//      of the step's parity; the owner of row j+1, who never updates it in
+//      place after step j-1, writes it into every CTA as well;
 //  -- cluster barrier --
-//  (c) every CTA reads p and the parts of v^H p from all CTAs (summed in
-//      CTA order, so K = tau/2 Re(v^H p) is the same everywhere), and row
-//      j+1 from its owner, who never updates it in place: w = p - K v; the
-//      own rows i > j+1 get A[i][k] -= v_i conj(w_k) + w_i conj(v_k), and
-//      row j+1 gets the same update in xrow, in every CTA.
-// Reading row j+1 with p merges the reflector's round of remote loads into
-// the one that follows the barrier; FP64 work as fused multiply-adds.
+//  (c) every CTA sums the parts of v^H p in CTA order (so K = tau/2
+//      Re(v^H p) is the same everywhere), forms w = p - K v, updates its own
+//      rows i > j+1 by A[i][k] -= v_i conj(w_k) + w_i conj(v_k), and row j+1
+//      the same way in xrow.
+// Everything a CTA needs after the barrier is in its own shared memory: the
+// writes to other CTAs go out before the barrier, no remote load waits after
+// it.  FP64 work as fused multiply-adds.
 template <class T>
 __global__ void __launch_bounds__(TRD_THREADS, 1)
     sytrd_cluster_kernel(int m, const T *__restrict__ A, long lda, T *__restrict__ Vr, double *__restrict__ tau,
@@ -150,12 +151,13 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
   const int rl = (m + C - 1) / C;
   extern __shared__ __align__(16) unsigned char smem[];
   T *L = reinterpret_cast<T *>(smem);  // [rl][m]
-  T *pown = L + (size_t)rl * m;        // [2][rl] p of this CTA's rows, by step parity
-  T *vfull = pown + 2 * (size_t)rl;    // [m] v of the current step
+  T *pfull = L + (size_t)rl * m;       // [2][m] p of every row, by step parity (written by the rows' CTAs)
+  T *xnext = pfull + 2 * (size_t)m;    // [2][m] row j+1 as its owner holds it, by step parity
+  T *vfull = xnext + 2 * (size_t)m;    // [m] v of the current step
   T *wfull = vfull + m;                // [m] w of the current step
   T *xrow = wfull + m;                 // [m] row j as updated by the steps before j
   __shared__ T s_pvw[NW];              // each warp's part of v^H p
-  __shared__ T s_pcta[2];              // this CTA's part of v^H p, by step parity
+  __shared__ T s_parts[2][16];         // every CTA's part of v^H p, by step parity
   __shared__ double s_tau;
   __shared__ T s_sc, s_tot;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -227,32 +229,33 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
       T s = X::zero();
       for (int k = j + 1 + lane; k < m; k += 32) s = X::fma(Li[k], vfull[k], s);
       s = scl(warp_sum(s), tj);
-      if (lane == 0) pown[(size_t)par * rl + il] = s;
+      if (lane < C) cl.map_shared_rank(pfull, lane)[(size_t)par * m + i] = s;
       pv = X::fma(X::conj(vfull[i]), s, pv);
     }
     if (lane == 0) s_pvw[warp] = pv;
+    if ((j + 1) % C == q) {  // row j+1, as the step j-1 update left it, into every CTA
+      const T *rn = L + (size_t)((j + 1) / C) * m;
+      for (int k = j + 1 + tid; k < m; k += blockDim.x) {
+        const T v = rn[k];
+        for (int d = 0; d < C; ++d) cl.map_shared_rank(xnext, d)[(size_t)par * m + k] = v;
+      }
+    }
     __syncthreads();
     if (warp == 0) {
       const T r = warp_sum(lane < NW ? s_pvw[lane] : X::zero());
-      if (lane == 0) s_pcta[par] = r;
+      if (lane < C) cl.map_shared_rank(&s_parts[0][0], lane)[par * 16 + q] = r;
     }
-    cl.sync();  // every CTA's p and part of v^H p visible
-    // (c) v^H p: warp 0 reads the C parts (one remote load per lane, then
-    // the same sum in every CTA); row j+1 as its owner holds it
+    cl.sync();  // every CTA's p, part of v^H p and row j+1 in every CTA
+    // (c) v^H p: the C parts in CTA order (the same sum in every CTA)
     if (warp == 0) {
-      const T tot = warp_sum(lane < C ? *cl.map_shared_rank(&s_pcta[par], lane) : X::zero());
+      const T tot = warp_sum(lane < C ? s_parts[par][lane] : X::zero());
       if (lane == 0) s_tot = tot;
     }
-    {
-      const T *rn = cl.map_shared_rank(L, (j + 1) % C) + (size_t)((j + 1) / C) * m;
-      for (int k = j + 1 + tid; k < m; k += blockDim.x) xrow[k] = rn[k];
-    }
+    for (int k = j + 1 + tid; k < m; k += blockDim.x) xrow[k] = xnext[(size_t)par * m + k];
     __syncthreads();
     const double kk = 0.5 * tj * X::re(s_tot);
-    for (int k = j + 1 + tid; k < m; k += blockDim.x) {
-      const T pk = *cl.map_shared_rank(&pown[(size_t)par * rl + k / C], k % C);
-      wfull[k] = X::sub(pk, scl(vfull[k], kk));
-    }
+    for (int k = j + 1 + tid; k < m; k += blockDim.x)
+      wfull[k] = X::sub(pfull[(size_t)par * m + k], scl(vfull[k], kk));
     __syncthreads();
     // A[i][k] -= v_i conj(w_k) + w_i conj(v_k): own rows i > j+1 (one warp
     // per row, lanes over the columns k > j), and row j+1 in xrow
@@ -647,9 +650,8 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
   const int rl = (m + C - 1) / C;
   extern __shared__ __align__(16) unsigned char smem[];
   T *L = reinterpret_cast<T *>(smem);  // [rl][m]
-  T *lpub = L + (size_t)rl * m;        // [m] column j of L, published by the owner of row j
-  T *lfull = lpub + m;                 // [m] copy
-  __shared__ int s_fail;
+  T *lcol = L + (size_t)rl * m;        // [2][m] column j of L, written here by the owner of row j
+  __shared__ int s_fail[2];            // the owner's pivot test, written here with the column
   __shared__ double s_r, s_ir;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (long t = tid; t < (long)rl * m; t += blockDim.x) {
@@ -659,47 +661,49 @@ __global__ void __launch_bounds__(TRD_THREADS, 1)
   }
   __syncthreads();
   for (int j = 0; j < m; ++j) {
-    const int own = j % C;
+    const int own = j % C, par = j & 1;
+    T *lc = lcol + (size_t)par * m;
     if (q == own) {
+      // the owner forms column j from its row j (Hermitian: column j below
+      // the diagonal is the conjugate of row j right of it) and writes it,
+      // with the pivot test, into every CTA's buffer of this parity
       const T *Lj = L + (long)(j / C) * m;
       if (tid == 0) {  // the pivot's root and reciprocal, once
         const double piv = X::re(Lj[j]);
         const bool okp = piv > 0.0;
-        s_fail = okp ? 0 : j + 1;
+        const int f = okp ? 0 : j + 1;
         const double ir = okp ? fast_rsqrt(piv) : 0.0;  // one reciprocal square root
         s_r = piv * ir;
         s_ir = ir;
+        for (int d = 0; d < C; ++d) cl.map_shared_rank(s_fail, d)[par] = f;
       }
       __syncthreads();
-      const bool ok = s_fail == 0;
-      if (ok) {
-        const double r = s_r, ir = s_ir;
-        for (int k = tid; k < m; k += blockDim.x) {
-          T l = X::zero();
-          if (k == j)
-            l = cvt<T, double>(r);
-          else if (k > j)
-            l = scl(X::conj(Lj[k]), ir);
-          if (k >= j) lpub[k] = l;
-          Lout[k + (long)j * m] = l;
-        }
+      const double r = s_r, ir = s_ir;
+      for (int k = j + tid; k < m; k += blockDim.x) {
+        const T l = (k == j) ? cvt<T, double>(r) : scl(X::conj(Lj[k]), ir);
+        for (int d = 0; d < C; ++d) cl.map_shared_rank(lc, d)[k] = l;
+      }
+      for (int k = tid; k < m; k += blockDim.x) {
+        T l = X::zero();
+        if (k == j)
+          l = cvt<T, double>(r);
+        else if (k > j)
+          l = scl(X::conj(Lj[k]), ir);
+        Lout[k + (long)j * m] = l;
       }
     }
-    cl.sync();  // column j of L published (or the failure)
-    const int f = *cl.map_shared_rank(&s_fail, own);
-    if (f) {  // uniform: every CTA reads the owner's flag
+    cl.sync();  // column j of L (or the failure) in every CTA
+    const int f = s_fail[par];
+    if (f) {  // uniform: every CTA holds the owner's flag
       if (tid == 0 && q == 0) *fail = f;
       break;
     }
-    const T *lsrc = cl.map_shared_rank(lpub, own);
-    for (int k = j + 1 + tid; k < m; k += blockDim.x) lfull[k] = lsrc[k];
-    __syncthreads();
     for (int il = warp; il < rl; il += nw) {
       const int i = il * C + q;
       if (i <= j || i >= m) continue;
       T *Li = L + (long)il * m;
-      const T li = X::neg(lfull[i]);
-      for (int k = j + 1 + lane; k < m; k += 32) Li[k] = X::fma(li, X::conj(lfull[k]), Li[k]);
+      const T li = X::neg(lc[i]);
+      for (int k = j + 1 + lane; k < m; k += 32) Li[k] = X::fma(li, X::conj(lc[k]), Li[k]);
     }
     __syncthreads();
   }
@@ -768,7 +772,7 @@ int heev_tridiag(cudaStream_t st, int m, const T *A, double *w, T *V, void *work
   if (m < 2 || m > OR_THREADS * OR_PER) return 1;
   if (heev_tridiag_work(m, tr<T>::cplx) > work_bytes) return 1;
   size_t sm_t = 0;
-  const int C = cluster_shape<T>(m, 2, 3, &sm_t);
+  const int C = cluster_shape<T>(m, 0, 7, &sm_t);
   if (C == 0) return 1;
   const size_t mm = (size_t)m * m;
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
