@@ -194,3 +194,38 @@ def test_initial_subspace_is_the_hermitian_oracles():
         for i in range(5):
             t = i + 5 * j
             assert Y[i, j] == complex(u(2 * t), u(2 * t + 1))
+
+
+@pytest.mark.parametrize("gen", [False, True])
+def test_hermitian_pencil_matches_hermitian_oracle(gen):
+    """On a Hermitian A (and Hermitian positive definite B) every eigenvalue
+    is real, so the non-Hermitian iteration on a circle centred on the real
+    axis must find exactly the Hermitian oracle's eigenvalues in the
+    diameter's interval, with right and left vectors alike."""
+    n = 90
+    rng = np.random.default_rng(11)
+    X = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A = 0.5 * (X + X.conj().T) / np.sqrt(n)
+    B = None
+    if gen:
+        Y = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        B = np.eye(n) + 0.05 * (Y @ Y.conj().T) / n
+    w = sla.eigvalsh(A, B)
+    emid = 0.05
+    d = np.sort(np.abs(w - emid))
+    r = 0.5 * (d[7] + d[8])
+    ref = oracle.feast(A, B, emid - r, emid + r, 12, hermitian=True)
+    assert ref["info"] == 0 and ref["M"] == 8
+    fpm = G.feastinit_gen()
+    o = G.feast_gen(A, B, emid, r, 11, fpm)
+    assert o["info"] == 0 and o["M"] == 8
+    E = o["E"][:8]
+    assert np.max(np.abs(E.imag)) < 1e-12
+    assert np.max(np.abs(np.sort(E.real) - ref["E"][:8])) < 1e-12
+    # a Hermitian pencil's left eigenvectors are its right ones: x^_j is a
+    # multiple of x_j (distinct eigenvalues)
+    Xr, Xl = o["X"][:, :8], o["X"][:, 11:19]
+    for j in range(8):
+        x, y = Xr[:, j], Xl[:, j]
+        cosang = abs(np.vdot(x, y)) / (np.linalg.norm(x) * np.linalg.norm(y))
+        assert abs(cosang - 1.0) < 1e-9
