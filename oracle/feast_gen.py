@@ -52,7 +52,13 @@ Readings where the guide is silent (each listed in the design notes):
     pairs inside, fpm(6)=0 on |trace - trace_prev| / alpha with the complex
     trace of the pairs inside; epsout = 1 at loop 0;
   - info 6 when, at convergence, max |X^_M^H B X_M - I| exceeds 1e-8;
-  - no spurious-pair test (the guide gives no criterion for this variant).
+  - no spurious-pair test (the guide gives no criterion for this variant);
+  - Q and Q^ are replaced by orthonormal bases of their numerical ranges
+    (Gram eigenvalues above 1e-12 of the largest), both cut to the smaller
+    rank mk: the returned "new suitable M0" of Table tab_common.  Without
+    it, the columns of eigenvalues far outside (filter values below the
+    solves' rounding level) turn into noise and the reduced pencil becomes
+    singular when M0 exceeds the count by a wide margin.
 """
 from __future__ import annotations
 
@@ -144,6 +150,17 @@ def _res(Mx, Nx, lam, alpha):
     return num / den
 
 
+def _range_basis(M):
+    """Orthonormal basis of the numerical range of M's columns: the Gram
+    matrix M^H M diagonalised (library eigh), directions with eigenvalue at
+    most 1e-12 of the largest dropped, the rest scaled to unit length
+    (M V diag(w)^-1/2).  Returns the basis (largest directions last) and its
+    size."""
+    w, V = np.linalg.eigh(M.conj().T @ M)
+    keep = w > 1e-12 * w[-1]
+    return (M @ V[:, keep]) / np.sqrt(w[keep])[None, :], int(keep.sum())
+
+
 def feast_gen(A, B, emid, r, m0, fpm=None, X0=None, zne=None, wne=None):
     """Non-Hermitian FEAST on the dense pencil (A, B) (B None: identity).
     Returns dict(E (m0 complex), X (n x 2 m0), res (2 m0), M, loop, epsout,
@@ -162,7 +179,7 @@ def feast_gen(A, B, emid, r, m0, fpm=None, X0=None, zne=None, wne=None):
     E = np.zeros(m0, dtype=np.complex128)
     X = np.zeros((n, 2 * m0), dtype=np.complex128, order="F")
     res = np.zeros(2 * m0)
-    out = dict(E=E, X=X, res=res, M=0, loop=0, epsout=1.0, info=0, biorth=0.0)
+    out = dict(E=E, X=X, res=res, M=0, loop=0, epsout=1.0, info=0, biorth=0.0, m0=m0)
     if fpm[4] == 1 and X0 is not None:
         Y = np.array(X0[:, :m0], dtype=np.complex128)
         Yh = np.array(X0[:, m0:2 * m0], dtype=np.complex128)
@@ -185,6 +202,13 @@ def feast_gen(A, B, emid, r, m0, fpm=None, X0=None, zne=None, wne=None):
             X[:, m0:m0 + m] = Qh
             out.update(loop=k, info=4)
             return out
+        # numerical ranges: directions the filter reduced below the solves'
+        # rounding level carry noise that makes the reduced pencil singular;
+        # both subspaces keep their mk largest directions (the new M0)
+        Qo, r1 = _range_basis(Q)
+        Qho, r2 = _range_basis(Qh)
+        m = min(r1, r2)
+        Q, Qh = Qo[:, -m:], Qho[:, -m:]
         # Rayleigh-Ritz on the dual subspaces (cases 30/31, 40/41)
         AQ, BQ = A @ Q, Bm @ Q
         AhQh, BhQh = A.conj().T @ Qh, Bm.conj().T @ Qh
@@ -220,7 +244,7 @@ def feast_gen(A, B, emid, r, m0, fpm=None, X0=None, zne=None, wne=None):
         res[m0:m0 + m] = rl[order]
         X[:, :m] = Xr[:, order]
         X[:, m0:m0 + m] = Xl[:, order]
-        out.update(M=nin, loop=k, epsout=eout)
+        out.update(M=nin, loop=k, epsout=eout, m0=m)
         info = None
         if not (np.all(np.isfinite(lam)) and np.all(np.isfinite(rr)) and np.all(np.isfinite(rl))):
             info = -2

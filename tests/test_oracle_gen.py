@@ -217,15 +217,43 @@ def test_hermitian_pencil_matches_hermitian_oracle(gen):
     ref = oracle.feast(A, B, emid - r, emid + r, 12, hermitian=True)
     assert ref["info"] == 0 and ref["M"] == 8
     fpm = G.feastinit_gen()
-    o = G.feast_gen(A, B, emid, r, 11, fpm)
-    assert o["info"] == 0 and o["M"] == 8
+    fpm[7] = 24
+    # M0 = 14: the sparse real spectrum leaves most of the 6 extra columns
+    # with filter values at rounding level; the numerical-range cut keeps
+    # the pencil regular (m0 returned below 14)
+    o = G.feast_gen(A, B, emid, r, 14, fpm)
+    assert o["info"] == 0 and o["M"] == 8 and 8 <= o["m0"] <= 14
     E = o["E"][:8]
     assert np.max(np.abs(E.imag)) < 1e-12
     assert np.max(np.abs(np.sort(E.real) - ref["E"][:8])) < 1e-12
     # a Hermitian pencil's left eigenvectors are its right ones: x^_j is a
     # multiple of x_j (distinct eigenvalues)
-    Xr, Xl = o["X"][:, :8], o["X"][:, 11:19]
+    Xr, Xl = o["X"][:, :8], o["X"][:, 14:22]
     for j in range(8):
         x, y = Xr[:, j], Xl[:, j]
         cosang = abs(np.vdot(x, y)) / (np.linalg.norm(x) * np.linalg.norm(y))
         assert abs(cosang - 1.0) < 1e-9
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_large_subspace_keeps_the_pencil_regular(cplx):
+    """M0 = 16 for 6 eigenvalues inside: without the numerical-range cut the
+    reduced pencil turns singular (non-finite Ritz values); with it the
+    iteration converges to the known eigenvalues."""
+    P = W.dense_nonsymmetric(300, count=6, m0=16, complex_=cplx, generalized=True, seed=13)
+    o = G.feast_gen(P.A, P.B, P.emid, P.r, P.m0, P.apply_fpm(G.feastinit_gen()))
+    assert o["info"] == 0 and o["M"] == 6
+    for lam in P.spectrum[G.inside(P.spectrum, P.emid, P.r)]:
+        assert np.min(np.abs(o["E"][:6] - lam)) < 1e-12
+    assert np.max(o["res"][:6]) < 1e-10 and np.max(o["res"][16:22]) < 1e-10
+
+
+def test_range_basis_is_orthonormal_and_drops_noise():
+    rng = np.random.default_rng(2)
+    U = np.linalg.qr(rng.standard_normal((50, 5)) + 1j * rng.standard_normal((50, 5)))[0]
+    M = U @ np.diag([3.0, 1.0, 0.5, 1e-3, 2.0]) @ (rng.standard_normal((5, 8)))
+    M[:, 7] += 1e-14 * rng.standard_normal(50)      # noise direction beyond the rank
+    Bq, k = G._range_basis(M)
+    assert k == 5
+    assert np.allclose(Bq.conj().T @ Bq, np.eye(5), atol=1e-10)
+    assert np.allclose(Bq @ (Bq.conj().T @ U), U, atol=1e-8)
