@@ -258,7 +258,10 @@ int gbf_grationalx(const double *Zne, const double *Wne, int ne, const double *e
  *    results reach FP64 accuracy.  For real A, B, a real Emid, fpm(19) = 0 and an even
  *    fpm(8), the nodes pair up as z and conj(z) and only fpm(8)/2 systems are
  *    factored (the guide's remark on real non-symmetric problems).
- *  - *M0 (1..min(n, 1024)): subspace size.  dE: M0 complex eigenvalues,
+ *  - *M0 (1..min(n, 1024)): subspace size; on exit the size kept (each
+ *    loop replaces Q and Q^ by orthonormal bases of their numerical ranges,
+ *    dropping directions whose Gram eigenvalue is at most 1e-12 of the
+ *    largest; entries past it are zero).  dE: M0 complex eigenvalues,
  *    the M inside first, each group ordered by ascending (Re, Im).  dX:
  *    complex n x 2 M0 (ld n): right eigenvectors in columns 0..M0-1 (unit
  *    2-norm), left ones in columns M0..2 M0-1, scaled so that the returned

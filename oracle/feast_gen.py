@@ -52,6 +52,7 @@ Readings where the guide is silent (each listed in the design notes):
     pairs inside, fpm(6)=0 on |trace - trace_prev| / alpha with the complex
     trace of the pairs inside; epsout = 1 at loop 0;
   - info 6 when, at convergence, max |X^_M^H B X_M - I| exceeds 1e-8;
+  - info 3 when every one of the kept mk Ritz values is inside and mk < N;
   - no spurious-pair test (the guide gives no criterion for this variant);
   - Q and Q^ are replaced by orthonormal bases of their numerical ranges
     (Gram eigenvalues above 1e-12 of the largest), both cut to the smaller
@@ -250,7 +251,7 @@ def feast_gen(A, B, emid, r, m0, fpm=None, X0=None, zne=None, wne=None):
             info = -2
         elif nin == 0:
             info = 1
-        elif nin >= m0 and m0 < n:
+        elif nin >= m and m < n:
             info = 3
         elif (eout < eps) if fpm[5] == 0 else (maxres < eps):
             info = 0

@@ -985,6 +985,8 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
     size_t tcw_bytes, kw_bytes, rrw_bytes;
     char *acache_base;
     size_t acache_bytes;
+    void *trw;  // Gram eigenproblems of the numerical-range cut
+    size_t trw_bytes;
   } ws;
   SliceCache acache;
   auto layout = [&](Bump &b) {
@@ -997,13 +999,13 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
     ws.Ytmp = b.take<TL>((size_t)nf * n * mw);
     ws.Yadj = b.take<TL>((size_t)nf * n * mw);
     ws.R2 = b.take<zd>((size_t)n * mw);
-    ws.AYr = mixed ? b.take<zd>(nm) : nullptr;
-    ws.AYl = mixed ? b.take<zd>(nm) : nullptr;
-    ws.YlN = mixed ? b.take<zd>(nm) : nullptr;
-    ws.Rres = mixed ? b.take<zd>(nm) : nullptr;
-    ws.SCr = mixed ? b.take<zd>((size_t)nf * mw) : nullptr;
-    ws.SCl = mixed ? b.take<zd>((size_t)nf * mw) : nullptr;
-    ws.fv = mixed ? b.take<zd>(m0) : nullptr;
+    ws.AYr = b.take<zd>(nm);
+    ws.AYl = b.take<zd>(nm);
+    ws.YlN = b.take<zd>(nm);
+    ws.Rres = b.take<zd>(nm);
+    ws.SCr = b.take<zd>((size_t)nf * mw);
+    ws.SCl = b.take<zd>((size_t)nf * mw);
+    ws.fv = b.take<zd>(m0);
     zd **nmb[] = {&ws.Q, &ws.Qh, &ws.AQ, &ws.AhQh, &ws.Xr, &ws.AXr, &ws.Xl, &ws.AXl, &ws.Yr, &ws.Yl, &ws.RBr,
                   &ws.RBl, &ws.Tmp};
     for (zd **p : nmb) *p = b.take<zd>(nm);
@@ -1063,6 +1065,8 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
     ws.pjw = b.take<char>(sliced_op_bytes(m0, Km, 1));
     ws.rrw_bytes = gemm_sliced_k_work(true, m0, m0, m0, 1);
     ws.rrw = b.take<char>(ws.rrw_bytes);
+    ws.trw_bytes = heev_tridiag_work(m0, true);
+    ws.trw = b.take<char>(ws.trw_bytes);
   };
   {
     Bump sizing(nullptr);
@@ -1097,7 +1101,7 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
   tcr.kbytes = ws.kw_r_bytes;
   TcScope tc_scope(tcS ? &tcx : nullptr);
   AuxScope aux_scope(ensure_aux(h));
-  if (ensure_hbuf(h, (size_t)std::max(m0, ne) + 64)) return out.info = -1;
+  if (ensure_hbuf(h, (size_t)std::max(2 * m0, ne) + 64)) return out.info = -1;
   h->f_prec = -1;
 
   GBF_CUDA(cudaMemcpyAsync(ws.z, zh.data(), sizeof(zd) * ne, cudaMemcpyHostToDevice, st));
@@ -1170,7 +1174,7 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
   };
 
   // initial subspaces: right/left guesses from X (fpm(5)=1) or the seeded one
-  const int m = m0;
+  int m = m0;
   if (fpm[4] == 1) {
     GBF_CUDA(cudaMemcpyAsync(ws.Yr, q.X, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
     GBF_CUDA(cudaMemcpyAsync(ws.Yl, (const zd *)q.X + nm, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
@@ -1190,12 +1194,17 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
   zd trace_prev{0.0, 0.0};
   for (int k = 0;; ++k) {
     // ---- spectral projections (cases 11 and 21) ----
-    // FP32 factors after the first loop: the residual-correction form
+    // After the first loop, the residual-correction form
     // S_e^{-1} B X = X D_e + S_e^{-1} R D_e, R = A X - B X Lambda, D_e =
     // (z_e - Lambda)^{-1}, so Q = X f(Lambda) + sum_e w_e S_e^{-1} R D_e; on
     // the left S_e^{-H} B^H X^ = X^ conj(D_e) + S_e^{-H} R^ conj(D_e), R^ =
-    // A^H X^ - B^H X^ conj(Lambda): the FP32 solves see only the residuals
-    const bool rc_form = mixed && k > 0;
+    // A^H X^ - B^H X^ conj(Lambda).  The same Q in exact arithmetic; the
+    // solves see only the residuals, so FP32 factors reach FP64 results, and
+    // a column whose filter value is far below the rounding level of the
+    // solves (an eigenvalue far outside) stays accurate relative to its own
+    // size instead of turning into solve noise that makes Q^^H B Q singular
+    const bool rc_form = k > 0;
+    const int mwk = half ? 2 * m : m;  // right-hand sides per factored node this loop
     const zd *rr_src = ws.RBr, *rl_src = ws.RBl;
     if (rc_form) {
       CK(gen_scales(st, m, nf, ne, ws.z, ws.w, ws.Eo, half ? 1 : 0, ws.SCr, ws.SCl, ws.fv));
@@ -1206,9 +1215,10 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
       CK(gen_conj_pair(st, n, m, rr_src, ws.R2));
       rr_src = ws.R2;
     }
-    CK(gather_rhs<TL>(st, n, nf, mw, ws.perm, 1, rr_src, n, rc_form ? ws.SCr : nullptr, ws.Ysol));
-    CK(getrs_inplace<TL>(st, 0, n, nf, mw, ws.S, ws.Linv, ws.Uinv, bs, ws.Ysol, nullptr));
-    CK(gen_accumulate<TL>(st, n, m, nf, ws.w, ws.Ysol, mw, half ? 1 : 0, 0, rc_form ? ws.Yr : nullptr, ws.fv, ws.Q));
+    CK(gather_rhs<TL>(st, n, nf, mwk, ws.perm, 1, rr_src, n, rc_form ? ws.SCr : nullptr, ws.Ysol));
+    CK(getrs_inplace<TL>(st, 0, n, nf, mwk, ws.S, ws.Linv, ws.Uinv, bs, ws.Ysol, nullptr));
+    CK(gen_accumulate<TL>(st, n, m, nf, ws.w, ws.Ysol, mwk, half ? 1 : 0, 0, rc_form ? ws.Yr : nullptr, ws.fv,
+                          ws.Q));
     if (rc_form) {
       CK(gen_eig_residual(st, n, m, ws.AYl, ws.RBl, ws.Eo, 1, nullptr, ws.Rres));
       rl_src = ws.Rres;
@@ -1217,10 +1227,10 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
       CK(gen_conj_pair(st, n, m, rl_src, ws.R2));
       rl_src = ws.R2;
     }
-    CK(gather_rhs<TL>(st, n, nf, mw, nullptr, 1, rl_src, n, rc_form ? ws.SCl : nullptr, ws.Ytmp));
-    CK(getrs_inplace<TL>(st, 1, n, nf, mw, ws.S, ws.Linv, ws.Uinv, bs, ws.Ytmp, nullptr));
-    CK(scatter_perm<TL>(st, n, nf, mw, ws.perm, ws.Ytmp, ws.Yadj));
-    CK(gen_accumulate<TL>(st, n, m, nf, ws.w, ws.Yadj, mw, half ? 1 : 0, 1, rc_form ? ws.YlN : nullptr, ws.fv,
+    CK(gather_rhs<TL>(st, n, nf, mwk, nullptr, 1, rl_src, n, rc_form ? ws.SCl : nullptr, ws.Ytmp));
+    CK(getrs_inplace<TL>(st, 1, n, nf, mwk, ws.S, ws.Linv, ws.Uinv, bs, ws.Ytmp, nullptr));
+    CK(scatter_perm<TL>(st, n, nf, mwk, ws.perm, ws.Ytmp, ws.Yadj));
+    CK(gen_accumulate<TL>(st, n, m, nf, ws.w, ws.Yadj, mwk, half ? 1 : 0, 1, rc_form ? ws.YlN : nullptr, ws.fv,
                           ws.Qh));
     if (fpm[13] == 1) {  // the subspaces after one contour
       GBF_CUDA(cudaMemcpyAsync(q.X, ws.Q, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
@@ -1230,6 +1240,62 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
       GBF_CUDA(cudaStreamSynchronize(st));
       out.loop = k;
       return out.info = 4;
+    }
+    // ---- numerical ranges of Q and Q^: orthonormal bases of the directions
+    // whose Gram eigenvalue exceeds 1e-12 of the largest, both cut to the
+    // smaller rank mk (the new M0).  Columns of eigenvalues far outside fall
+    // below the solves' rounding level and would make the pencil singular.
+    {
+      CatScope cat_red(CAT_REDUCED);
+      zd *Gq = ws.Aq, *Gh = ws.Bq, *Vq = ws.Z, *Vh = ws.Yv, *Tq = ws.W, *Th = ws.V;
+      double *wq = ws.rr, *wl = ws.rl;
+      const zd *src[2] = {ws.Q, ws.Qh};
+      zd *gram[2] = {Gq, Gh}, *vec[2] = {Vq, Vh};
+      double *ev[2] = {wq, wl};
+      for (int t = 0; t < 2; ++t) {
+        SlicedOp opH, opC;
+        CK(slice_rows<zd>(st, 'C', m, n, src[t], n, 0, 1, ws.pjh, &opH));
+        CK(slice_cols<zd>(st, 'N', n, m, src[t], n, 0, 1, ws.pjq, &opC));
+        CK(gemm_sliced_ops<zd>(st, opH, opC, 1, 1.0, 0, gram[t], m, 0, ws.tc_err));
+        CK(hermitize<zd>(st, m, gram[t], ws.G));
+        if (m == 1) {
+          GBF_CUDA(cudaMemcpyAsync(ev[t], ws.G, sizeof(double), cudaMemcpyDeviceToDevice, st));
+          CK(gen_identity(st, 1, vec[t]));
+        } else {
+          const int trc = heev_tridiag<zd>(st, m, ws.G, ev[t], vec[t], ws.trw, ws.trw_bytes);
+          if (trc == 1) {
+            set_error("subspace Gram eigenproblem: the cluster kernel cannot take m = %d", m);
+            return out.info = -4;
+          }
+          CK(trc);
+        }
+      }
+      double *hd = h->hbuf;
+      GBF_CUDA(cudaMemcpyAsync(hd, wq, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+      GBF_CUDA(cudaMemcpyAsync(hd + m, wl, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+      GBF_CUDA(cudaStreamSynchronize(st));
+      int r1 = 0, r2 = 0;
+      for (int i = 0; i < m; ++i) {
+        r1 += hd[i] > 1e-12 * hd[m - 1] ? 1 : 0;
+        r2 += hd[m + i] > 1e-12 * hd[2 * m - 1] ? 1 : 0;
+      }
+      const int mk = std::min(r1, r2);
+      if (mk < 1 || !(hd[m - 1] > 0.0) || !(hd[2 * m - 1] > 0.0)) {
+        set_error("the filtered subspaces are empty (no direction above the rounding level)");
+        return out.info = -3;
+      }
+      CK(make_t<zd>(st, m, mk, m - mk, Vq, wq, Tq));
+      CK(make_t<zd>(st, m, mk, m - mk, Vh, wl, Th));
+      SlicedOp opT, opM;
+      CK(slice_cols<zd>(st, 'N', m, mk, Tq, m, 0, 1, ws.pjw, &opT));
+      CK(slice_rows<zd>(st, 'N', n, m, ws.Q, n, 0, 1, ws.pjx, &opM));
+      CK(gemm_sliced_ops<zd>(st, opM, opT, 1, 1.0, 0, ws.AQ, n, 0, ws.tc_err));
+      CK(slice_cols<zd>(st, 'N', m, mk, Th, m, 0, 1, ws.pjw, &opT));
+      CK(slice_rows<zd>(st, 'N', n, m, ws.Qh, n, 0, 1, ws.pjx, &opM));
+      CK(gemm_sliced_ops<zd>(st, opM, opT, 1, 1.0, 0, ws.AhQh, n, 0, ws.tc_err));
+      GBF_CUDA(cudaMemcpyAsync(ws.Q, ws.AQ, sizeof(zd) * (size_t)n * mk, cudaMemcpyDeviceToDevice, st));
+      GBF_CUDA(cudaMemcpyAsync(ws.Qh, ws.AhQh, sizeof(zd) * (size_t)n * mk, cudaMemcpyDeviceToDevice, st));
+      m = mk;
     }
     // ---- Rayleigh-Ritz on the dual subspaces (cases 30, 31, 40, 41) ----
     {
@@ -1304,7 +1370,7 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
     CK(permute_cols<zd>(st, n, m, ws.pos, ws.Xr, ws.Yr));
     CK(permute_cols<zd>(st, n, m, ws.pos, ws.Xl, ws.Yl));
     if (hasB) CK(permute_cols<zd>(st, n, m, ws.pos, ws.BXr, ws.RBr));
-    else GBF_CUDA(cudaMemcpyAsync(ws.RBr, ws.Yr, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
+    else GBF_CUDA(cudaMemcpyAsync(ws.RBr, ws.Yr, sizeof(zd) * (size_t)n * m, cudaMemcpyDeviceToDevice, st));
     CK(gen_col_norms(st, n, m, ws.Yl, ws.nl));
     if (hasB) {
       CK(permute_cols<zd>(st, n, m, ws.pos, ws.BXl, ws.Tmp));
@@ -1312,12 +1378,11 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
     } else {
       CK(gen_col_scale(st, n, m, ws.Yl, ws.RBl, ws.nl, 1));
     }
-    if constexpr (mixed) {  // A X and A^H X^ of the next subspaces, for the residuals
-      CK(permute_cols<zd>(st, n, m, ws.pos, ws.AXr, ws.AYr));
-      CK(permute_cols<zd>(st, n, m, ws.pos, ws.AXl, ws.Tmp));
-      CK(gen_col_scale(st, n, m, ws.Tmp, ws.AYl, ws.nl, 1));
-      CK(gen_col_scale(st, n, m, ws.Yl, ws.YlN, ws.nl, 1));
-    }
+    // A X and A^H X^ of the next subspaces, for the residuals
+    CK(permute_cols<zd>(st, n, m, ws.pos, ws.AXr, ws.AYr));
+    CK(permute_cols<zd>(st, n, m, ws.pos, ws.AXl, ws.Tmp));
+    CK(gen_col_scale(st, n, m, ws.Tmp, ws.AYl, ws.nl, 1));
+    CK(gen_col_scale(st, n, m, ws.Yl, ws.YlN, ws.nl, 1));
     double *hs = h->hbuf;
     GBF_CUDA(cudaMemcpyAsync(hs, ws.stats, sizeof(double) * 5, cudaMemcpyDeviceToHost, st));
     GBF_CUDA(cudaMemcpyAsync(h->hflag, ws.flag, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
@@ -1354,7 +1419,7 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
       info = -2;
     } else if (nin == 0) {
       info = 1;
-    } else if (nin >= m0 && m0 < n) {
+    } else if (nin >= m && m < n) {
       info = 3;
     } else if ((fpm[5] == 0) ? (eout < eps) : (maxres < eps)) {
       info = 0;
@@ -1368,13 +1433,17 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
     } else if (k >= fpm[3]) {
       info = 2;
     }
-    if (info != -99) {
+    if (info != -99) {  // outputs: m pairs, zero past them; m is the new M0
+      GBF_CUDA(cudaMemsetAsync(q.E, 0, sizeof(zd) * m0, st));
+      GBF_CUDA(cudaMemsetAsync(q.res, 0, sizeof(double) * 2 * m0, st));
+      GBF_CUDA(cudaMemsetAsync(q.X, 0, sizeof(zd) * 2 * nm, st));
       GBF_CUDA(cudaMemcpyAsync(q.E, ws.Eo, sizeof(zd) * m, cudaMemcpyDeviceToDevice, st));
       GBF_CUDA(cudaMemcpyAsync(q.res, ws.Rr, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
       GBF_CUDA(cudaMemcpyAsync(q.res + m0, ws.Rl, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
-      GBF_CUDA(cudaMemcpyAsync(q.X, ws.Yr, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
-      GBF_CUDA(cudaMemcpyAsync((zd *)q.X + nm, ws.Yl, sizeof(zd) * nm, cudaMemcpyDeviceToDevice, st));
+      GBF_CUDA(cudaMemcpyAsync(q.X, ws.Yr, sizeof(zd) * (size_t)n * m, cudaMemcpyDeviceToDevice, st));
+      GBF_CUDA(cudaMemcpyAsync((zd *)q.X + nm, ws.Yl, sizeof(zd) * (size_t)n * m, cudaMemcpyDeviceToDevice, st));
       GBF_CUDA(cudaStreamSynchronize(st));
+      out.m0 = m;
       return out.info = info;
     }
     trace_prev = trace;
@@ -1470,6 +1539,7 @@ static int run_gen_dev(gbf_handle h, void *stream, bool real, int n, const doubl
     if (epsout) *epsout = out.epsout;
     if (loop) *loop = out.loop;
     if (M) *M = out.M;
+    if (M0 && code >= 0) *M0 = out.m0;
   }
   if (info) *info = code;
   return code;

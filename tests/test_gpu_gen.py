@@ -251,3 +251,19 @@ def test_host_entry_and_expert_nodes(gbf, cplx):
     for lam in og["E"][:og["M"]]:
         assert np.min(np.abs(Ed - lam)) < 1e-10
     h.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_large_subspace_sparse_spectrum(gbf, prec, cplx):
+    """M0 well above the count (here 2.7 times): the columns of Q for the
+    eigenvalues far outside carry filter values far below the solves'
+    rounding level.  From the second loop on they are formed in the
+    residual-correction form, exact relative to their own size, so the
+    reduced pencil stays regular and the pairs inside converge."""
+    P = W.dense_nonsymmetric(300, count=6, m0=16, complex_=cplx, generalized=True, seed=13)
+    fpm = P.apply_fpm(gbf.gbf_init())
+    fpm[41] = prec
+    o = _run(gbf, P, fpm, gbf.Handle())
+    known = P.spectrum[G.inside(P.spectrum, P.emid, P.r)]
+    _check_outputs(P, o, fpm, known)
