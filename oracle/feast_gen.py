@@ -55,11 +55,14 @@ Readings where the guide is silent (each listed in the design notes):
   - info 3 when every one of the kept mk Ritz values is inside and mk < N;
   - no spurious-pair test (the guide gives no criterion for this variant);
   - Q and Q^ are replaced by orthonormal bases of their numerical ranges
-    (Gram eigenvalues above 1e-12 of the largest), both cut to the smaller
+    (Gram eigenvalues above 1e-14 of the largest), both cut to the smaller
     rank mk: the returned "new suitable M0" of Table tab_common.  Without
     it, the columns of eigenvalues far outside (filter values below the
-    solves' rounding level) turn into noise and the reduced pencil becomes
-    singular when M0 exceeds the count by a wide margin.
+    solves' rounding level) shrink by orders of magnitude against the
+    others and the reduced pencil becomes numerically singular when M0
+    exceeds the count by a wide margin; the threshold sits at the Gram's
+    resolution, so the nearly parallel eigenvectors of a nearly defective
+    pair are kept down to angles of about 1e-7.
 """
 from __future__ import annotations
 
@@ -154,11 +157,12 @@ def _res(Mx, Nx, lam, alpha):
 def _range_basis(M):
     """Orthonormal basis of the numerical range of M's columns: the Gram
     matrix M^H M diagonalised (library eigh), directions with eigenvalue at
-    most 1e-12 of the largest dropped, the rest scaled to unit length
+    most 1e-14 of the largest (the Gram matrix's own rounding level; singular
+    values below 1e-7 of the largest) dropped, the rest scaled to unit length
     (M V diag(w)^-1/2).  Returns the basis (largest directions last) and its
     size."""
     w, V = np.linalg.eigh(M.conj().T @ M)
-    keep = w > 1e-12 * w[-1]
+    keep = w > 1e-14 * w[-1]
     return (M @ V[:, keep]) / np.sqrt(w[keep])[None, :], int(keep.sum())
 
 

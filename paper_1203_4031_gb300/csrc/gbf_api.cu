@@ -1242,9 +1242,11 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
       return out.info = 4;
     }
     // ---- numerical ranges of Q and Q^: orthonormal bases of the directions
-    // whose Gram eigenvalue exceeds 1e-12 of the largest, both cut to the
-    // smaller rank mk (the new M0).  Columns of eigenvalues far outside fall
-    // below the solves' rounding level and would make the pencil singular.
+    // whose Gram eigenvalue exceeds 1e-14 of the largest (the Gram's own
+    // rounding level), both cut to the smaller rank mk (the new M0).  Columns
+    // of eigenvalues far outside shrink below the solves' rounding level and
+    // would make the pencil singular; nearly parallel eigenvectors of a
+    // nearly defective pair stay (down to angles of about 1e-7).
     {
       CatScope cat_red(CAT_REDUCED);
       zd *Gq = ws.Aq, *Gh = ws.Bq, *Vq = ws.Z, *Vh = ws.Yv, *Tq = ws.W, *Th = ws.V;
@@ -1276,8 +1278,8 @@ static int feast_run_gen(gbf_context *h, cudaStream_t st, const GenReq &q, Res &
       GBF_CUDA(cudaStreamSynchronize(st));
       int r1 = 0, r2 = 0;
       for (int i = 0; i < m; ++i) {
-        r1 += hd[i] > 1e-12 * hd[m - 1] ? 1 : 0;
-        r2 += hd[m + i] > 1e-12 * hd[2 * m - 1] ? 1 : 0;
+        r1 += hd[i] > 1e-14 * hd[m - 1] ? 1 : 0;
+        r2 += hd[m + i] > 1e-14 * hd[2 * m - 1] ? 1 : 0;
       }
       const int mk = std::min(r1, r2);
       if (mk < 1 || !(hd[m - 1] > 0.0) || !(hd[2 * m - 1] > 0.0)) {

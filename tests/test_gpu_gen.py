@@ -267,3 +267,22 @@ def test_large_subspace_sparse_spectrum(gbf, prec, cplx):
     o = _run(gbf, P, fpm, gbf.Handle())
     known = P.spectrum[G.inside(P.spectrum, P.emid, P.r)]
     _check_outputs(P, o, fpm, known)
+
+
+def test_nearly_defective_pair(gbf):
+    """A 2 x 2 block [[0, 1], [0, 1e-6]] inside the circle: nearly parallel
+    eigenvectors, a tiny Gram eigenvalue in the wanted span; both
+    eigenvalues found, as by the oracle."""
+    rng = np.random.default_rng(7)
+    n = 60
+    T = np.diag(rng.uniform(1.0, 3.0, n)).astype(complex)
+    T[0, 0], T[1, 1], T[0, 1] = 0.0, 1e-6, 1.0
+    U = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))[0]
+    A = U @ T @ U.conj().T
+    fpm = gbf.gbf_init()
+    o = gbf.feast_gen_dev(_dev(A), None, 0.0, 0.5, 4, fpm, handle=gbf.Handle())
+    torch.cuda.synchronize()
+    ref = G.feast_gen(A, None, 0.0, 0.5, 4, G.feastinit_gen())
+    assert ref["info"] == 0 and o["info"] == 0 and o["M"] == 2
+    E = o["E"].cpu().numpy()[:2]
+    assert np.min(np.abs(E)) < 1e-9 and np.min(np.abs(E - 1e-6)) < 1e-9

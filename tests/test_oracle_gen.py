@@ -252,8 +252,26 @@ def test_range_basis_is_orthonormal_and_drops_noise():
     rng = np.random.default_rng(2)
     U = np.linalg.qr(rng.standard_normal((50, 5)) + 1j * rng.standard_normal((50, 5)))[0]
     M = U @ np.diag([3.0, 1.0, 0.5, 1e-3, 2.0]) @ (rng.standard_normal((5, 8)))
-    M[:, 7] += 1e-14 * rng.standard_normal(50)      # noise direction beyond the rank
+    M[:, 7] += 1e-9 * rng.standard_normal(50)       # a direction far below the Gram's resolution
     Bq, k = G._range_basis(M)
     assert k == 5
     assert np.allclose(Bq.conj().T @ Bq, np.eye(5), atol=1e-10)
     assert np.allclose(Bq @ (Bq.conj().T @ U), U, atol=1e-8)
+
+
+@pytest.mark.parametrize("delta", [1e-5, 1e-6])
+def test_nearly_defective_pair_is_kept(delta):
+    """A 2 x 2 block [[0, 1], [0, delta]] inside the circle: its two
+    eigenvectors are nearly parallel (angle ~ delta), so the filtered
+    subspace has a direction with a tiny Gram eigenvalue (~delta^2) that
+    belongs to the wanted span; the numerical-range cut must keep it."""
+    rng = np.random.default_rng(7)
+    n = 60
+    T = np.diag(rng.uniform(1.0, 3.0, n)).astype(complex)
+    T[0, 0], T[1, 1], T[0, 1] = 0.0, delta, 1.0
+    U = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))[0]
+    A = U @ T @ U.conj().T
+    fpm = G.feastinit_gen()
+    o = G.feast_gen(A, None, 0.0, 0.5, 4, fpm)
+    assert o["info"] == 0 and o["M"] == 2 and o["m0"] == 4
+    assert np.min(np.abs(o["E"][:2])) < 1e-9 and np.min(np.abs(o["E"][:2] - delta)) < 1e-9
