@@ -96,6 +96,23 @@ def test_driver_argument_validation_without_gpu():
         assert g.feast_host(A, None, 0.5, 3.5, 5, fpm=f)["info"] == code, (idx, bad)
 
 
+def test_gen_driver_argument_validation_without_gpu():
+    """Non-Hermitian drivers: the codes decided before any device work."""
+    A = np.diag(np.arange(1.0, 11.0)) + np.triu(np.ones((10, 10)), 1)
+    assert g.feast_gen_host(A[:0, :0].reshape(0, 0), None, 0.0, 1.0, 1)["info"] == 202
+    assert g.feast_gen_host(A, None, 2.0, 1.5, 0)["info"] == 201
+    assert g.feast_gen_host(A, None, 2.0, 1.5, 11)["info"] == 201
+    assert g.feast_gen_host(A, None, 2.0, 0.0, 4)["info"] == 200
+    assert g.feast_gen_host(A, None, 2.0, -1.0, 4)["info"] == 200
+    base = g.gbf_init()
+    for idx, bad, code in [(2, -1, 103), (2, 17, 103), (3, -1, 104), (4, 2, 105), (5, 3, 106), (7, 0, 108),
+                           (7, 2000, 108), (13, 2, 114), (16, 2, 117), (17, 0, 118), (18, 181, 119),
+                           (18, -181, 119), (41, 2, 142), (42, 5, 143), (43, 2, 144)]:
+        f = base.copy()
+        f[idx] = bad
+        assert g.feast_gen_host(A, None, 2.0 + 0.5j, 1.5, 5, fpm=f)["info"] == code, (idx, bad)
+
+
 def test_tensor_core_workspace_sizes():
     """Workspace sizes are host arithmetic on the operand layouts: S digit
     planes of bf16 (64 per embedded row) plus one 8-byte scale slot per row
